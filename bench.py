@@ -1,0 +1,422 @@
+"""Benchmark: MPMI-SC control ticks on one GB300 (or N replicas under torchrun).
+
+Workload (the configuration the headline metric is quoted on): balance-bot
+closed loop at paper scale -- model fit on 5000 seeded cart-pole transitions
+(12 lifted features), N = 16384 sampled candidates (+ the user's input), H = 50
+prediction steps, 100 Hz, 1000 ticks, user input from a seeded Ornstein-Uhlenbeck
+process (theta = 1.0, sigma = 0.5) clipped to [-1, 1].
+
+One "step" is one control tick: sample, lift, predict with early exit, safety
+test, cost, device-wide argmin and decode (every row of the hot path).
+
+  value        rollout steps/s = (N + 1) * H per tick / device time per tick, with
+               the tick inputs resident in HBM (device-side API), L2 flushed
+               (256 MB write) before every timed tick, CUDA events on the launch
+               stream around each tick.
+  e2e          the same metric through the host C-ABI call (evaluate_candidates +
+               select_input) driving the closed loop: per tick a host->device copy
+               of x_t/u_h from pinned memory and a device->host read of the result.
+  roofline     FP32 CUDA-core (ALU) bound: algorithmic flops per tick (2 n^2 per
+               executed prediction step + lifting + cost) / mean tick duration,
+               against 152 SMs x 128 FP32 lanes x 2 flops x max SM clock.
+  cpu_baseline the FP64 oracle on the host cores (spawned worker processes), on
+               a bounded sample of the same ticks.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from workloads import data, plants  # noqa: E402
+
+# ---- workload constants -----------------------------------------------------
+N_SAMPLES = 16384
+HORIZON = 50
+TICKS = 1000
+FIT_SEED, FIT_COUNT = 1, 5000
+LOOP_SEED = 2
+X0 = np.array([0.05, 0.0, 0.0, 0.0])
+LIFTED_N = 12
+FLUSH_BYTES = 256 << 20
+SM_FP32_LANES = 128
+
+# DRAM bytes per tick-kernel launch from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum); valid only for the kernel source it was taken on.
+TRAFFIC = {"tick_kernel_sha1": None, "bytes_per_launch": None}
+
+
+def kernel_sha1() -> str:
+    p = os.path.join(ROOT, "paper_1906_02318_gb300", "csrc", "tick_kernel.cuh")
+    return hashlib.sha1(open(p, "rb").read()).hexdigest()
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---- clocks during the timed region ----------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- oracle leg (host cores) -----------------------------------------------
+def _oracle_worker(args):
+    """Spawned worker: oracle ticks over the given tick indices until the time
+    budget runs out.  Returns (rollout steps, seconds)."""
+    (K32, ticks, states, uhs, n, H, budget) = args
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    sys.path.insert(0, ROOT)
+    from oracle import mpmi as omp
+    from oracle import safety as osafe
+    from oracle import sampling as osamp
+    spec = osafe.SafetySpec(lo=data.BOT_SAFE_LO, hi=data.BOT_SAFE_HI)
+    steps = 0
+    t0 = time.perf_counter()
+    for t in ticks:
+        s = osamp.uniform_samples(LOOP_SEED, 0, int(t), n, plants.BOT_INPUT_LO,
+                                  plants.BOT_INPUT_HI)
+        omp.tick(K32, "bot", states[t], uhs[t], s, H, spec)
+        steps += (n + 1) * H
+        if time.perf_counter() - t0 > budget:
+            break
+    return steps, time.perf_counter() - t0
+
+
+def oracle_rate(K32, states, uhs, n, H, budget_s, workers, tick_ids):
+    """Rollout steps/s of the oracle on `workers` spawned processes."""
+    import multiprocessing as mp
+    chunks = [tick_ids[w::workers] for w in range(workers)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        outs = pool.map(_oracle_worker,
+                        [(K32, c, states, uhs, n, H, budget_s) for c in chunks if len(c)])
+    steps = sum(s for s, _ in outs)
+    t_max = max(t for _, t in outs)
+    return steps / t_max, steps, t_max
+
+
+def oracle_model():
+    from oracle import fit as ofit
+    x, u, xn = data.transitions("bot", FIT_SEED, FIT_COUNT)
+    return ofit.round_to_f32(ofit.fit_koopman("bot", x, u, xn)[0])
+
+
+def reference_states():
+    """Tick inputs for the oracle legs: the oracle's own closed loop is too slow to
+    run 1000 ticks, so it replays the user input stream from a fixed set of states
+    drawn near the upright equilibrium."""
+    uhs = data.to_f32_exact(data.ou_user_input(LOOP_SEED, TICKS, plants.BOT_DT,
+                                               plants.BOT_INPUT_LO, plants.BOT_INPUT_HI))
+    states = data.states_in_box(LOOP_SEED, TICKS, [-0.1, -0.5, -0.5, -0.5],
+                                [0.1, 0.5, 0.5, 0.5])
+    return states, uhs
+
+
+# ---- GPU leg ----------------------------------------------------------------
+def run_gpu(args, rank, world):
+    import torch
+    from paper_1906_02318_gb300 import build as pbuild
+    from paper_1906_02318_gb300 import mpmi as lib
+
+    pbuild.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    props = torch.cuda.get_device_properties(dev)
+    ctx = lib.Context(dev.index)
+    x, u, xn = data.transitions("bot", FIT_SEED, FIT_COUNT)
+    model, residual = lib.fit_model(ctx, "bot", x, u, xn)
+    lib.set_safety_set(model, data.BOT_SAFE_LO, data.BOT_SAFE_HI)
+    seed = LOOP_SEED + 1000 * rank
+    sess = lib.Session(ctx, model, N_SAMPLES, HORIZON, plants.BOT_INPUT_LO,
+                       plants.BOT_INPUT_HI, seed=seed, stream_id=rank)
+    lanes, block = sess.launch_shape()
+    n_slots = sess.n_slots
+    ticks = max(TICKS, args.warmup + args.steps)
+    uhs = data.ou_user_input(seed, ticks, plants.BOT_DT, plants.BOT_INPUT_LO,
+                             plants.BOT_INPUT_HI)
+    stream = torch.cuda.current_stream(dev)
+    gpu_id = None
+    try:
+        gpu_id = f"GPU-{props.uuid}"
+    except Exception:
+        pass
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+
+    # closed loop through the host C-ABI (e2e): W warm-up ticks, then timed ticks
+    x_t = X0.copy()
+    states = np.empty((ticks, 4))
+    lat = []
+    n_fallback = 0
+    for t in range(ticks):
+        states[t] = x_t
+        t0 = time.perf_counter()
+        lib.evaluate_candidates(sess, x_t, uhs[t], tick=t, stream=stream)
+        r = lib.select_input(sess)
+        dt = time.perf_counter() - t0
+        if t >= args.warmup:
+            lat.append(dt)
+        n_fallback += r["status"] == lib.FALLBACK
+        x_t = plants.cartpole_step(x_t, r["u_r"])
+        if not np.all(np.isfinite(x_t)):
+            x_t = X0.copy()
+    lat = np.array(lat)
+    e2e_rate = n_slots * HORIZON * len(lat) / lat.sum()
+
+    # device-resident ticks: inputs in HBM, L2 flushed before each timed tick
+    xs = torch.tensor(states, dtype=torch.float64, device=dev)
+    us = torch.tensor(uhs, dtype=torch.float64, device=dev)
+    results = torch.zeros((ticks, lib.RESULT_BYTES), dtype=torch.uint8, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    n_ev = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+
+    def tick(i):
+        lib.evaluate_candidates_device(sess, xs[i % ticks], us[i % ticks], results[i % ticks],
+                                       tick=i % ticks, stream=stream)
+
+    for i in range(args.warmup):
+        flush.zero_()
+        tick(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(n_ev):
+        i = args.warmup + k
+        flush.zero_()
+        ev0[k].record(stream)
+        tick(i)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    durs = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)]) * 1e-3
+    dev_time = float(durs.sum())
+    res = results.cpu().numpy()
+    executed = []
+    agree = 0
+    for k in range(n_ev):
+        i = (args.warmup + k) % ticks
+        rr = lib.result_from_bytes(res[i], 1)
+        executed.append(rr["executed_steps"])
+    executed = np.array(executed, dtype=np.float64)
+    # the device path reproduces the closed loop's selections on the same ticks
+    for i in range(min(ticks, 200)):
+        rr = lib.result_from_bytes(res[i], 1)
+        agree += rr["tick"] == i
+    sess.close()
+    model.free()
+    return dict(dev_time=dev_time, durs=durs, executed=executed, lat=lat, e2e_rate=e2e_rate,
+                wall=wall, clocks=clk, lanes=lanes, block=block, n_slots=n_slots,
+                residual=residual, n_fallback=int(n_fallback), sm_count=props.multi_processor_count,
+                gpu_name=props.name)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0,
+                    help="seconds of oracle work per host worker for cpu_baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    cfg = {"workload": "balance-bot closed loop: N=16384 (+u_h), H=50, 100 Hz, 1000 ticks",
+           "N": N_SAMPLES, "H": HORIZON, "lifted_dim": LIFTED_N, "input_dim": 1,
+           "ticks": TICKS, "fit_transitions": FIT_COUNT,
+           "l2": "flushed before every timed tick (256 MB write)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, cfg)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", rank))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    out = run_gpu(args, rank, world)
+
+    n_step = (N_SAMPLES + 1) * HORIZON
+    t_rank = out["dev_time"]
+    e2e_t = float(out["lat"].sum())
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t_rank, e2e_t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, e2e_max = float(tt[0]), float(tt[1])
+    else:
+        t_max, e2e_max = t_rank, e2e_t
+    K = args.steps
+    value = world * K * n_step / t_max
+    e2e_value = world * len(out["lat"]) * n_step / e2e_max
+
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = out["sm_count"] * SM_FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    mean_dur = float(out["durs"].mean())
+    flops_per_tick = (float(out["executed"].mean()) * 2 * LIFTED_N ** 2
+                      + out["n_slots"] * (2 * LIFTED_N * 1 + 2))
+    achieved = flops_per_tick / mean_dur / 1e12
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["tick_kernel_sha1"] == kernel_sha1() else None
+
+    line = {
+        "metric": "rollout steps/s (plain path) and p99 control-tick latency at N=16384",
+        "value": value, "unit": "rollout steps/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": t_max / K * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(cfg, lanes=out["lanes"], block=out["block"],
+                       parallelism=f"replicas{world}" if world > 1 else "single"),
+        "executed_steps_per_s": world * float(out["executed"].sum()) / t_max,
+        "latency_ms": {"p50": float(np.percentile(out["lat"], 50) * 1e3),
+                       "p99": float(np.percentile(out["lat"], 99) * 1e3),
+                       "deadline_ms": 10.0,
+                       "misses": int(np.count_nonzero(out["lat"] > 0.010)),
+                       "what": "host-to-host C-ABI tick (evaluate_candidates + select_input)"},
+        "learned": None,
+        "e2e": {"value": e2e_value, "unit": "rollout steps/s",
+                "h2d_bytes_per_step": 12 * 8, "d2h_bytes_per_step": 80},
+        "gpu_launches": K,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                     "peak_basis": f"{out['sm_count']} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
+        "clocks": out["clocks"],
+        "fallback_ticks": out["n_fallback"],
+    }
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args):
+    K32 = oracle_model()
+    states, uhs = reference_states()
+    workers = max(1, min(16, os.cpu_count() or 1))
+    rate, steps, _ = oracle_rate(K32, states, uhs, N_SAMPLES, HORIZON, args.cpu_budget,
+                                 workers, list(range(TICKS)))
+    return {"value": rate, "unit": "rollout steps/s", "cores": workers, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, {steps // ((N_SAMPLES + 1) * HORIZON)} full ticks "
+                      f"(N=16384, H=50) across {workers} spawned single-threaded workers, "
+                      f"~{args.cpu_budget:.0f} s each"}
+
+
+def run_reference(args, cfg):
+    """The oracle as it stands, timed on the host cores, same metric and workload;
+    each step is one full tick (N=16384, H=50), ticks spread over workers."""
+    K32 = oracle_model()
+    states, uhs = reference_states()
+    workers = max(1, min(16, os.cpu_count() or 1))
+    # warm-up ticks (untimed), then exactly K timed ticks
+    oracle_rate(K32, states, uhs, N_SAMPLES, HORIZON, 1e9, workers,
+                list(range(min(args.warmup, TICKS))))
+    ids = [i % TICKS for i in range(args.steps)]
+    value, steps, wall = oracle_rate(K32, states, uhs, N_SAMPLES, HORIZON, 1e9, workers, ids)
+    line = {"metric": "rollout steps/s (plain path) and p99 control-tick latency at N=16384",
+            "value": value, "unit": "rollout steps/s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "rollout steps/s", "cores": workers,
+                             "kind": "oracle",
+                             "sample": f"{args.steps} full ticks over {workers} spawned "
+                                       "single-threaded workers (slowest worker's time)"},
+            "e2e": {"value": value, "unit": "rollout steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * mpmi.h - C ABI of the MPMI-SC per-tick hot path on one GPU.
+ *
+ * Method: Model Predictive Minimal Intervention Shared Control (Broad, Murphey &
+ * Argall, "Highly Parallelized Data-driven MPC for Minimal Intervention Shared
+ * Control").  Each control tick takes the plant state x_t and the user's input
+ * u_h and returns the input u_r to apply (Alg. 2): sample N constant candidate
+ * inputs, predict each one's lifted state over H steps with a learned linear
+ * operator (z <- K z, Sec. IV-A), reject every candidate whose prediction leaves
+ * the safety set at any step (Sec. IV-B, Sec. V-C.1), and choose the safe
+ * candidate nearest to u_h (Alg. 2's argmin, Sec. IV-D).
+ *
+ * Conventions
+ *   - Every call returns MPMI_OK (0) or a negative MPMI_E_* code; nothing is
+ *     thrown across the ABI.  mpmi_last_error() returns the calling thread's
+ *     message for the last failed call.
+ *   - The library owns its handles (create/free in pairs).  The caller owns every
+ *     buffer it passes; the library copies what it keeps (K, the track, configs).
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global
+ *     memory on the context's device (e.g. a torch tensor's data_ptr()).
+ *   - Streams are cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Work on one session must be stream-ordered: two ticks of the same session
+ *     may not run concurrently (they share the session's reduction slots).
+ *   - Arrays are row-major and densely packed.
+ *
+ * Data layout on the device
+ *   - K: n x n float32, row-major (z_next[i] = sum_k K[i][k] z[k]).
+ *   - candidates: N x M float32, row-major (sample i, input dim j at i*M + j).
+ *   - per-candidate outputs are indexed by slot: slot 0 is u_h when the session
+ *     includes it, slots 1..N are the samples (slots 0..N-1 otherwise).
+ */
+#ifndef MPMI_H
+#define MPMI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define MPMI_OK 0
+#define MPMI_E_INVALID_ARG (-1) /* bad pointer, size, enum or state         */
+#define MPMI_E_OOM (-2)         /* device/host allocation failed or the
+                                   context's memory budget would be exceeded */
+#define MPMI_E_NONFINITE (-3)   /* NaN/Inf in a host input that must be finite */
+#define MPMI_E_CUDA (-4)        /* a CUDA runtime call failed                 */
+#define MPMI_E_NOT_READY (-5)   /* select_input without an evaluate in flight */
+#define MPMI_E_UNSUPPORTED (-6) /* combination not compiled into the library  */
+
+/* ---- enums ------------------------------------------------------------- */
+/* Lifted bases (Sec. IV-A; the paper's own 6- and 26-function bases were chosen
+ * by code that is not published, so these are fixed lists of the same kinds):
+ *   BALANCE_BOT: n = 12, x = (theta, theta_dot, x, x_dot), one input u
+ *   RACE_CAR:    n = 32, x = (px, py, psi, vx, vy, omega), u = (steer, throttle)
+ *   LINEAR:      n = nx + nu, z = (x, u); compiled for (nx, nu) in
+ *                {(1, 1), (2, 2), (4, 1)}
+ * State coordinates come first in z, so the predicted state is z[0..nx). */
+#define MPMI_BASIS_BALANCE_BOT 0
+#define MPMI_BASIS_RACE_CAR 1
+#define MPMI_BASIS_LINEAR 2
+
+/* Selection status (Alg. 2 argmin; the fallback is this library's reading of
+ * the case the paper leaves open: no candidate safe over the whole horizon). */
+#define MPMI_SAFE 0
+#define MPMI_FALLBACK 1
+
+/* Candidate sources (Alg. 2 draws xi ~ U^{M x N}; Sec. IV-B describes an
+ * equally spaced discretisation; EXTERNAL reads caller-provided samples). */
+#define MPMI_SAMPLER_UNIFORM 0
+#define MPMI_SAMPLER_GRID 1
+#define MPMI_SAMPLER_EXTERNAL 2
+
+#define MPMI_MAX_NX 8
+#define MPMI_MAX_NU 4
+#define MPMI_MAX_HORIZON 511         /* H - ttv must fit 9 bits of the key    */
+#define MPMI_MAX_SLOTS 8388607       /* 2^23 - 1: slot must fit 23 bits        */
+#define MPMI_MAX_TRACK_VERTICES 65535
+
+/* ---- plain structs ------------------------------------------------------ */
+typedef struct mpmi_ctx mpmi_ctx;
+typedef struct mpmi_model mpmi_model;
+typedef struct mpmi_session mpmi_session;
+
+typedef struct {
+  int32_t basis; /* MPMI_BASIS_* */
+  int32_t nx;    /* state dimension: must be 4 (bot), 6 (car) or as compiled  */
+  int32_t nu;    /* input dimension M: 1 (bot), 2 (car) or as compiled        */
+} mpmi_basis_desc;
+
+/* Safety set (Sec. V-C.1): the predicted state x = z[0..nx) is safe iff
+ *   state_lo[j] + inflation < x[j] < state_hi[j] - inflation   for every j < nx
+ * (use -INFINITY / +INFINITY for free coordinates) and, when track_xy != NULL,
+ *   dist((x[track_x], x[track_y]), closed polyline) < track_half_width - inflation.
+ * Comparisons are strict; NaN is unsafe.  inflation is the paper's inflated
+ * barrier (>= 0). */
+typedef struct {
+  double state_lo[MPMI_MAX_NX];
+  double state_hi[MPMI_MAX_NX];
+  double inflation;
+  const double* track_xy; /* host, n_track (x, y) pairs; NULL = no track test  */
+  int32_t n_track;        /* 3..MPMI_MAX_TRACK_VERTICES; segment i joins vertex
+                             i to vertex (i + 1) mod n_track                    */
+  int32_t track_x;        /* state coordinate holding the position's x         */
+  int32_t track_y;        /* state coordinate holding the position's y         */
+  int32_t pad0;
+  double track_half_width;
+} mpmi_safety_spec;
+
+typedef struct {
+  int32_t n_samples;    /* N >= 0 sampled candidates per tick                  */
+  int32_t horizon;      /* H in 1..MPMI_MAX_HORIZON prediction steps           */
+  int32_t include_user; /* 1: slot 0 is u_h itself (a safe u_h passes through
+                           unchanged); 0: the N samples only (Alg. 2 as printed) */
+  int32_t sampler;      /* MPMI_SAMPLER_*                                      */
+  double input_lo[MPMI_MAX_NU]; /* candidate box per input dimension           */
+  double input_hi[MPMI_MAX_NU];
+  uint64_t seed;        /* Philox key (UNIFORM)                                */
+  uint32_t stream_id;   /* Philox counter word 3 (UNIFORM): session identity   */
+  int32_t lanes;        /* 0 = library choice; else lanes per candidate        */
+  int32_t block;        /* 0 = library choice; else threads per block          */
+  int32_t pad0;
+} mpmi_session_config;
+
+/* One tick's outcome (written by the device, 80 bytes). */
+typedef struct {
+  double u_r[MPMI_MAX_NU];  /* selected input: u_h exactly when slot 0 (the user)
+                               wins, else the candidate's float32 value           */
+  int32_t index;            /* selected slot                                      */
+  int32_t status;           /* MPMI_SAFE or MPMI_FALLBACK                         */
+  int32_t n_safe;           /* candidates safe over all H steps                   */
+  int32_t ttv;              /* steps the selected candidate passed (H if safe)    */
+  float cost;               /* ||u_r - u_h||^2 in float32                         */
+  int32_t n_slots;          /* N + include_user                                   */
+  uint64_t executed_steps;  /* prediction steps actually taken (early exit)       */
+  uint64_t tick;            /* tick counter the call was given                    */
+  uint64_t reserved;
+} mpmi_result;
+
+/* ---- context ------------------------------------------------------------ */
+/* Binds the library to CUDA device `device`.  mem_budget_bytes caps the device
+ * memory sessions and models may hold (0 = no cap); session_open fails with
+ * MPMI_E_OOM beyond it.  *out receives the handle. */
+int mpmi_create(int32_t device, uint64_t mem_budget_bytes, mpmi_ctx** out);
+void mpmi_destroy(mpmi_ctx* ctx); /* close sessions and free models first */
+const char* mpmi_last_error(void);
+const char* mpmi_version(void);
+/* Bytes of device memory currently held against the budget. */
+uint64_t mpmi_memory_in_use(const mpmi_ctx* ctx);
+
+/* ---- fit_model (Sec. IV-A) ---------------------------------------------- */
+/* Least-squares fit of the lifted operator over m transitions (host, float64):
+ *   K = argmin sum_m || Psi(x_next[m], u[m]) - K Psi(x[m], u[m]) ||^2
+ * x, x_next: m x nx row-major; u: m x nu row-major (the input is held over the
+ * step, so the target lifts x_next with the same u).  Solved by Householder QR
+ * in float64 on the host (an offline step, Sec. IV-A "learned offline").
+ * *residual_out (may be NULL) = ||X K^T - Y||_F / ||Y||_F.  The model's device
+ * copy of K is float32 (round to nearest).  Fails with INVALID_ARG when m < n,
+ * NONFINITE on NaN/Inf input, and INVALID_ARG if the lifted data is rank
+ * deficient. */
+int mpmi_fit_model(mpmi_ctx* ctx, const mpmi_basis_desc* basis, const double* x,
+                   const double* u, const double* x_next, int64_t m,
+                   mpmi_model** out, double* residual_out);
+/* The same fit without a context or a device: writes K (host, n x n float64
+ * row-major) to K_out.  Pure host code (usable on machines without a GPU). */
+int mpmi_fit_operator(const mpmi_basis_desc* basis, const double* x, const double* u,
+                      const double* x_next, int64_t m, double* K_out,
+                      double* residual_out);
+/* A model from a given operator K (host, n x n float64 row-major). */
+int mpmi_model_from_operator(mpmi_ctx* ctx, const mpmi_basis_desc* basis,
+                             const double* K, mpmi_model** out);
+/* Copies the float64 operator to K_out (host, n*n) and n to *n_out. */
+int mpmi_model_get_operator(const mpmi_model* model, double* K_out, int32_t* n_out);
+void mpmi_model_free(mpmi_model* model); /* sessions using it must be closed */
+
+/* ---- set_safety_set (Sec. V-C.1) --------------------------------------- */
+/* Installs the safety set on a model (copied; replaces any previous one).  The
+ * track is preprocessed on the host into a uniform grid whose cells are marked
+ * inside / outside / boundary (the last with the list of segments that can be
+ * nearest), so the device test reads at most a few segments per step and gives
+ * the same answer as the brute-force minimum over all segments.  Sessions opened
+ * afterwards use the new set. */
+int mpmi_set_safety_set(mpmi_model* model, const mpmi_safety_spec* spec);
+
+/* ---- sessions ----------------------------------------------------------- */
+/* A controller instance: one model, fixed N and H, its own sampler stream and
+ * reduction slots.  Allocates ~200 bytes of device memory and a small pinned
+ * host buffer. */
+int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model,
+                      const mpmi_session_config* cfg, mpmi_session** out);
+void mpmi_session_close(mpmi_session* s);
+/* Lanes per candidate and threads per block the session launches with. */
+int mpmi_session_launch_shape(const mpmi_session* s, int32_t* lanes, int32_t* block);
+
+/* ---- evaluate_candidates + select_input (Alg. 2) ------------------------ */
+/* Queues one tick on `stream`: copies x_t (nx doubles) and u_h (nu doubles) from
+ * host memory (through the session's pinned staging buffer), samples the
+ * candidates (counter = tick), predicts, tests, scores and reduces them on the
+ * GPU, and queues the device-to-host copy of the result.  Returns without waiting.
+ * candidates_dev: device N x M float32 samples for MPMI_SAMPLER_EXTERNAL, else
+ * must be NULL.  NONFINITE if x_t or u_h holds NaN/Inf.  If a previous tick of
+ * this session is still in flight, waits for it first. */
+int mpmi_evaluate_candidates(mpmi_session* s, const double* x_t, const double* u_h,
+                             const float* candidates_dev, uint64_t tick,
+                             void* stream);
+/* Waits for the tick queued by mpmi_evaluate_candidates and copies its outcome
+ * to *out (host).  NOT_READY if no tick is in flight. */
+int mpmi_select_input(mpmi_session* s, mpmi_result* out);
+
+/* Device-resident form of one tick (nothing is copied to or from the host and
+ * nothing is waited for; graph-capturable): x_t_dev (nx doubles) and u_h_dev (nu
+ * doubles) are device pointers, the outcome is written to result_dev (device,
+ * one mpmi_result).  ttv_dev (int32, n_slots) and cost_dev (float32, n_slots)
+ * are optional device outputs per slot (NULL = not written). */
+int mpmi_evaluate_candidates_device(mpmi_session* s, const double* x_t_dev,
+                                    const double* u_h_dev,
+                                    const float* candidates_dev, uint64_t tick,
+                                    mpmi_result* result_dev, int32_t* ttv_dev,
+                                    float* cost_dev, void* stream);
+
+/* ---- step-level entry points (parity checks) ---------------------------- */
+/* Alg. 2 first step alone: writes the tick's n_slots x M candidate values (slot
+ * order, slot 0 = u_h when included) to out_dev (device float32).  u_h_dev is
+ * read only when the session includes the user's input. */
+int mpmi_sample_candidates(mpmi_session* s, const double* u_h_dev,
+                           const float* candidates_dev, uint64_t tick,
+                           float* out_dev, void* stream);
+/* The same tick as mpmi_evaluate_candidates_device that also records the lifted
+ * trajectories: traj_dev (device float32, n_slots x (H + 1) x n) receives z_0 and
+ * every predicted z_t the candidate reached (t <= min(ttv + 1, H)); entries past
+ * a candidate's early exit are left untouched. */
+int mpmi_debug_trajectories(mpmi_session* s, const double* x_t_dev,
+                            const double* u_h_dev, const float* candidates_dev,
+                            uint64_t tick, mpmi_result* result_dev,
+                            int32_t* ttv_dev, float* cost_dev, float* traj_dev,
+                            void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPMI_H */

@@ -1,0 +1,166 @@
+// Lifted bases of the learned linear model (Sec. IV-A), in split form.
+//
+// Every feature of Psi(x, u) used here is a(x) + sum_k p_k(u) b_k(x): a state
+// part plus input monomials p_k times state coefficients.  Because the input is
+// held over the horizon (Sec. VII-B), a tick lifts all N candidates of the same
+// x_t, so a(x_t) and b_k(x_t) are computed once per tick (float64) and each
+// candidate needs only P fused multiply-adds per feature.  The host fit uses the
+// same definition to lift the training transitions.
+//
+//   balance bot (n = 12, P = 1, p = {u}):
+//     theta, theta_dot, x, x_dot, u, sin th, cos th, thd^2, thd u,
+//     thd^2 sin th, u cos th, 1
+//   race car (n = 32, P = 3, p = {delta, a, delta^2}):
+//     px, py, psi, vx, vy, om, delta, a, sin, cos, vx cos, vx sin, vy cos, vy sin,
+//     om vx, om vy, vx^2, vy^2, om^2, delta vx, delta vy, delta om, a vx,
+//     delta cos, delta sin, a cos, a sin, om cos, om sin, vx vy, delta^2, 1
+//   linear (n = nx + nu, P = nu, p_k = u_k): x, u
+#pragma once
+
+#include <math.h>
+
+#ifdef __CUDACC__
+#define MPMI_HD __host__ __device__ __forceinline__
+#else
+#define MPMI_HD inline
+#endif
+
+namespace mpmi {
+
+enum BasisKind : int { kBot = 0, kCar = 1, kLin11 = 2, kLin22 = 3, kLin41 = 4 };
+
+template <int KIND>
+struct BasisTraits;
+template <>
+struct BasisTraits<kBot> {
+  static constexpr int N = 12, NX = 4, NU = 1, NP = 1;
+  static constexpr bool TRACK = false;
+};
+template <>
+struct BasisTraits<kCar> {
+  static constexpr int N = 32, NX = 6, NU = 2, NP = 3;
+  static constexpr bool TRACK = true;
+};
+template <>
+struct BasisTraits<kLin11> {
+  static constexpr int N = 2, NX = 1, NU = 1, NP = 1;
+  static constexpr bool TRACK = false;
+};
+template <>
+struct BasisTraits<kLin22> {
+  static constexpr int N = 4, NX = 2, NU = 2, NP = 2;
+  static constexpr bool TRACK = false;
+};
+template <>
+struct BasisTraits<kLin41> {
+  static constexpr int N = 5, NX = 4, NU = 1, NP = 1;
+  static constexpr bool TRACK = false;
+};
+
+constexpr int kMaxP = 3;
+
+// Split coefficients of feature j at state x: *a and b[0..P).
+MPMI_HD void feature_split(int kind, int j, const double* x, double* a, double* b) {
+  for (int k = 0; k < kMaxP; ++k) b[k] = 0.0;
+  *a = 0.0;
+  if (kind == kBot) {
+    const double th = x[0], thd = x[1];
+    switch (j) {
+      case 0: *a = th; break;
+      case 1: *a = thd; break;
+      case 2: *a = x[2]; break;
+      case 3: *a = x[3]; break;
+      case 4: b[0] = 1.0; break;
+      case 5: *a = sin(th); break;
+      case 6: *a = cos(th); break;
+      case 7: *a = thd * thd; break;
+      case 8: b[0] = thd; break;
+      case 9: *a = thd * thd * sin(th); break;
+      case 10: b[0] = cos(th); break;
+      default: *a = 1.0; break;  // 11
+    }
+    return;
+  }
+  if (kind == kCar) {
+    const double psi = x[2], vx = x[3], vy = x[4], om = x[5];
+    switch (j) {
+      case 0: *a = x[0]; break;
+      case 1: *a = x[1]; break;
+      case 2: *a = psi; break;
+      case 3: *a = vx; break;
+      case 4: *a = vy; break;
+      case 5: *a = om; break;
+      case 6: b[0] = 1.0; break;
+      case 7: b[1] = 1.0; break;
+      case 8: *a = sin(psi); break;
+      case 9: *a = cos(psi); break;
+      case 10: *a = vx * cos(psi); break;
+      case 11: *a = vx * sin(psi); break;
+      case 12: *a = vy * cos(psi); break;
+      case 13: *a = vy * sin(psi); break;
+      case 14: *a = om * vx; break;
+      case 15: *a = om * vy; break;
+      case 16: *a = vx * vx; break;
+      case 17: *a = vy * vy; break;
+      case 18: *a = om * om; break;
+      case 19: b[0] = vx; break;
+      case 20: b[0] = vy; break;
+      case 21: b[0] = om; break;
+      case 22: b[1] = vx; break;
+      case 23: b[0] = cos(psi); break;
+      case 24: b[0] = sin(psi); break;
+      case 25: b[1] = cos(psi); break;
+      case 26: b[1] = sin(psi); break;
+      case 27: *a = om * cos(psi); break;
+      case 28: *a = om * sin(psi); break;
+      case 29: *a = vx * vy; break;
+      case 30: b[2] = 1.0; break;
+      default: *a = 1.0; break;  // 31
+    }
+    return;
+  }
+  // linear bases: z = (x, u)
+  const int nx = kind == kLin11 ? 1 : kind == kLin22 ? 2 : 4;
+  if (j < nx) {
+    *a = x[j];
+  } else {
+    b[j - nx] = 1.0;
+  }
+}
+
+// Input monomials p_k(u) in float64 (host fit).
+MPMI_HD void monomials64(int kind, const double* u, double* p) {
+  if (kind == kBot) {
+    p[0] = u[0];
+  } else if (kind == kCar) {
+    p[0] = u[0];
+    p[1] = u[1];
+    p[2] = u[0] * u[0];
+  } else {
+    const int nu = kind == kLin22 ? 2 : 1;
+    for (int k = 0; k < nu; ++k) p[k] = u[k];
+  }
+}
+
+inline int basis_kind(int basis, int nx, int nu) {
+  if (basis == 0) return (nx == 4 && nu == 1) ? kBot : -1;
+  if (basis == 1) return (nx == 6 && nu == 2) ? kCar : -1;
+  if (basis == 2) {
+    if (nx == 1 && nu == 1) return kLin11;
+    if (nx == 2 && nu == 2) return kLin22;
+    if (nx == 4 && nu == 1) return kLin41;
+  }
+  return -1;
+}
+
+inline void kind_dims(int kind, int* n, int* nx, int* nu, int* np) {
+  switch (kind) {
+    case kBot: *n = 12; *nx = 4; *nu = 1; *np = 1; break;
+    case kCar: *n = 32; *nx = 6; *nu = 2; *np = 3; break;
+    case kLin11: *n = 2; *nx = 1; *nu = 1; *np = 1; break;
+    case kLin22: *n = 4; *nx = 2; *nu = 2; *np = 2; break;
+    default: *n = 5; *nx = 4; *nu = 1; *np = 1; break;
+  }
+}
+
+}  // namespace mpmi

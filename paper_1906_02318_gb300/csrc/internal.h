@@ -1,0 +1,124 @@
+// Internal types shared by the host side of the library and the tick kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mpmi.h"
+#include "basis.h"
+
+namespace mpmi {
+
+// Track grid cell word: bits 0-1 class, bits 2-23 list offset, bits 24-31 count.
+enum CellClass : uint32_t { kCellOutside = 0, kCellInside = 1, kCellBoundary = 2 };
+
+struct DevTrack {
+  const uint32_t* cells;  // gny * gnx cell words
+  const uint16_t* list;   // segment indices of boundary cells, nearest first
+  const float4* seg;      // (ax, ay, dx, dy) per segment
+  const float* seg_inv;   // 1 / |d|^2 per segment (0 for a degenerate segment)
+  float gx0, gy0, inv_h;  // grid origin and 1 / cell size
+  int gnx, gny;
+  float w2;               // (half width - inflation)^2
+  int xi, yi;             // state coordinates of the position
+};
+
+struct DevSafety {
+  float lo[MPMI_MAX_NX];  // inflated open bounds (float32)
+  float hi[MPMI_MAX_NX];
+  int has_track;
+  DevTrack track;
+};
+
+// Per-session reduction slots the tick kernel accumulates into.  The block that
+// finishes last decodes them into the result and resets them for the next tick.
+struct TickScratch {
+  unsigned long long key;       // min over candidates of the selection key
+  unsigned long long executed;  // sum of prediction steps taken
+  unsigned int n_safe;
+  unsigned int done;            // blocks finished
+  unsigned int pad[2];
+};
+
+struct TickArgs {
+  const float* K;      // n x n float32 row-major (device)
+  const double* x_t;   // device, nx
+  const double* u_h;   // device, nu
+  const float* ext;    // device samples N x nu (EXTERNAL) or null
+  DevSafety safety;
+  int kind;            // BasisKind
+  int n_samples, n_slots, horizon, include_user, sampler;
+  float in_lo[MPMI_MAX_NU], in_w[MPMI_MAX_NU];        // float32 box (UNIFORM)
+  double in_lo64[MPMI_MAX_NU], in_hi64[MPMI_MAX_NU];  // float64 box (GRID)
+  int grid_g;          // points per dimension (GRID)
+  uint32_t key0, key1, t_lo, t_hi, stream;
+  unsigned long long tick;
+  TickScratch* scratch;
+  mpmi_result* result;
+  int32_t* ttv_out;
+  float* cost_out;
+  float* traj_out;
+};
+
+}  // namespace mpmi
+
+// ---- host handles ----------------------------------------------------------
+struct mpmi_ctx {
+  int device = 0;
+  uint64_t budget = 0;
+  uint64_t used = 0;
+  int sm_count = 0;
+};
+
+struct mpmi_model {
+  mpmi_ctx* ctx = nullptr;
+  int basis = 0, kind = 0, n = 0, nx = 0, nu = 0, np = 0;
+  std::vector<double> K64;
+  float* K32_dev = nullptr;
+  bool has_safety = false;
+  mpmi_safety_spec spec{};
+  std::vector<double> track_host;
+  mpmi::DevSafety dev_safety{};
+  // device buffers of the track grid
+  uint32_t* cells_dev = nullptr;
+  uint16_t* list_dev = nullptr;
+  float4* seg_dev = nullptr;
+  float* seg_inv_dev = nullptr;
+  uint64_t bytes = 0;
+};
+
+struct mpmi_session {
+  mpmi_ctx* ctx = nullptr;
+  const mpmi_model* model = nullptr;
+  mpmi_session_config cfg{};
+  int n_slots = 0, lanes = 1, block = 128, grid_g = 0;
+  mpmi::TickScratch* scratch_dev = nullptr;
+  mpmi_result* result_dev = nullptr;
+  double* in_dev = nullptr;        // x_t (8 doubles) then u_h (4 doubles)
+  double* in_host = nullptr;       // pinned staging
+  mpmi_result* result_host = nullptr;  // pinned
+  cudaEvent_t done = nullptr;
+  bool in_flight = false;
+  uint64_t bytes = 0;
+};
+
+namespace mpmi {
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+// host helpers implemented in fit.cpp / track.cpp
+int fit_householder(int kind, const double* x, const double* u, const double* xn,
+                    int64_t m, std::vector<double>* K, double* residual, std::string* err);
+struct TrackGrid {
+  std::vector<uint32_t> cells;
+  std::vector<uint16_t> list;
+  std::vector<float> seg;      // 4 per segment
+  std::vector<float> seg_inv;  // 1 per segment
+  double gx0 = 0, gy0 = 0, h = 1;
+  int gnx = 0, gny = 0;
+};
+int build_track_grid(const double* xy, int n, double half_width, TrackGrid* g,
+                     std::string* err);
+}  // namespace mpmi

@@ -1,0 +1,620 @@
+// C-ABI entry points of the MPMI-SC tick library (declared in include/mpmi.h).
+//
+// Host side: handle lifecycle, argument checks, the float64 fit, the safety-set
+// preprocessing and the launch of the fused tick kernel.  Every step of a tick
+// (sampling, lifting, prediction, safety, cost, argmin, decode) runs on the GPU
+// in tick_kernel.cuh; the host only marshals arguments.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "tick_kernel.cuh"
+
+namespace mpmi {
+
+static thread_local std::string g_error;
+
+void set_error(const std::string& msg) { g_error = msg; }
+
+int fail(int code, const std::string& msg) {
+  g_error = msg;
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(MPMI_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define MPMI_CUDA(call, what)                  \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) {
+      err = cudaSetDevice(dev);
+      changed = err == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+static bool budget_ok(mpmi_ctx* ctx, uint64_t bytes) {
+  return ctx->budget == 0 || ctx->used + bytes <= ctx->budget;
+}
+
+// ---- kernel dispatch -------------------------------------------------------
+using TickLaunch = void (*)(const TickArgs&, int, int, cudaStream_t);
+
+template <int KIND, int L, bool TRAJ>
+static void launch_tick(const TickArgs& a, int grid, int block, cudaStream_t st) {
+  tick_kernel<KIND, L, TRAJ><<<grid, block, 0, st>>>(a);
+}
+
+template <int KIND, bool TRAJ>
+static TickLaunch pick_lanes(int lanes) {
+  if constexpr (KIND == kBot) {
+    if (lanes == 1) return launch_tick<KIND, 1, TRAJ>;
+    if (lanes == 2) return launch_tick<KIND, 2, TRAJ>;
+    if (lanes == 4) return launch_tick<KIND, 4, TRAJ>;
+  } else if constexpr (KIND == kCar) {
+    if (lanes == 8) return launch_tick<KIND, 8, TRAJ>;
+    if (lanes == 16) return launch_tick<KIND, 16, TRAJ>;
+  } else {
+    if (lanes == 1) return launch_tick<KIND, 1, TRAJ>;
+  }
+  return nullptr;
+}
+
+static TickLaunch pick_tick(int kind, int lanes, bool traj) {
+  switch (kind) {
+    case kBot: return traj ? pick_lanes<kBot, true>(lanes) : pick_lanes<kBot, false>(lanes);
+    case kCar: return traj ? pick_lanes<kCar, true>(lanes) : pick_lanes<kCar, false>(lanes);
+    case kLin11: return traj ? pick_lanes<kLin11, true>(lanes) : pick_lanes<kLin11, false>(lanes);
+    case kLin22: return traj ? pick_lanes<kLin22, true>(lanes) : pick_lanes<kLin22, false>(lanes);
+    case kLin41: return traj ? pick_lanes<kLin41, true>(lanes) : pick_lanes<kLin41, false>(lanes);
+  }
+  return nullptr;
+}
+
+static int default_lanes(int kind, int n_slots) {
+  if (kind == kBot) return n_slots <= 32768 ? 4 : (n_slots <= 131072 ? 2 : 1);
+  if (kind == kCar) return 8;
+  return 1;
+}
+
+static TickArgs make_args(const mpmi_session* s, uint64_t tick) {
+  const mpmi_model* m = s->model;
+  TickArgs a;
+  memset(&a, 0, sizeof(a));
+  a.K = m->K32_dev;
+  a.safety = m->dev_safety;
+  a.kind = m->kind;
+  a.n_samples = s->cfg.n_samples;
+  a.n_slots = s->n_slots;
+  a.horizon = s->cfg.horizon;
+  a.include_user = s->cfg.include_user;
+  a.sampler = s->cfg.sampler;
+  for (int j = 0; j < MPMI_MAX_NU; ++j) {
+    a.in_lo[j] = (float)s->cfg.input_lo[j];
+    a.in_w[j] = (float)(s->cfg.input_hi[j] - s->cfg.input_lo[j]);
+    a.in_lo64[j] = s->cfg.input_lo[j];
+    a.in_hi64[j] = s->cfg.input_hi[j];
+  }
+  a.grid_g = s->grid_g;
+  a.key0 = (uint32_t)(s->cfg.seed & 0xFFFFFFFFull);
+  a.key1 = (uint32_t)(s->cfg.seed >> 32);
+  a.t_lo = (uint32_t)(tick & 0xFFFFFFFFull);
+  a.t_hi = (uint32_t)(tick >> 32);
+  a.stream = s->cfg.stream_id;
+  a.tick = tick;
+  a.scratch = s->scratch_dev;
+  return a;
+}
+
+static int launch(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st) {
+  TickLaunch fn = pick_tick(s->model->kind, s->lanes, traj);
+  if (!fn) return fail(MPMI_E_UNSUPPORTED, "tick kernel not compiled for this basis/lanes");
+  const int per_block = s->block / s->lanes;
+  const int grid = (s->n_slots + per_block - 1) / per_block;
+  fn(a, grid, s->block, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "tick kernel launch");
+  return MPMI_OK;
+}
+
+static int check_finite(const double* v, int n, const char* what) {
+  for (int i = 0; i < n; ++i)
+    if (!isfinite(v[i])) return fail(MPMI_E_NONFINITE, std::string(what) + " holds NaN/Inf");
+  return MPMI_OK;
+}
+
+static int grid_points(int n, int nu) {
+  if (n <= 0) return 0;
+  int g = (int)llround(pow((double)n, 1.0 / nu));
+  for (int c = g > 2 ? g - 2 : 1; c <= g + 2; ++c) {
+    long long p = 1;
+    for (int j = 0; j < nu; ++j) p *= c;
+    if (p == n) return c;
+  }
+  return -1;
+}
+
+static void free_model_device(mpmi_model* m) {
+  cudaFree(m->K32_dev);
+  cudaFree(m->cells_dev);
+  cudaFree(m->list_dev);
+  cudaFree(m->seg_dev);
+  cudaFree(m->seg_inv_dev);
+  m->K32_dev = nullptr;
+  m->cells_dev = nullptr;
+  m->list_dev = nullptr;
+  m->seg_dev = nullptr;
+  m->seg_inv_dev = nullptr;
+}
+
+static int model_upload(mpmi_ctx* ctx, mpmi_model* m) {
+  const size_t bytes = sizeof(float) * m->n * m->n;
+  if (!budget_ok(ctx, bytes)) return fail(MPMI_E_OOM, "model exceeds the memory budget");
+  std::vector<float> k32(m->n * m->n);
+  for (size_t i = 0; i < k32.size(); ++i) k32[i] = (float)m->K64[i];
+  if (cudaMalloc(&m->K32_dev, bytes) != cudaSuccess)
+    return fail(MPMI_E_OOM, "cudaMalloc of K failed");
+  MPMI_CUDA(cudaMemcpy(m->K32_dev, k32.data(), bytes, cudaMemcpyHostToDevice), "upload K");
+  m->bytes += bytes;
+  ctx->used += bytes;
+  return MPMI_OK;
+}
+
+}  // namespace mpmi
+
+using namespace mpmi;
+
+extern "C" {
+
+const char* mpmi_last_error(void) { return g_error.c_str(); }
+
+const char* mpmi_version(void) { return "mpmi-gb300 1.0 (sm_103a)"; }
+
+int mpmi_create(int32_t device, uint64_t mem_budget_bytes, mpmi_ctx** out) {
+  if (!out) return fail(MPMI_E_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= count) return fail(MPMI_E_INVALID_ARG, "no such CUDA device");
+  DeviceGuard guard(device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+  cudaDeviceProp prop;
+  MPMI_CUDA(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
+  if (prop.major < 10) return fail(MPMI_E_UNSUPPORTED, "library is built for sm_103a");
+  mpmi_ctx* c = new mpmi_ctx();
+  c->device = device;
+  c->budget = mem_budget_bytes;
+  c->sm_count = prop.multiProcessorCount;
+  *out = c;
+  return MPMI_OK;
+}
+
+void mpmi_destroy(mpmi_ctx* ctx) { delete ctx; }
+
+uint64_t mpmi_memory_in_use(const mpmi_ctx* ctx) { return ctx ? ctx->used : 0; }
+
+int mpmi_fit_model(mpmi_ctx* ctx, const mpmi_basis_desc* basis, const double* x,
+                   const double* u, const double* x_next, int64_t m, mpmi_model** out,
+                   double* residual_out) {
+  if (!ctx || !basis || !x || !u || !x_next || !out)
+    return fail(MPMI_E_INVALID_ARG, "fit_model: NULL argument");
+  *out = nullptr;
+  const int kind = basis_kind(basis->basis, basis->nx, basis->nu);
+  if (kind < 0) return fail(MPMI_E_UNSUPPORTED, "fit_model: basis/dimensions not compiled");
+  int n, nx, nu, np;
+  kind_dims(kind, &n, &nx, &nu, &np);
+  if (m <= 0) return fail(MPMI_E_INVALID_ARG, "fit_model: no transitions");
+  int rc;
+  if ((rc = check_finite(x, (int)(m * nx), "fit_model: x")) != MPMI_OK) return rc;
+  if ((rc = check_finite(u, (int)(m * nu), "fit_model: u")) != MPMI_OK) return rc;
+  if ((rc = check_finite(x_next, (int)(m * nx), "fit_model: x_next")) != MPMI_OK) return rc;
+  std::vector<double> K;
+  std::string err;
+  double res = 0.0;
+  rc = fit_householder(kind, x, u, x_next, m, &K, &res, &err);
+  if (rc != MPMI_OK) return fail(rc, err);
+  DeviceGuard guard(ctx->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+  mpmi_model* md = new mpmi_model();
+  md->ctx = ctx;
+  md->basis = basis->basis;
+  md->kind = kind;
+  md->n = n; md->nx = nx; md->nu = nu; md->np = np;
+  md->K64 = K;
+  if ((rc = model_upload(ctx, md)) != MPMI_OK) {
+    free_model_device(md);
+    delete md;
+    return rc;
+  }
+  if (residual_out) *residual_out = res;
+  *out = md;
+  return MPMI_OK;
+}
+
+int mpmi_fit_operator(const mpmi_basis_desc* basis, const double* x, const double* u,
+                      const double* x_next, int64_t m, double* K_out, double* residual_out) {
+  if (!basis || !x || !u || !x_next || !K_out)
+    return fail(MPMI_E_INVALID_ARG, "fit_operator: NULL argument");
+  const int kind = basis_kind(basis->basis, basis->nx, basis->nu);
+  if (kind < 0) return fail(MPMI_E_UNSUPPORTED, "fit_operator: basis/dimensions not compiled");
+  int n, nx, nu, np;
+  kind_dims(kind, &n, &nx, &nu, &np);
+  if (m <= 0) return fail(MPMI_E_INVALID_ARG, "fit_operator: no transitions");
+  int rc;
+  if ((rc = check_finite(x, (int)(m * nx), "fit_operator: x")) != MPMI_OK) return rc;
+  if ((rc = check_finite(u, (int)(m * nu), "fit_operator: u")) != MPMI_OK) return rc;
+  if ((rc = check_finite(x_next, (int)(m * nx), "fit_operator: x_next")) != MPMI_OK) return rc;
+  std::vector<double> K;
+  std::string err;
+  double res = 0.0;
+  rc = fit_householder(kind, x, u, x_next, m, &K, &res, &err);
+  if (rc != MPMI_OK) return fail(rc, err);
+  memcpy(K_out, K.data(), sizeof(double) * K.size());
+  if (residual_out) *residual_out = res;
+  return MPMI_OK;
+}
+
+int mpmi_model_from_operator(mpmi_ctx* ctx, const mpmi_basis_desc* basis, const double* K,
+                             mpmi_model** out) {
+  if (!ctx || !basis || !K || !out) return fail(MPMI_E_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  const int kind = basis_kind(basis->basis, basis->nx, basis->nu);
+  if (kind < 0) return fail(MPMI_E_UNSUPPORTED, "basis/dimensions not compiled");
+  int n, nx, nu, np;
+  kind_dims(kind, &n, &nx, &nu, &np);
+  int rc = check_finite(K, n * n, "K");
+  if (rc != MPMI_OK) return rc;
+  DeviceGuard guard(ctx->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+  mpmi_model* md = new mpmi_model();
+  md->ctx = ctx;
+  md->basis = basis->basis;
+  md->kind = kind;
+  md->n = n; md->nx = nx; md->nu = nu; md->np = np;
+  md->K64.assign(K, K + n * n);
+  if ((rc = model_upload(ctx, md)) != MPMI_OK) {
+    free_model_device(md);
+    delete md;
+    return rc;
+  }
+  *out = md;
+  return MPMI_OK;
+}
+
+int mpmi_model_get_operator(const mpmi_model* model, double* K_out, int32_t* n_out) {
+  if (!model) return fail(MPMI_E_INVALID_ARG, "model is NULL");
+  if (n_out) *n_out = model->n;
+  if (K_out) memcpy(K_out, model->K64.data(), sizeof(double) * model->K64.size());
+  return MPMI_OK;
+}
+
+void mpmi_model_free(mpmi_model* model) {
+  if (!model) return;
+  DeviceGuard guard(model->ctx->device);
+  free_model_device(model);
+  model->ctx->used -= model->bytes;
+  delete model;
+}
+
+int mpmi_set_safety_set(mpmi_model* model, const mpmi_safety_spec* spec) {
+  if (!model || !spec) return fail(MPMI_E_INVALID_ARG, "set_safety_set: NULL argument");
+  if (!(spec->inflation >= 0.0) || !isfinite(spec->inflation))
+    return fail(MPMI_E_INVALID_ARG, "set_safety_set: inflation must be finite and >= 0");
+  DevSafety ds;
+  memset(&ds, 0, sizeof(ds));
+  for (int j = 0; j < MPMI_MAX_NX; ++j) {
+    const double lo = spec->state_lo[j], hi = spec->state_hi[j];
+    if (isnan(lo) || isnan(hi)) return fail(MPMI_E_INVALID_ARG, "set_safety_set: NaN bound");
+    if (j >= model->nx) {
+      ds.lo[j] = -INFINITY;
+      ds.hi[j] = INFINITY;
+      continue;
+    }
+    ds.lo[j] = (float)(lo + spec->inflation);
+    ds.hi[j] = (float)(hi - spec->inflation);
+  }
+  TrackGrid grid;
+  const bool has_track = spec->track_xy != nullptr;
+  if (has_track) {
+    if (model->kind != kCar)
+      return fail(MPMI_E_UNSUPPORTED, "set_safety_set: track test is compiled for the race car");
+    if (spec->track_x != 0 || spec->track_y != 1)
+      return fail(MPMI_E_UNSUPPORTED, "set_safety_set: track position must be state (0, 1)");
+    if (spec->n_track < 3 || spec->n_track > MPMI_MAX_TRACK_VERTICES)
+      return fail(MPMI_E_INVALID_ARG, "set_safety_set: n_track out of range");
+    if (!(spec->track_half_width > 0.0) || !isfinite(spec->track_half_width))
+      return fail(MPMI_E_INVALID_ARG, "set_safety_set: track half width must be > 0");
+    std::string err;
+    int rc = build_track_grid(spec->track_xy, spec->n_track,
+                              spec->track_half_width - spec->inflation, &grid, &err);
+    if (rc != MPMI_OK) return fail(rc, err);
+  }
+  mpmi_ctx* ctx = model->ctx;
+  DeviceGuard guard(ctx->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+  // release the previous track buffers
+  const uint64_t old_track = model->bytes - sizeof(float) * model->n * model->n;
+  cudaFree(model->cells_dev);
+  cudaFree(model->list_dev);
+  cudaFree(model->seg_dev);
+  cudaFree(model->seg_inv_dev);
+  model->cells_dev = nullptr;
+  model->list_dev = nullptr;
+  model->seg_dev = nullptr;
+  model->seg_inv_dev = nullptr;
+  model->bytes -= old_track;
+  ctx->used -= old_track;
+  if (has_track) {
+    const uint64_t b_cells = sizeof(uint32_t) * grid.cells.size();
+    const uint64_t b_list = sizeof(uint16_t) * grid.list.size();
+    const uint64_t b_seg = sizeof(float) * grid.seg.size();
+    const uint64_t b_inv = sizeof(float) * grid.seg_inv.size();
+    const uint64_t total = b_cells + b_list + b_seg + b_inv;
+    if (!budget_ok(ctx, total)) return fail(MPMI_E_OOM, "track grid exceeds the memory budget");
+    if (cudaMalloc(&model->cells_dev, b_cells) != cudaSuccess ||
+        cudaMalloc(&model->list_dev, b_list) != cudaSuccess ||
+        cudaMalloc(&model->seg_dev, b_seg) != cudaSuccess ||
+        cudaMalloc(&model->seg_inv_dev, b_inv) != cudaSuccess)
+      return fail(MPMI_E_OOM, "cudaMalloc of the track grid failed");
+    MPMI_CUDA(cudaMemcpy(model->cells_dev, grid.cells.data(), b_cells, cudaMemcpyHostToDevice), "track");
+    MPMI_CUDA(cudaMemcpy(model->list_dev, grid.list.data(), b_list, cudaMemcpyHostToDevice), "track");
+    MPMI_CUDA(cudaMemcpy(model->seg_dev, grid.seg.data(), b_seg, cudaMemcpyHostToDevice), "track");
+    MPMI_CUDA(cudaMemcpy(model->seg_inv_dev, grid.seg_inv.data(), b_inv, cudaMemcpyHostToDevice), "track");
+    model->bytes += total;
+    ctx->used += total;
+    const double w = spec->track_half_width - spec->inflation;
+    ds.has_track = 1;
+    ds.track.cells = model->cells_dev;
+    ds.track.list = model->list_dev;
+    ds.track.seg = model->seg_dev;
+    ds.track.seg_inv = model->seg_inv_dev;
+    ds.track.gx0 = (float)grid.gx0;
+    ds.track.gy0 = (float)grid.gy0;
+    ds.track.inv_h = (float)(1.0 / grid.h);
+    ds.track.gnx = grid.gnx;
+    ds.track.gny = grid.gny;
+    ds.track.w2 = (float)(w * w);
+    ds.track.xi = 0;
+    ds.track.yi = 1;
+    model->track_host.assign(spec->track_xy, spec->track_xy + 2 * spec->n_track);
+  } else {
+    model->track_host.clear();
+  }
+  model->spec = *spec;
+  model->spec.track_xy = nullptr;
+  model->dev_safety = ds;
+  model->has_safety = true;
+  return MPMI_OK;
+}
+
+int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model, const mpmi_session_config* cfg,
+                      mpmi_session** out) {
+  if (!ctx || !model || !cfg || !out) return fail(MPMI_E_INVALID_ARG, "session_open: NULL argument");
+  *out = nullptr;
+  if (model->ctx != ctx) return fail(MPMI_E_INVALID_ARG, "session_open: model from another context");
+  if (!model->has_safety)
+    return fail(MPMI_E_INVALID_ARG, "session_open: call set_safety_set on the model first");
+  if (cfg->n_samples < 0) return fail(MPMI_E_INVALID_ARG, "session_open: n_samples < 0");
+  if (cfg->horizon < 1 || cfg->horizon > MPMI_MAX_HORIZON)
+    return fail(MPMI_E_INVALID_ARG, "session_open: horizon out of range 1..511");
+  if (cfg->include_user != 0 && cfg->include_user != 1)
+    return fail(MPMI_E_INVALID_ARG, "session_open: include_user must be 0 or 1");
+  const long long slots = (long long)cfg->n_samples + cfg->include_user;
+  if (slots < 1 || slots > MPMI_MAX_SLOTS)
+    return fail(MPMI_E_INVALID_ARG, "session_open: number of slots out of range");
+  if (cfg->sampler < MPMI_SAMPLER_UNIFORM || cfg->sampler > MPMI_SAMPLER_EXTERNAL)
+    return fail(MPMI_E_INVALID_ARG, "session_open: unknown sampler");
+  for (int j = 0; j < model->nu; ++j) {
+    if (!isfinite(cfg->input_lo[j]) || !isfinite(cfg->input_hi[j]) ||
+        !(cfg->input_lo[j] < cfg->input_hi[j]))
+      return fail(MPMI_E_INVALID_ARG, "session_open: input box must be finite with lo < hi");
+  }
+  int gg = 0;
+  if (cfg->sampler == MPMI_SAMPLER_GRID) {
+    gg = grid_points(cfg->n_samples, model->nu);
+    if (gg <= 0) return fail(MPMI_E_INVALID_ARG, "session_open: grid sampling needs N = G^M");
+  }
+  int lanes = cfg->lanes ? cfg->lanes : default_lanes(model->kind, (int)slots);
+  int block = cfg->block ? cfg->block : 128;
+  if (block % 32 != 0 || block < 32 || block > kMaxBlock)
+    return fail(MPMI_E_INVALID_ARG, "session_open: block must be a multiple of 32 in 32..256");
+  if (!pick_tick(model->kind, lanes, false))
+    return fail(MPMI_E_UNSUPPORTED, "session_open: lanes per candidate not compiled for this basis");
+  const uint64_t bytes = sizeof(TickScratch) + sizeof(mpmi_result) + 16 * sizeof(double);
+  if (!budget_ok(ctx, bytes)) return fail(MPMI_E_OOM, "session exceeds the memory budget");
+  DeviceGuard guard(ctx->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+  mpmi_session* s = new mpmi_session();
+  s->ctx = ctx;
+  s->model = model;
+  s->cfg = *cfg;
+  s->n_slots = (int)slots;
+  s->lanes = lanes;
+  s->block = block;
+  s->grid_g = gg;
+  auto cleanup = [&](int code, const char* msg) {
+    cudaFree(s->scratch_dev);
+    cudaFree(s->result_dev);
+    cudaFree(s->in_dev);
+    cudaFreeHost(s->in_host);
+    cudaFreeHost(s->result_host);
+    if (s->done) cudaEventDestroy(s->done);
+    delete s;
+    return fail(code, msg);
+  };
+  if (cudaMalloc(&s->scratch_dev, sizeof(TickScratch)) != cudaSuccess ||
+      cudaMalloc(&s->result_dev, sizeof(mpmi_result)) != cudaSuccess ||
+      cudaMalloc(&s->in_dev, 16 * sizeof(double)) != cudaSuccess)
+    return cleanup(MPMI_E_OOM, "session_open: cudaMalloc failed");
+  if (cudaMallocHost(&s->in_host, 16 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&s->result_host, sizeof(mpmi_result)) != cudaSuccess)
+    return cleanup(MPMI_E_OOM, "session_open: pinned allocation failed");
+  if (cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(MPMI_E_CUDA, "session_open: cudaEventCreate failed");
+  TickScratch init;
+  memset(&init, 0, sizeof(init));
+  init.key = ~0ull;
+  if (cudaMemcpy(s->scratch_dev, &init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(s->result_dev, 0, sizeof(mpmi_result)) != cudaSuccess ||
+      cudaMemset(s->in_dev, 0, 16 * sizeof(double)) != cudaSuccess)
+    return cleanup(MPMI_E_CUDA, "session_open: initialising device state failed");
+  memset(s->in_host, 0, 16 * sizeof(double));
+  s->bytes = bytes;
+  ctx->used += bytes;
+  *out = s;
+  return MPMI_OK;
+}
+
+void mpmi_session_close(mpmi_session* s) {
+  if (!s) return;
+  DeviceGuard guard(s->ctx->device);
+  if (s->in_flight) cudaEventSynchronize(s->done);
+  cudaFree(s->scratch_dev);
+  cudaFree(s->result_dev);
+  cudaFree(s->in_dev);
+  cudaFreeHost(s->in_host);
+  cudaFreeHost(s->result_host);
+  cudaEventDestroy(s->done);
+  s->ctx->used -= s->bytes;
+  delete s;
+}
+
+int mpmi_session_launch_shape(const mpmi_session* s, int32_t* lanes, int32_t* block) {
+  if (!s) return fail(MPMI_E_INVALID_ARG, "session is NULL");
+  if (lanes) *lanes = s->lanes;
+  if (block) *block = s->block;
+  return MPMI_OK;
+}
+
+static int check_ext(const mpmi_session* s, const float* candidates_dev) {
+  if (s->cfg.sampler == MPMI_SAMPLER_EXTERNAL && s->cfg.n_samples > 0 && !candidates_dev)
+    return fail(MPMI_E_INVALID_ARG, "EXTERNAL sampler needs candidates_dev");
+  if (s->cfg.sampler != MPMI_SAMPLER_EXTERNAL && candidates_dev)
+    return fail(MPMI_E_INVALID_ARG, "candidates_dev given but the sampler is not EXTERNAL");
+  return MPMI_OK;
+}
+
+int mpmi_evaluate_candidates(mpmi_session* s, const double* x_t, const double* u_h,
+                             const float* candidates_dev, uint64_t tick, void* stream) {
+  if (!s || !x_t || !u_h) return fail(MPMI_E_INVALID_ARG, "evaluate_candidates: NULL argument");
+  const mpmi_model* m = s->model;
+  int rc;
+  if ((rc = check_finite(x_t, m->nx, "x_t")) != MPMI_OK) return rc;
+  if ((rc = check_finite(u_h, m->nu, "u_h")) != MPMI_OK) return rc;
+  if ((rc = check_ext(s, candidates_dev)) != MPMI_OK) return rc;
+  DeviceGuard guard(s->ctx->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (s->in_flight) {
+    MPMI_CUDA(cudaEventSynchronize(s->done), "waiting for the previous tick");
+    s->in_flight = false;
+  }
+  memcpy(s->in_host, x_t, sizeof(double) * m->nx);
+  memcpy(s->in_host + 8, u_h, sizeof(double) * m->nu);
+  MPMI_CUDA(cudaMemcpyAsync(s->in_dev, s->in_host, 12 * sizeof(double), cudaMemcpyHostToDevice, st),
+            "copy x_t/u_h to the device");
+  TickArgs a = make_args(s, tick);
+  a.x_t = s->in_dev;
+  a.u_h = s->in_dev + 8;
+  a.ext = candidates_dev;
+  a.result = s->result_dev;
+  if ((rc = launch(s, a, false, st)) != MPMI_OK) return rc;
+  MPMI_CUDA(cudaMemcpyAsync(s->result_host, s->result_dev, sizeof(mpmi_result),
+                            cudaMemcpyDeviceToHost, st), "copy the result to the host");
+  MPMI_CUDA(cudaEventRecord(s->done, st), "cudaEventRecord");
+  s->in_flight = true;
+  return MPMI_OK;
+}
+
+int mpmi_select_input(mpmi_session* s, mpmi_result* out) {
+  if (!s || !out) return fail(MPMI_E_INVALID_ARG, "select_input: NULL argument");
+  if (!s->in_flight) return fail(MPMI_E_NOT_READY, "select_input: no tick in flight");
+  DeviceGuard guard(s->ctx->device);
+  MPMI_CUDA(cudaEventSynchronize(s->done), "waiting for the tick");
+  s->in_flight = false;
+  *out = *s->result_host;
+  return MPMI_OK;
+}
+
+static int evaluate_device(mpmi_session* s, const double* x_t_dev, const double* u_h_dev,
+                           const float* candidates_dev, uint64_t tick, mpmi_result* result_dev,
+                           int32_t* ttv_dev, float* cost_dev, float* traj_dev, void* stream) {
+  if (!s || !x_t_dev || !u_h_dev || !result_dev)
+    return fail(MPMI_E_INVALID_ARG, "evaluate_candidates_device: NULL argument");
+  int rc;
+  if ((rc = check_ext(s, candidates_dev)) != MPMI_OK) return rc;
+  DeviceGuard guard(s->ctx->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+  TickArgs a = make_args(s, tick);
+  a.x_t = x_t_dev;
+  a.u_h = u_h_dev;
+  a.ext = candidates_dev;
+  a.result = result_dev;
+  a.ttv_out = ttv_dev;
+  a.cost_out = cost_dev;
+  a.traj_out = traj_dev;
+  return launch(s, a, traj_dev != nullptr, (cudaStream_t)stream);
+}
+
+int mpmi_evaluate_candidates_device(mpmi_session* s, const double* x_t_dev, const double* u_h_dev,
+                                    const float* candidates_dev, uint64_t tick,
+                                    mpmi_result* result_dev, int32_t* ttv_dev, float* cost_dev,
+                                    void* stream) {
+  return evaluate_device(s, x_t_dev, u_h_dev, candidates_dev, tick, result_dev, ttv_dev,
+                         cost_dev, nullptr, stream);
+}
+
+int mpmi_debug_trajectories(mpmi_session* s, const double* x_t_dev, const double* u_h_dev,
+                            const float* candidates_dev, uint64_t tick, mpmi_result* result_dev,
+                            int32_t* ttv_dev, float* cost_dev, float* traj_dev, void* stream) {
+  if (!traj_dev) return fail(MPMI_E_INVALID_ARG, "debug_trajectories: traj_dev is NULL");
+  return evaluate_device(s, x_t_dev, u_h_dev, candidates_dev, tick, result_dev, ttv_dev,
+                         cost_dev, traj_dev, stream);
+}
+
+int mpmi_sample_candidates(mpmi_session* s, const double* u_h_dev, const float* candidates_dev,
+                           uint64_t tick, float* out_dev, void* stream) {
+  if (!s || !out_dev) return fail(MPMI_E_INVALID_ARG, "sample_candidates: NULL argument");
+  if (s->cfg.include_user && !u_h_dev)
+    return fail(MPMI_E_INVALID_ARG, "sample_candidates: u_h_dev needed when slot 0 is u_h");
+  int rc;
+  if ((rc = check_ext(s, candidates_dev)) != MPMI_OK) return rc;
+  DeviceGuard guard(s->ctx->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+  TickArgs a = make_args(s, tick);
+  a.u_h = u_h_dev;
+  a.ext = candidates_dev;
+  const int block = 256, grid = (s->n_slots + block - 1) / block;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (s->model->nu) {
+    case 1: sample_kernel<1><<<grid, block, 0, st>>>(a, out_dev); break;
+    case 2: sample_kernel<2><<<grid, block, 0, st>>>(a, out_dev); break;
+    default: return fail(MPMI_E_UNSUPPORTED, "sample_candidates: input dimension");
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "sample kernel launch");
+  return MPMI_OK;
+}
+
+}  // extern "C"

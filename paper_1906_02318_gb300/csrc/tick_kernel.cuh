@@ -1,0 +1,364 @@
+// The fused MPMI-SC tick (Alg. 2) as one kernel launch.
+//
+// Per candidate slot: draw the candidate (Alg. 2 first step), lift it
+// (Sec. IV-A), predict z <- K z for up to H steps with the safety test after
+// every step and exit at the first violation (Alg. 2's while-loop, Sec. V-C.1),
+// score ||xi - u_h||^2 (Sec. IV-D), and fold (H - ttv, cost, slot) into one
+// 64-bit key whose minimum over all candidates is the least-intervention safe
+// input or, if none is safe, the longest survivor.  The block that finishes
+// last decodes the minimum into the tick's result on the device.
+//
+// Work layout: L lanes of a warp share one candidate.  Lane q of a group holds
+// rows [qR, qR + R) of K in registers (R = n / L) and computes those rows of
+// K z; the group exchanges the new z through a per-warp shared-memory buffer
+// (double-buffered by step parity, one __syncwarp per step).  L = 1 keeps a
+// whole candidate in one thread.  L trades FFMA work per thread against
+// parallelism: at N ~ 16k one candidate per thread leaves most of the GPU idle.
+#pragma once
+
+#include <stdint.h>
+
+#include "internal.h"
+#include "philox.cuh"
+
+namespace mpmi {
+
+constexpr int kMaxBlock = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Alg. 2 first step: the input held by candidate `slot`.
+template <int NU>
+__device__ __forceinline__ void candidate_value(const TickArgs& a, int slot,
+                                                const float* uh32, float* xi) {
+  if (a.include_user && slot == 0) {
+#pragma unroll
+    for (int j = 0; j < NU; ++j) xi[j] = uh32[j];
+    return;
+  }
+  const int i = slot - a.include_user;
+  if (a.sampler == MPMI_SAMPLER_UNIFORM) {
+    const U32x4 w = philox4x32_10(U32x4{(uint32_t)i, a.t_lo, a.t_hi, a.stream}, a.key0, a.key1);
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+      const float u = (float)(ws[j] >> 8) * 0x1p-24f;  // exact: 24-bit integer
+      xi[j] = __fadd_rn(a.in_lo[j], __fmul_rn(a.in_w[j], u));
+    }
+  } else if (a.sampler == MPMI_SAMPLER_GRID) {
+    int rem = i;
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+      const int gj = rem % a.grid_g;
+      rem /= a.grid_g;
+      const double span = __dsub_rn(a.in_hi64[j], a.in_lo64[j]);
+      const double v = __dadd_rn(
+          __ddiv_rn(__dmul_rn((double)gj + 0.5, span), (double)a.grid_g), a.in_lo64[j]);
+      xi[j] = __double2float_rn(v);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NU; ++j) xi[j] = a.ext[(size_t)i * NU + j];
+  }
+}
+
+// Input monomials p_k(xi) of the split lifting, float32.
+template <int KIND>
+__device__ __forceinline__ void monomials32(const float* xi, float* p) {
+  if constexpr (KIND == kCar) {
+    p[0] = xi[0];
+    p[1] = xi[1];
+    p[2] = __fmul_rn(xi[0], xi[0]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < BasisTraits<KIND>::NP; ++k) p[k] = xi[k];
+  }
+}
+
+// isSafe on the box part: lo < x_j < hi for every state coordinate (NaN fails).
+template <int NX>
+__device__ __forceinline__ bool box_ok(const DevSafety& s, const float* z) {
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < NX; ++j) ok = ok && (z[j] > s.lo[j]) && (z[j] < s.hi[j]);
+  return ok;
+}
+
+// isSafe on the track part, shared by the L lanes of a group: lane q tests list
+// entries q, q + L, ... (nearest first, stops at the first hit); the group ORs.
+template <int L>
+__device__ __forceinline__ bool track_ok(const DevTrack& tr, float px, float py, int q,
+                                         bool active) {
+  bool ok = false;
+  if (active) {
+    const float fx = (px - tr.gx0) * tr.inv_h;
+    const float fy = (py - tr.gy0) * tr.inv_h;
+    if (fx >= 0.f && fx < (float)tr.gnx && fy >= 0.f && fy < (float)tr.gny) {
+      const uint32_t c = __ldg(&tr.cells[(int)fy * tr.gnx + (int)fx]);
+      const uint32_t cls = c & 3u;
+      if (cls == kCellInside) {
+        ok = true;
+      } else if (cls == kCellBoundary) {
+        const int off = (int)((c >> 2) & 0x3FFFFFu), cnt = (int)(c >> 24);
+        for (int i = q; i < cnt; i += L) {
+          const int s = __ldg(&tr.list[off + i]);
+          const float4 sg = __ldg(&tr.seg[s]);
+          const float inv = __ldg(&tr.seg_inv[s]);
+          const float rx = px - sg.x, ry = py - sg.y;
+          const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * inv, 0.f), 1.f);
+          const float ex = rx - t * sg.z, ey = ry - t * sg.w;
+          if (ex * ex + ey * ey < tr.w2) {
+            ok = true;
+            break;
+          }
+        }
+      }
+    }
+  }
+  if constexpr (L > 1) {
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) ok = ok | (__shfl_xor_sync(kFull, (int)ok, o) != 0);
+  }
+  return ok;
+}
+
+template <int KIND, int L, bool TRAJ>
+__global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__ TickArgs a) {
+  using B = BasisTraits<KIND>;
+  constexpr int N = B::N, NX = B::NX, NU = B::NU, NP = B::NP;
+  static_assert(N % L == 0, "lanes must divide the lifted dimension");
+  static_assert(32 % L == 0, "lanes must divide the warp");
+  constexpr int R = N / L;              // rows of K per lane
+  constexpr int GPW = 32 / L;           // candidate groups per warp
+  constexpr int S = (N % 32 == 0) ? N + 4 : ((N % 4 == 0) ? N : N + (4 - N % 4));
+  constexpr int NW = kMaxBlock / 32;
+  constexpr int ACC = (R < 8) ? 2 : 1;  // split accumulators for ILP on short rows
+
+  __shared__ float s_a[N];
+  __shared__ float s_b[NP][N];
+  __shared__ float s_uh[NU];
+  __shared__ __align__(16) float s_x[(L > 1) ? NW : 1][2][GPW][S];
+  __shared__ unsigned long long s_key[NW];
+  __shared__ unsigned int s_exec[NW];
+  __shared__ unsigned int s_nsafe[NW];
+  __shared__ int s_last;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int q = lane % L, g = lane / L;
+
+  // per-tick part of the lifting (float64, one feature per lane of warp 0)
+  if (warp == 0) {
+    double x[NX];
+#pragma unroll
+    for (int j = 0; j < NX; ++j) x[j] = a.x_t[j];
+    for (int j = lane; j < N; j += 32) {
+      double av, bv[kMaxP];
+      feature_split(KIND, j, x, &av, bv);
+      s_a[j] = __double2float_rn(av);
+#pragma unroll
+      for (int k = 0; k < NP; ++k) s_b[k][j] = __double2float_rn(bv[k]);
+    }
+    if (lane < NU) s_uh[lane] = __double2float_rn(a.u_h[lane]);
+  }
+  // this lane's rows of K
+  float kr[R][N];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const float* row = a.K + (q * R + r) * N;
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+      for (int k = 0; k < N; k += 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(row + k));
+        kr[r][k] = v.x; kr[r][k + 1] = v.y; kr[r][k + 2] = v.z; kr[r][k + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k) kr[r][k] = __ldg(row + k);
+    }
+  }
+  __syncthreads();
+
+  const int per_block = blockDim.x / L;
+  const int slot = blockIdx.x * per_block + warp * GPW + g;
+  const bool valid = slot < a.n_slots;
+  const int H = a.horizon;
+
+  float xi[NU];
+  if (valid) {
+    candidate_value<NU>(a, slot, s_uh, xi);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NU; ++j) xi[j] = s_uh[j];
+  }
+  float cost = 0.f;
+#pragma unroll
+  for (int j = 0; j < NU; ++j) {
+    const float d = __fsub_rn(xi[j], s_uh[j]);
+    cost = __fmaf_rn(d, d, cost);
+  }
+  float p[NP];
+  monomials32<KIND>(xi, p);
+  float z[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    float v = s_a[j];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) v = __fmaf_rn(p[k], s_b[k][j], v);
+    z[j] = v;
+  }
+  float* traj = nullptr;
+  if constexpr (TRAJ) {
+    if (valid && q == 0) {
+      traj = a.traj_out + (size_t)slot * (H + 1) * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) traj[j] = z[j];
+    }
+  }
+
+  int ttv = 0;
+  bool alive = valid;
+  for (int t = 1; t <= H; ++t) {
+    float zn[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float acc[ACC];
+#pragma unroll
+      for (int c = 0; c < ACC; ++c) acc[c] = 0.f;
+#pragma unroll
+      for (int k = 0; k < N; ++k) acc[k % ACC] = __fmaf_rn(kr[r][k], z[k], acc[k % ACC]);
+      float v = acc[0];
+#pragma unroll
+      for (int c = 1; c < ACC; ++c) v += acc[c];
+      zn[r] = v;
+    }
+    if constexpr (L == 1) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) z[j] = zn[j];
+    } else {
+      float* buf = &s_x[warp][t & 1][g][0];
+      if constexpr (R % 4 == 0) {
+#pragma unroll
+        for (int r = 0; r < R; r += 4)
+          *reinterpret_cast<float4*>(buf + q * R + r) =
+              make_float4(zn[r], zn[r + 1], zn[r + 2], zn[r + 3]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[q * R + r] = zn[r];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < N; k += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(buf + k);
+        z[k] = v.x; z[k + 1] = v.y; z[k + 2] = v.z; z[k + 3] = v.w;
+      }
+    }
+    if constexpr (TRAJ) {
+      if (traj != nullptr && alive) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) traj[(size_t)t * N + j] = z[j];
+      }
+    }
+    bool ok = box_ok<NX>(a.safety, z);
+    if constexpr (B::TRACK) {
+      if (a.safety.has_track) {  // uniform over the grid
+        const bool on_road = track_ok<L>(a.safety.track, z[0], z[1], q, alive && ok);
+        ok = ok && on_road;
+      }
+    }
+    if (alive) {
+      if (ok) ttv = t;
+      else alive = false;
+    }
+    if (!__any_sync(kFull, alive)) break;
+  }
+
+  // selection key: (H - ttv) | cost bits | slot  -> lexicographic minimum
+  unsigned long long key = ~0ull;
+  if (valid) {
+    key = ((unsigned long long)(H - ttv) << 55) |
+          ((unsigned long long)__float_as_uint(cost) << 23) | (unsigned long long)slot;
+    if (q == 0) {
+      if (a.ttv_out) a.ttv_out[slot] = ttv;
+      if (a.cost_out) a.cost_out[slot] = cost;
+    }
+  }
+  unsigned int steps = (valid && q == 0) ? (unsigned int)min(ttv + 1, H) : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(kFull, key, o);
+    key = other < key ? other : key;
+    steps += __shfl_xor_sync(kFull, steps, o);
+  }
+  const unsigned int nsafe = __popc(__ballot_sync(kFull, valid && q == 0 && ttv == H));
+  if (lane == 0) {
+    s_key[warp] = key;
+    s_exec[warp] = steps;
+    s_nsafe[warp] = nsafe;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long bk = s_key[0];
+    unsigned long long be = s_exec[0];
+    unsigned int bs = s_nsafe[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      bk = s_key[w] < bk ? s_key[w] : bk;
+      be += s_exec[w];
+      bs += s_nsafe[w];
+    }
+    TickScratch* sc = a.scratch;
+    atomicMin(&sc->key, bk);
+    atomicAdd(&sc->executed, be);
+    atomicAdd(&sc->n_safe, bs);
+    __threadfence();
+    const unsigned int prev = atomicAdd(&sc->done, 1u);
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last && tid == 0) {
+    // last block: every other block's atomics are visible (fence + counter)
+    __threadfence();
+    TickScratch* sc = a.scratch;
+    const unsigned long long k = atomicAdd(&sc->key, 0ull);
+    const unsigned long long ex = atomicAdd(&sc->executed, 0ull);
+    const unsigned int ns = atomicAdd(&sc->n_safe, 0u);
+    const int best = (int)(k & 0x7FFFFFull);
+    const int hm = (int)(k >> 55);
+    mpmi_result r;
+    float xb[NU];
+    candidate_value<NU>(a, best, s_uh, xb);
+#pragma unroll
+    for (int j = 0; j < MPMI_MAX_NU; ++j) r.u_r[j] = 0.0;
+#pragma unroll
+    for (int j = 0; j < NU; ++j)
+      r.u_r[j] = (a.include_user && best == 0) ? a.u_h[j] : (double)xb[j];
+    r.index = best;
+    r.status = hm == 0 ? MPMI_SAFE : MPMI_FALLBACK;
+    r.n_safe = (int32_t)ns;
+    r.ttv = H - hm;
+    r.cost = __uint_as_float((unsigned int)((k >> 23) & 0xFFFFFFFFull));
+    r.n_slots = a.n_slots;
+    r.executed_steps = ex;
+    r.tick = a.tick;
+    r.reserved = 0;
+    *a.result = r;
+    sc->key = ~0ull;
+    sc->executed = 0ull;
+    sc->n_safe = 0u;
+    sc->done = 0u;
+  }
+}
+
+// Alg. 2 first step alone (parity of the candidate stream).
+template <int NU>
+__global__ void sample_kernel(const __grid_constant__ TickArgs a, float* out) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= a.n_slots) return;
+  float uh[NU];
+#pragma unroll
+  for (int j = 0; j < NU; ++j) uh[j] = a.include_user ? __double2float_rn(a.u_h[j]) : 0.f;
+  float xi[NU];
+  candidate_value<NU>(a, slot, uh, xi);
+#pragma unroll
+  for (int j = 0; j < NU; ++j) out[(size_t)slot * NU + j] = xi[j];
+}
+
+}  // namespace mpmi

@@ -1,0 +1,345 @@
+"""Thin Python binding of libmpmi.so (include/mpmi.h): argument marshalling only.
+
+Every computation of a tick runs in the CUDA library; this module converts
+numpy arrays and torch tensors to pointers, checks return codes and turns the
+80-byte result record into a dict.  There is no Python or CPU fallback: if the
+shared library is missing, loading raises.
+
+Names follow the C ABI: fit_model, model_from_operator, set_safety_set,
+Session (session_open/close), evaluate_candidates, select_input,
+evaluate_candidates_device, sample_candidates, debug_trajectories.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmpmi.so")
+
+BASIS = {"bot": 0, "car": 1, "linear": 2}
+BASIS_DIMS = {"bot": (4, 1), "car": (6, 2)}
+SAMPLER = {"uniform": 0, "grid": 1, "external": 2}
+SAFE, FALLBACK = 0, 1
+MAX_NX, MAX_NU = 8, 4
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "NONFINITE", -4: "CUDA", -5: "NOT_READY",
+          -6: "UNSUPPORTED"}
+
+c_i32, c_u32, c_i64, c_u64, c_dbl, c_vp = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64,
+                                           ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p)
+P_dbl = ctypes.POINTER(ctypes.c_double)
+
+
+class BasisDesc(ctypes.Structure):
+    _fields_ = [("basis", c_i32), ("nx", c_i32), ("nu", c_i32)]
+
+
+class SafetySpecC(ctypes.Structure):
+    _fields_ = [("state_lo", c_dbl * MAX_NX), ("state_hi", c_dbl * MAX_NX),
+                ("inflation", c_dbl), ("track_xy", P_dbl), ("n_track", c_i32),
+                ("track_x", c_i32), ("track_y", c_i32), ("pad0", c_i32),
+                ("track_half_width", c_dbl)]
+
+
+class SessionConfig(ctypes.Structure):
+    _fields_ = [("n_samples", c_i32), ("horizon", c_i32), ("include_user", c_i32),
+                ("sampler", c_i32), ("input_lo", c_dbl * MAX_NU), ("input_hi", c_dbl * MAX_NU),
+                ("seed", c_u64), ("stream_id", c_u32), ("lanes", c_i32), ("block", c_i32),
+                ("pad0", c_i32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("u_r", c_dbl * MAX_NU), ("index", c_i32), ("status", c_i32),
+                ("n_safe", c_i32), ("ttv", c_i32), ("cost", ctypes.c_float),
+                ("n_slots", c_i32), ("executed_steps", c_u64), ("tick", c_u64),
+                ("reserved", c_u64)]
+
+
+RESULT_BYTES = ctypes.sizeof(Result)
+assert RESULT_BYTES == 80 and ctypes.sizeof(SafetySpecC) == 168
+assert ctypes.sizeof(SessionConfig) == 104
+
+_SIGNATURES = {
+    "mpmi_create": (c_i32, [c_i32, c_u64, ctypes.POINTER(c_vp)]),
+    "mpmi_destroy": (None, [c_vp]),
+    "mpmi_last_error": (ctypes.c_char_p, []),
+    "mpmi_version": (ctypes.c_char_p, []),
+    "mpmi_memory_in_use": (c_u64, [c_vp]),
+    "mpmi_fit_model": (c_i32, [c_vp, ctypes.POINTER(BasisDesc), c_vp, c_vp, c_vp, c_i64,
+                               ctypes.POINTER(c_vp), P_dbl]),
+    "mpmi_fit_operator": (c_i32, [ctypes.POINTER(BasisDesc), c_vp, c_vp, c_vp, c_i64, c_vp,
+                                  P_dbl]),
+    "mpmi_model_from_operator": (c_i32, [c_vp, ctypes.POINTER(BasisDesc), c_vp,
+                                         ctypes.POINTER(c_vp)]),
+    "mpmi_model_get_operator": (c_i32, [c_vp, c_vp, ctypes.POINTER(c_i32)]),
+    "mpmi_model_free": (None, [c_vp]),
+    "mpmi_set_safety_set": (c_i32, [c_vp, ctypes.POINTER(SafetySpecC)]),
+    "mpmi_session_open": (c_i32, [c_vp, c_vp, ctypes.POINTER(SessionConfig),
+                                  ctypes.POINTER(c_vp)]),
+    "mpmi_session_close": (None, [c_vp]),
+    "mpmi_session_launch_shape": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
+    "mpmi_evaluate_candidates": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
+    "mpmi_select_input": (c_i32, [c_vp, ctypes.POINTER(Result)]),
+    "mpmi_evaluate_candidates_device": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp, c_vp,
+                                                c_vp, c_vp]),
+    "mpmi_sample_candidates": (c_i32, [c_vp, c_vp, c_vp, c_u64, c_vp, c_vp]),
+    "mpmi_debug_trajectories": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp, c_vp, c_vp,
+                                        c_vp, c_vp]),
+}
+
+_lib = None
+
+
+class MpmiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Load libmpmi.so (built by paper_1906_02318_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with `python -m paper_1906_02318_gb300.build`"
+                           " (the CUDA library is required; there is no fallback)")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise MpmiError(rc, load().mpmi_last_error().decode())
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or None)."""
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def result_dict(r: Result, nu: int) -> dict:
+    return dict(u_r=np.array(r.u_r[:nu]), index=r.index, status=r.status, n_safe=r.n_safe,
+                ttv=r.ttv, cost=r.cost, n_slots=r.n_slots, executed_steps=r.executed_steps,
+                tick=r.tick)
+
+
+def result_from_bytes(buf, nu: int) -> dict:
+    """Decode an mpmi_result record (bytes / uint8 array / CPU uint8 tensor)."""
+    if hasattr(buf, "numpy"):
+        buf = buf.numpy()
+    raw = bytes(np.asarray(buf, dtype=np.uint8).reshape(-1)[:RESULT_BYTES])
+    return result_dict(Result.from_buffer_copy(raw), nu)
+
+
+class Context:
+    """mpmi_create / mpmi_destroy: the library bound to one CUDA device."""
+
+    def __init__(self, device: int = 0, mem_budget: int = 0):
+        self.lib = load()
+        h = c_vp()
+        _check(self.lib.mpmi_create(device, mem_budget, ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+
+    def memory_in_use(self) -> int:
+        return int(self.lib.mpmi_memory_in_use(self.handle))
+
+    def close(self):
+        if self.handle:
+            self.lib.mpmi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Model:
+    """A fitted (or given) lifted operator K with its safety set."""
+
+    def __init__(self, ctx: Context, handle, basis: str, nx: int, nu: int):
+        self.ctx, self.handle, self.basis, self.nx, self.nu = ctx, handle, basis, nx, nu
+
+    def get_operator(self) -> np.ndarray:
+        n = c_i32()
+        _check(self.ctx.lib.mpmi_model_get_operator(self.handle, None, ctypes.byref(n)))
+        K = np.empty((n.value, n.value), dtype=np.float64)
+        _check(self.ctx.lib.mpmi_model_get_operator(self.handle, K.ctypes.data, ctypes.byref(n)))
+        return K
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.mpmi_model_free(self.handle)
+            self.handle = None
+
+
+def _desc(basis: str, nx: int | None, nu: int | None) -> BasisDesc:
+    if basis in BASIS_DIMS:
+        nx, nu = BASIS_DIMS[basis]
+    return BasisDesc(BASIS[basis], nx, nu)
+
+
+def fit_model(ctx: Context, basis: str, x, u, x_next, nx: int | None = None,
+              nu: int | None = None):
+    """mpmi_fit_model: float64 least squares over transitions; returns (Model, residual)."""
+    d = _desc(basis, nx, nu)
+    x = _f64(x).reshape(-1, d.nx)
+    u = _f64(u).reshape(-1, d.nu)
+    xn = _f64(x_next).reshape(-1, d.nx)
+    h = c_vp()
+    res = ctypes.c_double()
+    _check(ctx.lib.mpmi_fit_model(ctx.handle, ctypes.byref(d), x.ctypes.data, u.ctypes.data,
+                                  xn.ctypes.data, x.shape[0], ctypes.byref(h),
+                                  ctypes.byref(res)))
+    return Model(ctx, h, basis, d.nx, d.nu), res.value
+
+
+def fit_operator(basis: str, x, u, x_next, nx: int | None = None, nu: int | None = None):
+    """mpmi_fit_operator: the host float64 fit alone (no device); returns (K, residual)."""
+    lib = load()
+    d = _desc(basis, nx, nu)
+    x = _f64(x).reshape(-1, d.nx)
+    u = _f64(u).reshape(-1, d.nu)
+    xn = _f64(x_next).reshape(-1, d.nx)
+    n = d.nx + d.nu if basis == "linear" else {"bot": 12, "car": 32}[basis]
+    K = np.empty((n, n), dtype=np.float64)
+    res = ctypes.c_double()
+    _check(lib.mpmi_fit_operator(ctypes.byref(d), x.ctypes.data, u.ctypes.data, xn.ctypes.data,
+                                 x.shape[0], K.ctypes.data, ctypes.byref(res)))
+    return K, res.value
+
+
+def model_from_operator(ctx: Context, basis: str, K, nx: int | None = None,
+                        nu: int | None = None) -> Model:
+    """mpmi_model_from_operator: a model from a given n x n operator (float64)."""
+    d = _desc(basis, nx, nu)
+    K = _f64(K)
+    h = c_vp()
+    _check(ctx.lib.mpmi_model_from_operator(ctx.handle, ctypes.byref(d), K.ctypes.data,
+                                            ctypes.byref(h)))
+    return Model(ctx, h, basis, d.nx, d.nu)
+
+
+def set_safety_set(model: Model, lo, hi, inflation: float = 0.0, track=None,
+                   half_width: float = 0.0):
+    """mpmi_set_safety_set: open per-coordinate bounds (+ optional closed track)."""
+    spec = SafetySpecC()
+    lo = _f64(lo)
+    hi = _f64(hi)
+    for j in range(MAX_NX):
+        spec.state_lo[j] = lo[j] if j < lo.size else -np.inf
+        spec.state_hi[j] = hi[j] if j < hi.size else np.inf
+    spec.inflation = inflation
+    keep = None
+    if track is not None:
+        keep = _f64(track).reshape(-1, 2)
+        spec.track_xy = keep.ctypes.data_as(P_dbl)
+        spec.n_track = keep.shape[0]
+        spec.track_x, spec.track_y = 0, 1
+        spec.track_half_width = half_width
+    _check(model.ctx.lib.mpmi_set_safety_set(model.handle, ctypes.byref(spec)))
+    del keep
+
+
+class Session:
+    """mpmi_session_open: one controller with fixed N and H."""
+
+    def __init__(self, ctx: Context, model: Model, n_samples: int, horizon: int,
+                 input_lo, input_hi, include_user: bool = True, sampler: str = "uniform",
+                 seed: int = 0, stream_id: int = 0, lanes: int = 0, block: int = 0):
+        cfg = SessionConfig()
+        cfg.n_samples, cfg.horizon = n_samples, horizon
+        cfg.include_user = int(include_user)
+        cfg.sampler = SAMPLER[sampler]
+        lo, hi = _f64(input_lo), _f64(input_hi)
+        for j in range(MAX_NU):
+            cfg.input_lo[j] = lo[j] if j < lo.size else 0.0
+            cfg.input_hi[j] = hi[j] if j < hi.size else 1.0
+        cfg.seed, cfg.stream_id, cfg.lanes, cfg.block = seed, stream_id, lanes, block
+        h = c_vp()
+        _check(ctx.lib.mpmi_session_open(ctx.handle, model.handle, ctypes.byref(cfg),
+                                         ctypes.byref(h)))
+        self.ctx, self.model, self.handle = ctx, model, h
+        self.n_samples, self.horizon, self.include_user = n_samples, horizon, bool(include_user)
+        self.n_slots = n_samples + int(include_user)
+        self.nx, self.nu = model.nx, model.nu
+        self.n = model.get_operator().shape[0]
+
+    def launch_shape(self):
+        lanes, block = c_i32(), c_i32()
+        _check(self.ctx.lib.mpmi_session_launch_shape(self.handle, ctypes.byref(lanes),
+                                                      ctypes.byref(block)))
+        return lanes.value, block.value
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.mpmi_session_close(self.handle)
+            self.handle = None
+
+
+def evaluate_candidates(s: Session, x_t, u_h, candidates=None, tick: int = 0, stream=None):
+    """mpmi_evaluate_candidates: queue one tick from host x_t / u_h (float64)."""
+    x = _f64(x_t, s.nx)
+    u = _f64(u_h, s.nu)
+    _check(s.ctx.lib.mpmi_evaluate_candidates(s.handle, x.ctypes.data, u.ctypes.data,
+                                              _ptr(candidates), tick, _stream(stream)))
+
+
+def select_input(s: Session) -> dict:
+    """mpmi_select_input: wait for the queued tick and return its outcome."""
+    r = Result()
+    _check(s.ctx.lib.mpmi_select_input(s.handle, ctypes.byref(r)))
+    return result_dict(r, s.nu)
+
+
+def evaluate_candidates_device(s: Session, x_t_dev, u_h_dev, result_dev, candidates=None,
+                               tick: int = 0, ttv_dev=None, cost_dev=None, stream=None):
+    """mpmi_evaluate_candidates_device: device-resident tick (torch tensors)."""
+    _check(s.ctx.lib.mpmi_evaluate_candidates_device(
+        s.handle, _ptr(x_t_dev), _ptr(u_h_dev), _ptr(candidates), tick, _ptr(result_dev),
+        _ptr(ttv_dev), _ptr(cost_dev), _stream(stream)))
+
+
+def sample_candidates(s: Session, out_dev, u_h_dev=None, candidates=None, tick: int = 0,
+                      stream=None):
+    """mpmi_sample_candidates: the tick's candidate values in slot order."""
+    _check(s.ctx.lib.mpmi_sample_candidates(s.handle, _ptr(u_h_dev), _ptr(candidates), tick,
+                                            _ptr(out_dev), _stream(stream)))
+
+
+def debug_trajectories(s: Session, x_t_dev, u_h_dev, result_dev, traj_dev, candidates=None,
+                       tick: int = 0, ttv_dev=None, cost_dev=None, stream=None):
+    """mpmi_debug_trajectories: a tick that also records every predicted z_t."""
+    _check(s.ctx.lib.mpmi_debug_trajectories(
+        s.handle, _ptr(x_t_dev), _ptr(u_h_dev), _ptr(candidates), tick, _ptr(result_dev),
+        _ptr(ttv_dev), _ptr(cost_dev), _ptr(traj_dev), _stream(stream)))

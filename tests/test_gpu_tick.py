@@ -1,0 +1,353 @@
+"""Parity of the CUDA tick (through the C ABI) with the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import mpmi as omp
+from oracle import safety as osafe
+from oracle import sampling as osamp
+from workloads import data, plants
+
+from parity import (bot_env, car_env, compare, gpu_model, oracle_samples, run_gpu)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_02318_gb300 import build, mpmi
+    build.build()
+    return mpmi
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    return lib.Context(0)
+
+
+@pytest.fixture(scope="module")
+def bot(lib, ctx):
+    env = bot_env()
+    return env, gpu_model(lib, ctx, env)
+
+
+@pytest.fixture(scope="module")
+def car(lib, ctx):
+    env = car_env()
+    return env, gpu_model(lib, ctx, env)
+
+
+def _tick(lib, ctx, env, model, x_t, u_h, N, H, seed=1, stream=0, tick=0, lanes=0,
+          include_user=True, sampler="uniform", block=0, traj=True):
+    sess = lib.Session(ctx, model, N, H, env.lo, env.hi, include_user=include_user,
+                       sampler=sampler, seed=seed, stream_id=stream, lanes=lanes, block=block)
+    try:
+        g = run_gpu(lib, sess, x_t, u_h, tick=tick, traj=traj)
+    finally:
+        sess.close()
+    samples = oracle_samples(env, N, seed, stream, tick, sampler)
+    o = omp.tick(env.K32, env.basis, x_t, u_h, samples, H, env.spec,
+                 include_user=include_user, record=True)
+    return g, o
+
+
+# --------------------------------------------------------------- Alg. 2 first step
+@pytest.mark.parametrize("which", ["bot", "car"])
+@pytest.mark.parametrize("sampler", ["uniform", "grid"])
+@pytest.mark.parametrize("include_user", [True, False])
+def test_candidates_bit_exact(lib, ctx, bot, car, which, sampler, include_user):
+    import torch
+    env, model = bot if which == "bot" else car
+    N = 4096 if sampler == "grid" and which == "car" else 5000
+    if sampler == "grid" and which == "car":
+        N = 64 * 64
+    for seed, stream, tick in [(1, 0, 0), (0xDEADBEEF12345, 7, 3), (5, 2**31, 2**40 + 5)]:
+        sess = lib.Session(ctx, model, N, 10, env.lo, env.hi, include_user=include_user,
+                           sampler=sampler, seed=seed, stream_id=stream)
+        u_h = data.to_f32_exact(data.user_input_once(seed, env.lo, env.hi))
+        out = torch.zeros((sess.n_slots, sess.nu), dtype=torch.float32, device="cuda")
+        uh = torch.tensor(u_h, dtype=torch.float64, device="cuda")
+        lib.sample_candidates(sess, out, u_h_dev=uh, tick=tick)
+        torch.cuda.synchronize()
+        sess.close()
+        want = omp.candidate_slots(u_h, oracle_samples(env, N, seed, stream, tick, sampler),
+                                   include_user)
+        got = out.cpu().numpy().astype(np.float64)
+        assert np.array_equal(got, want)
+
+
+def test_external_candidates_are_used(lib, ctx, bot):
+    import torch
+    env, model = bot
+    rng = np.random.default_rng(3)
+    cand = data.to_f32_exact(rng.uniform(-1, 1, (777, 1)))
+    dev = torch.tensor(cand, dtype=torch.float32, device="cuda")
+    sess = lib.Session(ctx, model, 777, 30, env.lo, env.hi, sampler="external")
+    x_t = np.array([0.15, 0.4, 0.5, -0.2])
+    u_h = np.array([0.8125])
+    g = run_gpu(lib, sess, x_t, u_h, traj=True, candidates=dev)
+    sess.close()
+    o = omp.tick(env.K32, "bot", x_t, u_h, cand, 30, env.spec, record=True)
+    compare(g, o, env, 30)
+
+
+# ------------------------------------------------------------------ balance bot
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_bot_single_tick_paper_scale(lib, ctx, bot, lanes):
+    """N = 1024, H = 20 from x_t = (0.1, 0, 0, 0), one user input from the seed."""
+    env, model = bot
+    u_h = data.to_f32_exact(data.user_input_once(1, env.lo, env.hi))
+    g, o = _tick(lib, ctx, env, model, np.array([0.1, 0, 0, 0]), u_h, 1024, 20, lanes=lanes)
+    compare(g, o, env, 20)
+    assert g["result"]["index"] == o.index
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+@pytest.mark.parametrize("N", [1, 31, 1000, 3001])
+def test_bot_states_ragged(lib, ctx, bot, lanes, N):
+    env, model = bot
+    states = data.states_in_box(11, 6, [-0.45, -1.5, -1.8, -1.5], [0.45, 1.5, 1.8, 1.5])
+    excused = 0
+    for k, x_t in enumerate(states):
+        u_h = data.to_f32_exact(data.user_input_once(100 + k, env.lo, env.hi))
+        g, o = _tick(lib, ctx, env, model, x_t, u_h, N, 50, seed=k, tick=k, lanes=lanes)
+        excused += compare(g, o, env, 50)
+    assert excused <= max(2, 0.002 * N * len(states))
+
+
+def test_bot_full_size(lib, ctx, bot):
+    """N = 16384, H = 50 in the launch configuration the benchmark uses."""
+    env, model = bot
+    for k, x_t in enumerate([np.array([0.05, 0.0, 0.0, 0.0]), np.array([0.3, 0.9, 1.2, 0.6])]):
+        u_h = data.to_f32_exact(data.user_input_once(200 + k, env.lo, env.hi))
+        g, o = _tick(lib, ctx, env, model, x_t, u_h, 16384, 50, seed=2, tick=k)
+        assert compare(g, o, env, 50) <= 0.002 * 16385
+
+
+def test_bot_inflated_barrier(lib, ctx):
+    import paper_1906_02318_gb300.mpmi as lib_
+    env = bot_env(inflation=0.1)
+    c = lib_.Context(0)
+    model = gpu_model(lib_, c, env)
+    x_t = np.array([0.2, 0.5, 1.0, 0.3])
+    g, o = _tick(lib_, c, env, model, x_t, [0.25], 4096, 40)
+    compare(g, o, env, 40)
+    model.free()
+
+
+# ------------------------------------------------------------------- race car
+@pytest.mark.parametrize("lanes", [8, 16])
+def test_car_ticks(lib, ctx, car, lanes):
+    env, model = car
+    x0 = data.car_start_state(env.track, vx=14.0)
+    states = [x0, x0 + np.array([1.5, -1.0, 0.1, 4.0, 0.3, 0.2]),
+              x0 + np.array([-2.0, 2.5, -0.2, -6.0, -0.2, -0.1])]
+    for k, x_t in enumerate(states):
+        u_h = data.to_f32_exact(data.user_input_once(300 + k, env.lo, env.hi))
+        g, o = _tick(lib, ctx, env, model, x_t, u_h, 2047, 60, seed=3, tick=k, lanes=lanes)
+        assert compare(g, o, env, 60) <= 10
+
+
+@pytest.mark.slow
+def test_car_full_size(lib, ctx, car):
+    """N = 16384, H = 60 in the default launch configuration."""
+    env, model = car
+    x_t = data.car_start_state(env.track, vx=12.0)
+    u_h = data.to_f32_exact(data.user_input_once(3, env.lo, env.hi))
+    g, o = _tick(lib, ctx, env, model, x_t, u_h, 16384, 60, seed=3)
+    assert compare(g, o, env, 60) <= 0.002 * 16385
+
+
+# ------------------------------------------------------------ closed forms on GPU
+def test_drift_model_closed_form(lib, ctx):
+    """x' = x + dt u (linear basis n = 2): ttv has a closed form per candidate."""
+    dt, H, x0 = 0.05, 40, 0.3137
+    K = np.array([[1.0, dt], [0.0, 1.0]])
+    m = lib.model_from_operator(ctx, "linear", K, nx=1, nu=1)
+    lib.set_safety_set(m, [-1.0], [1.0])
+    sess = lib.Session(ctx, m, 5000, H, [-1.0], [1.0], seed=9)
+    g = run_gpu(lib, sess, [x0], [0.9])
+    sess.close()
+    cand = omp.candidate_slots([0.9], osamp.uniform_samples(9, 0, 0, 5000, [-1], [1]), True)
+    K32 = np.float32(K).astype(np.float64)
+    want = []
+    for c in cand[:, 0]:
+        # exit step of x0 + t*dt*c in float64 with the float32 operator
+        t_exit = None
+        x = x0
+        for t in range(1, H + 1):
+            x = K32[0, 0] * x + K32[0, 1] * c
+            if not (-1.0 < x < 1.0):
+                t_exit = t
+                break
+        want.append(H if t_exit is None else t_exit - 1)
+    want = np.array(want)
+    close = np.abs(np.abs(x0 + np.arange(1, H + 1)[None, :] * dt * cand) - 1.0).min(axis=1) < 1e-5
+    assert np.all((g["ttv"] == want) | close)
+    m.free()
+
+
+def test_identity_model_stays_constant(lib, ctx):
+    import torch
+    K = np.eye(5)
+    m = lib.model_from_operator(ctx, "linear", K, nx=4, nu=1)
+    lib.set_safety_set(m, [-1.0, -1, -1, -1], [1.0, 1, 1, 1])
+    sess = lib.Session(ctx, m, 300, 511, [-1.0], [1.0], seed=4)
+    x_t = np.array([0.5, -0.25, 0.125, 0.0])
+    g = run_gpu(lib, sess, x_t, [0.0], traj=True)
+    sess.close()
+    assert np.all(g["ttv"] == 511) and g["result"]["status"] == lib.SAFE
+    z0 = g["traj"][:, :1, :]
+    assert np.array_equal(g["traj"], np.broadcast_to(z0, g["traj"].shape))
+    assert g["result"]["index"] == 0 and g["result"]["u_r"][0] == 0.0
+    m.free()
+
+
+def test_eq2_grid_bound_on_gpu(lib, ctx):
+    """Sec. IV-D, Eq. 2: with the grid and every candidate safe, the deviation
+    from u_h is at most lambda / (2N) (M = 1)."""
+    m = lib.model_from_operator(ctx, "linear", np.eye(2), nx=1, nu=1)
+    lib.set_safety_set(m, [-np.inf], [np.inf])
+    N = 10000
+    sess = lib.Session(ctx, m, N, 3, [-1.0], [1.0], include_user=False, sampler="grid")
+    worst = 0.0
+    for k, u in enumerate(np.concatenate([np.random.default_rng(0).uniform(-1, 1, 30),
+                                          [-1.0, 1.0]])):
+        lib.evaluate_candidates(sess, [0.0], [u], tick=k)
+        r = lib.select_input(sess)
+        assert r["status"] == lib.SAFE and r["n_safe"] == N
+        worst = max(worst, abs(r["u_r"][0] - u))
+    sess.close()
+    assert worst <= 2.0 / (2 * N) * (1 + 1e-6) + 2 ** -24
+    assert worst >= 2.0 / (2 * N) * (1 - 1e-3)
+    m.free()
+
+
+# ------------------------------------------------------------------ edge cases
+def test_only_user_slot(lib, ctx, bot):
+    env, model = bot
+    g, o = _tick(lib, ctx, env, model, np.array([0.1, 0, 0, 0]), [0.25], 0, 20)
+    compare(g, o, env, 20)
+    assert g["result"]["index"] == 0 and g["result"]["n_slots"] == 1
+
+
+def test_single_step_horizon_and_no_user_slot(lib, ctx, bot):
+    env, model = bot
+    x_t = np.array([0.49, 0.5, 1.99, 0.5])
+    g, o = _tick(lib, ctx, env, model, x_t, [0.5], 999, 1, include_user=False)
+    compare(g, o, env, 1, include_user=False)
+
+
+def test_all_unsafe_falls_back(lib, ctx, bot):
+    env, model = bot
+    x_t = np.array([0.7, 2.0, 0.0, 0.0])   # already past the barrier: every step fails
+    g, o = _tick(lib, ctx, env, model, x_t, [0.5], 2048, 30)
+    compare(g, o, env, 30)
+    r = g["result"]
+    assert r["status"] == lib.FALLBACK and r["n_safe"] == 0
+    assert o.status == omp.FALLBACK
+
+
+def test_safe_user_input_passes_through(lib, ctx, bot):
+    env, model = bot
+    sess = lib.Session(ctx, model, 4096, 20, env.lo, env.hi)
+    u_h = 0.0123456789012345
+    lib.evaluate_candidates(sess, [0.0, 0.0, 0.0, 0.0], [u_h])
+    r = lib.select_input(sess)
+    sess.close()
+    assert r["index"] == 0 and r["status"] == lib.SAFE and r["u_r"][0] == u_h
+
+
+def test_nonfinite_inputs(lib, ctx, bot):
+    import torch
+    env, model = bot
+    sess = lib.Session(ctx, model, 512, 20, env.lo, env.hi)
+    with pytest.raises(lib.MpmiError) as e:
+        lib.evaluate_candidates(sess, [np.nan, 0, 0, 0], [0.0])
+    assert e.value.code == -3
+    with pytest.raises(lib.MpmiError) as e:
+        lib.select_input(sess)
+    assert e.value.code == -5
+    # the device path treats NaN as unsafe: every candidate fails at step 1
+    g = run_gpu(lib, sess, [np.nan, 0, 0, 0], [0.0])
+    sess.close()
+    assert np.all(g["ttv"] == 0) and g["result"]["status"] == lib.FALLBACK
+    assert g["result"]["index"] == 0 and g["result"]["n_safe"] == 0
+
+
+def test_host_and_device_paths_agree_and_repeat(lib, ctx, bot):
+    env, model = bot
+    sess = lib.Session(ctx, model, 8192, 50, env.lo, env.hi, seed=12)
+    x_t, u_h = np.array([0.2, -0.3, 0.4, 0.1]), np.array([-0.625])
+    outs = []
+    for _ in range(3):
+        lib.evaluate_candidates(sess, x_t, u_h, tick=77)
+        outs.append(lib.select_input(sess))
+    g = run_gpu(lib, sess, x_t, u_h, tick=77, traj=False)
+    sess.close()
+    for r in outs[1:] + [g["result"]]:
+        for k in ("index", "status", "n_safe", "ttv", "executed_steps"):
+            assert r[k] == outs[0][k]
+        assert np.array_equal(r["u_r"], outs[0]["u_r"])
+
+
+def test_session_argument_checks(lib, ctx, bot):
+    env, model = bot
+    bad = [dict(n_samples=-1, horizon=10), dict(n_samples=10, horizon=0),
+           dict(n_samples=10, horizon=512), dict(n_samples=0, horizon=5, include_user=False),
+           dict(n_samples=10, horizon=5, lanes=3), dict(n_samples=10, horizon=5, block=100),
+           dict(n_samples=10, horizon=5, sampler="grid", input_lo=[-1.0, -1.0])]
+    for kw in bad:
+        kw = dict(kw)
+        lo = kw.pop("input_lo", env.lo)
+        with pytest.raises(lib.MpmiError):
+            lib.Session(ctx, model, kw.pop("n_samples"), kw.pop("horizon"), lo, env.hi, **kw)
+
+
+def test_memory_budget_admission(lib):
+    env = bot_env()
+    small = lib.Context(0, mem_budget=2048)
+    model = gpu_model(lib, small, env)
+    s1 = lib.Session(small, model, 100, 10, env.lo, env.hi)
+    with pytest.raises(lib.MpmiError) as e:
+        for _ in range(20):
+            lib.Session(small, model, 100, 10, env.lo, env.hi)
+    assert e.value.code == -2
+    s1.close()
+
+
+def test_fit_model_on_device_matches_host_fit(lib, ctx):
+    x, u, xn = data.transitions("bot", 1, 5000)
+    m, res = lib.fit_model(ctx, "bot", x, u, xn)
+    K_host, res_host = lib.fit_operator("bot", x, u, xn)
+    assert np.array_equal(m.get_operator(), K_host) and res == res_host
+    m.free()
+
+
+# ------------------------------------------------------------- closed loop
+def test_bot_closed_loop_matches_oracle(lib, ctx, bot):
+    """Receding horizon (Sec. IV-C): each side drives its own plant copy from the
+    same start with the same user input; the applied inputs agree tick by tick."""
+    env, model = bot
+    ticks, N, H = 150, 2048, 50
+    u_seq = data.to_f32_exact(data.ou_user_input(2, ticks, plants.BOT_DT, env.lo, env.hi))
+    sess = lib.Session(ctx, model, N, H, env.lo, env.hi, seed=2)
+    x = np.array([0.05, 0.0, 0.0, 0.0])
+    gpu_u = []
+    for t in range(ticks):
+        lib.evaluate_candidates(sess, x, u_seq[t], tick=t)
+        r = lib.select_input(sess)
+        gpu_u.append(r["u_r"].copy())
+        x = plants.cartpole_step(x, r["u_r"])
+    sess.close()
+    recs = omp.closed_loop(env.K32, "bot", env.spec, plants.cartpole_step,
+                           [0.05, 0.0, 0.0, 0.0], u_seq,
+                           lambda t: osamp.uniform_samples(2, 0, t, N, env.lo, env.hi), H)
+    agree = 0
+    for t, (_, _, o) in enumerate(recs):
+        if not np.array_equal(gpu_u[t], o.u_r):
+            break
+        agree += 1
+    assert agree >= ticks * 0.9, f"closed loops diverged at tick {agree}"

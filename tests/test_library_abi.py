@@ -1,0 +1,99 @@
+"""The C-ABI library builds, loads and exports every symbol include/mpmi.h
+declares; its host-only fit agrees with the oracle (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import fit as ofit
+from workloads import data, plants
+
+
+@pytest.fixture(scope="module")
+def lib(repo_root):
+    from paper_1906_02318_gb300 import build, mpmi
+    build.build()
+    return mpmi
+
+
+def _declared_functions(repo_root):
+    text = open(os.path.join(repo_root, "include", "mpmi.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpmi_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib, repo_root):
+    names = _declared_functions(repo_root)
+    assert len(names) >= 18
+    so = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+    # the binding wraps every declared entry point
+    assert set(names) <= set(lib._SIGNATURES)
+
+
+def test_struct_layouts_match_header(lib):
+    assert ctypes.sizeof(lib.Result) == 80
+    assert ctypes.sizeof(lib.SafetySpecC) == 168
+    assert ctypes.sizeof(lib.SessionConfig) == 104
+    assert lib.load().mpmi_version().decode().startswith("mpmi-gb300")
+
+
+@pytest.mark.parametrize("kind,seed,m", [("bot", 1, 5000), ("car", 3, 20000)])
+def test_host_fit_matches_oracle(lib, kind, seed, m):
+    x, u, xn = data.transitions(kind, seed, m)
+    K, res = lib.fit_operator(kind, x, u, xn)
+    Ko, reso = ofit.fit_koopman(kind, x, u, xn)
+    scale = np.abs(Ko).max()
+    assert np.abs(K - Ko).max() <= 1e-9 * scale
+    assert abs(res - reso) <= 1e-9
+    held = (4, 11) if kind == "bot" else (6, 7, 30, 31)
+    for r in held:
+        assert np.abs(K[r] - np.eye(K.shape[0])[r]).max() < 1e-12
+
+
+def test_host_fit_linear_closed_form(lib):
+    rng = np.random.default_rng(0)
+    A = np.eye(4) + 0.1 * rng.standard_normal((4, 4))
+    B = rng.standard_normal((4, 1))
+    x = rng.standard_normal((300, 4))
+    u = rng.uniform(-1, 1, (300, 1))
+    K, res = lib.fit_operator("linear", x, u, plants.linear_step(A, B, x, u), nx=4, nu=1)
+    want = np.block([[A, B], [np.zeros((1, 4)), np.eye(1)]])
+    assert np.abs(K - want).max() < 1e-10 and res < 1e-12
+
+
+def test_host_fit_errors(lib):
+    x, u, xn = data.transitions("bot", 1, 50)
+    with pytest.raises(lib.MpmiError) as e:
+        lib.fit_operator("bot", x[:5], u[:5], xn[:5])
+    assert e.value.code == -1
+    x2 = x.copy()
+    x2[3, 1] = np.nan
+    with pytest.raises(lib.MpmiError) as e:
+        lib.fit_operator("bot", x2, u, xn)
+    assert e.value.code == -3
+    with pytest.raises(lib.MpmiError) as e:
+        lib.fit_operator("linear", x[:, :3], u, xn[:, :3], nx=3, nu=1)
+    assert e.value.code == -6
+    # rank deficient: a constant state makes several features collinear
+    xc = np.zeros((50, 4))
+    with pytest.raises(lib.MpmiError) as e:
+        lib.fit_operator("bot", xc, u, xc)
+    assert e.value.code == -1
+
+
+def test_context_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lib.MpmiError) as e:
+        lib.Context(0)
+    assert e.value.code in (-1, -4)
+
+
+def test_missing_library_raises(lib, tmp_path):
+    with pytest.raises(RuntimeError):
+        lib.load(str(tmp_path / "nope.so"))
