@@ -74,6 +74,61 @@ def measured_peaks() -> dict:
 
 
 # ---- clocks during the timed region ----------------------------------------
+class NvmlClocks:
+    """Polls the SM clock and the clock-event reasons through NVML (read-only)
+    every ~2 ms from a background thread."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, uuid: str):
+        import ctypes
+        self.ct = ctypes
+        self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.nv.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("nvmlDeviceGetHandleByUUID failed")
+        self.samples: list[tuple[int, int]] = []
+        self.stop_flag = False
+        self.thread = None
+
+    def _one(self):
+        c = self.ct.c_uint()
+        r = self.ct.c_ulonglong()
+        self.nv.nvmlDeviceGetClockInfo(self.h, 1, self.ct.byref(c))
+        fn = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        fn(self.h, self.ct.byref(r))
+        return c.value, r.value
+
+    def _loop(self):
+        while not self.stop_flag:
+            self.samples.append(self._one())
+            time.sleep(0.002)
+
+    def start(self):
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+
+    def stop(self) -> dict | None:
+        self.stop_flag = True
+        if self.thread:
+            self.thread.join(timeout=2)
+        m = self.ct.c_uint()
+        self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, self.ct.byref(m))
+        if not self.samples:
+            return None
+        reasons = set()
+        for _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median([c for c, _ in self.samples]),
+                "sm_max_mhz": m.value, "reasons": sorted(reasons),
+                "samples": len(self.samples), "source": "nvml"}
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -214,14 +269,15 @@ def run_gpu(args, rank, world):
         gpu_id = f"GPU-{props.uuid}"
     except Exception:
         pass
-    clocks = ClockSampler(gpu_id)
-    clocks.start()
 
-    # closed loop through the host C-ABI (e2e): W warm-up ticks, then timed ticks
+    # closed loop through the host C-ABI (e2e): W warm-up ticks, then timed ticks.
+    # As in the paper's trials, a trial ends when the plant leaves the safe set
+    # and the next one starts from x_0.
     x_t = X0.copy()
     states = np.empty((ticks, 4))
     lat = []
     n_fallback = 0
+    trials = 1
     for t in range(ticks):
         states[t] = x_t
         t0 = time.perf_counter()
@@ -232,8 +288,11 @@ def run_gpu(args, rank, world):
             lat.append(dt)
         n_fallback += r["status"] == lib.FALLBACK
         x_t = plants.cartpole_step(x_t, r["u_r"])
-        if not np.all(np.isfinite(x_t)):
+        inside = np.all(np.isfinite(x_t)) and np.all(x_t > data.BOT_SAFE_LO) and \
+            np.all(x_t < data.BOT_SAFE_HI)
+        if not inside:
             x_t = X0.copy()
+            trials += 1
     lat = np.array(lat)
     e2e_rate = n_slots * HORIZON * len(lat) / lat.sum()
 
@@ -254,6 +313,11 @@ def run_gpu(args, rank, world):
         flush.zero_()
         tick(i)
     torch.cuda.synchronize()
+    try:
+        clocks = NvmlClocks(gpu_id)
+    except Exception:
+        clocks = ClockSampler(gpu_id)
+    clocks.start()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -289,7 +353,8 @@ def run_gpu(args, rank, world):
     model.free()
     return dict(dev_time=dev_time, durs=durs, executed=executed, lat=lat, e2e_rate=e2e_rate,
                 wall=wall, clocks=clk, lanes=lanes, block=block, n_slots=n_slots,
-                residual=residual, n_fallback=int(n_fallback), sm_count=props.multi_processor_count,
+                residual=residual, n_fallback=int(n_fallback), trials=trials,
+                sm_count=props.multi_processor_count,
                 gpu_name=props.name)
 
 
@@ -370,7 +435,7 @@ def main():
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                      "peak_basis": f"{out['sm_count']} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
         "clocks": out["clocks"],
-        "fallback_ticks": out["n_fallback"],
+        "fallback_ticks": out["n_fallback"], "trials": out["trials"],
     }
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args)

@@ -3,9 +3,9 @@
 // Every feature of Psi(x, u) used here is a(x) + sum_k p_k(u) b_k(x): a state
 // part plus input monomials p_k times state coefficients.  Because the input is
 // held over the horizon (Sec. VII-B), a tick lifts all N candidates of the same
-// x_t, so a(x_t) and b_k(x_t) are computed once per tick (float64) and each
-// candidate needs only P fused multiply-adds per feature.  The host fit uses the
-// same definition to lift the training transitions.
+// x_t: the state parts need one sine/cosine per tick and each candidate adds P
+// products per feature.  The host fit (float64) and the tick kernel (float32)
+// use this one definition.
 //
 //   balance bot (n = 12, P = 1, p = {u}):
 //     theta, theta_dot, x, x_dot, u, sin th, cos th, thd^2, thd u,
@@ -59,45 +59,48 @@ struct BasisTraits<kLin41> {
 
 constexpr int kMaxP = 3;
 
-// Split coefficients of feature j at state x: *a and b[0..P).
-MPMI_HD void feature_split(int kind, int j, const double* x, double* a, double* b) {
-  for (int k = 0; k < kMaxP; ++k) b[k] = 0.0;
-  *a = 0.0;
+// Split coefficients of feature j at state x: *a and b[0..P).  s, c are the
+// sine and cosine of the basis angle (bot: theta = x[0]; car: psi = x[2]),
+// computed once by the caller.  T is double on the host fit, float per tick.
+template <class T>
+MPMI_HD void feature_split(int kind, int j, const T* x, T s, T c, T* a, T* b) {
+  for (int k = 0; k < kMaxP; ++k) b[k] = T(0);
+  *a = T(0);
   if (kind == kBot) {
-    const double th = x[0], thd = x[1];
+    const T thd = x[1];
     switch (j) {
-      case 0: *a = th; break;
+      case 0: *a = x[0]; break;
       case 1: *a = thd; break;
       case 2: *a = x[2]; break;
       case 3: *a = x[3]; break;
-      case 4: b[0] = 1.0; break;
-      case 5: *a = sin(th); break;
-      case 6: *a = cos(th); break;
+      case 4: b[0] = T(1); break;
+      case 5: *a = s; break;
+      case 6: *a = c; break;
       case 7: *a = thd * thd; break;
       case 8: b[0] = thd; break;
-      case 9: *a = thd * thd * sin(th); break;
-      case 10: b[0] = cos(th); break;
-      default: *a = 1.0; break;  // 11
+      case 9: *a = thd * thd * s; break;
+      case 10: b[0] = c; break;
+      default: *a = T(1); break;  // 11
     }
     return;
   }
   if (kind == kCar) {
-    const double psi = x[2], vx = x[3], vy = x[4], om = x[5];
+    const T vx = x[3], vy = x[4], om = x[5];
     switch (j) {
       case 0: *a = x[0]; break;
       case 1: *a = x[1]; break;
-      case 2: *a = psi; break;
+      case 2: *a = x[2]; break;
       case 3: *a = vx; break;
       case 4: *a = vy; break;
       case 5: *a = om; break;
-      case 6: b[0] = 1.0; break;
-      case 7: b[1] = 1.0; break;
-      case 8: *a = sin(psi); break;
-      case 9: *a = cos(psi); break;
-      case 10: *a = vx * cos(psi); break;
-      case 11: *a = vx * sin(psi); break;
-      case 12: *a = vy * cos(psi); break;
-      case 13: *a = vy * sin(psi); break;
+      case 6: b[0] = T(1); break;
+      case 7: b[1] = T(1); break;
+      case 8: *a = s; break;
+      case 9: *a = c; break;
+      case 10: *a = vx * c; break;
+      case 11: *a = vx * s; break;
+      case 12: *a = vy * c; break;
+      case 13: *a = vy * s; break;
       case 14: *a = om * vx; break;
       case 15: *a = om * vy; break;
       case 16: *a = vx * vx; break;
@@ -107,15 +110,15 @@ MPMI_HD void feature_split(int kind, int j, const double* x, double* a, double* 
       case 20: b[0] = vy; break;
       case 21: b[0] = om; break;
       case 22: b[1] = vx; break;
-      case 23: b[0] = cos(psi); break;
-      case 24: b[0] = sin(psi); break;
-      case 25: b[1] = cos(psi); break;
-      case 26: b[1] = sin(psi); break;
-      case 27: *a = om * cos(psi); break;
-      case 28: *a = om * sin(psi); break;
+      case 23: b[0] = c; break;
+      case 24: b[0] = s; break;
+      case 25: b[1] = c; break;
+      case 26: b[1] = s; break;
+      case 27: *a = om * c; break;
+      case 28: *a = om * s; break;
       case 29: *a = vx * vy; break;
-      case 30: b[2] = 1.0; break;
-      default: *a = 1.0; break;  // 31
+      case 30: b[2] = T(1); break;
+      default: *a = T(1); break;  // 31
     }
     return;
   }
@@ -124,9 +127,12 @@ MPMI_HD void feature_split(int kind, int j, const double* x, double* a, double* 
   if (j < nx) {
     *a = x[j];
   } else {
-    b[j - nx] = 1.0;
+    b[j - nx] = T(1);
   }
 }
+
+// Index of the state coordinate whose sine/cosine the basis uses (-1: none).
+MPMI_HD int angle_index(int kind) { return kind == kBot ? 0 : (kind == kCar ? 2 : -1); }
 
 // Input monomials p_k(u) in float64 (host fit).
 MPMI_HD void monomials64(int kind, const double* u, double* p) {

@@ -17,9 +17,11 @@ namespace mpmi {
 static void lift_row(int kind, int n, const double* x, const double* u, double* out) {
   double p[kMaxP] = {0, 0, 0};
   monomials64(kind, u, p);
+  const int ai = angle_index(kind);
+  const double s = ai >= 0 ? sin(x[ai]) : 0.0, c = ai >= 0 ? cos(x[ai]) : 0.0;
   for (int j = 0; j < n; ++j) {
     double a, b[kMaxP];
-    feature_split(kind, j, x, &a, b);
+    feature_split<double>(kind, j, x, s, c, &a, b);
     double v = a;
     for (int k = 0; k < kMaxP; ++k)
       if (b[k] != 0.0) v += p[k] * b[k];

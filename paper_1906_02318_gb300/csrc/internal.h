@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mpmi.h"
+#include "mpmi.h"
 #include "basis.h"
 
 namespace mpmi {
@@ -15,15 +15,16 @@ namespace mpmi {
 // Track grid cell word: bits 0-1 class, bits 2-23 list offset, bits 24-31 count.
 enum CellClass : uint32_t { kCellOutside = 0, kCellInside = 1, kCellBoundary = 2 };
 
+// Track grid staged into shared memory by every block: one blob of 16-byte
+// aligned sections  cells (u32) | segment lists (u16) | segments (float4
+// ax, ay, dx, dy) | 1/|d|^2 (float).
 struct DevTrack {
-  const uint32_t* cells;  // gny * gnx cell words
-  const uint16_t* list;   // segment indices of boundary cells, nearest first
-  const float4* seg;      // (ax, ay, dx, dy) per segment
-  const float* seg_inv;   // 1 / |d|^2 per segment (0 for a degenerate segment)
+  const uint4* blob;      // device copy of the blob
+  int blob_bytes;         // multiple of 16
+  int off_list, off_seg, off_inv;  // byte offsets of the sections
   float gx0, gy0, inv_h;  // grid origin and 1 / cell size
   int gnx, gny;
   float w2;               // (half width - inflation)^2
-  int xi, yi;             // state coordinates of the position
 };
 
 struct DevSafety {
@@ -36,11 +37,10 @@ struct DevSafety {
 // Per-session reduction slots the tick kernel accumulates into.  The block that
 // finishes last decodes them into the result and resets them for the next tick.
 struct TickScratch {
-  unsigned long long key;       // min over candidates of the selection key
-  unsigned long long executed;  // sum of prediction steps taken
-  unsigned int n_safe;
-  unsigned int done;            // blocks finished
-  unsigned int pad[2];
+  unsigned long long key;     // min over candidates of the selection key
+  unsigned long long counts;  // (n_safe << 40) + executed prediction steps
+  unsigned int done;          // blocks finished
+  unsigned int pad[3];
 };
 
 struct TickArgs {
@@ -82,11 +82,8 @@ struct mpmi_model {
   mpmi_safety_spec spec{};
   std::vector<double> track_host;
   mpmi::DevSafety dev_safety{};
-  // device buffers of the track grid
-  uint32_t* cells_dev = nullptr;
-  uint16_t* list_dev = nullptr;
-  float4* seg_dev = nullptr;
-  float* seg_inv_dev = nullptr;
+  uint4* track_dev = nullptr;  // packed track grid (see DevTrack)
+  uint64_t track_bytes = 0;
   uint64_t bytes = 0;
 };
 
@@ -95,6 +92,8 @@ struct mpmi_session {
   const mpmi_model* model = nullptr;
   mpmi_session_config cfg{};
   int n_slots = 0, lanes = 1, block = 128, grid_g = 0;
+  int max_grid[2] = {0, 0};  // resident blocks on the device (plain, trajectories)
+  size_t grid_smem[2] = {0, 0};  // dynamic shared memory max_grid was computed for
   mpmi::TickScratch* scratch_dev = nullptr;
   mpmi_result* result_dev = nullptr;
   double* in_dev = nullptr;        // x_t (8 doubles) then u_h (4 doubles)
@@ -114,11 +113,13 @@ int fit_householder(int kind, const double* x, const double* u, const double* xn
 struct TrackGrid {
   std::vector<uint32_t> cells;
   std::vector<uint16_t> list;
-  std::vector<float> seg;      // 4 per segment
-  std::vector<float> seg_inv;  // 1 per segment
   double gx0 = 0, gy0 = 0, h = 1;
   int gnx = 0, gny = 0;
+  // packed blob (16-byte aligned sections) and its section offsets
+  std::vector<uint8_t> blob;
+  int off_list = 0, off_seg = 0, off_inv = 0;
 };
+constexpr int kMaxTrackBytes = 96 * 1024;  // shared-memory budget of the grid
 int build_track_grid(const double* xy, int n, double half_width, TrackGrid* g,
                      std::string* err);
 }  // namespace mpmi

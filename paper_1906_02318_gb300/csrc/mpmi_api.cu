@@ -58,29 +58,40 @@ static bool budget_ok(mpmi_ctx* ctx, uint64_t bytes) {
 }
 
 // ---- kernel dispatch -------------------------------------------------------
-using TickLaunch = void (*)(const TickArgs&, int, int, cudaStream_t);
+struct TickKernel {
+  const void* fn = nullptr;
+  void (*launch)(const TickArgs&, int, int, size_t, cudaStream_t) = nullptr;
+};
 
 template <int KIND, int L, bool TRAJ>
-static void launch_tick(const TickArgs& a, int grid, int block, cudaStream_t st) {
-  tick_kernel<KIND, L, TRAJ><<<grid, block, 0, st>>>(a);
+static void launch_tick(const TickArgs& a, int grid, int block, size_t smem, cudaStream_t st) {
+  tick_kernel<KIND, L, TRAJ><<<grid, block, smem, st>>>(a);
+}
+
+template <int KIND, int L, bool TRAJ>
+static TickKernel make_kernel() {
+  TickKernel k;
+  k.fn = reinterpret_cast<const void*>(&tick_kernel<KIND, L, TRAJ>);
+  k.launch = &launch_tick<KIND, L, TRAJ>;
+  return k;
 }
 
 template <int KIND, bool TRAJ>
-static TickLaunch pick_lanes(int lanes) {
+static TickKernel pick_lanes(int lanes) {
   if constexpr (KIND == kBot) {
-    if (lanes == 1) return launch_tick<KIND, 1, TRAJ>;
-    if (lanes == 2) return launch_tick<KIND, 2, TRAJ>;
-    if (lanes == 4) return launch_tick<KIND, 4, TRAJ>;
+    if (lanes == 1) return make_kernel<KIND, 1, TRAJ>();
+    if (lanes == 2) return make_kernel<KIND, 2, TRAJ>();
+    if (lanes == 4) return make_kernel<KIND, 4, TRAJ>();
   } else if constexpr (KIND == kCar) {
-    if (lanes == 8) return launch_tick<KIND, 8, TRAJ>;
-    if (lanes == 16) return launch_tick<KIND, 16, TRAJ>;
+    if (lanes == 8) return make_kernel<KIND, 8, TRAJ>();
+    if (lanes == 16) return make_kernel<KIND, 16, TRAJ>();
   } else {
-    if (lanes == 1) return launch_tick<KIND, 1, TRAJ>;
+    if (lanes == 1) return make_kernel<KIND, 1, TRAJ>();
   }
-  return nullptr;
+  return TickKernel{};
 }
 
-static TickLaunch pick_tick(int kind, int lanes, bool traj) {
+static TickKernel pick_tick(int kind, int lanes, bool traj) {
   switch (kind) {
     case kBot: return traj ? pick_lanes<kBot, true>(lanes) : pick_lanes<kBot, false>(lanes);
     case kCar: return traj ? pick_lanes<kCar, true>(lanes) : pick_lanes<kCar, false>(lanes);
@@ -88,7 +99,7 @@ static TickLaunch pick_tick(int kind, int lanes, bool traj) {
     case kLin22: return traj ? pick_lanes<kLin22, true>(lanes) : pick_lanes<kLin22, false>(lanes);
     case kLin41: return traj ? pick_lanes<kLin41, true>(lanes) : pick_lanes<kLin41, false>(lanes);
   }
-  return nullptr;
+  return TickKernel{};
 }
 
 static int default_lanes(int kind, int n_slots) {
@@ -126,12 +137,32 @@ static TickArgs make_args(const mpmi_session* s, uint64_t tick) {
   return a;
 }
 
+// Persistent grid: no more blocks than are resident at once, and no more than
+// the warp-tiles need.  Occupancy is cached per dynamic shared-memory size.
 static int launch(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st) {
-  TickLaunch fn = pick_tick(s->model->kind, s->lanes, traj);
-  if (!fn) return fail(MPMI_E_UNSUPPORTED, "tick kernel not compiled for this basis/lanes");
-  const int per_block = s->block / s->lanes;
-  const int grid = (s->n_slots + per_block - 1) / per_block;
-  fn(a, grid, s->block, st);
+  TickKernel k = pick_tick(s->model->kind, s->lanes, traj);
+  if (!k.fn) return fail(MPMI_E_UNSUPPORTED, "tick kernel not compiled for this basis/lanes");
+  const size_t smem = a.safety.has_track ? (size_t)a.safety.track.blob_bytes : 0;
+  const int t = traj ? 1 : 0;
+  if (s->max_grid[t] == 0 || s->grid_smem[t] != smem) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           kMaxTrackBytes);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    }
+    int nb = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.fn, s->block, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (nb < 1) return fail(MPMI_E_UNSUPPORTED, "tick kernel cannot be resident with this block");
+    s->max_grid[t] = nb * s->ctx->sm_count;
+    s->grid_smem[t] = smem;
+  }
+  const int wpb = s->block / 32;
+  const int per_warp = 32 / s->lanes;
+  const int n_wtiles = (s->n_slots + per_warp - 1) / per_warp;
+  int grid = (n_wtiles + wpb - 1) / wpb;
+  if (grid > s->max_grid[t]) grid = s->max_grid[t];
+  k.launch(a, grid, s->block, smem, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "tick kernel launch");
   return MPMI_OK;
@@ -156,15 +187,9 @@ static int grid_points(int n, int nu) {
 
 static void free_model_device(mpmi_model* m) {
   cudaFree(m->K32_dev);
-  cudaFree(m->cells_dev);
-  cudaFree(m->list_dev);
-  cudaFree(m->seg_dev);
-  cudaFree(m->seg_inv_dev);
+  cudaFree(m->track_dev);
   m->K32_dev = nullptr;
-  m->cells_dev = nullptr;
-  m->list_dev = nullptr;
-  m->seg_dev = nullptr;
-  m->seg_inv_dev = nullptr;
+  m->track_dev = nullptr;
 }
 
 static int model_upload(mpmi_ctx* ctx, mpmi_model* m) {
@@ -353,50 +378,36 @@ int mpmi_set_safety_set(mpmi_model* model, const mpmi_safety_spec* spec) {
   mpmi_ctx* ctx = model->ctx;
   DeviceGuard guard(ctx->device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
-  // release the previous track buffers
-  const uint64_t old_track = model->bytes - sizeof(float) * model->n * model->n;
-  cudaFree(model->cells_dev);
-  cudaFree(model->list_dev);
-  cudaFree(model->seg_dev);
-  cudaFree(model->seg_inv_dev);
-  model->cells_dev = nullptr;
-  model->list_dev = nullptr;
-  model->seg_dev = nullptr;
-  model->seg_inv_dev = nullptr;
-  model->bytes -= old_track;
-  ctx->used -= old_track;
+  // ticks in flight may still read the previous grid
+  MPMI_CUDA(cudaDeviceSynchronize(), "set_safety_set: waiting for ticks in flight");
+  cudaFree(model->track_dev);
+  model->track_dev = nullptr;
+  model->bytes -= model->track_bytes;
+  ctx->used -= model->track_bytes;
+  model->track_bytes = 0;
   if (has_track) {
-    const uint64_t b_cells = sizeof(uint32_t) * grid.cells.size();
-    const uint64_t b_list = sizeof(uint16_t) * grid.list.size();
-    const uint64_t b_seg = sizeof(float) * grid.seg.size();
-    const uint64_t b_inv = sizeof(float) * grid.seg_inv.size();
-    const uint64_t total = b_cells + b_list + b_seg + b_inv;
+    const uint64_t total = grid.blob.size();
     if (!budget_ok(ctx, total)) return fail(MPMI_E_OOM, "track grid exceeds the memory budget");
-    if (cudaMalloc(&model->cells_dev, b_cells) != cudaSuccess ||
-        cudaMalloc(&model->list_dev, b_list) != cudaSuccess ||
-        cudaMalloc(&model->seg_dev, b_seg) != cudaSuccess ||
-        cudaMalloc(&model->seg_inv_dev, b_inv) != cudaSuccess)
+    if (cudaMalloc(&model->track_dev, total) != cudaSuccess)
       return fail(MPMI_E_OOM, "cudaMalloc of the track grid failed");
-    MPMI_CUDA(cudaMemcpy(model->cells_dev, grid.cells.data(), b_cells, cudaMemcpyHostToDevice), "track");
-    MPMI_CUDA(cudaMemcpy(model->list_dev, grid.list.data(), b_list, cudaMemcpyHostToDevice), "track");
-    MPMI_CUDA(cudaMemcpy(model->seg_dev, grid.seg.data(), b_seg, cudaMemcpyHostToDevice), "track");
-    MPMI_CUDA(cudaMemcpy(model->seg_inv_dev, grid.seg_inv.data(), b_inv, cudaMemcpyHostToDevice), "track");
+    MPMI_CUDA(cudaMemcpy(model->track_dev, grid.blob.data(), total, cudaMemcpyHostToDevice),
+              "upload the track grid");
+    model->track_bytes = total;
     model->bytes += total;
     ctx->used += total;
     const double w = spec->track_half_width - spec->inflation;
     ds.has_track = 1;
-    ds.track.cells = model->cells_dev;
-    ds.track.list = model->list_dev;
-    ds.track.seg = model->seg_dev;
-    ds.track.seg_inv = model->seg_inv_dev;
+    ds.track.blob = model->track_dev;
+    ds.track.blob_bytes = (int)total;
+    ds.track.off_list = grid.off_list;
+    ds.track.off_seg = grid.off_seg;
+    ds.track.off_inv = grid.off_inv;
     ds.track.gx0 = (float)grid.gx0;
     ds.track.gy0 = (float)grid.gy0;
     ds.track.inv_h = (float)(1.0 / grid.h);
     ds.track.gnx = grid.gnx;
     ds.track.gny = grid.gny;
     ds.track.w2 = (float)(w * w);
-    ds.track.xi = 0;
-    ds.track.yi = 1;
     model->track_host.assign(spec->track_xy, spec->track_xy + 2 * spec->n_track);
   } else {
     model->track_host.clear();
@@ -439,7 +450,7 @@ int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model, const mpmi_session
   int block = cfg->block ? cfg->block : 128;
   if (block % 32 != 0 || block < 32 || block > kMaxBlock)
     return fail(MPMI_E_INVALID_ARG, "session_open: block must be a multiple of 32 in 32..256");
-  if (!pick_tick(model->kind, lanes, false))
+  if (!pick_tick(model->kind, lanes, false).fn)
     return fail(MPMI_E_UNSUPPORTED, "session_open: lanes per candidate not compiled for this basis");
   const uint64_t bytes = sizeof(TickScratch) + sizeof(mpmi_result) + 16 * sizeof(double);
   if (!budget_ok(ctx, bytes)) return fail(MPMI_E_OOM, "session exceeds the memory budget");

@@ -12,8 +12,9 @@
 // rows [qR, qR + R) of K in registers (R = n / L) and computes those rows of
 // K z; the group exchanges the new z through a per-warp shared-memory buffer
 // (double-buffered by step parity, one __syncwarp per step).  L = 1 keeps a
-// whole candidate in one thread.  L trades FFMA work per thread against
-// parallelism: at N ~ 16k one candidate per thread leaves most of the GPU idle.
+// whole candidate in one thread.  Warps are persistent: warp w of the grid takes
+// the warp-tiles (32 / L candidates each) w, w + W, w + 2W, ... so K is loaded
+// once per thread and the race-car track grid once per block.
 #pragma once
 
 #include <stdint.h>
@@ -83,28 +84,35 @@ __device__ __forceinline__ bool box_ok(const DevSafety& s, const float* z) {
   return ok;
 }
 
+// Shared-memory view of the staged track grid.
+struct TrackView {
+  const uint32_t* cells;
+  const uint16_t* list;
+  const float4* seg;
+  const float* inv;
+};
+
 // isSafe on the track part, shared by the L lanes of a group: lane q tests list
 // entries q, q + L, ... (nearest first, stops at the first hit); the group ORs.
 template <int L>
-__device__ __forceinline__ bool track_ok(const DevTrack& tr, float px, float py, int q,
-                                         bool active) {
+__device__ __forceinline__ bool track_ok(const DevTrack& tr, const TrackView& v, float px,
+                                         float py, int q, bool active) {
   bool ok = false;
   if (active) {
     const float fx = (px - tr.gx0) * tr.inv_h;
     const float fy = (py - tr.gy0) * tr.inv_h;
     if (fx >= 0.f && fx < (float)tr.gnx && fy >= 0.f && fy < (float)tr.gny) {
-      const uint32_t c = __ldg(&tr.cells[(int)fy * tr.gnx + (int)fx]);
+      const uint32_t c = v.cells[(int)fy * tr.gnx + (int)fx];
       const uint32_t cls = c & 3u;
       if (cls == kCellInside) {
         ok = true;
       } else if (cls == kCellBoundary) {
         const int off = (int)((c >> 2) & 0x3FFFFFu), cnt = (int)(c >> 24);
         for (int i = q; i < cnt; i += L) {
-          const int s = __ldg(&tr.list[off + i]);
-          const float4 sg = __ldg(&tr.seg[s]);
-          const float inv = __ldg(&tr.seg_inv[s]);
+          const int s = v.list[off + i];
+          const float4 sg = v.seg[s];
           const float rx = px - sg.x, ry = py - sg.y;
-          const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * inv, 0.f), 1.f);
+          const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * v.inv[s], 0.f), 1.f);
           const float ex = rx - t * sg.z, ey = ry - t * sg.w;
           if (ex * ex + ey * ey < tr.w2) {
             ok = true;
@@ -132,33 +140,39 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   constexpr int S = (N % 32 == 0) ? N + 4 : ((N % 4 == 0) ? N : N + (4 - N % 4));
   constexpr int NW = kMaxBlock / 32;
   constexpr int ACC = (R < 8) ? 2 : 1;  // split accumulators for ILP on short rows
+  constexpr int ANG = (KIND == kBot) ? 0 : ((KIND == kCar) ? 2 : -1);
 
-  __shared__ float s_a[N];
-  __shared__ float s_b[NP][N];
-  __shared__ float s_uh[NU];
+  extern __shared__ uint4 s_track[];
   __shared__ __align__(16) float s_x[(L > 1) ? NW : 1][2][GPW][S];
   __shared__ unsigned long long s_key[NW];
-  __shared__ unsigned int s_exec[NW];
-  __shared__ unsigned int s_nsafe[NW];
+  __shared__ unsigned long long s_cnt[NW];
   __shared__ int s_last;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int q = lane % L, g = lane / L;
+  const int H = a.horizon;
 
-  // per-tick part of the lifting (float64, one feature per lane of warp 0)
-  if (warp == 0) {
-    double x[NX];
-#pragma unroll
-    for (int j = 0; j < NX; ++j) x[j] = a.x_t[j];
-    for (int j = lane; j < N; j += 32) {
-      double av, bv[kMaxP];
-      feature_split(KIND, j, x, &av, bv);
-      s_a[j] = __double2float_rn(av);
-#pragma unroll
-      for (int k = 0; k < NP; ++k) s_b[k][j] = __double2float_rn(bv[k]);
+  // stage the track grid (race car) while the per-tick state is prepared
+  TrackView tv{nullptr, nullptr, nullptr, nullptr};
+  if constexpr (B::TRACK) {
+    if (a.safety.has_track) {
+      const int words = a.safety.track.blob_bytes >> 4;
+      for (int i = tid; i < words; i += blockDim.x) s_track[i] = __ldg(&a.safety.track.blob[i]);
+      const char* base = reinterpret_cast<const char*>(s_track);
+      tv.cells = reinterpret_cast<const uint32_t*>(base);
+      tv.list = reinterpret_cast<const uint16_t*>(base + a.safety.track.off_list);
+      tv.seg = reinterpret_cast<const float4*>(base + a.safety.track.off_seg);
+      tv.inv = reinterpret_cast<const float*>(base + a.safety.track.off_inv);
     }
-    if (lane < NU) s_uh[lane] = __double2float_rn(a.u_h[lane]);
   }
+  // per-tick state: x_t and u_h in float32, the basis angle's sine and cosine
+  float xs[NX], uh[NU];
+#pragma unroll
+  for (int j = 0; j < NX; ++j) xs[j] = __double2float_rn(a.x_t[j]);
+#pragma unroll
+  for (int j = 0; j < NU; ++j) uh[j] = __double2float_rn(a.u_h[j]);
+  float sn = 0.f, cs = 1.f;
+  if constexpr (ANG >= 0) sincosf(xs[ANG], &sn, &cs);
   // this lane's rows of K
   float kr[R][N];
 #pragma unroll
@@ -175,139 +189,143 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
       for (int k = 0; k < N; ++k) kr[r][k] = __ldg(row + k);
     }
   }
-  __syncthreads();
+  if constexpr (B::TRACK) __syncthreads();
 
-  const int per_block = blockDim.x / L;
-  const int slot = blockIdx.x * per_block + warp * GPW + g;
-  const bool valid = slot < a.n_slots;
-  const int H = a.horizon;
-
-  float xi[NU];
-  if (valid) {
-    candidate_value<NU>(a, slot, s_uh, xi);
-  } else {
-#pragma unroll
-    for (int j = 0; j < NU; ++j) xi[j] = s_uh[j];
-  }
-  float cost = 0.f;
-#pragma unroll
-  for (int j = 0; j < NU; ++j) {
-    const float d = __fsub_rn(xi[j], s_uh[j]);
-    cost = __fmaf_rn(d, d, cost);
-  }
-  float p[NP];
-  monomials32<KIND>(xi, p);
-  float z[N];
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    float v = s_a[j];
-#pragma unroll
-    for (int k = 0; k < NP; ++k) v = __fmaf_rn(p[k], s_b[k][j], v);
-    z[j] = v;
-  }
-  float* traj = nullptr;
-  if constexpr (TRAJ) {
-    if (valid && q == 0) {
-      traj = a.traj_out + (size_t)slot * (H + 1) * N;
-#pragma unroll
-      for (int j = 0; j < N; ++j) traj[j] = z[j];
-    }
-  }
-
-  int ttv = 0;
-  bool alive = valid;
-  for (int t = 1; t <= H; ++t) {
-    float zn[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      float acc[ACC];
-#pragma unroll
-      for (int c = 0; c < ACC; ++c) acc[c] = 0.f;
-#pragma unroll
-      for (int k = 0; k < N; ++k) acc[k % ACC] = __fmaf_rn(kr[r][k], z[k], acc[k % ACC]);
-      float v = acc[0];
-#pragma unroll
-      for (int c = 1; c < ACC; ++c) v += acc[c];
-      zn[r] = v;
-    }
-    if constexpr (L == 1) {
-#pragma unroll
-      for (int j = 0; j < N; ++j) z[j] = zn[j];
+  unsigned long long best = ~0ull;
+  unsigned int n_safe = 0, n_exec = 0;
+  const int wpb = blockDim.x >> 5;
+  const int n_wtiles = (a.n_slots + GPW - 1) / GPW;
+  for (int wt = blockIdx.x * wpb + warp; wt < n_wtiles; wt += gridDim.x * wpb) {
+    const int slot = wt * GPW + g;
+    const bool valid = slot < a.n_slots;
+    float xi[NU];
+    if (valid) {
+      candidate_value<NU>(a, slot, uh, xi);
     } else {
-      float* buf = &s_x[warp][t & 1][g][0];
-      if constexpr (R % 4 == 0) {
 #pragma unroll
-        for (int r = 0; r < R; r += 4)
-          *reinterpret_cast<float4*>(buf + q * R + r) =
-              make_float4(zn[r], zn[r + 1], zn[r + 2], zn[r + 3]);
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) buf[q * R + r] = zn[r];
-      }
-      __syncwarp();
-#pragma unroll
-      for (int k = 0; k < N; k += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(buf + k);
-        z[k] = v.x; z[k + 1] = v.y; z[k + 2] = v.z; z[k + 3] = v.w;
-      }
+      for (int j = 0; j < NU; ++j) xi[j] = uh[j];
     }
+    float cost = 0.f;
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+      const float d = __fsub_rn(xi[j], uh[j]);
+      cost = __fmaf_rn(d, d, cost);
+    }
+    // lift: z_0 = a(x_t) + sum_k p_k(xi) b_k(x_t)
+    float p[NP];
+    monomials32<KIND>(xi, p);
+    float z[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float av, bv[kMaxP];
+      feature_split<float>(KIND, j, xs, sn, cs, &av, bv);
+#pragma unroll
+      for (int k = 0; k < NP; ++k) av = __fmaf_rn(p[k], bv[k], av);
+      z[j] = av;
+    }
+    float* traj = nullptr;
     if constexpr (TRAJ) {
-      if (traj != nullptr && alive) {
+      if (valid && q == 0) {
+        traj = a.traj_out + (size_t)slot * (H + 1) * N;
 #pragma unroll
-        for (int j = 0; j < N; ++j) traj[(size_t)t * N + j] = z[j];
+        for (int j = 0; j < N; ++j) traj[j] = z[j];
       }
     }
-    bool ok = box_ok<NX>(a.safety, z);
-    if constexpr (B::TRACK) {
-      if (a.safety.has_track) {  // uniform over the grid
-        const bool on_road = track_ok<L>(a.safety.track, z[0], z[1], q, alive && ok);
-        ok = ok && on_road;
+
+    int ttv = 0;
+    bool alive = valid;
+    for (int t = 1; t <= H; ++t) {
+      float zn[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float acc[ACC];
+#pragma unroll
+        for (int c = 0; c < ACC; ++c) acc[c] = 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k) acc[k % ACC] = __fmaf_rn(kr[r][k], z[k], acc[k % ACC]);
+        float v = acc[0];
+#pragma unroll
+        for (int c = 1; c < ACC; ++c) v += acc[c];
+        zn[r] = v;
+      }
+      if constexpr (L == 1) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) z[j] = zn[j];
+      } else {
+        float* buf = &s_x[warp][t & 1][g][0];
+        if constexpr (R % 4 == 0) {
+#pragma unroll
+          for (int r = 0; r < R; r += 4)
+            *reinterpret_cast<float4*>(buf + q * R + r) =
+                make_float4(zn[r], zn[r + 1], zn[r + 2], zn[r + 3]);
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) buf[q * R + r] = zn[r];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < N; k += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(buf + k);
+          z[k] = v.x; z[k + 1] = v.y; z[k + 2] = v.z; z[k + 3] = v.w;
+        }
+      }
+      if constexpr (TRAJ) {
+        if (traj != nullptr && alive) {
+#pragma unroll
+          for (int j = 0; j < N; ++j) traj[(size_t)t * N + j] = z[j];
+        }
+      }
+      bool ok = box_ok<NX>(a.safety, z);
+      if constexpr (B::TRACK) {
+        if (a.safety.has_track) {  // uniform over the grid
+          const bool on_road = track_ok<L>(a.safety.track, tv, z[0], z[1], q, alive && ok);
+          ok = ok && on_road;
+        }
+      }
+      if (alive) {
+        if (ok) ttv = t;
+        else alive = false;
+      }
+      if (!__any_sync(kFull, alive)) break;
+    }
+
+    if (valid) {
+      // selection key: (H - ttv) | cost bits | slot -> lexicographic minimum
+      const unsigned long long key = ((unsigned long long)(H - ttv) << 55) |
+                                     ((unsigned long long)__float_as_uint(cost) << 23) |
+                                     (unsigned long long)slot;
+      best = key < best ? key : best;
+      if (q == 0) {
+        n_exec += (unsigned int)min(ttv + 1, H);
+        n_safe += ttv == H;
+        if (a.ttv_out) a.ttv_out[slot] = ttv;
+        if (a.cost_out) a.cost_out[slot] = cost;
       }
     }
-    if (alive) {
-      if (ok) ttv = t;
-      else alive = false;
-    }
-    if (!__any_sync(kFull, alive)) break;
   }
 
-  // selection key: (H - ttv) | cost bits | slot  -> lexicographic minimum
-  unsigned long long key = ~0ull;
-  if (valid) {
-    key = ((unsigned long long)(H - ttv) << 55) |
-          ((unsigned long long)__float_as_uint(cost) << 23) | (unsigned long long)slot;
-    if (q == 0) {
-      if (a.ttv_out) a.ttv_out[slot] = ttv;
-      if (a.cost_out) a.cost_out[slot] = cost;
-    }
-  }
-  unsigned int steps = (valid && q == 0) ? (unsigned int)min(ttv + 1, H) : 0u;
+  // warp -> block -> grid reduction
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long other = __shfl_xor_sync(kFull, key, o);
-    key = other < key ? other : key;
-    steps += __shfl_xor_sync(kFull, steps, o);
+    const unsigned long long other = __shfl_xor_sync(kFull, best, o);
+    best = other < best ? other : best;
+    n_exec += __shfl_xor_sync(kFull, n_exec, o);
+    n_safe += __shfl_xor_sync(kFull, n_safe, o);
   }
-  const unsigned int nsafe = __popc(__ballot_sync(kFull, valid && q == 0 && ttv == H));
   if (lane == 0) {
-    s_key[warp] = key;
-    s_exec[warp] = steps;
-    s_nsafe[warp] = nsafe;
+    s_key[warp] = best;
+    s_cnt[warp] = ((unsigned long long)n_safe << 40) + n_exec;
   }
   __syncthreads();
   if (tid == 0) {
-    unsigned long long bk = s_key[0];
-    unsigned long long be = s_exec[0];
-    unsigned int bs = s_nsafe[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+    unsigned long long bk = s_key[0], bc = s_cnt[0];
+    for (int w = 1; w < wpb; ++w) {
       bk = s_key[w] < bk ? s_key[w] : bk;
-      be += s_exec[w];
-      bs += s_nsafe[w];
+      bc += s_cnt[w];
     }
     TickScratch* sc = a.scratch;
     atomicMin(&sc->key, bk);
-    atomicAdd(&sc->executed, be);
-    atomicAdd(&sc->n_safe, bs);
+    atomicAdd(&sc->counts, bc);
     __threadfence();
     const unsigned int prev = atomicAdd(&sc->done, 1u);
     s_last = (prev == gridDim.x - 1);
@@ -317,32 +335,30 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
     // last block: every other block's atomics are visible (fence + counter)
     __threadfence();
     TickScratch* sc = a.scratch;
-    const unsigned long long k = atomicAdd(&sc->key, 0ull);
-    const unsigned long long ex = atomicAdd(&sc->executed, 0ull);
-    const unsigned int ns = atomicAdd(&sc->n_safe, 0u);
-    const int best = (int)(k & 0x7FFFFFull);
+    const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&sc->key);
+    const unsigned long long cnt = *reinterpret_cast<volatile unsigned long long*>(&sc->counts);
+    const int pick = (int)(k & 0x7FFFFFull);
     const int hm = (int)(k >> 55);
     mpmi_result r;
     float xb[NU];
-    candidate_value<NU>(a, best, s_uh, xb);
+    candidate_value<NU>(a, pick, uh, xb);
 #pragma unroll
     for (int j = 0; j < MPMI_MAX_NU; ++j) r.u_r[j] = 0.0;
 #pragma unroll
     for (int j = 0; j < NU; ++j)
-      r.u_r[j] = (a.include_user && best == 0) ? a.u_h[j] : (double)xb[j];
-    r.index = best;
+      r.u_r[j] = (a.include_user && pick == 0) ? a.u_h[j] : (double)xb[j];
+    r.index = pick;
     r.status = hm == 0 ? MPMI_SAFE : MPMI_FALLBACK;
-    r.n_safe = (int32_t)ns;
+    r.n_safe = (int32_t)(cnt >> 40);
     r.ttv = H - hm;
     r.cost = __uint_as_float((unsigned int)((k >> 23) & 0xFFFFFFFFull));
     r.n_slots = a.n_slots;
-    r.executed_steps = ex;
+    r.executed_steps = cnt & ((1ull << 40) - 1);
     r.tick = a.tick;
     r.reserved = 0;
     *a.result = r;
     sc->key = ~0ull;
-    sc->executed = 0ull;
-    sc->n_safe = 0u;
+    sc->counts = 0ull;
     sc->done = 0u;
   }
 }

@@ -13,7 +13,10 @@
 // w + r of the cell centre whenever p is safe, so the minimum over the list
 // decides "< w" exactly as the minimum over all segments would.  The margin e
 // also covers float32 rounding that puts a point into a neighbouring cell.
+// The grid is packed into one blob that every block stages in shared memory;
+// the cell size grows until the blob fits kMaxTrackBytes.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <string>
@@ -32,6 +35,8 @@ static double seg_dist(double px, double py, double ax, double ay, double dx, do
   const double ex = rx - t * dx, ey = ry - t * dy;
   return sqrt(ex * ex + ey * ey);
 }
+
+static size_t up16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 int build_track_grid(const double* xy, int n, double w, TrackGrid* g, std::string* err) {
   if (n < 3) {
@@ -63,52 +68,67 @@ int build_track_grid(const double* xy, int n, double w, TrackGrid* g, std::strin
   const double extent = fmax(xmax - xmin, ymax - ymin);
   double h = w / 2.0;
   if (extent / h > 1024.0) h = extent / 1024.0;
-  const int gnx = (int)ceil((xmax - xmin) / h), gny = (int)ceil((ymax - ymin) / h);
-  const double r = h * sqrt(2.0) / 2.0;
   const double e = 1e-3 + 2e-5 * (cmax + pad);
-  g->gx0 = xmin; g->gy0 = ymin; g->h = h; g->gnx = gnx; g->gny = gny;
-  g->cells.assign((size_t)gnx * gny, 0);
-  g->list.clear();
   std::vector<std::pair<double, int>> near;
-  for (int cy = 0; cy < gny; ++cy) {
-    for (int cx = 0; cx < gnx; ++cx) {
-      const double px = xmin + (cx + 0.5) * h, py = ymin + (cy + 0.5) * h;
-      near.clear();
-      double dmin = INFINITY;
-      for (int i = 0; i < n; ++i) {
-        const double d = seg_dist(px, py, ax[i], ay[i], dx[i], dy[i], inv[i]);
-        dmin = fmin(dmin, d);
-        if (d < w + r + e) near.emplace_back(d, i);
-      }
-      uint32_t word;
-      if (dmin + r < w - e) {
-        word = kCellInside;
-      } else if (dmin - r > w + e) {
-        word = kCellOutside;
-      } else {
-        std::sort(near.begin(), near.end());
-        if (near.size() > 255 || g->list.size() + near.size() >= (1u << 22)) {
-          *err = "set_safety_set: track too dense for the grid (segment list overflow)";
-          return MPMI_E_UNSUPPORTED;
+  for (int attempt = 0; attempt < 12; ++attempt, h *= 1.25) {
+    const int gnx = (int)ceil((xmax - xmin) / h), gny = (int)ceil((ymax - ymin) / h);
+    const double r = h * sqrt(2.0) / 2.0;
+    if (up16(4 * (size_t)gnx * gny) > (size_t)kMaxTrackBytes) continue;
+    g->gx0 = xmin; g->gy0 = ymin; g->h = h; g->gnx = gnx; g->gny = gny;
+    g->cells.assign((size_t)gnx * gny, 0);
+    g->list.clear();
+    bool overflow = false;
+    for (int cy = 0; cy < gny && !overflow; ++cy) {
+      for (int cx = 0; cx < gnx; ++cx) {
+        const double px = xmin + (cx + 0.5) * h, py = ymin + (cy + 0.5) * h;
+        near.clear();
+        double dmin = INFINITY;
+        for (int i = 0; i < n; ++i) {
+          const double d = seg_dist(px, py, ax[i], ay[i], dx[i], dy[i], inv[i]);
+          dmin = fmin(dmin, d);
+          if (d < w + r + e) near.emplace_back(d, i);
         }
-        word = kCellBoundary | ((uint32_t)g->list.size() << 2) |
-               ((uint32_t)near.size() << 24);
-        for (auto& pr : near) g->list.push_back((uint16_t)pr.second);
+        uint32_t word;
+        if (dmin + r < w - e) {
+          word = kCellInside;
+        } else if (dmin - r > w + e) {
+          word = kCellOutside;
+        } else {
+          std::sort(near.begin(), near.end());
+          if (near.size() > 255 || g->list.size() + near.size() >= (1u << 22)) {
+            overflow = true;
+            break;
+          }
+          word = kCellBoundary | ((uint32_t)g->list.size() << 2) |
+                 ((uint32_t)near.size() << 24);
+          for (auto& pr : near) g->list.push_back((uint16_t)pr.second);
+        }
+        g->cells[(size_t)cy * gnx + cx] = word;
       }
-      g->cells[(size_t)cy * gnx + cx] = word;
     }
+    if (overflow) continue;
+    if (g->list.empty()) g->list.push_back(0);
+    const size_t b_cells = up16(4 * g->cells.size());
+    const size_t b_list = up16(2 * g->list.size());
+    const size_t b_seg = 16 * (size_t)n, b_inv = up16(4 * (size_t)n);
+    const size_t total = b_cells + b_list + b_seg + b_inv;
+    if (total > (size_t)kMaxTrackBytes) continue;
+    g->off_list = (int)b_cells;
+    g->off_seg = (int)(b_cells + b_list);
+    g->off_inv = (int)(b_cells + b_list + b_seg);
+    g->blob.assign(total, 0);
+    memcpy(g->blob.data(), g->cells.data(), 4 * g->cells.size());
+    memcpy(g->blob.data() + g->off_list, g->list.data(), 2 * g->list.size());
+    for (int i = 0; i < n; ++i) {
+      const float sg[4] = {(float)ax[i], (float)ay[i], (float)dx[i], (float)dy[i]};
+      memcpy(g->blob.data() + g->off_seg + 16 * (size_t)i, sg, 16);
+      const float iv = (float)inv[i];
+      memcpy(g->blob.data() + g->off_inv + 4 * (size_t)i, &iv, 4);
+    }
+    return MPMI_OK;
   }
-  g->seg.resize(4 * (size_t)n);
-  g->seg_inv.resize(n);
-  for (int i = 0; i < n; ++i) {
-    g->seg[4 * i + 0] = (float)ax[i];
-    g->seg[4 * i + 1] = (float)ay[i];
-    g->seg[4 * i + 2] = (float)dx[i];
-    g->seg[4 * i + 3] = (float)dy[i];
-    g->seg_inv[i] = (float)inv[i];
-  }
-  if (g->list.empty()) g->list.push_back(0);
-  return MPMI_OK;
+  *err = "set_safety_set: track grid does not fit the shared-memory budget";
+  return MPMI_E_UNSUPPORTED;
 }
 
 }  // namespace mpmi

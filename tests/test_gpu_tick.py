@@ -297,13 +297,20 @@ def test_session_argument_checks(lib, ctx, bot):
     env, model = bot
     bad = [dict(n_samples=-1, horizon=10), dict(n_samples=10, horizon=0),
            dict(n_samples=10, horizon=512), dict(n_samples=0, horizon=5, include_user=False),
-           dict(n_samples=10, horizon=5, lanes=3), dict(n_samples=10, horizon=5, block=100),
-           dict(n_samples=10, horizon=5, sampler="grid", input_lo=[-1.0, -1.0])]
+           dict(n_samples=10, horizon=5, lanes=3), dict(n_samples=10, horizon=5, block=100)]
     for kw in bad:
         kw = dict(kw)
-        lo = kw.pop("input_lo", env.lo)
         with pytest.raises(lib.MpmiError):
-            lib.Session(ctx, model, kw.pop("n_samples"), kw.pop("horizon"), lo, env.hi, **kw)
+            lib.Session(ctx, model, kw.pop("n_samples"), kw.pop("horizon"), env.lo, env.hi, **kw)
+    with pytest.raises(lib.MpmiError):
+        lib.Session(ctx, model, 10, 5, [0.5], [-0.5])     # empty input box
+
+
+def test_grid_needs_a_perfect_power(lib, ctx, car):
+    env, model = car
+    with pytest.raises(lib.MpmiError):
+        lib.Session(ctx, model, 10, 5, env.lo, env.hi, sampler="grid")   # 10 != G^2
+    lib.Session(ctx, model, 49, 5, env.lo, env.hi, sampler="grid").close()
 
 
 def test_memory_budget_admission(lib):
