@@ -236,6 +236,36 @@ int mpmi_debug_trajectories(mpmi_session* s, const double* x_t_dev,
                             int32_t* ttv_dev, float* cost_dev, float* traj_dev,
                             void* stream);
 
+/* ---- a tick that allocates nothing -------------------------------------- */
+/* The paper has no counterpart to this entry point; it serves callers that may
+ * not allocate device memory while they run: a hard real-time control loop that
+ * forbids allocation after start-up (cudaMalloc/cudaFree can block and
+ * synchronise the device, breaking the tick deadline), or a framework that owns
+ * all device memory and only hands this library finished buffers.  It performs
+ * the same tick as mpmi_evaluate_candidates_device without a session and calls
+ * no cudaMalloc, cudaFree or other allocating routine.
+ *   basis          the lifted basis (as for mpmi_model_from_operator)
+ *   K_dev          device, n x n float32 row-major operator (caller-owned)
+ *   spec           host; per-coordinate box and inflation only: track_xy must be
+ *                  NULL (a track needs the grid a model allocates)
+ *   cfg            host; N, H, include_user, sampler (UNIFORM or EXTERNAL),
+ *                  input box, seed, stream_id, lanes, block (0 = defaults)
+ *   x_t_dev, u_h_dev, candidates_dev, tick, result_dev, stream: as for
+ *                  mpmi_evaluate_candidates_device
+ * Scratch: one partial result per thread block lives in a static device array of
+ * 16,392 bytes inside the library, held by every GPU that loads the library until
+ * the process exits.  A call may use at most 1024 blocks, i.e. at most
+ * 1024 * (block / lanes) candidate slots; larger calls fail with
+ * MPMI_E_INVALID_ARG and a message giving the limit.  All calls share that array:
+ * calls whose kernels overlap on the GPU race and must not be issued (keep them on
+ * one stream).  The first call on each device looks up the array's address; make
+ * it before any stream capture begins.  Returns without waiting. */
+int mpmi_evaluate_candidates_noalloc(const mpmi_basis_desc* basis, const float* K_dev,
+                                     const mpmi_safety_spec* spec,
+                                     const mpmi_session_config* cfg, const double* x_t_dev,
+                                     const double* u_h_dev, const float* candidates_dev,
+                                     uint64_t tick, mpmi_result* result_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

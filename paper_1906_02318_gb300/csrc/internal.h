@@ -61,6 +61,10 @@ struct TickArgs {
   int32_t* ttv_out;
   float* cost_out;
   float* traj_out;
+  // per-block partial results (no-allocation variant only): keys [0, cap),
+  // counts [cap, 2 cap), block counter at [2 cap]
+  unsigned long long* partials;
+  int partials_cap;
 };
 
 }  // namespace mpmi

@@ -129,7 +129,36 @@ __device__ __forceinline__ bool track_ok(const DevTrack& tr, const TrackView& v,
   return ok;
 }
 
-template <int KIND, int L, bool TRAJ>
+// Decode of the winning key into the result record (no-allocation variant).
+template <int NU>
+__device__ __forceinline__ void write_result(const TickArgs& a, unsigned long long k,
+                                             unsigned long long cnt, const float* uh) {
+  const int pick = (int)(k & 0x7FFFFFull);
+  const int hm = (int)(k >> 55);
+  mpmi_result r;
+  float xb[NU];
+  candidate_value<NU>(a, pick, uh, xb);
+#pragma unroll
+  for (int j = 0; j < MPMI_MAX_NU; ++j) r.u_r[j] = 0.0;
+#pragma unroll
+  for (int j = 0; j < NU; ++j)
+    r.u_r[j] = (a.include_user && pick == 0) ? a.u_h[j] : (double)xb[j];
+  r.index = pick;
+  r.status = hm == 0 ? MPMI_SAFE : MPMI_FALLBACK;
+  r.n_safe = (int32_t)(cnt >> 40);
+  r.ttv = a.horizon - hm;
+  r.cost = __uint_as_float((unsigned int)((k >> 23) & 0xFFFFFFFFull));
+  r.n_slots = a.n_slots;
+  r.executed_steps = cnt & ((1ull << 40) - 1);
+  r.tick = a.tick;
+  r.reserved = 0;
+  *a.result = r;
+}
+
+// PARTIALS = true is the no-allocation variant: instead of atomics on a
+// session's reduction record, each block stores its partial (key, counts) in
+// a.partials and the last block folds them.
+template <int KIND, int L, bool TRAJ, bool PARTIALS = false>
 __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__ TickArgs a) {
   using B = BasisTraits<KIND>;
   constexpr int N = B::N, NX = B::NX, NU = B::NU, NP = B::NP;
@@ -317,6 +346,53 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
     s_cnt[warp] = ((unsigned long long)n_safe << 40) + n_exec;
   }
   __syncthreads();
+  if constexpr (PARTIALS) {
+    unsigned long long* pk = a.partials;
+    unsigned long long* pc = a.partials + a.partials_cap;
+    unsigned long long* blocks_done = a.partials + 2 * a.partials_cap;
+    if (tid == 0) {
+      unsigned long long bk = s_key[0], bc = s_cnt[0];
+      for (int w = 1; w < wpb; ++w) {
+        bk = s_key[w] < bk ? s_key[w] : bk;
+        bc += s_cnt[w];
+      }
+      pk[blockIdx.x] = bk;
+      pc[blockIdx.x] = bc;
+      __threadfence();
+      const unsigned long long prev = atomicAdd(blocks_done, 1ull);
+      s_last = (prev == (unsigned long long)gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    unsigned long long k = ~0ull, c = 0ull;
+    for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+      const unsigned long long kb = *reinterpret_cast<volatile unsigned long long*>(pk + b);
+      k = kb < k ? kb : k;
+      c += *reinterpret_cast<volatile unsigned long long*>(pc + b);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(kFull, k, o);
+      k = other < k ? other : k;
+      c += __shfl_xor_sync(kFull, c, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+      s_key[warp] = k;
+      s_cnt[warp] = c;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < wpb; ++w) {
+        k = s_key[w] < k ? s_key[w] : k;
+        c += s_cnt[w];
+      }
+      write_result<NU>(a, k, c, uh);
+      *blocks_done = 0ull;
+    }
+    return;
+  }
   if (tid == 0) {
     unsigned long long bk = s_key[0], bc = s_cnt[0];
     for (int w = 1; w < wpb; ++w) {

@@ -87,6 +87,10 @@ _SIGNATURES = {
     "mpmi_sample_candidates": (c_i32, [c_vp, c_vp, c_vp, c_u64, c_vp, c_vp]),
     "mpmi_debug_trajectories": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp, c_vp, c_vp,
                                         c_vp, c_vp]),
+    "mpmi_evaluate_candidates_noalloc": (c_i32, [ctypes.POINTER(BasisDesc), c_vp,
+                                                 ctypes.POINTER(SafetySpecC),
+                                                 ctypes.POINTER(SessionConfig), c_vp, c_vp,
+                                                 c_vp, c_u64, c_vp, c_vp]),
 }
 
 _lib = None
@@ -343,3 +347,33 @@ def debug_trajectories(s: Session, x_t_dev, u_h_dev, result_dev, traj_dev, candi
     _check(s.ctx.lib.mpmi_debug_trajectories(
         s.handle, _ptr(x_t_dev), _ptr(u_h_dev), _ptr(candidates), tick, _ptr(result_dev),
         _ptr(ttv_dev), _ptr(cost_dev), _ptr(traj_dev), _stream(stream)))
+
+
+def evaluate_candidates_noalloc(basis: str, K_dev, lo, hi, n_samples: int, horizon: int,
+                                input_lo, input_hi, x_t_dev, u_h_dev, result_dev,
+                                inflation: float = 0.0, include_user: bool = True,
+                                sampler: str = "uniform", seed: int = 0, stream_id: int = 0,
+                                lanes: int = 0, block: int = 0, candidates=None, tick: int = 0,
+                                nx: int | None = None, nu: int | None = None, stream=None):
+    """mpmi_evaluate_candidates_noalloc: one tick from caller-owned device buffers
+    only (K, x_t, u_h, result); the library allocates nothing for it."""
+    lib = load()
+    d = _desc(basis, nx, nu)
+    spec = SafetySpecC()
+    lo, hi = _f64(lo), _f64(hi)
+    for j in range(MAX_NX):
+        spec.state_lo[j] = lo[j] if j < lo.size else -np.inf
+        spec.state_hi[j] = hi[j] if j < hi.size else np.inf
+    spec.inflation = inflation
+    cfg = SessionConfig()
+    cfg.n_samples, cfg.horizon = n_samples, horizon
+    cfg.include_user = int(include_user)
+    cfg.sampler = SAMPLER[sampler]
+    ilo, ihi = _f64(input_lo), _f64(input_hi)
+    for j in range(MAX_NU):
+        cfg.input_lo[j] = ilo[j] if j < ilo.size else 0.0
+        cfg.input_hi[j] = ihi[j] if j < ihi.size else 1.0
+    cfg.seed, cfg.stream_id, cfg.lanes, cfg.block = seed, stream_id, lanes, block
+    _check(lib.mpmi_evaluate_candidates_noalloc(
+        ctypes.byref(d), _ptr(K_dev), ctypes.byref(spec), ctypes.byref(cfg), _ptr(x_t_dev),
+        _ptr(u_h_dev), _ptr(candidates), tick, _ptr(result_dev), _stream(stream)))
