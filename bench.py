@@ -258,7 +258,7 @@ def run_gpu(args, rank, world):
     seed = LOOP_SEED + 1000 * rank
     sess = lib.Session(ctx, model, N_SAMPLES, HORIZON, plants.BOT_INPUT_LO,
                        plants.BOT_INPUT_HI, seed=seed, stream_id=rank)
-    lanes, block = sess.launch_shape()
+    lanes, cands, block = sess.launch_shape()
     n_slots = sess.n_slots
     ticks = max(TICKS, args.warmup + args.steps)
     uhs = data.ou_user_input(seed, ticks, plants.BOT_DT, plants.BOT_INPUT_LO,
@@ -352,7 +352,7 @@ def run_gpu(args, rank, world):
     sess.close()
     model.free()
     return dict(dev_time=dev_time, durs=durs, executed=executed, lat=lat, e2e_rate=e2e_rate,
-                wall=wall, clocks=clk, lanes=lanes, block=block, n_slots=n_slots,
+                wall=wall, clocks=clk, lanes=lanes, cands=cands, block=block, n_slots=n_slots,
                 residual=residual, n_fallback=int(n_fallback), trials=trials,
                 sm_count=props.multi_processor_count,
                 gpu_name=props.name)
@@ -419,7 +419,7 @@ def main():
         "value": value, "unit": "rollout steps/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": t_max / K * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(cfg, lanes=out["lanes"], block=out["block"],
+        "config": dict(cfg, lanes=out["lanes"], cands_per_thread=out["cands"], block=out["block"],
                        parallelism=f"replicas{world}" if world > 1 else "single"),
         "executed_steps_per_s": world * float(out["executed"].sum()) / t_max,
         "latency_ms": {"p50": float(np.percentile(out["lat"], 50) * 1e3),

@@ -120,7 +120,8 @@ typedef struct {
   uint32_t stream_id;   /* Philox counter word 3 (UNIFORM): session identity   */
   int32_t lanes;        /* 0 = library choice; else lanes per candidate        */
   int32_t block;        /* 0 = library choice; else threads per block          */
-  int32_t pad0;
+  int32_t cands_per_thread; /* 0 = library choice; else candidates per thread
+                               (with one lane per candidate)                    */
 } mpmi_session_config;
 
 /* One tick's outcome (written by the device, 80 bytes). */
@@ -190,8 +191,10 @@ int mpmi_set_safety_set(mpmi_model* model, const mpmi_safety_spec* spec);
 int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model,
                       const mpmi_session_config* cfg, mpmi_session** out);
 void mpmi_session_close(mpmi_session* s);
-/* Lanes per candidate and threads per block the session launches with. */
-int mpmi_session_launch_shape(const mpmi_session* s, int32_t* lanes, int32_t* block);
+/* Lanes per candidate, candidates per thread and threads per block the session
+ * launches with (any output pointer may be NULL). */
+int mpmi_session_launch_shape(const mpmi_session* s, int32_t* lanes, int32_t* cands,
+                              int32_t* block);
 
 /* ---- evaluate_candidates + select_input (Alg. 2) ------------------------ */
 /* Queues one tick on `stream`: copies x_t (nx doubles) and u_h (nu doubles) from

@@ -95,7 +95,7 @@ struct mpmi_session {
   mpmi_ctx* ctx = nullptr;
   const mpmi_model* model = nullptr;
   mpmi_session_config cfg{};
-  int n_slots = 0, lanes = 1, block = 128, grid_g = 0;
+  int n_slots = 0, lanes = 1, cands = 1, block = 128, grid_g = 0;
   int max_grid[2] = {0, 0};  // resident blocks on the device (plain, trajectories)
   size_t grid_smem[2] = {0, 0};  // dynamic shared memory max_grid was computed for
   mpmi::TickScratch* scratch_dev = nullptr;

@@ -61,51 +61,65 @@ static bool budget_ok(mpmi_ctx* ctx, uint64_t bytes) {
 struct TickKernel {
   const void* fn = nullptr;
   void (*launch)(const TickArgs&, int, int, size_t, cudaStream_t) = nullptr;
+  size_t k_smem = 0;  // bytes of K staged in shared memory
 };
 
-template <int KIND, int L, bool TRAJ>
+template <int KIND, int L, int C, bool KSMEM, bool TRAJ>
 static void launch_tick(const TickArgs& a, int grid, int block, size_t smem, cudaStream_t st) {
-  tick_kernel<KIND, L, TRAJ><<<grid, block, smem, st>>>(a);
+  tick_kernel<KIND, L, C, KSMEM, TRAJ><<<grid, block, smem, st>>>(a);
 }
 
-template <int KIND, int L, bool TRAJ>
+template <int KIND, int L, int C, bool KSMEM, bool TRAJ>
 static TickKernel make_kernel() {
   TickKernel k;
-  k.fn = reinterpret_cast<const void*>(&tick_kernel<KIND, L, TRAJ>);
-  k.launch = &launch_tick<KIND, L, TRAJ>;
+  k.fn = reinterpret_cast<const void*>(&tick_kernel<KIND, L, C, KSMEM, TRAJ>);
+  k.launch = &launch_tick<KIND, L, C, KSMEM, TRAJ>;
+  k.k_smem = KSMEM ? (size_t)BasisTraits<KIND>::N * BasisTraits<KIND>::N * sizeof(float) : 0;
   return k;
 }
 
+// Compiled launch shapes: (lanes, candidates per thread); the race car with one
+// lane keeps K in shared memory.
 template <int KIND, bool TRAJ>
-static TickKernel pick_lanes(int lanes) {
+static TickKernel pick_shape(int lanes, int cands) {
   if constexpr (KIND == kBot) {
-    if (lanes == 1) return make_kernel<KIND, 1, TRAJ>();
-    if (lanes == 2) return make_kernel<KIND, 2, TRAJ>();
-    if (lanes == 4) return make_kernel<KIND, 4, TRAJ>();
+    if (lanes == 1 && cands == 1) return make_kernel<KIND, 1, 1, false, TRAJ>();
+    if (lanes == 1 && cands == 2) return make_kernel<KIND, 1, 2, false, TRAJ>();
+    if (lanes == 2 && cands == 1) return make_kernel<KIND, 2, 1, false, TRAJ>();
+    if (lanes == 4 && cands == 1) return make_kernel<KIND, 4, 1, false, TRAJ>();
   } else if constexpr (KIND == kCar) {
-    if (lanes == 8) return make_kernel<KIND, 8, TRAJ>();
-    if (lanes == 16) return make_kernel<KIND, 16, TRAJ>();
+    if (lanes == 1 && cands == 1) return make_kernel<KIND, 1, 1, true, TRAJ>();
+    if (lanes == 1 && cands == 2) return make_kernel<KIND, 1, 2, true, TRAJ>();
+    if (lanes == 8 && cands == 1) return make_kernel<KIND, 8, 1, false, TRAJ>();
+    if (lanes == 16 && cands == 1) return make_kernel<KIND, 16, 1, false, TRAJ>();
   } else {
-    if (lanes == 1) return make_kernel<KIND, 1, TRAJ>();
+    if (lanes == 1 && cands == 1) return make_kernel<KIND, 1, 1, false, TRAJ>();
   }
   return TickKernel{};
 }
 
-static TickKernel pick_tick(int kind, int lanes, bool traj) {
+static TickKernel pick_tick(int kind, int lanes, int cands, bool traj) {
   switch (kind) {
-    case kBot: return traj ? pick_lanes<kBot, true>(lanes) : pick_lanes<kBot, false>(lanes);
-    case kCar: return traj ? pick_lanes<kCar, true>(lanes) : pick_lanes<kCar, false>(lanes);
-    case kLin11: return traj ? pick_lanes<kLin11, true>(lanes) : pick_lanes<kLin11, false>(lanes);
-    case kLin22: return traj ? pick_lanes<kLin22, true>(lanes) : pick_lanes<kLin22, false>(lanes);
-    case kLin41: return traj ? pick_lanes<kLin41, true>(lanes) : pick_lanes<kLin41, false>(lanes);
+    case kBot: return traj ? pick_shape<kBot, true>(lanes, cands) : pick_shape<kBot, false>(lanes, cands);
+    case kCar: return traj ? pick_shape<kCar, true>(lanes, cands) : pick_shape<kCar, false>(lanes, cands);
+    case kLin11: return traj ? pick_shape<kLin11, true>(lanes, cands) : pick_shape<kLin11, false>(lanes, cands);
+    case kLin22: return traj ? pick_shape<kLin22, true>(lanes, cands) : pick_shape<kLin22, false>(lanes, cands);
+    case kLin41: return traj ? pick_shape<kLin41, true>(lanes, cands) : pick_shape<kLin41, false>(lanes, cands);
   }
   return TickKernel{};
 }
 
-static int default_lanes(int kind, int n_slots) {
-  if (kind == kBot) return n_slots <= 32768 ? 4 : (n_slots <= 131072 ? 2 : 1);
-  if (kind == kCar) return 8;
-  return 1;
+// Default launch shape (lanes, candidates per thread, block): one lane per
+// candidate; the race car keeps K in shared memory and takes two candidates per
+// thread once there are enough candidates to fill the GPU; small grids use
+// 64-thread blocks so every SM gets work.
+static void default_shape(int kind, int n_slots, int sms, int* lanes, int* cands, int* block) {
+  *lanes = 1;
+  *cands = (kind == kCar && n_slots > 48 * 1024) ? 2 : 1;
+  if (*block == 0) {
+    const long long threads = ((long long)n_slots * *lanes + *cands - 1) / *cands;
+    *block = threads <= (long long)sms * 128 ? 64 : (threads <= (long long)sms * 256 ? 128 : 256);
+  }
 }
 
 static TickArgs make_args(const mpmi_session* s, uint64_t tick) {
@@ -140,14 +154,14 @@ static TickArgs make_args(const mpmi_session* s, uint64_t tick) {
 // Persistent grid: no more blocks than are resident at once, and no more than
 // the warp-tiles need.  Occupancy is cached per dynamic shared-memory size.
 static int launch(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st) {
-  TickKernel k = pick_tick(s->model->kind, s->lanes, traj);
-  if (!k.fn) return fail(MPMI_E_UNSUPPORTED, "tick kernel not compiled for this basis/lanes");
-  const size_t smem = a.safety.has_track ? (size_t)a.safety.track.blob_bytes : 0;
+  TickKernel k = pick_tick(s->model->kind, s->lanes, s->cands, traj);
+  if (!k.fn) return fail(MPMI_E_UNSUPPORTED, "tick kernel not compiled for this launch shape");
+  const size_t smem = k.k_smem + (a.safety.has_track ? (size_t)a.safety.track.blob_bytes : 0);
   const int t = traj ? 1 : 0;
   if (s->max_grid[t] == 0 || s->grid_smem[t] != smem) {
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           kMaxTrackBytes);
+                                           (int)(k.k_smem + kMaxTrackBytes));
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }
     int nb = 0;
@@ -158,7 +172,7 @@ static int launch(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st) {
     s->grid_smem[t] = smem;
   }
   const int wpb = s->block / 32;
-  const int per_warp = 32 / s->lanes;
+  const int per_warp = 32 / s->lanes * s->cands;
   const int n_wtiles = (s->n_slots + per_warp - 1) / per_warp;
   int grid = (n_wtiles + wpb - 1) / wpb;
   if (grid > s->max_grid[t]) grid = s->max_grid[t];
@@ -446,12 +460,19 @@ int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model, const mpmi_session
     gg = grid_points(cfg->n_samples, model->nu);
     if (gg <= 0) return fail(MPMI_E_INVALID_ARG, "session_open: grid sampling needs N = G^M");
   }
-  int lanes = cfg->lanes ? cfg->lanes : default_lanes(model->kind, (int)slots);
-  int block = cfg->block ? cfg->block : 128;
+  int lanes = cfg->lanes, cands = cfg->cands_per_thread, block = cfg->block;
+  {
+    int dl, dc, db = block;
+    default_shape(model->kind, (int)slots, ctx->sm_count, &dl, &dc, &db);
+    if (lanes == 0) lanes = dl;
+    if (cands == 0) cands = lanes == 1 ? dc : 1;
+    if (block == 0) block = db;
+  }
   if (block % 32 != 0 || block < 32 || block > kMaxBlock)
     return fail(MPMI_E_INVALID_ARG, "session_open: block must be a multiple of 32 in 32..256");
-  if (!pick_tick(model->kind, lanes, false).fn)
-    return fail(MPMI_E_UNSUPPORTED, "session_open: lanes per candidate not compiled for this basis");
+  if (!pick_tick(model->kind, lanes, cands, false).fn)
+    return fail(MPMI_E_UNSUPPORTED, "session_open: launch shape (lanes, candidates per thread) "
+                                    "not compiled for this basis");
   const uint64_t bytes = sizeof(TickScratch) + sizeof(mpmi_result) + 16 * sizeof(double);
   if (!budget_ok(ctx, bytes)) return fail(MPMI_E_OOM, "session exceeds the memory budget");
   DeviceGuard guard(ctx->device);
@@ -462,6 +483,7 @@ int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model, const mpmi_session
   s->cfg = *cfg;
   s->n_slots = (int)slots;
   s->lanes = lanes;
+  s->cands = cands;
   s->block = block;
   s->grid_g = gg;
   auto cleanup = [&](int code, const char* msg) {
@@ -511,9 +533,11 @@ void mpmi_session_close(mpmi_session* s) {
   delete s;
 }
 
-int mpmi_session_launch_shape(const mpmi_session* s, int32_t* lanes, int32_t* block) {
+int mpmi_session_launch_shape(const mpmi_session* s, int32_t* lanes, int32_t* cands,
+                              int32_t* block) {
   if (!s) return fail(MPMI_E_INVALID_ARG, "session is NULL");
   if (lanes) *lanes = s->lanes;
+  if (cands) *cands = s->cands;
   if (block) *block = s->block;
   return MPMI_OK;
 }

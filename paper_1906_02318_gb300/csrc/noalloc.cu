@@ -64,29 +64,41 @@ static int scratch_address(int dev, unsigned long long** out) {
   return MPMI_OK;
 }
 
-using NoAllocLaunch = void (*)(const TickArgs&, int, int, cudaStream_t);
+struct NoAllocKernel {
+  void (*launch)(const TickArgs&, int, int, size_t, cudaStream_t) = nullptr;
+  size_t k_smem = 0;
+};
 
-template <int KIND, int L>
-static void launch_noalloc(const TickArgs& a, int grid, int block, cudaStream_t st) {
-  tick_kernel<KIND, L, false, true><<<grid, block, 0, st>>>(a);
+template <int KIND, int L, bool KSMEM>
+static void launch_noalloc(const TickArgs& a, int grid, int block, size_t smem, cudaStream_t st) {
+  tick_kernel<KIND, L, 1, KSMEM, false, true><<<grid, block, smem, st>>>(a);
 }
 
-static NoAllocLaunch pick_noalloc(int kind, int lanes) {
+template <int KIND, int L, bool KSMEM>
+static NoAllocKernel make_noalloc() {
+  NoAllocKernel k;
+  k.launch = &launch_noalloc<KIND, L, KSMEM>;
+  k.k_smem = KSMEM ? (size_t)BasisTraits<KIND>::N * BasisTraits<KIND>::N * sizeof(float) : 0;
+  return k;
+}
+
+static NoAllocKernel pick_noalloc(int kind, int lanes) {
   switch (kind) {
     case kBot:
-      if (lanes == 1) return launch_noalloc<kBot, 1>;
-      if (lanes == 2) return launch_noalloc<kBot, 2>;
-      if (lanes == 4) return launch_noalloc<kBot, 4>;
-      return nullptr;
+      if (lanes == 1) return make_noalloc<kBot, 1, false>();
+      if (lanes == 2) return make_noalloc<kBot, 2, false>();
+      if (lanes == 4) return make_noalloc<kBot, 4, false>();
+      break;
     case kCar:
-      if (lanes == 8) return launch_noalloc<kCar, 8>;
-      if (lanes == 16) return launch_noalloc<kCar, 16>;
-      return nullptr;
-    case kLin11: return lanes == 1 ? launch_noalloc<kLin11, 1> : nullptr;
-    case kLin22: return lanes == 1 ? launch_noalloc<kLin22, 1> : nullptr;
-    case kLin41: return lanes == 1 ? launch_noalloc<kLin41, 1> : nullptr;
+      if (lanes == 1) return make_noalloc<kCar, 1, true>();
+      if (lanes == 8) return make_noalloc<kCar, 8, false>();
+      if (lanes == 16) return make_noalloc<kCar, 16, false>();
+      break;
+    case kLin11: if (lanes == 1) return make_noalloc<kLin11, 1, false>(); break;
+    case kLin22: if (lanes == 1) return make_noalloc<kLin22, 1, false>(); break;
+    case kLin41: if (lanes == 1) return make_noalloc<kLin41, 1, false>(); break;
   }
-  return nullptr;
+  return NoAllocKernel{};
 }
 
 }  // namespace mpmi
@@ -124,13 +136,14 @@ extern "C" int mpmi_evaluate_candidates_noalloc(
         !(cfg->input_lo[j] < cfg->input_hi[j]))
       return fail(MPMI_E_INVALID_ARG, "evaluate_candidates_noalloc: bad input box");
   }
-  int lanes = cfg->lanes;
-  if (lanes == 0) lanes = kind == kBot ? 1 : (kind == kCar ? 8 : 1);
+  int lanes = cfg->lanes ? cfg->lanes : 1;
   const int block = cfg->block ? cfg->block : 128;
   if (block % 32 != 0 || block < 32 || block > kMaxBlock)
     return fail(MPMI_E_INVALID_ARG, "evaluate_candidates_noalloc: block must be 32..256, x32");
-  NoAllocLaunch fn = pick_noalloc(kind, lanes);
-  if (!fn) return fail(MPMI_E_UNSUPPORTED, "evaluate_candidates_noalloc: lanes not compiled");
+  if (cfg->cands_per_thread > 1)
+    return fail(MPMI_E_UNSUPPORTED, "evaluate_candidates_noalloc: one candidate per thread");
+  NoAllocKernel kn = pick_noalloc(kind, lanes);
+  if (!kn.launch) return fail(MPMI_E_UNSUPPORTED, "evaluate_candidates_noalloc: lanes not compiled");
   const long long per_block = (long long)block / lanes;
   const long long grid = (slots + per_block - 1) / per_block;
   if (grid > kNoAllocMaxBlocks)
@@ -191,7 +204,7 @@ extern "C" int mpmi_evaluate_candidates_noalloc(
   e = cudaMemsetAsync(scratch + 2 * kNoAllocMaxBlocks, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess)
     return fail(MPMI_E_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-  fn(a, (int)grid, block, st);
+  kn.launch(a, (int)grid, block, kn.k_smem, st);
   e = cudaGetLastError();
   if (e != cudaSuccess)
     return fail(MPMI_E_CUDA, std::string("no-allocation tick launch: ") + cudaGetErrorString(e));

@@ -12,9 +12,11 @@
 // rows [qR, qR + R) of K in registers (R = n / L) and computes those rows of
 // K z; the group exchanges the new z through a per-warp shared-memory buffer
 // (double-buffered by step parity, one __syncwarp per step).  L = 1 keeps a
-// whole candidate in one thread.  Warps are persistent: warp w of the grid takes
-// the warp-tiles (32 / L candidates each) w, w + W, w + 2W, ... so K is loaded
-// once per thread and the race-car track grid once per block.
+// whole candidate in one thread; with L = 1 a thread may also carry C
+// candidates, and K may sit in shared memory instead of registers (KSMEM).
+// Warps are persistent: warp w of the grid takes the warp-tiles (32 C / L
+// candidates each) w, w + W, w + 2W, ... so K is loaded once per thread (or
+// block) and the race-car track grid once per block.
 #pragma once
 
 #include <stdint.h>
@@ -129,7 +131,7 @@ __device__ __forceinline__ bool track_ok(const DevTrack& tr, const TrackView& v,
   return ok;
 }
 
-// Decode of the winning key into the result record (no-allocation variant).
+// Decode of the winning key into the tick's result record.
 template <int NU>
 __device__ __forceinline__ void write_result(const TickArgs& a, unsigned long long k,
                                              unsigned long long cnt, const float* uh) {
@@ -155,23 +157,33 @@ __device__ __forceinline__ void write_result(const TickArgs& a, unsigned long lo
   *a.result = r;
 }
 
-// PARTIALS = true is the no-allocation variant: instead of atomics on a
-// session's reduction record, each block stores its partial (key, counts) in
-// a.partials and the last block folds them.
-template <int KIND, int L, bool TRAJ, bool PARTIALS = false>
+// Template parameters of the tick kernel:
+//   L        lanes per candidate (K rows split across the lanes, see above);
+//   C        candidates per thread (L = 1 only): more independent FMA chains;
+//   KSMEM    K staged once per block in shared memory and read with broadcast
+//            LDS.128 (L = 1 only) instead of held in registers: frees the
+//            registers of a large K (race car, n = 32) for occupancy;
+//   TRAJ     record every predicted z_t (parity checks);
+//   PARTIALS no-allocation variant: each block stores its partial (key,
+//            counts) in a.partials and the last block folds them, instead of
+//            atomics on a session's reduction record.
+template <int KIND, int L, int C, bool KSMEM, bool TRAJ, bool PARTIALS = false>
 __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__ TickArgs a) {
   using B = BasisTraits<KIND>;
   constexpr int N = B::N, NX = B::NX, NU = B::NU, NP = B::NP;
   static_assert(N % L == 0, "lanes must divide the lifted dimension");
   static_assert(32 % L == 0, "lanes must divide the warp");
+  static_assert(C == 1 || L == 1, "several candidates per thread need L = 1");
+  static_assert(!KSMEM || (L == 1 && N % 4 == 0), "K in shared memory needs L = 1, n % 4 == 0");
   constexpr int R = N / L;              // rows of K per lane
   constexpr int GPW = 32 / L;           // candidate groups per warp
   constexpr int S = (N % 32 == 0) ? N + 4 : ((N % 4 == 0) ? N : N + (4 - N % 4));
   constexpr int NW = kMaxBlock / 32;
-  constexpr int ACC = (R < 8) ? 2 : 1;  // split accumulators for ILP on short rows
+  constexpr int ACC = (R < 8 && C == 1) ? 2 : 1;  // split accumulators for ILP on short rows
   constexpr int ANG = (KIND == kBot) ? 0 : ((KIND == kCar) ? 2 : -1);
+  constexpr int KWORDS = KSMEM ? (N * N) / 4 : 0;  // 16-byte words of K in shared memory
 
-  extern __shared__ uint4 s_track[];
+  extern __shared__ uint4 s_dyn[];  // [K (KSMEM)] [track blob (race car)]
   __shared__ __align__(16) float s_x[(L > 1) ? NW : 1][2][GPW][S];
   __shared__ unsigned long long s_key[NW];
   __shared__ unsigned long long s_cnt[NW];
@@ -181,19 +193,25 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   const int q = lane % L, g = lane / L;
   const int H = a.horizon;
 
-  // stage the track grid (race car) while the per-tick state is prepared
+  // stage K (KSMEM) and the track grid (race car) while the per-tick state is prepared
+  if constexpr (KSMEM) {
+    const uint4* src = reinterpret_cast<const uint4*>(a.K);
+    for (int i = tid; i < KWORDS; i += blockDim.x) s_dyn[i] = __ldg(&src[i]);
+  }
   TrackView tv{nullptr, nullptr, nullptr, nullptr};
   if constexpr (B::TRACK) {
     if (a.safety.has_track) {
+      uint4* dst = s_dyn + KWORDS;
       const int words = a.safety.track.blob_bytes >> 4;
-      for (int i = tid; i < words; i += blockDim.x) s_track[i] = __ldg(&a.safety.track.blob[i]);
-      const char* base = reinterpret_cast<const char*>(s_track);
+      for (int i = tid; i < words; i += blockDim.x) dst[i] = __ldg(&a.safety.track.blob[i]);
+      const char* base = reinterpret_cast<const char*>(dst);
       tv.cells = reinterpret_cast<const uint32_t*>(base);
       tv.list = reinterpret_cast<const uint16_t*>(base + a.safety.track.off_list);
       tv.seg = reinterpret_cast<const float4*>(base + a.safety.track.off_seg);
       tv.inv = reinterpret_cast<const float*>(base + a.safety.track.off_inv);
     }
   }
+  const float4* sK4 = reinterpret_cast<const float4*>(s_dyn);
   // per-tick state: x_t and u_h in float32, the basis angle's sine and cosine
   float xs[NX], uh[NU];
 #pragma unroll
@@ -202,85 +220,145 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   for (int j = 0; j < NU; ++j) uh[j] = __double2float_rn(a.u_h[j]);
   float sn = 0.f, cs = 1.f;
   if constexpr (ANG >= 0) sincosf(xs[ANG], &sn, &cs);
-  // this lane's rows of K
-  float kr[R][N];
+  // this lane's rows of K (registers)
+  float kr[KSMEM ? 1 : R][KSMEM ? 1 : N];
+  if constexpr (!KSMEM) {
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const float* row = a.K + (q * R + r) * N;
-    if constexpr (N % 4 == 0) {
+    for (int r = 0; r < R; ++r) {
+      const float* row = a.K + (q * R + r) * N;
+      if constexpr (N % 4 == 0) {
 #pragma unroll
-      for (int k = 0; k < N; k += 4) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(row + k));
-        kr[r][k] = v.x; kr[r][k + 1] = v.y; kr[r][k + 2] = v.z; kr[r][k + 3] = v.w;
+        for (int k = 0; k < N; k += 4) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(row + k));
+          kr[r][k] = v.x; kr[r][k + 1] = v.y; kr[r][k + 2] = v.z; kr[r][k + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) kr[r][k] = __ldg(row + k);
       }
-    } else {
-#pragma unroll
-      for (int k = 0; k < N; ++k) kr[r][k] = __ldg(row + k);
     }
   }
-  if constexpr (B::TRACK) __syncthreads();
+  if constexpr (KSMEM || B::TRACK) __syncthreads();
 
   unsigned long long best = ~0ull;
   unsigned int n_safe = 0, n_exec = 0;
   const int wpb = blockDim.x >> 5;
-  const int n_wtiles = (a.n_slots + GPW - 1) / GPW;
+  constexpr int PER_WARP = GPW * C;  // candidate slots per warp-tile
+  const int n_wtiles = (a.n_slots + PER_WARP - 1) / PER_WARP;
   for (int wt = blockIdx.x * wpb + warp; wt < n_wtiles; wt += gridDim.x * wpb) {
-    const int slot = wt * GPW + g;
-    const bool valid = slot < a.n_slots;
-    float xi[NU];
-    if (valid) {
-      candidate_value<NU>(a, slot, uh, xi);
-    } else {
+    int slot[C];
+    bool valid[C], alive[C];
+    float cost[C];
+    int ttv[C];
+    float z[C][N];
+    float* traj[C];
 #pragma unroll
-      for (int j = 0; j < NU; ++j) xi[j] = uh[j];
-    }
-    float cost = 0.f;
+    for (int c = 0; c < C; ++c) {
+      slot[c] = wt * PER_WARP + c * GPW + g;
+      valid[c] = slot[c] < a.n_slots;
+      float xi[NU];
+      if (valid[c]) {
+        candidate_value<NU>(a, slot[c], uh, xi);
+      } else {
 #pragma unroll
-    for (int j = 0; j < NU; ++j) {
-      const float d = __fsub_rn(xi[j], uh[j]);
-      cost = __fmaf_rn(d, d, cost);
-    }
-    // lift: z_0 = a(x_t) + sum_k p_k(xi) b_k(x_t)
-    float p[NP];
-    monomials32<KIND>(xi, p);
-    float z[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      float av, bv[kMaxP];
-      feature_split<float>(KIND, j, xs, sn, cs, &av, bv);
-#pragma unroll
-      for (int k = 0; k < NP; ++k) av = __fmaf_rn(p[k], bv[k], av);
-      z[j] = av;
-    }
-    float* traj = nullptr;
-    if constexpr (TRAJ) {
-      if (valid && q == 0) {
-        traj = a.traj_out + (size_t)slot * (H + 1) * N;
-#pragma unroll
-        for (int j = 0; j < N; ++j) traj[j] = z[j];
+        for (int j = 0; j < NU; ++j) xi[j] = uh[j];
       }
+      cost[c] = 0.f;
+#pragma unroll
+      for (int j = 0; j < NU; ++j) {
+        const float d = __fsub_rn(xi[j], uh[j]);
+        cost[c] = __fmaf_rn(d, d, cost[c]);
+      }
+      // lift: z_0 = a(x_t) + sum_k p_k(xi) b_k(x_t)
+      float p[NP];
+      monomials32<KIND>(xi, p);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        float av, bv[kMaxP];
+        feature_split<float>(KIND, j, xs, sn, cs, &av, bv);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) av = __fmaf_rn(p[k], bv[k], av);
+        z[c][j] = av;
+      }
+      traj[c] = nullptr;
+      if constexpr (TRAJ) {
+        if (valid[c] && q == 0) {
+          traj[c] = a.traj_out + (size_t)slot[c] * (H + 1) * N;
+#pragma unroll
+          for (int j = 0; j < N; ++j) traj[c][j] = z[c][j];
+        }
+      }
+      ttv[c] = 0;
+      alive[c] = valid[c];
     }
 
-    int ttv = 0;
-    bool alive = valid;
     for (int t = 1; t <= H; ++t) {
-      float zn[R];
+      if constexpr (KSMEM) {
+        // z <- K z with K read from shared memory (one broadcast LDS.128 feeds 4 C
+        // FMAs).  The empty asm keeps the compiler from hoisting the loop-invariant
+        // K loads out of the step loop (1024 values would not fit in registers).
+        asm volatile("" ::: "memory");
+        float acc[C][N];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float acc[ACC];
+        for (int r = 0; r < N; ++r) {
+          float av[C];
 #pragma unroll
-        for (int c = 0; c < ACC; ++c) acc[c] = 0.f;
+          for (int c = 0; c < C; ++c) av[c] = 0.f;
 #pragma unroll
-        for (int k = 0; k < N; ++k) acc[k % ACC] = __fmaf_rn(kr[r][k], z[k], acc[k % ACC]);
-        float v = acc[0];
+          for (int k4 = 0; k4 < N / 4; ++k4) {
+            const float4 kv = sK4[r * (N / 4) + k4];
 #pragma unroll
-        for (int c = 1; c < ACC; ++c) v += acc[c];
-        zn[r] = v;
-      }
-      if constexpr (L == 1) {
+            for (int c = 0; c < C; ++c) {
+              av[c] = __fmaf_rn(kv.x, z[c][4 * k4], av[c]);
+              av[c] = __fmaf_rn(kv.y, z[c][4 * k4 + 1], av[c]);
+              av[c] = __fmaf_rn(kv.z, z[c][4 * k4 + 2], av[c]);
+              av[c] = __fmaf_rn(kv.w, z[c][4 * k4 + 3], av[c]);
+            }
+          }
 #pragma unroll
-        for (int j = 0; j < N; ++j) z[j] = zn[j];
+          for (int c = 0; c < C; ++c) acc[c][r] = av[c];
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int r = 0; r < N; ++r) z[c][r] = acc[c][r];
+      } else if constexpr (L == 1) {
+        float zn[C][N];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+#pragma unroll
+          for (int r = 0; r < N; ++r) {
+            float accv[ACC];
+#pragma unroll
+            for (int e = 0; e < ACC; ++e) accv[e] = 0.f;
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+              accv[k % ACC] = __fmaf_rn(kr[r][k], z[c][k], accv[k % ACC]);
+            float v = accv[0];
+#pragma unroll
+            for (int e = 1; e < ACC; ++e) v += accv[e];
+            zn[c][r] = v;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int j = 0; j < N; ++j) z[c][j] = zn[c][j];
       } else {
+        // L lanes per candidate: this lane's rows, then exchange through shared memory
+        float zn[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          float accv[ACC];
+#pragma unroll
+          for (int e = 0; e < ACC; ++e) accv[e] = 0.f;
+#pragma unroll
+          for (int k = 0; k < N; ++k) accv[k % ACC] = __fmaf_rn(kr[r][k], z[0][k], accv[k % ACC]);
+          float v = accv[0];
+#pragma unroll
+          for (int e = 1; e < ACC; ++e) v += accv[e];
+          zn[r] = v;
+        }
         float* buf = &s_x[warp][t & 1][g][0];
         if constexpr (R % 4 == 0) {
 #pragma unroll
@@ -295,40 +373,49 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
 #pragma unroll
         for (int k = 0; k < N; k += 4) {
           const float4 v = *reinterpret_cast<const float4*>(buf + k);
-          z[k] = v.x; z[k + 1] = v.y; z[k + 2] = v.z; z[k + 3] = v.w;
+          z[0][k] = v.x; z[0][k + 1] = v.y; z[0][k + 2] = v.z; z[0][k + 3] = v.w;
         }
       }
-      if constexpr (TRAJ) {
-        if (traj != nullptr && alive) {
+      bool any_alive = false;
 #pragma unroll
-          for (int j = 0; j < N; ++j) traj[(size_t)t * N + j] = z[j];
+      for (int c = 0; c < C; ++c) {
+        if constexpr (TRAJ) {
+          if (traj[c] != nullptr && alive[c]) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) traj[c][(size_t)t * N + j] = z[c][j];
+          }
         }
-      }
-      bool ok = box_ok<NX>(a.safety, z);
-      if constexpr (B::TRACK) {
-        if (a.safety.has_track) {  // uniform over the grid
-          const bool on_road = track_ok<L>(a.safety.track, tv, z[0], z[1], q, alive && ok);
-          ok = ok && on_road;
+        bool ok = box_ok<NX>(a.safety, z[c]);
+        if constexpr (B::TRACK) {
+          if (a.safety.has_track) {  // uniform over the grid
+            const bool on_road =
+                track_ok<L>(a.safety.track, tv, z[c][0], z[c][1], q, alive[c] && ok);
+            ok = ok && on_road;
+          }
         }
+        if (alive[c]) {
+          if (ok) ttv[c] = t;
+          else alive[c] = false;
+        }
+        any_alive = any_alive || alive[c];
       }
-      if (alive) {
-        if (ok) ttv = t;
-        else alive = false;
-      }
-      if (!__any_sync(kFull, alive)) break;
+      if (!__any_sync(kFull, any_alive)) break;
     }
 
-    if (valid) {
-      // selection key: (H - ttv) | cost bits | slot -> lexicographic minimum
-      const unsigned long long key = ((unsigned long long)(H - ttv) << 55) |
-                                     ((unsigned long long)__float_as_uint(cost) << 23) |
-                                     (unsigned long long)slot;
-      best = key < best ? key : best;
-      if (q == 0) {
-        n_exec += (unsigned int)min(ttv + 1, H);
-        n_safe += ttv == H;
-        if (a.ttv_out) a.ttv_out[slot] = ttv;
-        if (a.cost_out) a.cost_out[slot] = cost;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      if (valid[c]) {
+        // selection key: (H - ttv) | cost bits | slot -> lexicographic minimum
+        const unsigned long long key = ((unsigned long long)(H - ttv[c]) << 55) |
+                                       ((unsigned long long)__float_as_uint(cost[c]) << 23) |
+                                       (unsigned long long)slot[c];
+        best = key < best ? key : best;
+        if (q == 0) {
+          n_exec += (unsigned int)min(ttv[c] + 1, H);
+          n_safe += ttv[c] == H;
+          if (a.ttv_out) a.ttv_out[slot[c]] = ttv[c];
+          if (a.cost_out) a.cost_out[slot[c]] = cost[c];
+        }
       }
     }
   }
@@ -365,30 +452,30 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    unsigned long long k = ~0ull, c = 0ull;
+    unsigned long long k = ~0ull, cc = 0ull;
     for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
       const unsigned long long kb = *reinterpret_cast<volatile unsigned long long*>(pk + b);
       k = kb < k ? kb : k;
-      c += *reinterpret_cast<volatile unsigned long long*>(pc + b);
+      cc += *reinterpret_cast<volatile unsigned long long*>(pc + b);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long other = __shfl_xor_sync(kFull, k, o);
       k = other < k ? other : k;
-      c += __shfl_xor_sync(kFull, c, o);
+      cc += __shfl_xor_sync(kFull, cc, o);
     }
     __syncthreads();
     if (lane == 0) {
       s_key[warp] = k;
-      s_cnt[warp] = c;
+      s_cnt[warp] = cc;
     }
     __syncthreads();
     if (tid == 0) {
       for (int w = 1; w < wpb; ++w) {
         k = s_key[w] < k ? s_key[w] : k;
-        c += s_cnt[w];
+        cc += s_cnt[w];
       }
-      write_result<NU>(a, k, c, uh);
+      write_result<NU>(a, k, cc, uh);
       *blocks_done = 0ull;
     }
     return;
@@ -413,26 +500,7 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
     TickScratch* sc = a.scratch;
     const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&sc->key);
     const unsigned long long cnt = *reinterpret_cast<volatile unsigned long long*>(&sc->counts);
-    const int pick = (int)(k & 0x7FFFFFull);
-    const int hm = (int)(k >> 55);
-    mpmi_result r;
-    float xb[NU];
-    candidate_value<NU>(a, pick, uh, xb);
-#pragma unroll
-    for (int j = 0; j < MPMI_MAX_NU; ++j) r.u_r[j] = 0.0;
-#pragma unroll
-    for (int j = 0; j < NU; ++j)
-      r.u_r[j] = (a.include_user && pick == 0) ? a.u_h[j] : (double)xb[j];
-    r.index = pick;
-    r.status = hm == 0 ? MPMI_SAFE : MPMI_FALLBACK;
-    r.n_safe = (int32_t)(cnt >> 40);
-    r.ttv = H - hm;
-    r.cost = __uint_as_float((unsigned int)((k >> 23) & 0xFFFFFFFFull));
-    r.n_slots = a.n_slots;
-    r.executed_steps = cnt & ((1ull << 40) - 1);
-    r.tick = a.tick;
-    r.reserved = 0;
-    *a.result = r;
+    write_result<NU>(a, k, cnt, uh);
     sc->key = ~0ull;
     sc->counts = 0ull;
     sc->done = 0u;

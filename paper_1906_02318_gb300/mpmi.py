@@ -47,7 +47,7 @@ class SessionConfig(ctypes.Structure):
     _fields_ = [("n_samples", c_i32), ("horizon", c_i32), ("include_user", c_i32),
                 ("sampler", c_i32), ("input_lo", c_dbl * MAX_NU), ("input_hi", c_dbl * MAX_NU),
                 ("seed", c_u64), ("stream_id", c_u32), ("lanes", c_i32), ("block", c_i32),
-                ("pad0", c_i32)]
+                ("cands_per_thread", c_i32)]
 
 
 class Result(ctypes.Structure):
@@ -79,7 +79,8 @@ _SIGNATURES = {
     "mpmi_session_open": (c_i32, [c_vp, c_vp, ctypes.POINTER(SessionConfig),
                                   ctypes.POINTER(c_vp)]),
     "mpmi_session_close": (None, [c_vp]),
-    "mpmi_session_launch_shape": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
+    "mpmi_session_launch_shape": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32),
+                                          ctypes.POINTER(c_i32)]),
     "mpmi_evaluate_candidates": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
     "mpmi_select_input": (c_i32, [c_vp, ctypes.POINTER(Result)]),
     "mpmi_evaluate_candidates_device": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp, c_vp,
@@ -280,7 +281,8 @@ class Session:
 
     def __init__(self, ctx: Context, model: Model, n_samples: int, horizon: int,
                  input_lo, input_hi, include_user: bool = True, sampler: str = "uniform",
-                 seed: int = 0, stream_id: int = 0, lanes: int = 0, block: int = 0):
+                 seed: int = 0, stream_id: int = 0, lanes: int = 0, block: int = 0,
+                 cands: int = 0):
         cfg = SessionConfig()
         cfg.n_samples, cfg.horizon = n_samples, horizon
         cfg.include_user = int(include_user)
@@ -290,6 +292,7 @@ class Session:
             cfg.input_lo[j] = lo[j] if j < lo.size else 0.0
             cfg.input_hi[j] = hi[j] if j < hi.size else 1.0
         cfg.seed, cfg.stream_id, cfg.lanes, cfg.block = seed, stream_id, lanes, block
+        cfg.cands_per_thread = cands
         h = c_vp()
         _check(ctx.lib.mpmi_session_open(ctx.handle, model.handle, ctypes.byref(cfg),
                                          ctypes.byref(h)))
@@ -300,10 +303,11 @@ class Session:
         self.n = model.get_operator().shape[0]
 
     def launch_shape(self):
-        lanes, block = c_i32(), c_i32()
+        """(lanes per candidate, candidates per thread, threads per block)."""
+        lanes, cands, block = c_i32(), c_i32(), c_i32()
         _check(self.ctx.lib.mpmi_session_launch_shape(self.handle, ctypes.byref(lanes),
-                                                      ctypes.byref(block)))
-        return lanes.value, block.value
+                                                      ctypes.byref(cands), ctypes.byref(block)))
+        return lanes.value, cands.value, block.value
 
     def close(self):
         if self.handle:

@@ -32,6 +32,7 @@ def main():
     ap.add_argument("--ticks", type=int, default=20)
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--cands", type=int, default=0, help="candidates per thread (one lane)")
     ap.add_argument("--flush", action="store_true", help="write 256 MB before each tick")
     args = ap.parse_args()
 
@@ -56,7 +57,7 @@ def main():
         states = x0[None, :] + jit
     uhs = data.ou_user_input(2, args.ticks, 0.01, lo, hi)
     sess = lib.Session(ctx, model, args.n, args.horizon, lo, hi, seed=2, lanes=args.lanes,
-                       block=args.block)
+                       block=args.block, cands=args.cands)
     dev = torch.device("cuda")
     xs = torch.tensor(states, dtype=torch.float64, device=dev)
     us = torch.tensor(uhs, dtype=torch.float64, device=dev)
@@ -74,10 +75,10 @@ def main():
     torch.cuda.synchronize()
     ms = np.array([a.elapsed_time(b) for a, b in zip(e0, e1)])
     ex = [lib.result_from_bytes(r, sess.nu)["executed_steps"] for r in res.cpu().numpy()]
-    lanes, block = sess.launch_shape()
+    lanes, cands, block = sess.launch_shape()
     n = 12 if args.basis == "bot" else 32
     fl = np.mean(ex) * 2 * n * n
-    print(f"{args.basis} N={args.n} H={args.horizon} lanes={lanes} block={block} "
+    print(f"{args.basis} N={args.n} H={args.horizon} lanes={lanes} cands={cands} block={block} "
           f"ticks={args.ticks} mean_us={ms[1:].mean() * 1e3 if len(ms) > 1 else ms[0] * 1e3:.2f} "
           f"min_us={ms.min() * 1e3:.2f} executed={np.mean(ex):.0f} "
           f"nominal={(args.n + 1) * args.horizon} "

@@ -40,9 +40,10 @@ def car(lib, ctx):
 
 
 def _tick(lib, ctx, env, model, x_t, u_h, N, H, seed=1, stream=0, tick=0, lanes=0,
-          include_user=True, sampler="uniform", block=0, traj=True):
+          include_user=True, sampler="uniform", block=0, traj=True, cands=0):
     sess = lib.Session(ctx, model, N, H, env.lo, env.hi, include_user=include_user,
-                       sampler=sampler, seed=seed, stream_id=stream, lanes=lanes, block=block)
+                       sampler=sampler, seed=seed, stream_id=stream, lanes=lanes, block=block,
+                       cands=cands)
     try:
         g = run_gpu(lib, sess, x_t, u_h, tick=tick, traj=traj)
     finally:
@@ -104,15 +105,16 @@ def test_bot_single_tick_paper_scale(lib, ctx, bot, lanes):
     assert g["result"]["index"] == o.index
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4])
+@pytest.mark.parametrize("lanes,cands", [(1, 1), (1, 2), (2, 1), (4, 1)])
 @pytest.mark.parametrize("N", [1, 31, 1000, 3001])
-def test_bot_states_ragged(lib, ctx, bot, lanes, N):
+def test_bot_states_ragged(lib, ctx, bot, lanes, cands, N):
     env, model = bot
     states = data.states_in_box(11, 6, [-0.45, -1.5, -1.8, -1.5], [0.45, 1.5, 1.8, 1.5])
     excused = 0
     for k, x_t in enumerate(states):
         u_h = data.to_f32_exact(data.user_input_once(100 + k, env.lo, env.hi))
-        g, o = _tick(lib, ctx, env, model, x_t, u_h, N, 50, seed=k, tick=k, lanes=lanes)
+        g, o = _tick(lib, ctx, env, model, x_t, u_h, N, 50, seed=k, tick=k, lanes=lanes,
+                     cands=cands)
         excused += compare(g, o, env, 50)
     assert excused <= max(2, 0.002 * N * len(states))
 
@@ -138,15 +140,16 @@ def test_bot_inflated_barrier(lib, ctx):
 
 
 # ------------------------------------------------------------------- race car
-@pytest.mark.parametrize("lanes", [8, 16])
-def test_car_ticks(lib, ctx, car, lanes):
+@pytest.mark.parametrize("lanes,cands", [(1, 1), (1, 2), (8, 1), (16, 1)])
+def test_car_ticks(lib, ctx, car, lanes, cands):
     env, model = car
     x0 = data.car_start_state(env.track, vx=14.0)
     states = [x0, x0 + np.array([1.5, -1.0, 0.1, 4.0, 0.3, 0.2]),
               x0 + np.array([-2.0, 2.5, -0.2, -6.0, -0.2, -0.1])]
     for k, x_t in enumerate(states):
         u_h = data.to_f32_exact(data.user_input_once(300 + k, env.lo, env.hi))
-        g, o = _tick(lib, ctx, env, model, x_t, u_h, 2047, 60, seed=3, tick=k, lanes=lanes)
+        g, o = _tick(lib, ctx, env, model, x_t, u_h, 2047, 60, seed=3, tick=k, lanes=lanes,
+                     cands=cands)
         assert compare(g, o, env, 60) <= 10
 
 
@@ -304,6 +307,8 @@ def test_session_argument_checks(lib, ctx, bot):
             lib.Session(ctx, model, kw.pop("n_samples"), kw.pop("horizon"), env.lo, env.hi, **kw)
     with pytest.raises(lib.MpmiError):
         lib.Session(ctx, model, 10, 5, [0.5], [-0.5])     # empty input box
+    with pytest.raises(lib.MpmiError):
+        lib.Session(ctx, model, 10, 5, env.lo, env.hi, lanes=2, cands=2)  # not compiled
 
 
 def test_grid_needs_a_perfect_power(lib, ctx, car):
