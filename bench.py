@@ -358,6 +358,23 @@ def run_gpu(args, rank, world):
                 gpu_name=props.name)
 
 
+def max_over_ranks(values, world: int, device: str = "cpu"):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the job time)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_throughput(world: int, steps_per_rank: int, units_per_step: int, t_max: float) -> float:
+    """Whole-job rate: every rank processed steps_per_rank steps of units_per_step units
+    (weak scaling, independent replicas) within the slowest rank's time."""
+    return world * steps_per_rank * units_per_step / t_max
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,19 +408,11 @@ def main():
     out = run_gpu(args, rank, world)
 
     n_step = (N_SAMPLES + 1) * HORIZON
-    t_rank = out["dev_time"]
-    e2e_t = float(out["lat"].sum())
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        tt = torch.tensor([t_rank, e2e_t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max, e2e_max = float(tt[0]), float(tt[1])
-    else:
-        t_max, e2e_max = t_rank, e2e_t
     K = args.steps
-    value = world * K * n_step / t_max
-    e2e_value = world * len(out["lat"]) * n_step / e2e_max
+    t_max, e2e_max = max_over_ranks([out["dev_time"], float(out["lat"].sum())], world,
+                                    device="cuda")
+    value = job_throughput(world, K, n_step, t_max)
+    e2e_value = job_throughput(world, len(out["lat"]), n_step, e2e_max)
 
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
