@@ -129,3 +129,16 @@ def states_in_box(seed: int, count: int, lo, hi) -> np.ndarray:
 def to_f32_exact(a) -> np.ndarray:
     """Round to binary32 and return as float64 (values both sides can hold exactly)."""
     return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def screener_init(seed: int, hidden: int = 128, n_in: int = 12) -> dict:
+    """Initial weights of the learned screener (He-normal, zero biases), float32
+    values held in float64 so both implementations start from the same numbers."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    f32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)  # noqa: E731
+    return {"W1": f32(rng.normal(0.0, np.sqrt(2.0 / n_in), (hidden, n_in))),
+            "b1": np.zeros(hidden),
+            "W2": f32(rng.normal(0.0, np.sqrt(2.0 / hidden), (hidden, hidden))),
+            "b2": np.zeros(hidden),
+            "w3": f32(rng.normal(0.0, np.sqrt(1.0 / hidden), hidden)),
+            "b3": np.zeros(())}
