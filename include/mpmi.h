@@ -239,6 +239,65 @@ int mpmi_debug_trajectories(mpmi_session* s, const double* x_t_dev,
                             int32_t* ttv_dev, float* cost_dev, float* traj_dev,
                             void* stream);
 
+/* ---- learned candidate screener (not in the paper) ----------------------- */
+/* A small network (12 -> 128 -> 128 -> 1, tanh-form GELU, sigmoid output) that
+ * predicts, for the race car, each candidate's normalised time to violation
+ * ttv / H from the state, the track ahead and the candidate, so that only the
+ * most promising candidates go through the exact rollout.  Inputs: the signed
+ * lateral offset from the nearest centre-line segment / half width, sin and cos
+ * of the heading error, vx / 25, vy / 5, omega / 2, 10 x the curvature at the
+ * first vertex 5, 10, 20, 40 m ahead, delta / 0.4 and the throttle.  Weights
+ * are float32 (training, on the GPU with this library's own forward and
+ * backward kernels) with a bfloat16 copy for tensor-core inference.  Packed
+ * weight layout (float32, MPMI_SCREENER_PARAMS values): W1 (128 x 12, row-major),
+ * b1 (128), W2 (128 x 128), b2 (128), w3 (128), b3 (1). */
+#define MPMI_SCREENER_PARAMS 18305
+#define MPMI_SCREENER_INPUTS 12
+typedef struct mpmi_screener mpmi_screener;
+
+/* A screener for a race-car model whose safety set has a track (the features
+ * use the track).  weights: host, packed initial weights.  max_batch bounds the
+ * training minibatch; max_slots bounds the candidate slots of screened ticks. */
+int mpmi_screener_create(mpmi_ctx* ctx, const mpmi_model* model, const float* weights,
+                         int32_t max_batch, int32_t max_slots, mpmi_screener** out);
+void mpmi_screener_free(mpmi_screener* s);
+int mpmi_screener_get_weights(const mpmi_screener* s, float* weights_out);
+int mpmi_screener_set_weights(mpmi_screener* s, const float* weights);
+/* The 10 per-tick inputs of a state (device x_t_dev, 6 doubles -> out_dev). */
+int mpmi_screener_tick_features(mpmi_screener* s, const double* x_t_dev, float* out_dev,
+                                void* stream);
+/* The 12 inputs of every slot of a session's tick (slot order, slot 0 = u_h when
+ * included) -> out_dev (n_slots x 12 float32). */
+int mpmi_screener_features(mpmi_screener* s, mpmi_session* session, const double* x_t_dev,
+                           const double* u_h_dev, uint64_t tick, float* out_dev,
+                           void* stream);
+/* Mean squared error and its gradient (packed like the weights) on a minibatch:
+ * features (batch x 12) and targets (batch, in [0, 1]), all device float32. */
+int mpmi_screener_gradients(mpmi_screener* s, const float* features_dev,
+                            const float* targets_dev, int32_t batch, float* grad_dev,
+                            float* loss_dev, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on a minibatch; *loss_dev gets
+ * the minibatch loss before the step. */
+int mpmi_screener_train_step(mpmi_screener* s, const float* features_dev,
+                             const float* targets_dev, int32_t batch, float lr,
+                             float* loss_dev, void* stream);
+/* Network output (sigmoid, predicted ttv / H) for feature rows, computed with
+ * bfloat16 weights and activations on tensor cores with float32 accumulation. */
+int mpmi_screener_score(mpmi_screener* s, const float* features_dev, int32_t batch,
+                        float* scores_dev, void* stream);
+/* A screened tick: score every slot of the session's tick, keep the slots whose
+ * (score < tau, cost) key falls at or below the histogram bin where k slots are
+ * reached (slot 0, the user's input, is always kept), run the exact rollout on
+ * those, and -- on the device, with no host round trip -- fall back to the full
+ * evaluation when none of them is safe.  result_dev's reserved word carries
+ * flags: bit 0 the screened set was evaluated, bit 1 the full evaluation ran.
+ * list_dev (optional, n_slots int32) receives the screened slots and
+ * n_list_dev (optional, one int32) their number. */
+int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double* x_t_dev,
+                           const double* u_h_dev, uint64_t tick, int32_t k, float tau,
+                           mpmi_result* result_dev, int32_t* list_dev, int32_t* n_list_dev,
+                           void* stream);
+
 /* ---- a tick that allocates nothing -------------------------------------- */
 /* The paper has no counterpart to this entry point; it serves callers that may
  * not allocate device memory while they run: a hard real-time control loop that

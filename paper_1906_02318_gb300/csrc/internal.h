@@ -65,6 +65,13 @@ struct TickArgs {
   // counts [cap, 2 cap), block counter at [2 cap]
   unsigned long long* partials;
   int partials_cap;
+  // screened ticks: evaluate only the slots slot_list[0 .. *n_list) (device);
+  // skip the whole launch when *skip_if_safe already holds a SAFE result;
+  // result_flags is stored in the result's reserved word
+  const int* slot_list;
+  const int* n_list;
+  const mpmi_result* skip_if_safe;
+  unsigned long long result_flags;
 };
 
 }  // namespace mpmi
@@ -109,6 +116,9 @@ struct mpmi_session {
 };
 
 namespace mpmi {
+// tick launch helpers shared by the API and the screener (mpmi_api.cu)
+TickArgs make_tick_args(const mpmi_session* s, uint64_t tick);
+int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint);
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
 // host helpers implemented in fit.cpp / track.cpp

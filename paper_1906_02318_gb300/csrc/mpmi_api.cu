@@ -122,7 +122,7 @@ static void default_shape(int kind, int n_slots, int sms, int* lanes, int* cands
   }
 }
 
-static TickArgs make_args(const mpmi_session* s, uint64_t tick) {
+TickArgs make_tick_args(const mpmi_session* s, uint64_t tick) {
   const mpmi_model* m = s->model;
   TickArgs a;
   memset(&a, 0, sizeof(a));
@@ -153,7 +153,7 @@ static TickArgs make_args(const mpmi_session* s, uint64_t tick) {
 
 // Persistent grid: no more blocks than are resident at once, and no more than
 // the warp-tiles need.  Occupancy is cached per dynamic shared-memory size.
-static int launch(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st) {
+int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint) {
   TickKernel k = pick_tick(s->model->kind, s->lanes, s->cands, traj);
   if (!k.fn) return fail(MPMI_E_UNSUPPORTED, "tick kernel not compiled for this launch shape");
   const size_t smem = k.k_smem + (a.safety.has_track ? (size_t)a.safety.track.blob_bytes : 0);
@@ -173,7 +173,8 @@ static int launch(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st) {
   }
   const int wpb = s->block / 32;
   const int per_warp = 32 / s->lanes * s->cands;
-  const int n_wtiles = (s->n_slots + per_warp - 1) / per_warp;
+  const int n_work = (n_hint > 0 && n_hint < s->n_slots) ? n_hint : s->n_slots;
+  const int n_wtiles = (n_work + per_warp - 1) / per_warp;
   int grid = (n_wtiles + wpb - 1) / wpb;
   if (grid > s->max_grid[t]) grid = s->max_grid[t];
   k.launch(a, grid, s->block, smem, st);
@@ -569,12 +570,12 @@ int mpmi_evaluate_candidates(mpmi_session* s, const double* x_t, const double* u
   memcpy(s->in_host + 8, u_h, sizeof(double) * m->nu);
   MPMI_CUDA(cudaMemcpyAsync(s->in_dev, s->in_host, 12 * sizeof(double), cudaMemcpyHostToDevice, st),
             "copy x_t/u_h to the device");
-  TickArgs a = make_args(s, tick);
+  TickArgs a = make_tick_args(s, tick);
   a.x_t = s->in_dev;
   a.u_h = s->in_dev + 8;
   a.ext = candidates_dev;
   a.result = s->result_dev;
-  if ((rc = launch(s, a, false, st)) != MPMI_OK) return rc;
+  if ((rc = launch_tick_args(s, a, false, st, 0)) != MPMI_OK) return rc;
   MPMI_CUDA(cudaMemcpyAsync(s->result_host, s->result_dev, sizeof(mpmi_result),
                             cudaMemcpyDeviceToHost, st), "copy the result to the host");
   MPMI_CUDA(cudaEventRecord(s->done, st), "cudaEventRecord");
@@ -601,7 +602,7 @@ static int evaluate_device(mpmi_session* s, const double* x_t_dev, const double*
   if ((rc = check_ext(s, candidates_dev)) != MPMI_OK) return rc;
   DeviceGuard guard(s->ctx->device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
-  TickArgs a = make_args(s, tick);
+  TickArgs a = make_tick_args(s, tick);
   a.x_t = x_t_dev;
   a.u_h = u_h_dev;
   a.ext = candidates_dev;
@@ -609,7 +610,7 @@ static int evaluate_device(mpmi_session* s, const double* x_t_dev, const double*
   a.ttv_out = ttv_dev;
   a.cost_out = cost_dev;
   a.traj_out = traj_dev;
-  return launch(s, a, traj_dev != nullptr, (cudaStream_t)stream);
+  return launch_tick_args(s, a, traj_dev != nullptr, (cudaStream_t)stream, 0);
 }
 
 int mpmi_evaluate_candidates_device(mpmi_session* s, const double* x_t_dev, const double* u_h_dev,
@@ -637,7 +638,7 @@ int mpmi_sample_candidates(mpmi_session* s, const double* u_h_dev, const float* 
   if ((rc = check_ext(s, candidates_dev)) != MPMI_OK) return rc;
   DeviceGuard guard(s->ctx->device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
-  TickArgs a = make_args(s, tick);
+  TickArgs a = make_tick_args(s, tick);
   a.u_h = u_h_dev;
   a.ext = candidates_dev;
   const int block = 256, grid = (s->n_slots + block - 1) / block;

@@ -1,0 +1,862 @@
+// Learned candidate screener (not in the paper): training kernels (float32),
+// tensor-core inference (bfloat16 mma.sync, float32 accumulation), per-tick track
+// features, and the screened tick (score -> threshold -> compaction -> exact
+// rollout on the kept slots -> on-device fallback to the full evaluation).
+//
+// Network: 12 -> 128 -> 128 -> 1, GELU in its tanh form (Hendrycks & Gimpel),
+// sigmoid output trained on ttv / H with the mean squared error and Adam.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "tick_kernel.cuh"
+
+namespace mpmi {
+
+constexpr int kH = 128, kIn = 12, kInP = 16, kW2S = 136;
+constexpr int oW1 = 0, ob1 = kH * kIn, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, ow3 = ob2 + kH,
+              ob3 = ow3 + kH, kP = ob3 + 1;
+static_assert(kP == MPMI_SCREENER_PARAMS, "packed weight layout");
+constexpr int kBins = 2048;  // histogram of (predicted unsafe, cost) keys: key >> 21
+constexpr float kGeluC = 0.7978845608028654f, kGeluA = 0.044715f;
+
+// bfloat16 inference copy of the weights (W1 padded to 16 inputs, W2 rows padded to
+// 136 so the B-fragment loads of a warp hit 32 different banks)
+struct InferW {
+  __nv_bfloat16 W1[kH * kInP];
+  __nv_bfloat16 W2[kH * kW2S];
+  float b1[kH], b2[kH], w3[kH];
+  float b3, pad[3];
+};
+static_assert(sizeof(InferW) % 16 == 0, "InferW is staged with 16-byte copies");
+
+struct ScreenScratch {
+  unsigned int hist[kBins];
+  unsigned int done;  // score blocks finished
+  int bstar;          // threshold bin
+  int n_list;         // kept slots
+  int pad;
+};
+
+// ---------------------------------------------------------------- float32 training
+__device__ __forceinline__ float gelu_f(float z) {
+  return 0.5f * z * (1.f + tanhf(kGeluC * (z + kGeluA * z * z * z)));
+}
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  const float t = tanhf(kGeluC * (z + kGeluA * z * z * z));
+  return 0.5f * (1.f + t) + 0.5f * z * (1.f - t * t) * kGeluC * (1.f + 3.f * kGeluA * z * z);
+}
+
+// Forward pass, one sample per thread; activations stored feature-major ([unit][B])
+// so consecutive threads write consecutive addresses.  "aug" arrays carry a final
+// row of ones, which turns the bias gradients into one more column of the GEMMs.
+__global__ void __launch_bounds__(128) mlp_forward(const float* __restrict__ P,
+                                                   const float* __restrict__ feats, int B,
+                                                   float* faug, float* z1, float* h1aug,
+                                                   float* z2, float* h2aug, float* y) {
+  extern __shared__ float sP[];
+  for (int i = threadIdx.x; i < kP; i += blockDim.x) sP[i] = P[i];
+  __syncthreads();
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  float f[kIn];
+#pragma unroll
+  for (int k = 0; k < kIn; ++k) {
+    f[k] = feats[(size_t)b * kIn + k];
+    faug[(size_t)k * B + b] = f[k];
+  }
+  faug[(size_t)kIn * B + b] = 1.f;
+  float h1[kH];
+#pragma unroll
+  for (int j = 0; j < kH; ++j) {
+    float z = sP[ob1 + j];
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) z = fmaf(sP[oW1 + j * kIn + k], f[k], z);
+    z1[(size_t)j * B + b] = z;
+    h1[j] = gelu_f(z);
+    h1aug[(size_t)j * B + b] = h1[j];
+  }
+  h1aug[(size_t)kH * B + b] = 1.f;
+  float z3 = sP[ob3];
+  for (int j = 0; j < kH; ++j) {
+    float z = sP[ob2 + j];
+#pragma unroll
+    for (int k = 0; k < kH; ++k) z = fmaf(sP[oW2 + j * kH + k], h1[k], z);
+    z2[(size_t)j * B + b] = z;
+    const float h = gelu_f(z);
+    h2aug[(size_t)j * B + b] = h;
+    z3 = fmaf(sP[ow3 + j], h, z3);
+  }
+  h2aug[(size_t)kH * B + b] = 1.f;
+  y[b] = 1.f / (1.f + expf(-z3));
+}
+
+// Backward pass to the pre-activation deltas; accumulates the mean squared error.
+__global__ void __launch_bounds__(128) mlp_backward(const float* __restrict__ P,
+                                                    const float* __restrict__ target, int B,
+                                                    const float* z1, const float* z2,
+                                                    const float* y, float* d1, float* d2,
+                                                    float* d3, float* loss) {
+  extern __shared__ float sW[];  // W2 (kH x kH) then w3 (kH)
+  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) sW[i] = P[oW2 + i];
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) sW[kH * kH + i] = P[ow3 + i];
+  __shared__ float s_loss[4];
+  __syncthreads();
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  float sq = 0.f;
+  if (b < B) {
+    const float yv = y[b], t = target[b];
+    const float dz3 = (2.f / (float)B) * (yv - t) * yv * (1.f - yv);
+    sq = (yv - t) * (yv - t) / (float)B;
+    d3[b] = dz3;
+    float dv[kH];
+#pragma unroll
+    for (int j = 0; j < kH; ++j) {
+      dv[j] = dz3 * sW[kH * kH + j] * gelu_grad_f(z2[(size_t)j * B + b]);
+      d2[(size_t)j * B + b] = dv[j];
+    }
+    for (int k = 0; k < kH; ++k) {
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < kH; ++j) acc = fmaf(sW[j * kH + k], dv[j], acc);
+      d1[(size_t)k * B + b] = acc * gelu_grad_f(z1[(size_t)k * B + b]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_loss[w];
+    atomicAdd(loss, s);
+  }
+}
+
+// C[m][n] = sum_b A[m][b] Bm[n][b]  (A: M x K, Bm: N x K, both row-major over b).
+__global__ void __launch_bounds__(256) gemm_nt(const float* __restrict__ A, int M,
+                                               const float* __restrict__ Bm, int N, int K,
+                                               float* C) {
+  __shared__ float sA[32][33], sB[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      const int m = m0 + r, n = n0 + r, k = k0 + tx;
+      sA[r][tx] = (m < M && k < K) ? A[(size_t)m * K + k] : 0.f;
+      sB[r][tx] = (n < N && k < K) ? Bm[(size_t)n * K + k] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const float bv = sB[tx][kk];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] = fmaf(sA[ty + 8 * i][kk], bv, acc[i]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 8 * i, n = n0 + tx;
+    if (m < M && n < N) C[(size_t)m * N + n] = acc[i];
+  }
+}
+
+// Packs the three gradient GEMM outputs into the weight layout.
+__global__ void pack_grad(const float* dW1a, const float* dW2a, const float* dw3a, float* g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kP) return;
+  float v;
+  if (i < ob1) v = dW1a[(i / kIn) * (kIn + 1) + i % kIn];
+  else if (i < oW2) v = dW1a[(i - ob1) * (kIn + 1) + kIn];
+  else if (i < ob2) v = dW2a[((i - oW2) / kH) * (kH + 1) + (i - oW2) % kH];
+  else if (i < ow3) v = dW2a[(i - ob2) * (kH + 1) + kH];
+  else if (i < ob3) v = dw3a[i - ow3];
+  else v = dw3a[kH];
+  g[i] = v;
+}
+
+__global__ void adam(float* P, const float* g, float* m, float* v, float lr, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kP) return;
+  const float gi = g[i];
+  const float mi = 0.9f * m[i] + 0.1f * gi;
+  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+__global__ void to_infer(const float* P, InferW* w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kH * kInP) {
+    const int j = i / kInP, k = i % kInP;
+    w->W1[i] = __float2bfloat16_rn(k < kIn ? P[oW1 + j * kIn + k] : 0.f);
+  }
+  if (i < kH * kW2S) {
+    const int j = i / kW2S, k = i % kW2S;
+    w->W2[i] = __float2bfloat16_rn(k < kH ? P[oW2 + j * kH + k] : 0.f);
+  }
+  if (i < kH) {
+    w->b1[i] = P[ob1 + i];
+    w->b2[i] = P[ob2 + i];
+    w->w3[i] = P[ow3 + i];
+  }
+  if (i == 0) w->b3 = P[ob3];
+}
+
+// ---------------------------------------------------------------- inference (tensor cores)
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float gelu_fast(float z) {
+  return 0.5f * z * (1.f + tanh_approx(kGeluC * (z + kGeluA * z * z * z)));
+}
+
+// Scores 16 rows (one mma M tile) per call.  Lane l holds rows g = l / 4 and g + 8
+// (f0, f1: their 12 inputs) and receives their sigmoid outputs in *y0, *y1 (valid
+// in lanes with l % 4 == 0).  Weights in shared memory (sw).
+__device__ __forceinline__ void mlp_tile(const InferW* sw, const float* f0, const float* f1,
+                                         float* y0, float* y1) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  uint32_t a[4];
+  auto in = [&](const float* f, int k) { return k < kIn ? f[k] : 0.f; };
+  a[0] = pack_bf16(in(f0, 2 * q), in(f0, 2 * q + 1));
+  a[1] = pack_bf16(in(f1, 2 * q), in(f1, 2 * q + 1));
+  a[2] = pack_bf16(in(f0, 8 + 2 * q), in(f0, 9 + 2 * q));
+  a[3] = pack_bf16(in(f1, 8 + 2 * q), in(f1, 9 + 2 * q));
+  // layer 1: 16 n-tiles of 8 hidden units, one k step (16 padded inputs)
+  float c1[16][4];
+  const uint32_t* W1w = reinterpret_cast<const uint32_t*>(sw->W1);
+#pragma unroll
+  for (int nt = 0; nt < 16; ++nt) {
+    const int col = 8 * nt + 2 * q;
+    c1[nt][0] = sw->b1[col];
+    c1[nt][1] = sw->b1[col + 1];
+    c1[nt][2] = sw->b1[col];
+    c1[nt][3] = sw->b1[col + 1];
+    const int n = 8 * nt + g;
+    mma16816(c1[nt], a, W1w[(n * kInP + 2 * q) >> 1], W1w[(n * kInP + 8 + 2 * q) >> 1]);
+  }
+  // GELU, then the accumulator tiles become layer 2's A fragments
+  uint32_t a2[8][4];
+#pragma unroll
+  for (int kt = 0; kt < 8; ++kt) {
+    a2[kt][0] = pack_bf16(gelu_fast(c1[2 * kt][0]), gelu_fast(c1[2 * kt][1]));
+    a2[kt][1] = pack_bf16(gelu_fast(c1[2 * kt][2]), gelu_fast(c1[2 * kt][3]));
+    a2[kt][2] = pack_bf16(gelu_fast(c1[2 * kt + 1][0]), gelu_fast(c1[2 * kt + 1][1]));
+    a2[kt][3] = pack_bf16(gelu_fast(c1[2 * kt + 1][2]), gelu_fast(c1[2 * kt + 1][3]));
+  }
+  // layer 2 and the output unit
+  const uint32_t* W2w = reinterpret_cast<const uint32_t*>(sw->W2);
+  float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+  for (int nt = 0; nt < 16; ++nt) {
+    const int col = 8 * nt + 2 * q;
+    float c[4] = {sw->b2[col], sw->b2[col + 1], sw->b2[col], sw->b2[col + 1]};
+    const int n = 8 * nt + g;
+#pragma unroll
+    for (int kt = 0; kt < 8; ++kt)
+      mma16816(c, a2[kt], W2w[(n * kW2S + 16 * kt + 2 * q) >> 1],
+               W2w[(n * kW2S + 16 * kt + 8 + 2 * q) >> 1]);
+    const float w0 = sw->w3[col], w1 = sw->w3[col + 1];
+    p0 = fmaf(w0, gelu_fast(c[0]), fmaf(w1, gelu_fast(c[1]), p0));
+    p1 = fmaf(w0, gelu_fast(c[2]), fmaf(w1, gelu_fast(c[3]), p1));
+  }
+  p0 += __shfl_xor_sync(0xffffffffu, p0, 1);
+  p0 += __shfl_xor_sync(0xffffffffu, p0, 2);
+  p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
+  p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
+  *y0 = 1.f / (1.f + __expf(-(p0 + sw->b3)));
+  *y1 = 1.f / (1.f + __expf(-(p1 + sw->b3)));
+}
+
+__device__ void stage_weights(const InferW* w, InferW* sw) {
+  const uint4* src = reinterpret_cast<const uint4*>(w);
+  uint4* dst = reinterpret_cast<uint4*>(sw);
+  for (int i = threadIdx.x; i < (int)(sizeof(InferW) / 16); i += blockDim.x) dst[i] = src[i];
+}
+
+// Scores arbitrary feature rows (batch x 12).
+__global__ void __launch_bounds__(128) score_rows(const InferW* w, const float* feats, int B,
+                                                  float* out) {
+  extern __shared__ uint4 s_dyn[];
+  InferW* sw = reinterpret_cast<InferW*>(s_dyn);
+  stage_weights(w, sw);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  const int tiles = (B + 15) / 16;
+  for (int t = blockIdx.x * wpb + warp; t < tiles; t += gridDim.x * wpb) {
+    const int r0 = 16 * t + g, r1 = r0 + 8;
+    float f0[kIn], f1[kIn];
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) {
+      f0[k] = r0 < B ? feats[(size_t)r0 * kIn + k] : 0.f;
+      f1[k] = r1 < B ? feats[(size_t)r1 * kIn + k] : 0.f;
+    }
+    float y0, y1;
+    mlp_tile(sw, f0, f1, &y0, &y1);
+    if (q == 0) {
+      if (r0 < B) out[r0] = y0;
+      if (r1 < B) out[r1] = y1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- track features
+struct FeatureSrc {
+  DevTrack track;
+  const float* look;  // per segment start vertex: curvature 5, 10, 20, 40 m ahead
+  float half_width;
+};
+
+// The 10 per-tick inputs (plus the nearest segment and its distance) for the
+// state x_t, computed by the whole block; result in s_feat[0..12).
+__device__ void block_tick_features(const FeatureSrc& fs, const double* x_t, float* s_feat) {
+  __shared__ float s_d[32];
+  __shared__ int s_i[32];
+  const char* base = reinterpret_cast<const char*>(fs.track.blob);
+  const float4* seg = reinterpret_cast<const float4*>(base + fs.track.off_seg);
+  const float* inv = reinterpret_cast<const float*>(base + fs.track.off_inv);
+  const int S = (fs.track.off_inv - fs.track.off_seg) / 16;
+  const float px = (float)x_t[0], py = (float)x_t[1];
+  float best = INFINITY;
+  int bi = 0x7fffffff;
+  for (int i = threadIdx.x; i < S; i += blockDim.x) {
+    const float4 sg = seg[i];
+    const float rx = px - sg.x, ry = py - sg.y;
+    const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * inv[i], 0.f), 1.f);
+    const float ex = rx - t * sg.z, ey = ry - t * sg.w;
+    const float d2 = ex * ex + ey * ey;
+    if (d2 < best || (d2 == best && i < bi)) {
+      best = d2;
+      bi = i;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob < best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_d[warp] = best;
+    s_i[warp] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (s_d[w] < best || (s_d[w] == best && s_i[w] < bi)) {
+        best = s_d[w];
+        bi = s_i[w];
+      }
+    const float4 sg = seg[bi];
+    const float rx = px - sg.x, ry = py - sg.y;
+    const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * inv[bi], 0.f), 1.f);
+    const float len = sqrtf(sg.z * sg.z + sg.w * sg.w);
+    const float tx = sg.z / len, ty = sg.w / len;
+    const float ex = rx - t * sg.z, ey = ry - t * sg.w;
+    const float e_y = (ex * (-ty) + ey * tx) / fs.half_width;
+    float se, ce;
+    sincosf((float)x_t[2] - atan2f(ty, tx), &se, &ce);
+    s_feat[0] = e_y;
+    s_feat[1] = se;
+    s_feat[2] = ce;
+    s_feat[3] = (float)x_t[3] / 25.f;
+    s_feat[4] = (float)x_t[4] / 5.f;
+    s_feat[5] = (float)x_t[5] / 2.f;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) s_feat[6 + m] = 10.f * fs.look[4 * bi + m];
+    s_feat[10] = (float)bi;
+    s_feat[11] = sqrtf(best);
+  }
+  __syncthreads();
+}
+
+__global__ void tick_features(FeatureSrc fs, const double* x_t, float* out) {
+  __shared__ float s_feat[12];
+  block_tick_features(fs, x_t, s_feat);
+  if (threadIdx.x < 12) out[threadIdx.x] = s_feat[threadIdx.x];
+}
+
+// The 12 inputs of every slot of a tick (training data, parity).
+__global__ void slot_features(TickArgs a, FeatureSrc fs, float* out) {
+  __shared__ float s_feat[12];
+  block_tick_features(fs, a.x_t, s_feat);
+  float uh[2] = {__double2float_rn(a.u_h[0]), __double2float_rn(a.u_h[1])};
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < a.n_slots;
+       slot += gridDim.x * blockDim.x) {
+    float xi[2];
+    candidate_value<2>(a, slot, uh, xi);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) out[(size_t)slot * kIn + k] = s_feat[k];
+    out[(size_t)slot * kIn + 10] = xi[0] / 0.4f;
+    out[(size_t)slot * kIn + 11] = xi[1];
+  }
+}
+
+// ---------------------------------------------------------------- screened tick
+// Scores every slot, writes its key ((score < tau) << 31 | cost bits >> 1; slot 0,
+// the user's input, gets key 0 so it is always kept) and builds the histogram of
+// key >> 21.  The last block finds the smallest bin where k slots are reached,
+// clears the histogram and the list counter for the next tick.
+__global__ void __launch_bounds__(128) screen_score(TickArgs a, FeatureSrc fs, const InferW* w,
+                                                   float tau, int k, unsigned int* keys,
+                                                   ScreenScratch* ss) {
+  extern __shared__ uint4 s_dyn[];
+  InferW* sw = reinterpret_cast<InferW*>(s_dyn);
+  __shared__ unsigned int s_hist[kBins];
+  __shared__ float s_feat[12];
+  __shared__ int s_last;
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
+  stage_weights(w, sw);
+  block_tick_features(fs, a.x_t, s_feat);  // ends with __syncthreads
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  float uh[2] = {__double2float_rn(a.u_h[0]), __double2float_rn(a.u_h[1])};
+  const int tiles = (a.n_slots + 15) / 16;
+  for (int t = blockIdx.x * wpb + warp; t < tiles; t += gridDim.x * wpb) {
+    const int r0 = 16 * t + g, r1 = r0 + 8;
+    float f0[kIn], f1[kIn], x0[2], x1[2];
+    candidate_value<2>(a, r0 < a.n_slots ? r0 : 0, uh, x0);
+    candidate_value<2>(a, r1 < a.n_slots ? r1 : 0, uh, x1);
+#pragma unroll
+    for (int m = 0; m < 10; ++m) f0[m] = f1[m] = s_feat[m];
+    f0[10] = x0[0] / 0.4f;
+    f0[11] = x0[1];
+    f1[10] = x1[0] / 0.4f;
+    f1[11] = x1[1];
+    float y0, y1;
+    mlp_tile(sw, f0, f1, &y0, &y1);
+    if (q == 0) {
+      const int rr[2] = {r0, r1};
+      const float yy[2] = {y0, y1};
+      const float* xx[2] = {x0, x1};
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int r = rr[e];
+        if (r >= a.n_slots) continue;
+        const float d0 = __fsub_rn(xx[e][0], uh[0]), d1 = __fsub_rn(xx[e][1], uh[1]);
+        const float cost = __fmaf_rn(d1, d1, __fmul_rn(d0, d0));
+        unsigned int key = (yy[e] < tau ? 0x80000000u : 0u) | (__float_as_uint(cost) >> 1);
+        if (a.include_user && r == 0) key = 0u;
+        keys[r] = key;
+        atomicAdd(&s_hist[key >> 21], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x)
+    if (s_hist[i]) atomicAdd(&ss->hist[i], s_hist[i]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&ss->done, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last block: inclusive scan of the histogram (one thread per 16 bins)
+  __shared__ unsigned int s_sum[128];
+  const int per = kBins / 128;
+  unsigned int local = 0;
+  if (threadIdx.x < 128)
+    for (int i = 0; i < per; ++i)
+      local += *reinterpret_cast<volatile unsigned int*>(&ss->hist[threadIdx.x * per + i]);
+  if (threadIdx.x < 128) s_sum[threadIdx.x] = local;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int cum = 0;
+    int bstar = kBins - 1;
+    bool found = false;
+    for (int c = 0; c < 128 && !found; ++c) {
+      if (cum + s_sum[c] >= (unsigned int)k) {
+        for (int i = 0; i < per; ++i) {
+          cum += *reinterpret_cast<volatile unsigned int*>(&ss->hist[c * per + i]);
+          if (cum >= (unsigned int)k) {
+            bstar = c * per + i;
+            found = true;
+            break;
+          }
+        }
+      } else {
+        cum += s_sum[c];
+      }
+    }
+    ss->bstar = bstar;
+    ss->n_list = 0;
+    ss->done = 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x) ss->hist[i] = 0;
+}
+
+// Keeps the slots whose key bin is at or below the threshold (warp-aggregated append).
+__global__ void screen_compact(const unsigned int* keys, int n_slots, ScreenScratch* ss,
+                               int* list) {
+  const int bstar = ss->bstar;
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_slots;
+       base += gridDim.x * blockDim.x) {
+    const int slot = base + lane;
+    const bool keep = slot < n_slots && (int)(keys[slot] >> 21) <= bstar;
+    const unsigned int m = __ballot_sync(0xffffffffu, keep);
+    int at = 0;
+    if (lane == 0 && m) at = atomicAdd(&ss->n_list, __popc(m));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (keep) list[at + __popc(m & ((1u << lane) - 1))] = slot;
+  }
+}
+
+}  // namespace mpmi
+
+// ---------------------------------------------------------------- host side
+struct mpmi_screener {
+  mpmi_ctx* ctx = nullptr;
+  const mpmi_model* model = nullptr;
+  float *params = nullptr, *adam_m = nullptr, *adam_v = nullptr, *grad = nullptr;
+  int step = 0;
+  mpmi::InferW* infer = nullptr;
+  bool stale = true;
+  float* look = nullptr;
+  float half_width = 0.f;
+  int max_batch = 0, max_slots = 0;
+  float* act = nullptr;      // training activations
+  float* gemm_out = nullptr; // gradient GEMM outputs
+  unsigned int* keys = nullptr;
+  int* list = nullptr;
+  mpmi::ScreenScratch* ss = nullptr;
+  uint64_t bytes = 0;
+};
+
+namespace mpmi {
+
+static int cfail(cudaError_t e, const char* what) {
+  return fail(MPMI_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define SCR_CUDA(call, what)                       \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cfail(e_, what); \
+  } while (0)
+
+static FeatureSrc feature_src(const mpmi_screener* s) {
+  FeatureSrc fs;
+  fs.track = s->model->dev_safety.track;
+  fs.look = s->look;
+  fs.half_width = s->half_width;
+  return fs;
+}
+
+// Curvature ahead (float64 on the host): signed Menger curvature of every vertex
+// and, per vertex, the curvature at the first vertex 5, 10, 20, 40 m of arc ahead.
+static std::vector<float> lookahead(const std::vector<double>& xy) {
+  const int S = (int)xy.size() / 2;
+  std::vector<double> kappa(S), seg(S);
+  for (int i = 0; i < S; ++i) {
+    const int p = (i + S - 1) % S, n = (i + 1) % S;
+    const double ax = xy[2 * i] - xy[2 * p], ay = xy[2 * i + 1] - xy[2 * p + 1];
+    const double bx = xy[2 * n] - xy[2 * i], by = xy[2 * n + 1] - xy[2 * i + 1];
+    const double cx = xy[2 * n] - xy[2 * p], cy = xy[2 * n + 1] - xy[2 * p + 1];
+    const double cross = ax * by - ay * bx;
+    kappa[i] = 2.0 * cross / (sqrt(ax * ax + ay * ay) * sqrt(bx * bx + by * by) *
+                              sqrt(cx * cx + cy * cy));
+    seg[i] = sqrt(bx * bx + by * by);
+  }
+  const double ahead[4] = {5.0, 10.0, 20.0, 40.0};
+  std::vector<float> out(4 * (size_t)S);
+  for (int i = 0; i < S; ++i)
+    for (int m = 0; m < 4; ++m) {
+      double acc = 0.0;
+      int j = i;
+      do {
+        acc += seg[j % S];
+        ++j;
+      } while (acc < ahead[m]);
+      out[4 * (size_t)i + m] = (float)kappa[j % S];
+    }
+  return out;
+}
+
+static int refresh_infer(mpmi_screener* s, cudaStream_t st) {
+  if (!s->stale) return MPMI_OK;
+  to_infer<<<(kH * kW2S + 255) / 256, 256, 0, st>>>(s->params, s->infer);
+  SCR_CUDA(cudaGetLastError(), "to_infer launch");
+  s->stale = false;
+  return MPMI_OK;
+}
+
+static int gradients(mpmi_screener* s, const float* feats, const float* target, int B,
+                     float* grad, float* loss, cudaStream_t st) {
+  float* A = s->act;
+  const size_t Bz = (size_t)B;
+  float* faug = A;
+  float* z1 = faug + (kIn + 1) * Bz;
+  float* h1aug = z1 + kH * Bz;
+  float* z2 = h1aug + (kH + 1) * Bz;
+  float* h2aug = z2 + kH * Bz;
+  float* y = h2aug + (kH + 1) * Bz;
+  float* d1 = y + Bz;
+  float* d2 = d1 + kH * Bz;
+  float* d3 = d2 + kH * Bz;
+  float* dW2a = s->gemm_out;
+  float* dW1a = dW2a + kH * (kH + 1);
+  float* dw3a = dW1a + kH * (kIn + 1);
+  const int fwd_smem = kP * sizeof(float), bwd_smem = (kH * kH + kH) * sizeof(float);
+  SCR_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), st), "clear loss");
+  mlp_forward<<<(B + 127) / 128, 128, fwd_smem, st>>>(s->params, feats, B, faug, z1, h1aug, z2,
+                                                      h2aug, y);
+  mlp_backward<<<(B + 127) / 128, 128, bwd_smem, st>>>(s->params, target, B, z1, z2, y, d1, d2,
+                                                       d3, loss);
+  gemm_nt<<<dim3((kH + 1 + 31) / 32, kH / 32), 256, 0, st>>>(d2, kH, h1aug, kH + 1, B, dW2a);
+  gemm_nt<<<dim3((kIn + 1 + 31) / 32, kH / 32), 256, 0, st>>>(d1, kH, faug, kIn + 1, B, dW1a);
+  gemm_nt<<<dim3((kH + 1 + 31) / 32, 1), 256, 0, st>>>(d3, 1, h2aug, kH + 1, B, dw3a);
+  pack_grad<<<(kP + 255) / 256, 256, 0, st>>>(dW1a, dW2a, dw3a, grad);
+  SCR_CUDA(cudaGetLastError(), "screener gradient launches");
+  return MPMI_OK;
+}
+
+}  // namespace mpmi
+
+using namespace mpmi;
+
+extern "C" {
+
+int mpmi_screener_create(mpmi_ctx* ctx, const mpmi_model* model, const float* weights,
+                         int32_t max_batch, int32_t max_slots, mpmi_screener** out) {
+  if (!ctx || !model || !weights || !out) return fail(MPMI_E_INVALID_ARG, "screener: NULL argument");
+  *out = nullptr;
+  if (model->kind != kCar || !model->has_safety || !model->dev_safety.has_track)
+    return fail(MPMI_E_UNSUPPORTED, "screener: needs a race-car model with a track");
+  if (max_batch < 1 || max_slots < 1 || max_slots > MPMI_MAX_SLOTS)
+    return fail(MPMI_E_INVALID_ARG, "screener: max_batch and max_slots must be positive");
+  for (int i = 0; i < kP; ++i)
+    if (!isfinite(weights[i])) return fail(MPMI_E_NONFINITE, "screener: non-finite weight");
+  mpmi_screener* s = new mpmi_screener();
+  s->ctx = ctx;
+  s->model = model;
+  s->max_batch = max_batch;
+  s->max_slots = max_slots;
+  s->half_width = (float)(model->spec.track_half_width - model->spec.inflation);
+  std::vector<float> look = lookahead(model->track_host);
+  const size_t act_floats = (size_t)max_batch * (2 * (kIn + 1) + 4 * kH + 2 * (kH + 1) + 2);
+  const size_t gemm_floats = kH * (kH + 1) + kH * (kIn + 1) + (kH + 1);
+  const uint64_t bytes = 4 * kP * sizeof(float) + sizeof(InferW) + look.size() * sizeof(float) +
+                         act_floats * sizeof(float) + gemm_floats * sizeof(float) +
+                         (size_t)max_slots * (sizeof(unsigned int) + sizeof(int)) +
+                         sizeof(ScreenScratch);
+  if (ctx->budget && ctx->used + bytes > ctx->budget) {
+    delete s;
+    return fail(MPMI_E_OOM, "screener exceeds the memory budget");
+  }
+  bool ok = cudaMalloc(&s->params, kP * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&s->adam_m, kP * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&s->adam_v, kP * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&s->grad, kP * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&s->infer, sizeof(InferW)) == cudaSuccess &&
+            cudaMalloc(&s->look, look.size() * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&s->act, act_floats * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&s->gemm_out, gemm_floats * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&s->keys, (size_t)max_slots * sizeof(unsigned int)) == cudaSuccess &&
+            cudaMalloc(&s->list, (size_t)max_slots * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&s->ss, sizeof(ScreenScratch)) == cudaSuccess;
+  if (ok)
+    ok = cudaMemcpy(s->params, weights, kP * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(s->adam_m, 0, kP * sizeof(float)) == cudaSuccess &&
+         cudaMemset(s->adam_v, 0, kP * sizeof(float)) == cudaSuccess &&
+         cudaMemcpy(s->look, look.data(), look.size() * sizeof(float), cudaMemcpyHostToDevice) ==
+             cudaSuccess &&
+         cudaMemset(s->ss, 0, sizeof(ScreenScratch)) == cudaSuccess;
+  if (ok) {
+    const int fwd = kP * sizeof(float), bwd = (kH * kH + kH) * sizeof(float);
+    const int inf = (int)sizeof(InferW);
+    ok = cudaFuncSetAttribute(mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(mlp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(score_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, inf) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(screen_score, cudaFuncAttributeMaxDynamicSharedMemorySize, inf) ==
+             cudaSuccess;
+  }
+  if (!ok) {
+    mpmi_screener_free(s);
+    return fail(MPMI_E_OOM, "screener: device allocation failed");
+  }
+  s->bytes = bytes;
+  ctx->used += bytes;
+  *out = s;
+  return MPMI_OK;
+}
+
+void mpmi_screener_free(mpmi_screener* s) {
+  if (!s) return;
+  cudaFree(s->params);
+  cudaFree(s->adam_m);
+  cudaFree(s->adam_v);
+  cudaFree(s->grad);
+  cudaFree(s->infer);
+  cudaFree(s->look);
+  cudaFree(s->act);
+  cudaFree(s->gemm_out);
+  cudaFree(s->keys);
+  cudaFree(s->list);
+  cudaFree(s->ss);
+  if (s->ctx) s->ctx->used -= s->bytes;
+  delete s;
+}
+
+int mpmi_screener_get_weights(const mpmi_screener* s, float* out) {
+  if (!s || !out) return fail(MPMI_E_INVALID_ARG, "screener: NULL argument");
+  SCR_CUDA(cudaMemcpy(out, s->params, kP * sizeof(float), cudaMemcpyDeviceToHost), "read weights");
+  return MPMI_OK;
+}
+
+int mpmi_screener_set_weights(mpmi_screener* s, const float* w) {
+  if (!s || !w) return fail(MPMI_E_INVALID_ARG, "screener: NULL argument");
+  SCR_CUDA(cudaMemcpy(s->params, w, kP * sizeof(float), cudaMemcpyHostToDevice), "write weights");
+  SCR_CUDA(cudaMemset(s->adam_m, 0, kP * sizeof(float)), "reset Adam");
+  SCR_CUDA(cudaMemset(s->adam_v, 0, kP * sizeof(float)), "reset Adam");
+  s->step = 0;
+  s->stale = true;
+  return MPMI_OK;
+}
+
+int mpmi_screener_tick_features(mpmi_screener* s, const double* x_t_dev, float* out_dev,
+                                void* stream) {
+  if (!s || !x_t_dev || !out_dev) return fail(MPMI_E_INVALID_ARG, "screener: NULL argument");
+  tick_features<<<1, 256, 0, (cudaStream_t)stream>>>(feature_src(s), x_t_dev, out_dev);
+  SCR_CUDA(cudaGetLastError(), "tick_features launch");
+  return MPMI_OK;
+}
+
+int mpmi_screener_features(mpmi_screener* s, mpmi_session* session, const double* x_t_dev,
+                           const double* u_h_dev, uint64_t tick, float* out_dev, void* stream) {
+  if (!s || !session || !x_t_dev || !u_h_dev || !out_dev)
+    return fail(MPMI_E_INVALID_ARG, "screener: NULL argument");
+  if (session->model != s->model) return fail(MPMI_E_INVALID_ARG, "screener: another model");
+  if (session->cfg.sampler == MPMI_SAMPLER_EXTERNAL)
+    return fail(MPMI_E_UNSUPPORTED, "screener: sampled candidates only");
+  TickArgs a = make_tick_args(session, tick);
+  a.x_t = x_t_dev;
+  a.u_h = u_h_dev;
+  const int blocks = (session->n_slots + 255) / 256 < 1024 ? (session->n_slots + 255) / 256 : 1024;
+  slot_features<<<blocks, 256, 0, (cudaStream_t)stream>>>(a, feature_src(s), out_dev);
+  SCR_CUDA(cudaGetLastError(), "slot_features launch");
+  return MPMI_OK;
+}
+
+int mpmi_screener_gradients(mpmi_screener* s, const float* feats, const float* target,
+                            int32_t batch, float* grad_dev, float* loss_dev, void* stream) {
+  if (!s || !feats || !target || !grad_dev || !loss_dev)
+    return fail(MPMI_E_INVALID_ARG, "screener: NULL argument");
+  if (batch < 1 || batch > s->max_batch) return fail(MPMI_E_INVALID_ARG, "screener: batch size");
+  return gradients(s, feats, target, batch, grad_dev, loss_dev, (cudaStream_t)stream);
+}
+
+int mpmi_screener_train_step(mpmi_screener* s, const float* feats, const float* target,
+                             int32_t batch, float lr, float* loss_dev, void* stream) {
+  if (!s || !feats || !target || !loss_dev) return fail(MPMI_E_INVALID_ARG, "screener: NULL argument");
+  if (batch < 1 || batch > s->max_batch) return fail(MPMI_E_INVALID_ARG, "screener: batch size");
+  if (!(lr > 0.f)) return fail(MPMI_E_INVALID_ARG, "screener: learning rate must be > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = gradients(s, feats, target, batch, s->grad, loss_dev, st);
+  if (rc != MPMI_OK) return rc;
+  s->step += 1;
+  const float c1 = 1.f - powf(0.9f, (float)s->step), c2 = 1.f - powf(0.999f, (float)s->step);
+  adam<<<(kP + 255) / 256, 256, 0, st>>>(s->params, s->grad, s->adam_m, s->adam_v, lr, c1, c2);
+  SCR_CUDA(cudaGetLastError(), "adam launch");
+  s->stale = true;
+  return MPMI_OK;
+}
+
+int mpmi_screener_score(mpmi_screener* s, const float* feats, int32_t batch, float* scores,
+                        void* stream) {
+  if (!s || !feats || !scores) return fail(MPMI_E_INVALID_ARG, "screener: NULL argument");
+  if (batch < 1) return fail(MPMI_E_INVALID_ARG, "screener: batch size");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = refresh_infer(s, st);
+  if (rc != MPMI_OK) return rc;
+  const int tiles = (batch + 15) / 16;
+  int blocks = (tiles + 3) / 4;
+  if (blocks > 4 * s->ctx->sm_count) blocks = 4 * s->ctx->sm_count;
+  score_rows<<<blocks, 128, sizeof(InferW), st>>>(s->infer, feats, batch, scores);
+  SCR_CUDA(cudaGetLastError(), "score_rows launch");
+  return MPMI_OK;
+}
+
+int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double* x_t_dev,
+                           const double* u_h_dev, uint64_t tick, int32_t k, float tau,
+                           mpmi_result* result_dev, int32_t* list_dev, int32_t* n_list_dev,
+                           void* stream) {
+  if (!session || !s || !x_t_dev || !u_h_dev || !result_dev)
+    return fail(MPMI_E_INVALID_ARG, "evaluate_screened: NULL argument");
+  if (session->model != s->model) return fail(MPMI_E_INVALID_ARG, "screener: another model");
+  if (session->cfg.sampler == MPMI_SAMPLER_EXTERNAL)
+    return fail(MPMI_E_UNSUPPORTED, "evaluate_screened: sampled candidates only");
+  if (session->n_slots > s->max_slots)
+    return fail(MPMI_E_INVALID_ARG, "evaluate_screened: session has more slots than max_slots");
+  if (k < 1) return fail(MPMI_E_INVALID_ARG, "evaluate_screened: k must be >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = refresh_infer(s, st);
+  if (rc != MPMI_OK) return rc;
+  TickArgs a = make_tick_args(session, tick);
+  a.x_t = x_t_dev;
+  a.u_h = u_h_dev;
+  a.result = result_dev;
+  const int tiles = (session->n_slots + 15) / 16;
+  int blocks = (tiles + 3) / 4;
+  if (blocks > 2 * s->ctx->sm_count) blocks = 2 * s->ctx->sm_count;
+  screen_score<<<blocks, 128, sizeof(InferW), st>>>(a, feature_src(s), s->infer, tau, k, s->keys,
+                                                    s->ss);
+  int cb = (session->n_slots + 255) / 256;
+  if (cb > 4 * s->ctx->sm_count) cb = 4 * s->ctx->sm_count;
+  screen_compact<<<cb, 256, 0, st>>>(s->keys, session->n_slots, s->ss, s->list);
+  SCR_CUDA(cudaGetLastError(), "screen launches");
+  // exact rollout on the kept slots
+  TickArgs r = a;
+  r.slot_list = s->list;
+  r.n_list = &s->ss->n_list;
+  r.result_flags = 1;
+  rc = launch_tick_args(session, r, false, st, k + k / 4 + 32);
+  if (rc != MPMI_OK) return rc;
+  if (list_dev)
+    SCR_CUDA(cudaMemcpyAsync(list_dev, s->list, sizeof(int) * session->n_slots,
+                             cudaMemcpyDeviceToDevice, st), "copy list");
+  if (n_list_dev)
+    SCR_CUDA(cudaMemcpyAsync(n_list_dev, &s->ss->n_list, sizeof(int), cudaMemcpyDeviceToDevice,
+                             st), "copy list size");
+  // full evaluation only when the kept slots hold no safe candidate
+  TickArgs f = a;
+  f.skip_if_safe = result_dev;
+  f.result_flags = 3;
+  return launch_tick_args(session, f, false, st, 0);
+}
+
+}  // extern "C"

@@ -150,10 +150,10 @@ __device__ __forceinline__ void write_result(const TickArgs& a, unsigned long lo
   r.n_safe = (int32_t)(cnt >> 40);
   r.ttv = a.horizon - hm;
   r.cost = __uint_as_float((unsigned int)((k >> 23) & 0xFFFFFFFFull));
-  r.n_slots = a.n_slots;
+  r.n_slots = a.n_list ? *a.n_list : a.n_slots;
   r.executed_steps = cnt & ((1ull << 40) - 1);
   r.tick = a.tick;
-  r.reserved = 0;
+  r.reserved = a.result_flags;
   *a.result = r;
 }
 
@@ -192,6 +192,10 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int q = lane % L, g = lane / L;
   const int H = a.horizon;
+  // a fallback launch has nothing to do when the screened result is already safe
+  if (a.skip_if_safe != nullptr && a.skip_if_safe->status == MPMI_SAFE) return;
+  // number of candidates this launch evaluates (all slots, or a device-side list)
+  const int n_eval = a.n_list ? *a.n_list : a.n_slots;
 
   // stage K (KSMEM) and the track grid (race car) while the per-tick state is prepared
   if constexpr (KSMEM) {
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   unsigned int n_safe = 0, n_exec = 0;
   const int wpb = blockDim.x >> 5;
   constexpr int PER_WARP = GPW * C;  // candidate slots per warp-tile
-  const int n_wtiles = (a.n_slots + PER_WARP - 1) / PER_WARP;
+  const int n_wtiles = (n_eval + PER_WARP - 1) / PER_WARP;
   for (int wt = blockIdx.x * wpb + warp; wt < n_wtiles; wt += gridDim.x * wpb) {
     int slot[C];
     bool valid[C], alive[C];
@@ -254,8 +258,9 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
     float* traj[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      slot[c] = wt * PER_WARP + c * GPW + g;
-      valid[c] = slot[c] < a.n_slots;
+      const int pos = wt * PER_WARP + c * GPW + g;
+      valid[c] = pos < n_eval;
+      slot[c] = (valid[c] && a.slot_list) ? a.slot_list[pos] : pos;
       float xi[NU];
       if (valid[c]) {
         candidate_value<NU>(a, slot[c], uh, xi);

@@ -88,6 +88,17 @@ _SIGNATURES = {
     "mpmi_sample_candidates": (c_i32, [c_vp, c_vp, c_vp, c_u64, c_vp, c_vp]),
     "mpmi_debug_trajectories": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp, c_vp, c_vp,
                                         c_vp, c_vp]),
+    "mpmi_screener_create": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, ctypes.POINTER(c_vp)]),
+    "mpmi_screener_free": (None, [c_vp]),
+    "mpmi_screener_get_weights": (c_i32, [c_vp, c_vp]),
+    "mpmi_screener_set_weights": (c_i32, [c_vp, c_vp]),
+    "mpmi_screener_tick_features": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "mpmi_screener_features": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp, c_vp]),
+    "mpmi_screener_gradients": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
+    "mpmi_screener_train_step": (c_i32, [c_vp, c_vp, c_vp, c_i32, ctypes.c_float, c_vp, c_vp]),
+    "mpmi_screener_score": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
+    "mpmi_evaluate_screened": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_i32, ctypes.c_float,
+                                       c_vp, c_vp, c_vp, c_vp]),
     "mpmi_evaluate_candidates_noalloc": (c_i32, [ctypes.POINTER(BasisDesc), c_vp,
                                                  ctypes.POINTER(SafetySpecC),
                                                  ctypes.POINTER(SessionConfig), c_vp, c_vp,
@@ -153,7 +164,7 @@ def _f64(a, n=None):
 def result_dict(r: Result, nu: int) -> dict:
     return dict(u_r=np.array(r.u_r[:nu]), index=r.index, status=r.status, n_safe=r.n_safe,
                 ttv=r.ttv, cost=r.cost, n_slots=r.n_slots, executed_steps=r.executed_steps,
-                tick=r.tick)
+                tick=r.tick, flags=r.reserved)
 
 
 def result_from_bytes(buf, nu: int) -> dict:
@@ -381,3 +392,86 @@ def evaluate_candidates_noalloc(basis: str, K_dev, lo, hi, n_samples: int, horiz
     _check(lib.mpmi_evaluate_candidates_noalloc(
         ctypes.byref(d), _ptr(K_dev), ctypes.byref(spec), ctypes.byref(cfg), _ptr(x_t_dev),
         _ptr(u_h_dev), _ptr(candidates), tick, _ptr(result_dev), _stream(stream)))
+
+
+# ---------------------------------------------------------------- learned screener
+SCREENER_PARAMS = 18305
+SCREENER_KEYS = (("W1", (128, 12)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)),
+                 ("w3", (128,)), ("b3", ()))
+
+
+def pack_weights(w: dict) -> np.ndarray:
+    """Packed float32 weight vector (W1, b1, W2, b2, w3, b3) from a dict."""
+    return np.ascontiguousarray(np.concatenate(
+        [np.asarray(w[k], dtype=np.float32).reshape(-1) for k, _ in SCREENER_KEYS]))
+
+
+def unpack_weights(v) -> dict:
+    v = np.asarray(v, dtype=np.float64)
+    out, o = {}, 0
+    for k, shape in SCREENER_KEYS:
+        n = int(np.prod(shape)) if shape else 1
+        out[k] = v[o:o + n].reshape(shape) if shape else np.array(v[o])
+        o += n
+    return out
+
+
+class Screener:
+    """mpmi_screener_create: learned candidate screener for a race-car model."""
+
+    def __init__(self, ctx: Context, model: Model, weights: dict, max_batch: int = 8192,
+                 max_slots: int = 65537):
+        self.ctx, self.model = ctx, model
+        w = pack_weights(weights)
+        h = c_vp()
+        _check(ctx.lib.mpmi_screener_create(ctx.handle, model.handle, w.ctypes.data, max_batch,
+                                            max_slots, ctypes.byref(h)))
+        self.handle = h
+
+    def get_weights(self) -> dict:
+        v = np.empty(SCREENER_PARAMS, dtype=np.float32)
+        _check(self.ctx.lib.mpmi_screener_get_weights(self.handle, v.ctypes.data))
+        return unpack_weights(v)
+
+    def set_weights(self, weights: dict):
+        w = pack_weights(weights)
+        _check(self.ctx.lib.mpmi_screener_set_weights(self.handle, w.ctypes.data))
+
+    def tick_features(self, x_t_dev, out_dev, stream=None):
+        """12 floats: the 10 per-tick inputs, the nearest segment, its distance."""
+        _check(self.ctx.lib.mpmi_screener_tick_features(self.handle, _ptr(x_t_dev), _ptr(out_dev),
+                                                        _stream(stream)))
+
+    def features(self, session: Session, x_t_dev, u_h_dev, out_dev, tick: int = 0, stream=None):
+        _check(self.ctx.lib.mpmi_screener_features(self.handle, session.handle, _ptr(x_t_dev),
+                                                   _ptr(u_h_dev), tick, _ptr(out_dev),
+                                                   _stream(stream)))
+
+    def gradients(self, feats_dev, targets_dev, grad_dev, loss_dev, stream=None):
+        _check(self.ctx.lib.mpmi_screener_gradients(self.handle, _ptr(feats_dev),
+                                                    _ptr(targets_dev), feats_dev.shape[0],
+                                                    _ptr(grad_dev), _ptr(loss_dev),
+                                                    _stream(stream)))
+
+    def train_step(self, feats_dev, targets_dev, loss_dev, lr: float = 1e-3, stream=None):
+        _check(self.ctx.lib.mpmi_screener_train_step(self.handle, _ptr(feats_dev),
+                                                     _ptr(targets_dev), feats_dev.shape[0], lr,
+                                                     _ptr(loss_dev), _stream(stream)))
+
+    def score(self, feats_dev, scores_dev, stream=None):
+        _check(self.ctx.lib.mpmi_screener_score(self.handle, _ptr(feats_dev), feats_dev.shape[0],
+                                                _ptr(scores_dev), _stream(stream)))
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.mpmi_screener_free(self.handle)
+            self.handle = None
+
+
+def evaluate_screened(s: Session, scr: Screener, x_t_dev, u_h_dev, result_dev, k: int = 4096,
+                      tau: float = 0.9, tick: int = 0, list_dev=None, n_list_dev=None,
+                      stream=None):
+    """mpmi_evaluate_screened: screened tick with on-device fallback."""
+    _check(s.ctx.lib.mpmi_evaluate_screened(s.handle, scr.handle, _ptr(x_t_dev), _ptr(u_h_dev),
+                                            tick, k, tau, _ptr(result_dev), _ptr(list_dev),
+                                            _ptr(n_list_dev), _stream(stream)))

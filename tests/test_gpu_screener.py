@@ -1,0 +1,226 @@
+"""Parity of the learned screener's CUDA kernels with the float64 reference, and
+the invariants of the screened tick (through the C ABI)."""
+import numpy as np
+import pytest
+
+from oracle import screener as osc
+from oracle import sampling as osamp
+from workloads import data, plants
+
+from parity import car_env, gpu_model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_02318_gb300 import build, mpmi
+    build.build()
+    return mpmi
+
+
+@pytest.fixture(scope="module")
+def setup(lib):
+    ctx = lib.Context(0)
+    env = car_env()
+    model = gpu_model(lib, ctx, env)
+    w0 = data.screener_init(11)
+    scr = lib.Screener(ctx, model, w0, max_batch=4096, max_slots=20000)
+    return ctx, env, model, scr, w0
+
+
+def _states(env, count, seed):
+    x0 = data.car_start_state(env.track, vx=12.0)
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        v = env.track[(37 * i + 5) % len(env.track)]
+        nxt = env.track[((37 * i + 5) + 1) % len(env.track)]
+        head = np.arctan2(*(nxt - v)[::-1])
+        out.append(np.array([v[0] + rng.uniform(-2.5, 2.5), v[1] + rng.uniform(-2.5, 2.5),
+                             head + rng.uniform(-0.3, 0.3), rng.uniform(5, 22),
+                             rng.uniform(-1, 1), rng.uniform(-0.5, 0.5)]))
+    return [x0] + out
+
+
+def test_tick_features_match_reference(lib, setup):
+    import torch
+    ctx, env, model, scr, _ = setup
+    out = torch.zeros(12, dtype=torch.float32, device="cuda")
+    for x in _states(env, 12, 0):
+        scr.tick_features(torch.tensor(x, dtype=torch.float64, device="cuda"), out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.float64)
+        want = osc.tick_features(env.track, env.spec.half_width, x)
+        # nearest segment as the reference finds it (float64, lowest index on ties)
+        a = env.track
+        d = np.roll(a, -1, axis=0) - a
+        t = np.clip(np.sum((x[:2] - a) * d, axis=1) / np.sum(d * d, axis=1), 0, 1)
+        dist = np.linalg.norm(x[:2] - a - t[:, None] * d, axis=1)
+        i_ref = int(np.argmin(dist))
+        if int(got[10]) != i_ref:
+            # only a float32 near-tie may pick a neighbouring segment
+            assert abs(dist[int(got[10])] - dist[i_ref]) < 1e-4
+            continue
+        assert abs(got[11] - dist[i_ref]) < 1e-4
+        assert np.allclose(got[:10], want, atol=2e-4, rtol=0)
+
+
+def test_slot_features_match_candidates(lib, setup):
+    import torch
+    ctx, env, model, scr, _ = setup
+    N = 3000
+    sess = lib.Session(ctx, model, N, 60, env.lo, env.hi, seed=5)
+    x = _states(env, 1, 3)[1]
+    u_h = data.to_f32_exact(data.user_input_once(4, env.lo, env.hi))
+    feats = torch.zeros((N + 1, 12), dtype=torch.float32, device="cuda")
+    tf = torch.zeros(12, dtype=torch.float32, device="cuda")
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    scr.features(sess, xd, torch.tensor(u_h, dtype=torch.float64, device="cuda"), feats, tick=9)
+    scr.tick_features(xd, tf)
+    torch.cuda.synchronize()
+    sess.close()
+    f = feats.cpu().numpy().astype(np.float64)
+    cands = np.vstack([u_h, osamp.uniform_samples(5, 0, 9, N, env.lo, env.hi)])
+    assert np.array_equal(f[:, :10], np.broadcast_to(tf.cpu().numpy()[:10], (N + 1, 10)))
+    assert np.allclose(f[:, 10], cands[:, 0] / 0.4, rtol=1e-6, atol=1e-7)
+    assert np.array_equal(f[:, 11], cands[:, 1])
+
+
+def _batch(seed, B):
+    rng = np.random.default_rng(seed)
+    f = np.column_stack([rng.uniform(-1, 1, B), rng.uniform(-1, 1, B), rng.uniform(0.5, 1, B),
+                         rng.uniform(0, 1, B), rng.uniform(-0.3, 0.3, B), rng.uniform(-0.3, 0.3, B),
+                         rng.uniform(-0.5, 0.5, (B, 4)), rng.uniform(-1, 1, B),
+                         rng.uniform(-1, 1, B)])
+    f = data.to_f32_exact(f)
+    t = data.to_f32_exact(rng.uniform(0, 1, B))
+    return f, t
+
+
+def test_gradients_match_reference(lib, setup):
+    import torch
+    ctx, env, model, scr, w0 = setup
+    scr.set_weights(w0)
+    f, t = _batch(1, 512)
+    g = torch.zeros(lib.SCREENER_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    scr.gradients(torch.tensor(f, dtype=torch.float32, device="cuda"),
+                  torch.tensor(t, dtype=torch.float32, device="cuda"), g, loss)
+    torch.cuda.synchronize()
+    cache = osc.forward(w0, f)
+    ref = osc.backward(w0, cache, t)
+    got = lib.unpack_weights(g.cpu().numpy())
+    assert float(loss.item()) == pytest.approx(osc.loss(cache["y"], t), rel=1e-5)
+    for k in ref:
+        scale = float(np.max(np.abs(ref[k])))
+        assert np.max(np.abs(np.asarray(got[k]) - ref[k])) <= 1e-4 * scale + 1e-9, k
+
+
+def test_adam_step_matches_reference(lib, setup):
+    import torch
+    ctx, env, model, scr, w0 = setup
+    scr.set_weights(w0)
+    p = {k: v.copy() for k, v in w0.items()}
+    state = {}
+    for step in (1, 2, 3):
+        f, t = _batch(10 + step, 256)
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        scr.train_step(torch.tensor(f, dtype=torch.float32, device="cuda"),
+                       torch.tensor(t, dtype=torch.float32, device="cuda"), loss, lr=1e-3)
+        g = osc.backward(p, osc.forward(p, f), t)
+        osc.adam_step(p, g, state, step, lr=1e-3)
+    got = scr.get_weights()
+    for k in p:
+        assert np.max(np.abs(np.asarray(got[k]) - p[k])) <= 2e-6, k
+
+
+def test_tensor_core_scores_within_bf16_tolerance(lib, setup):
+    import torch
+    ctx, env, model, scr, w0 = setup
+    w = {k: v.copy() for k, v in w0.items()}
+    w["b1"] = np.random.default_rng(2).normal(0, 0.1, 128)
+    w["b3"] = np.array(0.2)
+    scr.set_weights(w)
+    f, _ = _batch(3, 4099)
+    out = torch.zeros(4099, dtype=torch.float32, device="cuda")
+    scr.score(torch.tensor(f, dtype=torch.float32, device="cuda"), out)
+    torch.cuda.synchronize()
+    want = osc.forward({k: data.to_f32_exact(v) for k, v in w.items()}, f)["y"]
+    err = np.abs(out.cpu().numpy() - want)
+    assert err.max() < 0.02 and err.mean() < 0.004
+
+
+def _plain_and_screened(lib, ctx, env, model, scr, x, u_h, N, k, tau, tick):
+    import torch
+    sess = lib.Session(ctx, model, N, 60, env.lo, env.hi, seed=7)
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    ud = torch.tensor(u_h, dtype=torch.float64, device="cuda")
+    rp = torch.zeros(lib.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    rs = torch.zeros(lib.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    ttv = torch.zeros(N + 1, dtype=torch.int32, device="cuda")
+    cost = torch.zeros(N + 1, dtype=torch.float32, device="cuda")
+    lst = torch.full((N + 1,), -1, dtype=torch.int32, device="cuda")
+    nl = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lib.evaluate_candidates_device(sess, xd, ud, rp, tick=tick, ttv_dev=ttv, cost_dev=cost)
+    lib.evaluate_screened(sess, scr, xd, ud, rs, k=k, tau=tau, tick=tick, list_dev=lst,
+                          n_list_dev=nl)
+    torch.cuda.synchronize()
+    sess.close()
+    n = int(nl.item())
+    return (lib.result_from_bytes(rp.cpu(), 2), lib.result_from_bytes(rs.cpu(), 2),
+            ttv.cpu().numpy(), cost.cpu().numpy(), lst.cpu().numpy()[:n])
+
+
+def test_screening_everything_equals_plain(lib, setup):
+    ctx, env, model, scr, w0 = setup
+    scr.set_weights(w0)
+    for i, x in enumerate(_states(env, 3, 4)):
+        u_h = data.to_f32_exact(data.user_input_once(20 + i, env.lo, env.hi))
+        a, b, ttv, cost, lst = _plain_and_screened(lib, ctx, env, model, scr, x, u_h, 5000,
+                                                   5001, 0.0, i)
+        assert sorted(lst.tolist()) == list(range(5001))
+        for key in ("index", "status", "n_safe", "ttv", "executed_steps"):
+            assert a[key] == b[key], key
+        assert b["flags"] & 1
+
+
+@pytest.mark.parametrize("k,tau", [(64, 0.5), (512, 0.9), (2048, 0.3)])
+def test_screened_tick_invariants(lib, setup, k, tau):
+    ctx, env, model, scr, w0 = setup
+    scr.set_weights(w0)
+    H = 60
+    for i, x in enumerate(_states(env, 4, 5 + k)):
+        u_h = data.to_f32_exact(data.user_input_once(40 + i, env.lo, env.hi))
+        a, b, ttv, cost, lst = _plain_and_screened(lib, ctx, env, model, scr, x, u_h, 8000, k,
+                                                   tau, 100 + i)
+        assert 0 in lst and len(set(lst.tolist())) == len(lst) >= min(k, 8001)
+        if b["flags"] & 2:
+            # nothing safe among the kept slots: the full evaluation ran
+            assert not np.any(ttv[lst] == H)
+            for key in ("index", "status", "n_safe", "ttv", "executed_steps"):
+                assert a[key] == b[key], key
+        else:
+            # the exact rollout's choice over the kept slots, by the plain path's values
+            safe = lst[ttv[lst] == H]
+            assert len(safe) > 0 and b["status"] == lib.SAFE
+            best = safe[np.lexsort((safe, cost[safe]))[0]]
+            assert b["index"] == best and ttv[b["index"]] == H
+            assert a["status"] == lib.SAFE and cost[a["index"]] <= cost[b["index"]]
+
+
+def test_training_reduces_loss(lib, setup):
+    from paper_1906_02318_gb300 import screener as drv
+    ctx, env, model, scr, w0 = setup
+    scr.set_weights(w0)
+    sess = lib.Session(ctx, model, 1023, 60, env.lo, env.hi, seed=3)
+    x0 = data.car_start_state(env.track, vx=12.0)
+    uhs = data.ou_user_input(3, 40, plants.CAR_DT, env.lo, env.hi)
+    feats, targets, _ = drv.collect_labels(sess, scr, plants.bicycle_step, x0, uhs, env.track,
+                                           env.spec.half_width)
+    sess.close()
+    losses = drv.train(scr, feats, targets, epochs=6, batch=1024, lr=2e-3)
+    assert losses[-1] < 0.7 * losses[0]
