@@ -358,6 +358,81 @@ def run_gpu(args, rank, world):
                 gpu_name=props.name)
 
 
+def run_learned(args):
+    """Learned screener vs plain exhaustive evaluation on the race car (N = 16384 and
+    65536, H = 60): a screener trained on ~2M labels from the plain path's own
+    closed-loop rollouts; agreement, safety misses and tick times on held-out
+    closed-loop states.  Also reports the exact cost-ordered search (tau = 0,
+    no network), the method without the learned part."""
+    import torch
+    from paper_1906_02318_gb300 import mpmi as lib
+    from paper_1906_02318_gb300 import screener as drv
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = lib.Context(dev.index)
+    x, u, xn = data.transitions("car", 3, 20000)
+    model, _ = lib.fit_model(ctx, "car", x, u, xn)
+    track = data.track_polyline(3)
+    lib.set_safety_set(model, data.CAR_SAFE_LO, data.CAR_SAFE_HI, 0.0, track,
+                       data.CAR_TRACK_HALF_WIDTH)
+    lo, hi = plants.CAR_INPUT_LO, plants.CAR_INPUT_HI
+    x0 = data.car_start_state(track, vx=12.0)
+    scr = lib.Screener(ctx, model, data.screener_init(5), max_batch=8192, max_slots=65537)
+    t0 = time.perf_counter()
+    sess = lib.Session(ctx, model, 16384, 60, lo, hi, seed=5)
+    feats, targets, _ = drv.collect_labels(sess, scr, plants.bicycle_step, x0,
+                                           data.ou_user_input(5, 122, plants.CAR_DT, lo, hi),
+                                           track, data.CAR_TRACK_HALF_WIDTH)
+    sess.close()
+    losses = drv.train(scr, feats, targets, epochs=6, batch=8192, lr=2e-3)
+    train_s = time.perf_counter() - t0
+    n_labels = int(feats.shape[0])
+    del feats, targets
+    sess = lib.Session(ctx, model, 1023, 60, lo, hi, seed=6)
+    ticks = args.learned_ticks
+    uev = data.ou_user_input(6, ticks, plants.CAR_DT, lo, hi)
+    _, _, xev = drv.collect_labels(sess, scr, plants.bicycle_step, x0, uev, track,
+                                   data.CAR_TRACK_HALF_WIDTH, tick0=10000)
+    sess.close()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    res = torch.zeros(lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    out = {"workload": "race car, H=60, held-out closed-loop states", "labels": n_labels,
+           "train_epochs": len(losses), "train_loss": losses[-1], "train_s": train_s,
+           "ticks": ticks, "tau_learned": 0.05, "runs": []}
+    for N in (16384, 65536):
+        sess = lib.Session(ctx, model, N, 60, lo, hi, seed=7)
+        k = N // 16
+
+        def timed(fn):
+            ts = []
+            for t in range(ticks):
+                xd = torch.tensor(xev[t], dtype=torch.float64, device=dev)
+                ud = torch.tensor(uev[t], dtype=torch.float64, device=dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.zero_()
+                e0.record()
+                fn(xd, ud, 40000 + t)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+            return np.array(ts)
+
+        tp = timed(lambda xd, ud, t: lib.evaluate_candidates_device(sess, xd, ud, res, tick=t))
+        run = {"N": N, "k": k, "plain": {"mean_us": tp.mean() * 1e6,
+                                         "p99_us": np.percentile(tp, 99) * 1e6,
+                                         "steps_per_s": (N + 1) * 60 / tp.mean()}}
+        for name, tau in (("cost_ordered", 0.0), ("learned", 0.05)):
+            st = drv.compare(sess, scr, xev, uev, k=k, tau=tau, tick0=40000)
+            ts = timed(lambda xd, ud, t: lib.evaluate_screened(sess, scr, xd, ud, res, k=k,
+                                                               tau=tau, tick=t))
+            run[name] = dict(st, mean_us=ts.mean() * 1e6, p99_us=np.percentile(ts, 99) * 1e6,
+                             steps_per_s=(N + 1) * 60 / ts.mean())
+        out["runs"].append(run)
+        sess.close()
+    scr.free()
+    model.free()
+    return out
+
+
 def max_over_ranks(values, world: int, device: str = "cpu"):
     """Element-wise maximum of per-rank timings (the slowest rank sets the job time)."""
     if world <= 1:
@@ -383,6 +458,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of oracle work per host worker for cpu_baseline")
+    ap.add_argument("--learned-ticks", type=int, default=300,
+                    help="held-out ticks for the learned-vs-plain comparison (0 = skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -446,6 +523,8 @@ def main():
         "clocks": out["clocks"],
         "fallback_ticks": out["n_fallback"], "trials": out["trials"],
     }
+    if rank == 0 and args.learned_ticks > 0:
+        line["learned"] = run_learned(args)
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)

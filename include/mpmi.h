@@ -292,7 +292,10 @@ int mpmi_screener_score(mpmi_screener* s, const float* features_dev, int32_t bat
  * evaluation when none of them is safe.  result_dev's reserved word carries
  * flags: bit 0 the screened set was evaluated, bit 1 the full evaluation ran.
  * list_dev (optional, n_slots int32) receives the screened slots and
- * n_list_dev (optional, one int32) their number. */
+ * n_list_dev (optional, one int32) their number.  tau <= 0 skips the network and
+ * keeps the k cheapest slots: an exact cost-ordered search (the kept slots either
+ * contain the least-cost safe candidate or are all cheaper than it and unsafe,
+ * which triggers the full evaluation). */
 int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double* x_t_dev,
                            const double* u_h_dev, uint64_t tick, int32_t k, float tau,
                            mpmi_result* result_dev, int32_t* list_dev, int32_t* n_list_dev,

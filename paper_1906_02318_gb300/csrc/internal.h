@@ -103,8 +103,10 @@ struct mpmi_session {
   const mpmi_model* model = nullptr;
   mpmi_session_config cfg{};
   int n_slots = 0, lanes = 1, cands = 1, block = 128, grid_g = 0;
-  int max_grid[2] = {0, 0};  // resident blocks on the device (plain, trajectories)
-  size_t grid_smem[2] = {0, 0};  // dynamic shared memory max_grid was computed for
+  // resident blocks on the device per launch kind (plain, trajectories, and both
+  // for the few-candidate shape) and the dynamic shared memory they assume
+  int max_grid[4] = {0, 0, 0, 0};
+  size_t grid_smem[4] = {0, 0, 0, 0};
   mpmi::TickScratch* scratch_dev = nullptr;
   mpmi_result* result_dev = nullptr;
   double* in_dev = nullptr;        // x_t (8 doubles) then u_h (4 doubles)

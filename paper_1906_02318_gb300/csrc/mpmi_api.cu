@@ -153,11 +153,24 @@ TickArgs make_tick_args(const mpmi_session* s, uint64_t tick) {
 
 // Persistent grid: no more blocks than are resident at once, and no more than
 // the warp-tiles need.  Occupancy is cached per dynamic shared-memory size.
+// Launch shape for a launch that evaluates few candidates (a screened list): more
+// lanes per candidate shorten the serial H-step chain each candidate carries.
+static void small_shape(int kind, int* lanes, int* cands, int* block) {
+  *cands = 1;
+  *block = 128;
+  *lanes = kind == kCar ? 8 : (kind == kBot ? 4 : 1);
+}
+
 int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint) {
-  TickKernel k = pick_tick(s->model->kind, s->lanes, s->cands, traj);
+  int lanes = s->lanes, cands = s->cands, block = s->block;
+  // a device-side list short enough that 8 lanes per candidate still fit one wave
+  const bool small = a.slot_list != nullptr && n_hint > 0 &&
+                     (long long)n_hint * 8 <= (long long)s->ctx->sm_count * 512;
+  if (small) small_shape(s->model->kind, &lanes, &cands, &block);
+  TickKernel k = pick_tick(s->model->kind, lanes, cands, traj);
   if (!k.fn) return fail(MPMI_E_UNSUPPORTED, "tick kernel not compiled for this launch shape");
   const size_t smem = k.k_smem + (a.safety.has_track ? (size_t)a.safety.track.blob_bytes : 0);
-  const int t = traj ? 1 : 0;
+  const int t = (traj ? 1 : 0) + (small ? 2 : 0);
   if (s->max_grid[t] == 0 || s->grid_smem[t] != smem) {
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -165,19 +178,19 @@ int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, i
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }
     int nb = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.fn, s->block, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.fn, block, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (nb < 1) return fail(MPMI_E_UNSUPPORTED, "tick kernel cannot be resident with this block");
     s->max_grid[t] = nb * s->ctx->sm_count;
     s->grid_smem[t] = smem;
   }
-  const int wpb = s->block / 32;
-  const int per_warp = 32 / s->lanes * s->cands;
+  const int wpb = block / 32;
+  const int per_warp = 32 / lanes * cands;
   const int n_work = (n_hint > 0 && n_hint < s->n_slots) ? n_hint : s->n_slots;
   const int n_wtiles = (n_work + per_warp - 1) / per_warp;
   int grid = (n_wtiles + wpb - 1) / wpb;
   if (grid > s->max_grid[t]) grid = s->max_grid[t];
-  k.launch(a, grid, s->block, smem, st);
+  k.launch(a, grid, block, smem, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "tick kernel launch");
   return MPMI_OK;

@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(128) screen_score(TickArgs a, FeatureSrc fs, c
   __shared__ float s_feat[12];
   __shared__ int s_last;
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
-  stage_weights(w, sw);
+  if (tau > 0.f) stage_weights(w, sw);
   block_tick_features(fs, a.x_t, s_feat);  // ends with __syncthreads
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
@@ -454,8 +454,8 @@ __global__ void __launch_bounds__(128) screen_score(TickArgs a, FeatureSrc fs, c
     f0[11] = x0[1];
     f1[10] = x1[0] / 0.4f;
     f1[11] = x1[1];
-    float y0, y1;
-    mlp_tile(sw, f0, f1, &y0, &y1);
+    float y0 = 1.f, y1 = 1.f;
+    if (tau > 0.f) mlp_tile(sw, f0, f1, &y0, &y1);  // tau <= 0: cost order only
     if (q == 0) {
       const int rr[2] = {r0, r1};
       const float yy[2] = {y0, y1};
@@ -482,38 +482,59 @@ __global__ void __launch_bounds__(128) screen_score(TickArgs a, FeatureSrc fs, c
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // last block: inclusive scan of the histogram (one thread per 16 bins)
-  __shared__ unsigned int s_sum[128];
-  const int per = kBins / 128;
-  unsigned int local = 0;
-  if (threadIdx.x < 128)
-    for (int i = 0; i < per; ++i)
-      local += *reinterpret_cast<volatile unsigned int*>(&ss->hist[threadIdx.x * per + i]);
-  if (threadIdx.x < 128) s_sum[threadIdx.x] = local;
+  // last block: find the first bin where the inclusive count reaches k.  The
+  // histogram is copied to shared memory, each thread sums a run of bins, the run
+  // sums are scanned, and the thread whose run crosses k walks it.
+  constexpr int kRun = kBins / 128;
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x)
+    s_hist[i] = *reinterpret_cast<volatile unsigned int*>(&ss->hist[i]);
+  __shared__ unsigned int s_run[128];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned int cum = 0;
-    int bstar = kBins - 1;
-    bool found = false;
-    for (int c = 0; c < 128 && !found; ++c) {
-      if (cum + s_sum[c] >= (unsigned int)k) {
-        for (int i = 0; i < per; ++i) {
-          cum += *reinterpret_cast<volatile unsigned int*>(&ss->hist[c * per + i]);
-          if (cum >= (unsigned int)k) {
-            bstar = c * per + i;
-            found = true;
-            break;
-          }
+  unsigned int run = 0;
+  if (threadIdx.x < 128)
+    for (int i = 0; i < kRun; ++i) run += s_hist[threadIdx.x * kRun + i];
+  if (threadIdx.x < 128) s_run[threadIdx.x] = run;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // exclusive prefix of the run sums: 4 runs per lane, then a warp scan
+    unsigned int v[4], tot = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[j] = s_run[threadIdx.x * 4 + j];
+      tot += v[j];
+    }
+    unsigned int incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int n = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)threadIdx.x >= o) incl += n;
+    }
+    unsigned int before = incl - tot;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      s_run[threadIdx.x * 4 + j] = before;  // exclusive prefix of run j
+      before += v[j];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ss->bstar = kBins - 1;  // fewer than k slots in total: keep all
+  __syncthreads();
+  if (threadIdx.x < 128) {
+    unsigned int cum = s_run[threadIdx.x];
+    if (cum < (unsigned int)k) {
+      for (int i = 0; i < kRun; ++i) {
+        cum += s_hist[threadIdx.x * kRun + i];
+        if (cum >= (unsigned int)k) {
+          ss->bstar = threadIdx.x * kRun + i;  // the only run that crosses k
+          break;
         }
-      } else {
-        cum += s_sum[c];
       }
     }
-    ss->bstar = bstar;
+  }
+  if (threadIdx.x == 0) {
     ss->n_list = 0;
     ss->done = 0;
   }
-  __syncthreads();
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) ss->hist[i] = 0;
 }
 

@@ -179,7 +179,9 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   constexpr int GPW = 32 / L;           // candidate groups per warp
   constexpr int S = (N % 32 == 0) ? N + 4 : ((N % 4 == 0) ? N : N + (4 - N % 4));
   constexpr int NW = kMaxBlock / 32;
-  constexpr int ACC = (R < 8 && C == 1) ? 2 : 1;  // split accumulators for ILP on short rows
+  // Every launch shape sums each row of K z in the same order (one FMA chain over
+  // k = 0..n-1), so all shapes produce bit-identical trajectories and decisions.
+  constexpr int ACC = 1;
   constexpr int ANG = (KIND == kBot) ? 0 : ((KIND == kCar) ? 2 : -1);
   constexpr int KWORDS = KSMEM ? (N * N) / 4 : 0;  // 16-byte words of K in shared memory
 

@@ -224,3 +224,18 @@ def test_training_reduces_loss(lib, setup):
     sess.close()
     losses = drv.train(scr, feats, targets, epochs=6, batch=1024, lr=2e-3)
     assert losses[-1] < 0.7 * losses[0]
+
+
+def test_cost_ordered_search_is_exact(lib, setup):
+    """tau = 0 keeps the k cheapest slots: either the least-cost safe candidate is
+    among them or every kept slot is cheaper, hence unsafe, and the full
+    evaluation runs -- the selection always equals the exhaustive one."""
+    ctx, env, model, scr, w0 = setup
+    for i, x in enumerate(_states(env, 8, 9)):
+        for u_h in (data.to_f32_exact(data.user_input_once(60 + i, env.lo, env.hi)),
+                    np.array([0.375, 1.0]), np.array([-0.4, -1.0])):
+            a, b, ttv, cost, lst = _plain_and_screened(lib, ctx, env, model, scr, x, u_h, 6000,
+                                                       128, 0.0, 200 + i)
+            for key in ("index", "status", "ttv"):
+                assert a[key] == b[key], key
+            assert np.array_equal(a["u_r"], b["u_r"])
