@@ -239,6 +239,42 @@ int mpmi_debug_trajectories(mpmi_session* s, const double* x_t_dev,
                             int32_t* ttv_dev, float* cost_dev, float* traj_dev,
                             void* stream);
 
+/* ---- continuous-batching server ------------------------------------------ */
+/* Serves many control sessions of one model together: each admitted session has
+ * its own N, H, input box, sampler seed/stream and tick counter; the requests
+ * staged for a batch run in one persistent launch (replayed from a CUDA graph)
+ * whose warps stride over all requests' candidates, and every request's result is
+ * bit-identical to the same tick evaluated alone (same per-candidate arithmetic,
+ * exact min-reduction).  Two batch buffers: requests for the next batch are staged
+ * on the host while the current one runs.  The server snapshots the model's
+ * operator and safety set when it is created.  Served sessions draw uniform
+ * samples. */
+typedef struct mpmi_server mpmi_server;
+/* max_sessions session slots; their reduction records and two batch tables are
+ * allocated here (and counted against the context's memory budget). */
+int mpmi_server_create(mpmi_ctx* ctx, const mpmi_model* model, int32_t max_sessions,
+                       mpmi_server** out);
+void mpmi_server_free(mpmi_server* s);
+/* Admission: a free slot and room in the context's memory budget for the
+ * session's share, else MPMI_E_OOM.  *slot_out identifies the session. */
+int mpmi_server_admit(mpmi_server* s, const mpmi_session_config* cfg, int32_t* slot_out);
+/* Frees a session slot (NOT_READY while it has a staged or running request). */
+int mpmi_server_release(mpmi_server* s, int32_t slot);
+/* Stages n requests for the next batch (host arrays): slots[n], x_t (n x nx),
+ * u_h (n x nu), ticks[n].  A session may have one request per batch. */
+int mpmi_server_submit(mpmi_server* s, int32_t n, const int32_t* slots, const double* x_t,
+                       const double* u_h, const uint64_t* ticks);
+/* Requests staged so far for the next batch. */
+int mpmi_server_staged(const mpmi_server* s, int32_t* n_out);
+/* Launches the staged batch on `stream` (one graph launch) and returns; NOT_READY
+ * while the previous batch has not been collected.  *n_launched may be 0. */
+int mpmi_server_launch(mpmi_server* s, void* stream, int32_t* n_launched);
+/* *done = 1 when the batch in flight has finished (0 if none is in flight). */
+int mpmi_server_poll(mpmi_server* s, int32_t* done);
+/* Waits for the batch in flight and copies its results (host, in submission
+ * order) with the sessions they belong to; *n_out = number of results. */
+int mpmi_server_collect(mpmi_server* s, mpmi_result* out, int32_t* slots_out, int32_t* n_out);
+
 /* ---- learned candidate screener (not in the paper) ----------------------- */
 /* A small network (12 -> 128 -> 128 -> 1, tanh-form GELU, sigmoid output) that
  * predicts, for the race car, each candidate's normalised time to violation

@@ -1,0 +1,511 @@
+// Continuous-batching tick server: many control sessions of one model, each with
+// its own N, H, sampler stream and tick counter, evaluated together in one
+// persistent launch that is replayed from a CUDA graph.
+//
+// Device side: the batch table lists the requests; their warp-tiles form one index
+// space (prefix sums in tile_begin).  Persistent warps stride over it; each
+// warp-tile runs the same per-tile code as the single-session tick (run_tile),
+// then folds its key and counts into the session's reduction record; the warp
+// that completes a session's last tile decodes its result.  A session's outcome
+// is therefore bit-identical whether it is served alone or in a mix.
+//
+// Host side: admission (a free session slot and room in the context's memory
+// budget), two batch buffers (one in flight while requests for the next are
+// staged), and one captured graph per buffer (table upload, kernel, result
+// download) so a batch costs one graph launch.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "tick_kernel.cuh"
+
+namespace mpmi {
+
+// One request in a batch; field names follow TickArgs so run_tile and the
+// decode read either.
+struct SessionTick {
+  int include_user, sampler, grid_g, n_slots;
+  float in_lo[MPMI_MAX_NU], in_w[MPMI_MAX_NU];
+  double in_lo64[MPMI_MAX_NU], in_hi64[MPMI_MAX_NU];
+  uint32_t key0, key1, t_lo, t_hi, stream, pad0;
+  const float* ext;
+  int horizon, n_tiles, tile_begin, pad1;
+  const int* slot_list;
+  const int* n_list;
+  int32_t* ttv_out;
+  float* cost_out;
+  float* traj_out;
+  const double* u_h;  // device address of u_h_buf below
+  mpmi_result* result;
+  unsigned long long tick, result_flags;
+  TickScratch* scratch;
+  double x_t_buf[MPMI_MAX_NX];
+  double u_h_buf[MPMI_MAX_NU];
+};
+
+struct ServeHeader {
+  int n_requests;
+  int total_tiles;
+  int pad[2];
+};
+
+struct ServeArgs {
+  const float* K;
+  DevSafety safety;
+  const ServeHeader* table;  // header followed by SessionTick entries
+};
+
+template <int KIND, int L, int C, bool KSMEM>
+__global__ void __launch_bounds__(kMaxBlock) serve_kernel(const __grid_constant__ ServeArgs sa) {
+  using B = BasisTraits<KIND>;
+  constexpr int N = B::N, NX = B::NX, NU = B::NU;
+  constexpr int R = N / L, GPW = 32 / L;
+  constexpr int S = (N % 32 == 0) ? N + 4 : ((N % 4 == 0) ? N : N + (4 - N % 4));
+  constexpr int NW = kMaxBlock / 32;
+  constexpr int ANG = (KIND == kBot) ? 0 : ((KIND == kCar) ? 2 : -1);
+  constexpr int KWORDS = KSMEM ? (N * N) / 4 : 0;
+  extern __shared__ uint4 s_dyn[];
+  __shared__ __align__(16) float s_x[(L > 1) ? NW : 1][2][GPW][S];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int q = lane % L;
+
+  if constexpr (KSMEM) {
+    const uint4* src = reinterpret_cast<const uint4*>(sa.K);
+    for (int i = tid; i < KWORDS; i += blockDim.x) s_dyn[i] = __ldg(&src[i]);
+  }
+  TrackView tv{nullptr, nullptr, nullptr, nullptr};
+  if constexpr (B::TRACK) {
+    if (sa.safety.has_track) {
+      uint4* dst = s_dyn + KWORDS;
+      const int words = sa.safety.track.blob_bytes >> 4;
+      for (int i = tid; i < words; i += blockDim.x) dst[i] = __ldg(&sa.safety.track.blob[i]);
+      const char* base = reinterpret_cast<const char*>(dst);
+      tv.cells = reinterpret_cast<const uint32_t*>(base);
+      tv.list = reinterpret_cast<const uint16_t*>(base + sa.safety.track.off_list);
+      tv.seg = reinterpret_cast<const float4*>(base + sa.safety.track.off_seg);
+      tv.inv = reinterpret_cast<const float*>(base + sa.safety.track.off_inv);
+    }
+  }
+  const float4* sK4 = reinterpret_cast<const float4*>(s_dyn);
+  float kr[KSMEM ? 1 : R][KSMEM ? 1 : N];
+  if constexpr (!KSMEM) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float* row = sa.K + (q * R + r) * N;
+#pragma unroll
+      for (int k = 0; k < N; ++k) kr[r][k] = __ldg(row + k);
+    }
+  }
+  if constexpr (KSMEM || B::TRACK) __syncthreads();
+
+  const ServeHeader* hdr = sa.table;
+  const int n_req = hdr->n_requests, total = hdr->total_tiles;
+  const SessionTick* ent = reinterpret_cast<const SessionTick*>(hdr + 1);
+  const int wpb = blockDim.x >> 5;
+  int cur = -1;
+  float xs[NX], uh[NU], sn = 0.f, cs = 1.f;
+  for (int gwt = blockIdx.x * wpb + warp; gwt < total; gwt += gridDim.x * wpb) {
+    // the request this warp-tile belongs to (warp-uniform binary search)
+    int lo = 0, hi = n_req - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ent[mid].tile_begin <= gwt) lo = mid;
+      else hi = mid - 1;
+    }
+    const SessionTick& st = ent[lo];
+    if (lo != cur) {
+#pragma unroll
+      for (int j = 0; j < NX; ++j) xs[j] = __double2float_rn(st.x_t_buf[j]);
+#pragma unroll
+      for (int j = 0; j < NU; ++j) uh[j] = __double2float_rn(st.u_h_buf[j]);
+      if constexpr (ANG >= 0) sincosf(xs[ANG], &sn, &cs);
+      cur = lo;
+    }
+    unsigned long long best = ~0ull;
+    unsigned int n_safe = 0, n_exec = 0;
+    run_tile<KIND, L, C, KSMEM, false>(st, sa.safety, gwt - st.tile_begin, st.n_slots, xs, uh,
+                                       sn, cs, kr, sK4, tv, &s_x[L > 1 ? warp : 0][0][0][0],
+                                       best, n_safe, n_exec);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(kFull, best, o);
+      best = other < best ? other : best;
+      n_exec += __shfl_xor_sync(kFull, n_exec, o);
+      n_safe += __shfl_xor_sync(kFull, n_safe, o);
+    }
+    if (lane == 0) {
+      TickScratch* sc = st.scratch;
+      atomicMin(&sc->key, best);
+      atomicAdd(&sc->counts, ((unsigned long long)n_safe << 40) + n_exec);
+      __threadfence();
+      const unsigned int prev = atomicAdd(&sc->done, 1u);
+      if (prev == (unsigned int)st.n_tiles - 1) {
+        // this warp finished the session's last tile: decode and reset its record
+        __threadfence();
+        const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&sc->key);
+        const unsigned long long cnt =
+            *reinterpret_cast<volatile unsigned long long*>(&sc->counts);
+        write_result<NU>(st, k, cnt, uh);
+        sc->key = ~0ull;
+        sc->counts = 0ull;
+        sc->done = 0u;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+struct ServeKernel {
+  const void* fn = nullptr;
+  void (*launch)(const ServeArgs&, int, int, size_t, cudaStream_t) = nullptr;
+  size_t k_smem = 0;
+  int per_warp = 32;
+};
+
+template <int KIND, int L, int C, bool KSMEM>
+static void launch_serve(const ServeArgs& a, int grid, int block, size_t smem, cudaStream_t st) {
+  serve_kernel<KIND, L, C, KSMEM><<<grid, block, smem, st>>>(a);
+}
+
+template <int KIND, int L, int C, bool KSMEM>
+static ServeKernel make_serve() {
+  ServeKernel k;
+  k.fn = reinterpret_cast<const void*>(&serve_kernel<KIND, L, C, KSMEM>);
+  k.launch = &launch_serve<KIND, L, C, KSMEM>;
+  k.k_smem = KSMEM ? (size_t)BasisTraits<KIND>::N * BasisTraits<KIND>::N * sizeof(float) : 0;
+  k.per_warp = 32 / L * C;
+  return k;
+}
+
+// One candidate per thread: the balance bot keeps K in registers, the race car in
+// shared memory (the shapes the single-session tick uses by default).
+static ServeKernel pick_serve(int kind) {
+  switch (kind) {
+    case kBot: return make_serve<kBot, 1, 1, false>();
+    case kCar: return make_serve<kCar, 1, 1, true>();
+    case kLin11: return make_serve<kLin11, 1, 1, false>();
+    case kLin22: return make_serve<kLin22, 1, 1, false>();
+    case kLin41: return make_serve<kLin41, 1, 1, false>();
+  }
+  return ServeKernel{};
+}
+
+}  // namespace mpmi
+
+// ---------------------------------------------------------------- host side
+struct mpmi_server {
+  mpmi_ctx* ctx = nullptr;
+  const mpmi_model* model = nullptr;
+  int max_sessions = 0;
+  std::vector<mpmi_session_config> cfg;
+  std::vector<char> used;
+  mpmi::TickScratch* scratch = nullptr;  // one record per session slot
+  // double-buffered batch state
+  mpmi::ServeHeader* table_host[2] = {nullptr, nullptr};  // pinned
+  mpmi::ServeHeader* table_dev[2] = {nullptr, nullptr};
+  mpmi_result* res_dev[2] = {nullptr, nullptr};
+  mpmi_result* res_host[2] = {nullptr, nullptr};         // pinned
+  std::vector<int> slots[2];
+  std::vector<char> in_batch;                            // per slot, staged this batch
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  cudaStream_t capture = nullptr;
+  int stage = 0;       // buffer receiving requests
+  int in_flight = -1;  // buffer on the GPU, or -1
+  size_t table_bytes = 0, smem = 0;
+  int grid = 0, block = 128;
+  mpmi::ServeKernel kern;
+  uint64_t per_session_bytes = 0, bytes = 0;
+};
+
+namespace mpmi {
+
+static int sfail(cudaError_t e, const char* what) {
+  return fail(MPMI_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define SRV_CUDA(call, what)                       \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return sfail(e_, what); \
+  } while (0)
+
+static int build_graph(mpmi_server* s, int b) {
+  ServeArgs a;
+  memset(&a, 0, sizeof(a));
+  a.K = s->model->K32_dev;
+  a.safety = s->model->dev_safety;
+  a.table = s->table_dev[b];
+  cudaGraph_t g = nullptr;
+  SRV_CUDA(cudaStreamBeginCapture(s->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+  cudaMemcpyAsync(s->table_dev[b], s->table_host[b], s->table_bytes, cudaMemcpyHostToDevice,
+                  s->capture);
+  s->kern.launch(a, s->grid, s->block, s->smem, s->capture);
+  cudaMemcpyAsync(s->res_host[b], s->res_dev[b], sizeof(mpmi_result) * s->max_sessions,
+                  cudaMemcpyDeviceToHost, s->capture);
+  cudaError_t e = cudaStreamEndCapture(s->capture, &g);
+  if (e != cudaSuccess) return sfail(e, "end capture");
+  e = cudaGraphInstantiate(&s->graph[b], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return sfail(e, "graph instantiate");
+  return MPMI_OK;
+}
+
+static void server_release_device(mpmi_server* s) {
+  for (int b = 0; b < 2; ++b) {
+    if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
+    if (s->done[b]) cudaEventDestroy(s->done[b]);
+    cudaFreeHost(s->table_host[b]);
+    cudaFreeHost(s->res_host[b]);
+    cudaFree(s->table_dev[b]);
+    cudaFree(s->res_dev[b]);
+  }
+  cudaFree(s->scratch);
+  if (s->capture) cudaStreamDestroy(s->capture);
+}
+
+}  // namespace mpmi
+
+using namespace mpmi;
+
+extern "C" {
+
+int mpmi_server_create(mpmi_ctx* ctx, const mpmi_model* model, int32_t max_sessions,
+                       mpmi_server** out) {
+  if (!ctx || !model || !out) return fail(MPMI_E_INVALID_ARG, "server: NULL argument");
+  *out = nullptr;
+  if (!model->has_safety) return fail(MPMI_E_INVALID_ARG, "server: set_safety_set first");
+  if (max_sessions < 1 || max_sessions > 65536)
+    return fail(MPMI_E_INVALID_ARG, "server: max_sessions out of range");
+  ServeKernel kern = pick_serve(model->kind);
+  if (!kern.fn) return fail(MPMI_E_UNSUPPORTED, "server: basis not compiled");
+  mpmi_server* s = new mpmi_server();
+  s->ctx = ctx;
+  s->model = model;
+  s->max_sessions = max_sessions;
+  s->kern = kern;
+  s->cfg.resize(max_sessions);
+  s->used.assign(max_sessions, 0);
+  s->in_batch.assign(max_sessions, 0);
+  s->table_bytes = sizeof(ServeHeader) + sizeof(SessionTick) * (size_t)max_sessions;
+  s->smem = kern.k_smem + (model->dev_safety.has_track ? (size_t)model->dev_safety.track.blob_bytes : 0);
+  s->per_session_bytes = sizeof(TickScratch) + 2 * (sizeof(SessionTick) + sizeof(mpmi_result));
+  const uint64_t fixed = 2 * (s->table_bytes + sizeof(mpmi_result) * (size_t)max_sessions) +
+                         sizeof(TickScratch) * (size_t)max_sessions;
+  if (ctx->budget && ctx->used + fixed > ctx->budget) {
+    delete s;
+    return fail(MPMI_E_OOM, "server: tables exceed the memory budget");
+  }
+  bool ok = cudaMalloc(&s->scratch, sizeof(TickScratch) * max_sessions) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking) == cudaSuccess;
+  for (int b = 0; b < 2 && ok; ++b)
+    ok = cudaMallocHost(&s->table_host[b], s->table_bytes) == cudaSuccess &&
+         cudaMalloc(&s->table_dev[b], s->table_bytes) == cudaSuccess &&
+         cudaMalloc(&s->res_dev[b], sizeof(mpmi_result) * max_sessions) == cudaSuccess &&
+         cudaMallocHost(&s->res_host[b], sizeof(mpmi_result) * max_sessions) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s->done[b], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    server_release_device(s);
+    delete s;
+    return fail(MPMI_E_OOM, "server: allocation failed");
+  }
+  std::vector<TickScratch> init(max_sessions);
+  for (auto& r : init) {
+    memset(&r, 0, sizeof(r));
+    r.key = ~0ull;
+  }
+  cudaMemcpy(s->scratch, init.data(), sizeof(TickScratch) * max_sessions, cudaMemcpyHostToDevice);
+  for (int b = 0; b < 2; ++b) {
+    memset(s->table_host[b], 0, s->table_bytes);
+    cudaMemset(s->table_dev[b], 0, s->table_bytes);
+  }
+  // persistent grid: every block resident at once
+  if (s->smem > 48 * 1024)
+    cudaFuncSetAttribute(kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern.fn, s->block, s->smem);
+  s->grid = (nb < 1 ? 1 : nb) * ctx->sm_count;
+  for (int b = 0; b < 2; ++b) {
+    int rc = build_graph(s, b);
+    if (rc != MPMI_OK) {
+      server_release_device(s);
+      delete s;
+      return rc;
+    }
+  }
+  s->bytes = fixed;
+  ctx->used += fixed;
+  *out = s;
+  return MPMI_OK;
+}
+
+void mpmi_server_free(mpmi_server* s) {
+  if (!s) return;
+  if (s->in_flight >= 0) cudaEventSynchronize(s->done[s->in_flight]);
+  server_release_device(s);
+  for (int i = 0; i < s->max_sessions; ++i)
+    if (s->used[i]) s->ctx->used -= s->per_session_bytes;
+  s->ctx->used -= s->bytes;
+  delete s;
+}
+
+int mpmi_server_admit(mpmi_server* s, const mpmi_session_config* cfg, int32_t* slot_out) {
+  if (!s || !cfg || !slot_out) return fail(MPMI_E_INVALID_ARG, "server_admit: NULL argument");
+  const mpmi_model* m = s->model;
+  if (cfg->horizon < 1 || cfg->horizon > MPMI_MAX_HORIZON || cfg->n_samples < 0 ||
+      (cfg->include_user != 0 && cfg->include_user != 1))
+    return fail(MPMI_E_INVALID_ARG, "server_admit: bad N, H or include_user");
+  const long long slots = (long long)cfg->n_samples + cfg->include_user;
+  if (slots < 1 || slots > MPMI_MAX_SLOTS)
+    return fail(MPMI_E_INVALID_ARG, "server_admit: slot count out of range");
+  if (cfg->sampler != MPMI_SAMPLER_UNIFORM)
+    return fail(MPMI_E_UNSUPPORTED, "server_admit: served sessions draw uniform samples");
+  for (int j = 0; j < m->nu; ++j)
+    if (!isfinite(cfg->input_lo[j]) || !isfinite(cfg->input_hi[j]) ||
+        !(cfg->input_lo[j] < cfg->input_hi[j]))
+      return fail(MPMI_E_INVALID_ARG, "server_admit: bad input box");
+  int free_slot = -1;
+  for (int i = 0; i < s->max_sessions; ++i)
+    if (!s->used[i]) {
+      free_slot = i;
+      break;
+    }
+  if (free_slot < 0) return fail(MPMI_E_OOM, "server_admit: every session slot is taken");
+  mpmi_ctx* ctx = s->ctx;
+  if (ctx->budget && ctx->used + s->per_session_bytes > ctx->budget)
+    return fail(MPMI_E_OOM, "server_admit: the context's memory budget is exhausted");
+  s->used[free_slot] = 1;
+  s->cfg[free_slot] = *cfg;
+  ctx->used += s->per_session_bytes;
+  *slot_out = free_slot;
+  return MPMI_OK;
+}
+
+int mpmi_server_release(mpmi_server* s, int32_t slot) {
+  if (!s || slot < 0 || slot >= s->max_sessions || !s->used[slot])
+    return fail(MPMI_E_INVALID_ARG, "server_release: no such session");
+  if (s->in_batch[slot]) return fail(MPMI_E_NOT_READY, "server_release: session has a staged request");
+  if (s->in_flight >= 0)
+    for (int v : s->slots[s->in_flight])
+      if (v == slot) return fail(MPMI_E_NOT_READY, "server_release: session is on the GPU");
+  s->used[slot] = 0;
+  s->ctx->used -= s->per_session_bytes;
+  return MPMI_OK;
+}
+
+int mpmi_server_submit(mpmi_server* s, int32_t n, const int32_t* slots, const double* x_t,
+                       const double* u_h, const uint64_t* ticks) {
+  if (!s || n < 0 || (n > 0 && (!slots || !x_t || !u_h || !ticks)))
+    return fail(MPMI_E_INVALID_ARG, "server_submit: NULL argument");
+  const mpmi_model* m = s->model;
+  ServeHeader* hdr = s->table_host[s->stage];
+  SessionTick* ent = reinterpret_cast<SessionTick*>(hdr + 1);
+  const char* dev_base = reinterpret_cast<const char*>(s->table_dev[s->stage]);
+  for (int r = 0; r < n; ++r) {
+    const int sl = slots[r];
+    if (sl < 0 || sl >= s->max_sessions || !s->used[sl])
+      return fail(MPMI_E_INVALID_ARG, "server_submit: no such session");
+    if (s->in_batch[sl]) return fail(MPMI_E_INVALID_ARG, "server_submit: session already staged");
+    for (int j = 0; j < m->nx; ++j)
+      if (!isfinite(x_t[(size_t)r * m->nx + j])) return fail(MPMI_E_NONFINITE, "server_submit: x_t");
+    for (int j = 0; j < m->nu; ++j)
+      if (!isfinite(u_h[(size_t)r * m->nu + j])) return fail(MPMI_E_NONFINITE, "server_submit: u_h");
+  }
+  for (int r = 0; r < n; ++r) {
+    const int sl = slots[r];
+    const mpmi_session_config& c = s->cfg[sl];
+    const int i = hdr->n_requests;
+    SessionTick& e = ent[i];
+    memset(&e, 0, sizeof(e));
+    e.include_user = c.include_user;
+    e.sampler = c.sampler;
+    e.n_slots = c.n_samples + c.include_user;
+    for (int j = 0; j < MPMI_MAX_NU; ++j) {
+      e.in_lo[j] = (float)c.input_lo[j];
+      e.in_w[j] = (float)(c.input_hi[j] - c.input_lo[j]);
+      e.in_lo64[j] = c.input_lo[j];
+      e.in_hi64[j] = c.input_hi[j];
+    }
+    e.key0 = (uint32_t)(c.seed & 0xFFFFFFFFull);
+    e.key1 = (uint32_t)(c.seed >> 32);
+    e.t_lo = (uint32_t)(ticks[r] & 0xFFFFFFFFull);
+    e.t_hi = (uint32_t)(ticks[r] >> 32);
+    e.stream = c.stream_id;
+    e.horizon = c.horizon;
+    e.n_tiles = (e.n_slots + s->kern.per_warp - 1) / s->kern.per_warp;
+    e.tile_begin = hdr->total_tiles;
+    e.tick = ticks[r];
+    e.scratch = s->scratch + sl;
+    e.result = s->res_dev[s->stage] + i;
+    for (int j = 0; j < m->nx; ++j) e.x_t_buf[j] = x_t[(size_t)r * m->nx + j];
+    for (int j = 0; j < m->nu; ++j) e.u_h_buf[j] = u_h[(size_t)r * m->nu + j];
+    e.u_h = reinterpret_cast<const double*>(
+        dev_base + sizeof(ServeHeader) + sizeof(SessionTick) * (size_t)i +
+        offsetof(SessionTick, u_h_buf));
+    hdr->n_requests += 1;
+    hdr->total_tiles += e.n_tiles;
+    s->slots[s->stage].push_back(sl);
+    s->in_batch[sl] = 1;
+  }
+  return MPMI_OK;
+}
+
+int mpmi_server_launch(mpmi_server* s, void* stream, int32_t* n_launched) {
+  if (!s) return fail(MPMI_E_INVALID_ARG, "server_launch: NULL argument");
+  if (s->in_flight >= 0) return fail(MPMI_E_NOT_READY, "server_launch: a batch is in flight");
+  const int b = s->stage;
+  const int n = s->table_host[b]->n_requests;
+  if (n_launched) *n_launched = n;
+  if (n == 0) return MPMI_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  SRV_CUDA(cudaGraphLaunch(s->graph[b], st), "server graph launch");
+  SRV_CUDA(cudaEventRecord(s->done[b], st), "server event");
+  s->in_flight = b;
+  s->stage = 1 - b;
+  for (int sl : s->slots[b]) s->in_batch[sl] = 0;
+  // the other buffer starts empty
+  s->table_host[s->stage]->n_requests = 0;
+  s->table_host[s->stage]->total_tiles = 0;
+  s->slots[s->stage].clear();
+  return MPMI_OK;
+}
+
+int mpmi_server_poll(mpmi_server* s, int32_t* done) {
+  if (!s || !done) return fail(MPMI_E_INVALID_ARG, "server_poll: NULL argument");
+  if (s->in_flight < 0) {
+    *done = 0;
+    return MPMI_OK;
+  }
+  const cudaError_t e = cudaEventQuery(s->done[s->in_flight]);
+  if (e == cudaSuccess) *done = 1;
+  else if (e == cudaErrorNotReady) *done = 0;
+  else return sfail(e, "server_poll");
+  return MPMI_OK;
+}
+
+int mpmi_server_collect(mpmi_server* s, mpmi_result* out, int32_t* slots_out, int32_t* n_out) {
+  if (!s || !out || !n_out) return fail(MPMI_E_INVALID_ARG, "server_collect: NULL argument");
+  if (s->in_flight < 0) return fail(MPMI_E_NOT_READY, "server_collect: no batch in flight");
+  const int b = s->in_flight;
+  SRV_CUDA(cudaEventSynchronize(s->done[b]), "server_collect");
+  const int n = (int)s->slots[b].size();
+  memcpy(out, s->res_host[b], sizeof(mpmi_result) * n);
+  if (slots_out) memcpy(slots_out, s->slots[b].data(), sizeof(int32_t) * n);
+  *n_out = n;
+  s->slots[b].clear();
+  s->table_host[b]->n_requests = 0;
+  s->table_host[b]->total_tiles = 0;
+  s->in_flight = -1;
+  return MPMI_OK;
+}
+
+int mpmi_server_staged(const mpmi_server* s, int32_t* n_out) {
+  if (!s || !n_out) return fail(MPMI_E_INVALID_ARG, "server_staged: NULL argument");
+  *n_out = s->table_host[s->stage]->n_requests;
+  return MPMI_OK;
+}
+
+}  // extern "C"

@@ -30,9 +30,9 @@ constexpr int kMaxBlock = 256;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Alg. 2 first step: the input held by candidate `slot`.
-template <int NU>
-__device__ __forceinline__ void candidate_value(const TickArgs& a, int slot,
-                                                const float* uh32, float* xi) {
+template <int NU, class P>
+__device__ __forceinline__ void candidate_value(const P& a, int slot, const float* uh32,
+                                                float* xi) {
   if (a.include_user && slot == 0) {
 #pragma unroll
     for (int j = 0; j < NU; ++j) xi[j] = uh32[j];
@@ -132,8 +132,8 @@ __device__ __forceinline__ bool track_ok(const DevTrack& tr, const TrackView& v,
 }
 
 // Decode of the winning key into the tick's result record.
-template <int NU>
-__device__ __forceinline__ void write_result(const TickArgs& a, unsigned long long k,
+template <int NU, class P>
+__device__ __forceinline__ void write_result(const P& a, unsigned long long k,
                                              unsigned long long cnt, const float* uh) {
   const int pick = (int)(k & 0x7FFFFFull);
   const int hm = (int)(k >> 55);
@@ -157,6 +157,202 @@ __device__ __forceinline__ void write_result(const TickArgs& a, unsigned long lo
   *a.result = r;
 }
 
+// One warp-tile: the PER_WARP = 32 C / L candidate positions wt * PER_WARP ...
+// of a tick (Alg. 2 for each: sample, lift, predict with early exit, test,
+// score), folded into the caller's running key minimum and counts.  P is the
+// tick's parameter record (TickArgs, or a served session's record).
+template <int KIND, int L, int C, bool KSMEM, bool TRAJ, class P, class KR>
+__device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, int wt, int n_eval,
+                                         const float* xs, const float* uh, float sn, float cs,
+                                         const KR& kr, const float4* sK4, const TrackView& tv,
+                                         float* xbuf, unsigned long long& best,
+                                         unsigned int& n_safe, unsigned int& n_exec) {
+  using B = BasisTraits<KIND>;
+  constexpr int N = B::N, NX = B::NX, NU = B::NU, NP = B::NP;
+  constexpr int R = N / L;
+  constexpr int GPW = 32 / L;
+  constexpr int S = (N % 32 == 0) ? N + 4 : ((N % 4 == 0) ? N : N + (4 - N % 4));
+  // Every launch shape sums each row of K z in the same order (one FMA chain over
+  // k = 0..n-1), so all shapes produce bit-identical trajectories and decisions.
+  constexpr int ACC = 1;
+  constexpr int PER_WARP = GPW * C;
+  const int lane = threadIdx.x & 31, q = lane % L, g = lane / L;
+  const int H = a.horizon;
+  int slot[C];
+  bool valid[C], alive[C];
+  float cost[C];
+  int ttv[C];
+  float z[C][N];
+  float* traj[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int pos = wt * PER_WARP + c * GPW + g;
+    valid[c] = pos < n_eval;
+    slot[c] = (valid[c] && a.slot_list) ? a.slot_list[pos] : pos;
+    float xi[NU];
+    if (valid[c]) {
+      candidate_value<NU>(a, slot[c], uh, xi);
+    } else {
+#pragma unroll
+      for (int j = 0; j < NU; ++j) xi[j] = uh[j];
+    }
+    cost[c] = 0.f;
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+      const float d = __fsub_rn(xi[j], uh[j]);
+      cost[c] = __fmaf_rn(d, d, cost[c]);
+    }
+    // lift: z_0 = a(x_t) + sum_k p_k(xi) b_k(x_t)
+    float p[NP];
+    monomials32<KIND>(xi, p);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float av, bv[kMaxP];
+      feature_split<float>(KIND, j, xs, sn, cs, &av, bv);
+#pragma unroll
+      for (int k = 0; k < NP; ++k) av = __fmaf_rn(p[k], bv[k], av);
+      z[c][j] = av;
+    }
+    traj[c] = nullptr;
+    if constexpr (TRAJ) {
+      if (valid[c] && q == 0) {
+        traj[c] = a.traj_out + (size_t)slot[c] * (H + 1) * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) traj[c][j] = z[c][j];
+      }
+    }
+    ttv[c] = 0;
+    alive[c] = valid[c];
+  }
+
+  for (int t = 1; t <= H; ++t) {
+    if constexpr (KSMEM) {
+      // z <- K z with K read from shared memory (one broadcast LDS.128 feeds 4 C
+      // FMAs).  The empty asm keeps the compiler from hoisting the loop-invariant
+      // K loads out of the step loop (1024 values would not fit in registers).
+      asm volatile("" ::: "memory");
+      float acc[C][N];
+#pragma unroll
+      for (int r = 0; r < N; ++r) {
+        float av[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) av[c] = 0.f;
+#pragma unroll
+        for (int k4 = 0; k4 < N / 4; ++k4) {
+          const float4 kv = sK4[r * (N / 4) + k4];
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            av[c] = __fmaf_rn(kv.x, z[c][4 * k4], av[c]);
+            av[c] = __fmaf_rn(kv.y, z[c][4 * k4 + 1], av[c]);
+            av[c] = __fmaf_rn(kv.z, z[c][4 * k4 + 2], av[c]);
+            av[c] = __fmaf_rn(kv.w, z[c][4 * k4 + 3], av[c]);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c][r] = av[c];
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int r = 0; r < N; ++r) z[c][r] = acc[c][r];
+    } else if constexpr (L == 1) {
+      float zn[C][N];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+          float accv[ACC];
+#pragma unroll
+          for (int e = 0; e < ACC; ++e) accv[e] = 0.f;
+#pragma unroll
+          for (int k = 0; k < N; ++k)
+            accv[k % ACC] = __fmaf_rn(kr[r][k], z[c][k], accv[k % ACC]);
+          float v = accv[0];
+#pragma unroll
+          for (int e = 1; e < ACC; ++e) v += accv[e];
+          zn[c][r] = v;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int j = 0; j < N; ++j) z[c][j] = zn[c][j];
+    } else {
+      // L lanes per candidate: this lane's rows, then exchange through shared memory
+      float zn[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float accv[ACC];
+#pragma unroll
+        for (int e = 0; e < ACC; ++e) accv[e] = 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k) accv[k % ACC] = __fmaf_rn(kr[r][k], z[0][k], accv[k % ACC]);
+        float v = accv[0];
+#pragma unroll
+        for (int e = 1; e < ACC; ++e) v += accv[e];
+        zn[r] = v;
+      }
+      float* buf = xbuf + ((t & 1) * GPW + g) * S;
+      if constexpr (R % 4 == 0) {
+#pragma unroll
+        for (int r = 0; r < R; r += 4)
+          *reinterpret_cast<float4*>(buf + q * R + r) =
+              make_float4(zn[r], zn[r + 1], zn[r + 2], zn[r + 3]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[q * R + r] = zn[r];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < N; k += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(buf + k);
+        z[0][k] = v.x; z[0][k + 1] = v.y; z[0][k + 2] = v.z; z[0][k + 3] = v.w;
+      }
+    }
+    bool any_alive = false;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      if constexpr (TRAJ) {
+        if (traj[c] != nullptr && alive[c]) {
+#pragma unroll
+          for (int j = 0; j < N; ++j) traj[c][(size_t)t * N + j] = z[c][j];
+        }
+      }
+      bool ok = box_ok<NX>(safety, z[c]);
+      if constexpr (B::TRACK) {
+        if (safety.has_track) {  // uniform over the grid
+          const bool on_road =
+              track_ok<L>(safety.track, tv, z[c][0], z[c][1], q, alive[c] && ok);
+          ok = ok && on_road;
+        }
+      }
+      if (alive[c]) {
+        if (ok) ttv[c] = t;
+        else alive[c] = false;
+      }
+      any_alive = any_alive || alive[c];
+    }
+    if (!__any_sync(kFull, any_alive)) break;
+  }
+
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    if (valid[c]) {
+      // selection key: (H - ttv) | cost bits | slot -> lexicographic minimum
+      const unsigned long long key = ((unsigned long long)(H - ttv[c]) << 55) |
+                                     ((unsigned long long)__float_as_uint(cost[c]) << 23) |
+                                     (unsigned long long)slot[c];
+      best = key < best ? key : best;
+      if (q == 0) {
+        n_exec += (unsigned int)min(ttv[c] + 1, H);
+        n_safe += ttv[c] == H;
+        if (a.ttv_out) a.ttv_out[slot[c]] = ttv[c];
+        if (a.cost_out) a.cost_out[slot[c]] = cost[c];
+      }
+    }
+  }
+}
+
 // Template parameters of the tick kernel:
 //   L        lanes per candidate (K rows split across the lanes, see above);
 //   C        candidates per thread (L = 1 only): more independent FMA chains;
@@ -170,7 +366,7 @@ __device__ __forceinline__ void write_result(const TickArgs& a, unsigned long lo
 template <int KIND, int L, int C, bool KSMEM, bool TRAJ, bool PARTIALS = false>
 __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__ TickArgs a) {
   using B = BasisTraits<KIND>;
-  constexpr int N = B::N, NX = B::NX, NU = B::NU, NP = B::NP;
+  constexpr int N = B::N, NX = B::NX, NU = B::NU;
   static_assert(N % L == 0, "lanes must divide the lifted dimension");
   static_assert(32 % L == 0, "lanes must divide the warp");
   static_assert(C == 1 || L == 1, "several candidates per thread need L = 1");
@@ -179,9 +375,6 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   constexpr int GPW = 32 / L;           // candidate groups per warp
   constexpr int S = (N % 32 == 0) ? N + 4 : ((N % 4 == 0) ? N : N + (4 - N % 4));
   constexpr int NW = kMaxBlock / 32;
-  // Every launch shape sums each row of K z in the same order (one FMA chain over
-  // k = 0..n-1), so all shapes produce bit-identical trajectories and decisions.
-  constexpr int ACC = 1;
   constexpr int ANG = (KIND == kBot) ? 0 : ((KIND == kCar) ? 2 : -1);
   constexpr int KWORDS = KSMEM ? (N * N) / 4 : 0;  // 16-byte words of K in shared memory
 
@@ -192,8 +385,7 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   __shared__ int s_last;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int q = lane % L, g = lane / L;
-  const int H = a.horizon;
+  const int q = lane % L;
   // a fallback launch has nothing to do when the screened result is already safe
   if (a.skip_if_safe != nullptr && a.skip_if_safe->status == MPMI_SAFE) return;
   // number of candidates this launch evaluates (all slots, or a device-side list)
@@ -251,181 +443,9 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   const int wpb = blockDim.x >> 5;
   constexpr int PER_WARP = GPW * C;  // candidate slots per warp-tile
   const int n_wtiles = (n_eval + PER_WARP - 1) / PER_WARP;
-  for (int wt = blockIdx.x * wpb + warp; wt < n_wtiles; wt += gridDim.x * wpb) {
-    int slot[C];
-    bool valid[C], alive[C];
-    float cost[C];
-    int ttv[C];
-    float z[C][N];
-    float* traj[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const int pos = wt * PER_WARP + c * GPW + g;
-      valid[c] = pos < n_eval;
-      slot[c] = (valid[c] && a.slot_list) ? a.slot_list[pos] : pos;
-      float xi[NU];
-      if (valid[c]) {
-        candidate_value<NU>(a, slot[c], uh, xi);
-      } else {
-#pragma unroll
-        for (int j = 0; j < NU; ++j) xi[j] = uh[j];
-      }
-      cost[c] = 0.f;
-#pragma unroll
-      for (int j = 0; j < NU; ++j) {
-        const float d = __fsub_rn(xi[j], uh[j]);
-        cost[c] = __fmaf_rn(d, d, cost[c]);
-      }
-      // lift: z_0 = a(x_t) + sum_k p_k(xi) b_k(x_t)
-      float p[NP];
-      monomials32<KIND>(xi, p);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        float av, bv[kMaxP];
-        feature_split<float>(KIND, j, xs, sn, cs, &av, bv);
-#pragma unroll
-        for (int k = 0; k < NP; ++k) av = __fmaf_rn(p[k], bv[k], av);
-        z[c][j] = av;
-      }
-      traj[c] = nullptr;
-      if constexpr (TRAJ) {
-        if (valid[c] && q == 0) {
-          traj[c] = a.traj_out + (size_t)slot[c] * (H + 1) * N;
-#pragma unroll
-          for (int j = 0; j < N; ++j) traj[c][j] = z[c][j];
-        }
-      }
-      ttv[c] = 0;
-      alive[c] = valid[c];
-    }
-
-    for (int t = 1; t <= H; ++t) {
-      if constexpr (KSMEM) {
-        // z <- K z with K read from shared memory (one broadcast LDS.128 feeds 4 C
-        // FMAs).  The empty asm keeps the compiler from hoisting the loop-invariant
-        // K loads out of the step loop (1024 values would not fit in registers).
-        asm volatile("" ::: "memory");
-        float acc[C][N];
-#pragma unroll
-        for (int r = 0; r < N; ++r) {
-          float av[C];
-#pragma unroll
-          for (int c = 0; c < C; ++c) av[c] = 0.f;
-#pragma unroll
-          for (int k4 = 0; k4 < N / 4; ++k4) {
-            const float4 kv = sK4[r * (N / 4) + k4];
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-              av[c] = __fmaf_rn(kv.x, z[c][4 * k4], av[c]);
-              av[c] = __fmaf_rn(kv.y, z[c][4 * k4 + 1], av[c]);
-              av[c] = __fmaf_rn(kv.z, z[c][4 * k4 + 2], av[c]);
-              av[c] = __fmaf_rn(kv.w, z[c][4 * k4 + 3], av[c]);
-            }
-          }
-#pragma unroll
-          for (int c = 0; c < C; ++c) acc[c][r] = av[c];
-        }
-#pragma unroll
-        for (int c = 0; c < C; ++c)
-#pragma unroll
-          for (int r = 0; r < N; ++r) z[c][r] = acc[c][r];
-      } else if constexpr (L == 1) {
-        float zn[C][N];
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-#pragma unroll
-          for (int r = 0; r < N; ++r) {
-            float accv[ACC];
-#pragma unroll
-            for (int e = 0; e < ACC; ++e) accv[e] = 0.f;
-#pragma unroll
-            for (int k = 0; k < N; ++k)
-              accv[k % ACC] = __fmaf_rn(kr[r][k], z[c][k], accv[k % ACC]);
-            float v = accv[0];
-#pragma unroll
-            for (int e = 1; e < ACC; ++e) v += accv[e];
-            zn[c][r] = v;
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < C; ++c)
-#pragma unroll
-          for (int j = 0; j < N; ++j) z[c][j] = zn[c][j];
-      } else {
-        // L lanes per candidate: this lane's rows, then exchange through shared memory
-        float zn[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          float accv[ACC];
-#pragma unroll
-          for (int e = 0; e < ACC; ++e) accv[e] = 0.f;
-#pragma unroll
-          for (int k = 0; k < N; ++k) accv[k % ACC] = __fmaf_rn(kr[r][k], z[0][k], accv[k % ACC]);
-          float v = accv[0];
-#pragma unroll
-          for (int e = 1; e < ACC; ++e) v += accv[e];
-          zn[r] = v;
-        }
-        float* buf = &s_x[warp][t & 1][g][0];
-        if constexpr (R % 4 == 0) {
-#pragma unroll
-          for (int r = 0; r < R; r += 4)
-            *reinterpret_cast<float4*>(buf + q * R + r) =
-                make_float4(zn[r], zn[r + 1], zn[r + 2], zn[r + 3]);
-        } else {
-#pragma unroll
-          for (int r = 0; r < R; ++r) buf[q * R + r] = zn[r];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < N; k += 4) {
-          const float4 v = *reinterpret_cast<const float4*>(buf + k);
-          z[0][k] = v.x; z[0][k + 1] = v.y; z[0][k + 2] = v.z; z[0][k + 3] = v.w;
-        }
-      }
-      bool any_alive = false;
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        if constexpr (TRAJ) {
-          if (traj[c] != nullptr && alive[c]) {
-#pragma unroll
-            for (int j = 0; j < N; ++j) traj[c][(size_t)t * N + j] = z[c][j];
-          }
-        }
-        bool ok = box_ok<NX>(a.safety, z[c]);
-        if constexpr (B::TRACK) {
-          if (a.safety.has_track) {  // uniform over the grid
-            const bool on_road =
-                track_ok<L>(a.safety.track, tv, z[c][0], z[c][1], q, alive[c] && ok);
-            ok = ok && on_road;
-          }
-        }
-        if (alive[c]) {
-          if (ok) ttv[c] = t;
-          else alive[c] = false;
-        }
-        any_alive = any_alive || alive[c];
-      }
-      if (!__any_sync(kFull, any_alive)) break;
-    }
-
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      if (valid[c]) {
-        // selection key: (H - ttv) | cost bits | slot -> lexicographic minimum
-        const unsigned long long key = ((unsigned long long)(H - ttv[c]) << 55) |
-                                       ((unsigned long long)__float_as_uint(cost[c]) << 23) |
-                                       (unsigned long long)slot[c];
-        best = key < best ? key : best;
-        if (q == 0) {
-          n_exec += (unsigned int)min(ttv[c] + 1, H);
-          n_safe += ttv[c] == H;
-          if (a.ttv_out) a.ttv_out[slot[c]] = ttv[c];
-          if (a.cost_out) a.cost_out[slot[c]] = cost[c];
-        }
-      }
-    }
-  }
+  for (int wt = blockIdx.x * wpb + warp; wt < n_wtiles; wt += gridDim.x * wpb)
+    run_tile<KIND, L, C, KSMEM, TRAJ>(a, a.safety, wt, n_eval, xs, uh, sn, cs, kr, sK4, tv,
+                                      &s_x[L > 1 ? warp : 0][0][0][0], best, n_safe, n_exec);
 
   // warp -> block -> grid reduction
 #pragma unroll

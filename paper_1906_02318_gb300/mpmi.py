@@ -88,6 +88,15 @@ _SIGNATURES = {
     "mpmi_sample_candidates": (c_i32, [c_vp, c_vp, c_vp, c_u64, c_vp, c_vp]),
     "mpmi_debug_trajectories": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp, c_vp, c_vp,
                                         c_vp, c_vp]),
+    "mpmi_server_create": (c_i32, [c_vp, c_vp, c_i32, ctypes.POINTER(c_vp)]),
+    "mpmi_server_free": (None, [c_vp]),
+    "mpmi_server_admit": (c_i32, [c_vp, ctypes.POINTER(SessionConfig), ctypes.POINTER(c_i32)]),
+    "mpmi_server_release": (c_i32, [c_vp, c_i32]),
+    "mpmi_server_submit": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "mpmi_server_staged": (c_i32, [c_vp, ctypes.POINTER(c_i32)]),
+    "mpmi_server_launch": (c_i32, [c_vp, c_vp, ctypes.POINTER(c_i32)]),
+    "mpmi_server_poll": (c_i32, [c_vp, ctypes.POINTER(c_i32)]),
+    "mpmi_server_collect": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(c_i32)]),
     "mpmi_screener_create": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, ctypes.POINTER(c_vp)]),
     "mpmi_screener_free": (None, [c_vp]),
     "mpmi_screener_get_weights": (c_i32, [c_vp, c_vp]),
@@ -475,3 +484,71 @@ def evaluate_screened(s: Session, scr: Screener, x_t_dev, u_h_dev, result_dev, k
     _check(s.ctx.lib.mpmi_evaluate_screened(s.handle, scr.handle, _ptr(x_t_dev), _ptr(u_h_dev),
                                             tick, k, tau, _ptr(result_dev), _ptr(list_dev),
                                             _ptr(n_list_dev), _stream(stream)))
+
+
+# ---------------------------------------------------------------- continuous-batching server
+class Server:
+    """mpmi_server_create: many sessions of one model served in batched launches."""
+
+    def __init__(self, ctx: Context, model: Model, max_sessions: int = 256):
+        self.ctx, self.model, self.max_sessions = ctx, model, max_sessions
+        self.nx, self.nu = model.nx, model.nu
+        h = c_vp()
+        _check(ctx.lib.mpmi_server_create(ctx.handle, model.handle, max_sessions, ctypes.byref(h)))
+        self.handle = h
+        self._res = (Result * max_sessions)()
+        self._slots = np.zeros(max_sessions, dtype=np.int32)
+
+    def admit(self, n_samples: int, horizon: int, input_lo, input_hi, seed: int = 0,
+              stream_id: int = 0, include_user: bool = True) -> int:
+        cfg = SessionConfig()
+        cfg.n_samples, cfg.horizon = n_samples, horizon
+        cfg.include_user = int(include_user)
+        cfg.sampler = SAMPLER["uniform"]
+        lo, hi = _f64(input_lo), _f64(input_hi)
+        for j in range(MAX_NU):
+            cfg.input_lo[j] = lo[j] if j < lo.size else 0.0
+            cfg.input_hi[j] = hi[j] if j < hi.size else 1.0
+        cfg.seed, cfg.stream_id = seed, stream_id
+        slot = c_i32()
+        _check(self.ctx.lib.mpmi_server_admit(self.handle, ctypes.byref(cfg), ctypes.byref(slot)))
+        return slot.value
+
+    def release(self, slot: int):
+        _check(self.ctx.lib.mpmi_server_release(self.handle, slot))
+
+    def submit(self, slots, x_t, u_h, ticks):
+        slots = np.ascontiguousarray(np.asarray(slots, dtype=np.int32))
+        n = slots.size
+        x = _f64(x_t).reshape(n, self.nx)
+        u = _f64(u_h).reshape(n, self.nu)
+        t = np.ascontiguousarray(np.asarray(ticks, dtype=np.uint64))
+        _check(self.ctx.lib.mpmi_server_submit(self.handle, n, slots.ctypes.data, x.ctypes.data,
+                                               u.ctypes.data, t.ctypes.data))
+
+    def staged(self) -> int:
+        n = c_i32()
+        _check(self.ctx.lib.mpmi_server_staged(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def launch(self, stream=None) -> int:
+        n = c_i32()
+        _check(self.ctx.lib.mpmi_server_launch(self.handle, _stream(stream), ctypes.byref(n)))
+        return n.value
+
+    def poll(self) -> bool:
+        d = c_i32()
+        _check(self.ctx.lib.mpmi_server_poll(self.handle, ctypes.byref(d)))
+        return bool(d.value)
+
+    def collect(self):
+        """[(slot, result dict), ...] of the batch in flight (waits for it)."""
+        n = c_i32()
+        _check(self.ctx.lib.mpmi_server_collect(self.handle, self._res, self._slots.ctypes.data,
+                                                ctypes.byref(n)))
+        return [(int(self._slots[i]), result_dict(self._res[i], self.nu)) for i in range(n.value)]
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.mpmi_server_free(self.handle)
+            self.handle = None

@@ -1,0 +1,156 @@
+"""The continuous-batching server (through the C ABI): every served result equals
+the same tick evaluated alone, admission follows slots and the memory budget, and
+a short real-time serving run completes every request."""
+import numpy as np
+import pytest
+
+from workloads import data, plants
+
+from parity import bot_env, car_env, gpu_model, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_02318_gb300 import build, mpmi
+    build.build()
+    return mpmi
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    return lib.Context(0)
+
+
+def _states(env, which, count, seed):
+    if which == "bot":
+        return data.states_in_box(seed, count, [-0.3, -1, -1, -1], [0.3, 1, 1, 1])
+    x0 = data.car_start_state(env.track, vx=13.0)
+    return x0[None, :] + data.states_in_box(seed, count, [-1.5, -1.5, -0.1, -3, -0.3, -0.2],
+                                            [1.5, 1.5, 0.1, 3, 0.3, 0.2])
+
+
+def _alone(lib, ctx, model, env, n, H, seed, stream, x, u, tick):
+    sess = lib.Session(ctx, model, n, H, env.lo, env.hi, seed=seed, stream_id=stream)
+    g = run_gpu(lib, sess, x, u, tick=tick)
+    sess.close()
+    return g["result"]
+
+
+@pytest.mark.parametrize("which", ["bot", "car"])
+def test_served_results_equal_alone(lib, ctx, which):
+    env = bot_env() if which == "bot" else car_env()
+    model = gpu_model(lib, ctx, env)
+    srv = lib.Server(ctx, model, max_sessions=16)
+    rng = np.random.default_rng(0)
+    specs = [(0, 7), (1, 50), (1023, 20), (4096, 100), (20000, 60), (65535, 33), (3000, 1)]
+    slots = [srv.admit(n, H, env.lo, env.hi, seed=100 + i, stream_id=i)
+             for i, (n, H) in enumerate(specs)]
+    for batch in range(3):          # both buffers, then the first again
+        xs = _states(env, which, len(specs), 10 + batch)
+        us = data.to_f32_exact(rng.uniform(env.lo, env.hi, (len(specs), len(env.lo))))
+        ticks = [batch * 1000 + i for i in range(len(specs))]
+        order = rng.permutation(len(specs))
+        srv.submit([slots[i] for i in order], xs[order], us[order], [ticks[i] for i in order])
+        assert srv.launch() == len(specs)
+        got = dict(srv.collect())
+        for i, (n, H) in enumerate(specs):
+            a = _alone(lib, ctx, model, env, n, H, 100 + i, i, xs[i], us[i], ticks[i])
+            r = got[slots[i]]
+            for k in ("index", "status", "n_safe", "ttv", "executed_steps", "n_slots", "tick"):
+                assert r[k] == a[k], (batch, i, k)
+            assert np.array_equal(r["u_r"], a["u_r"]) and r["cost"] == a["cost"]
+    srv.free()
+    model.free()
+
+
+def test_admission_by_slots_and_budget(lib):
+    env = bot_env()
+    big = lib.Context(0)
+    model = gpu_model(lib, big, env)
+    srv = lib.Server(big, model, max_sessions=4)
+    slots = [srv.admit(100, 10, env.lo, env.hi) for _ in range(4)]
+    with pytest.raises(lib.MpmiError) as e:
+        srv.admit(100, 10, env.lo, env.hi)
+    assert e.value.code == -2
+    srv.release(slots[1])
+    assert srv.admit(100, 10, env.lo, env.hi) == slots[1]
+    srv.free()
+    # a budget that holds the model, the server and exactly three sessions
+    ctx0 = lib.Context(0)
+    m0 = gpu_model(lib, ctx0, env)
+    s0 = lib.Server(ctx0, m0, max_sessions=8)
+    u1 = ctx0.memory_in_use()
+    s0.admit(10, 5, env.lo, env.hi)
+    per = ctx0.memory_in_use() - u1
+    assert per > 0
+    s0.free()
+    m0.free()
+    ctx4 = lib.Context(0, mem_budget=u1 + 3 * per)
+    m4 = gpu_model(lib, ctx4, env)
+    s4 = lib.Server(ctx4, m4, max_sessions=8)
+    got = [s4.admit(10, 5, env.lo, env.hi) for _ in range(3)]
+    with pytest.raises(lib.MpmiError) as e:
+        s4.admit(10, 5, env.lo, env.hi)
+    assert e.value.code == -2
+    s4.release(got[0])
+    s4.admit(10, 5, env.lo, env.hi)
+    s4.free()
+    m4.free()
+
+
+def test_protocol_errors(lib, ctx):
+    env = bot_env()
+    model = gpu_model(lib, ctx, env)
+    srv = lib.Server(ctx, model, max_sessions=4)
+    a = srv.admit(500, 10, env.lo, env.hi)
+    b = srv.admit(500, 10, env.lo, env.hi)
+    with pytest.raises(lib.MpmiError):
+        srv.collect()                                   # nothing in flight
+    srv.submit([a], [[0.1, 0, 0, 0]], [[0.2]], [0])
+    with pytest.raises(lib.MpmiError):
+        srv.submit([a], [[0.1, 0, 0, 0]], [[0.2]], [1])  # one request per batch
+    with pytest.raises(lib.MpmiError):
+        srv.release(a)                                  # staged
+    with pytest.raises(lib.MpmiError) as e:
+        srv.submit([b], [[np.nan, 0, 0, 0]], [[0.2]], [0])
+    assert e.value.code == -3
+    assert srv.launch() == 1
+    with pytest.raises(lib.MpmiError):
+        srv.launch()                                    # previous batch not collected
+    srv.submit([a, b], [[0.1, 0, 0, 0], [0.0, 0.1, 0, 0]], [[0.2], [0.3]], [1, 0])
+    assert len(srv.collect()) == 1
+    assert srv.launch() == 2
+    assert {s for s, _ in srv.collect()} == {a, b}
+    srv.free()
+    model.free()
+
+
+def test_short_serving_run(lib, ctx):
+    import torch
+    from paper_1906_02318_gb300 import serve
+    benv, cenv = bot_env(), car_env()
+    bm, cm = gpu_model(lib, ctx, benv), gpu_model(lib, ctx, cenv)
+    bs, cs = lib.Server(ctx, bm, 32), lib.Server(ctx, cm, 32)
+    pools = [data.states_in_box(1, 64, [-0.1, -0.3, -0.3, -0.3], [0.1, 0.3, 0.3, 0.3]),
+             _states(cenv, "car", 64, 2)]
+    meta = [(bs, benv.lo, benv.hi, 0.01), (cs, cenv.lo, cenv.hi, 1 / 60)]
+    sessions = serve.make_sessions(meta, 16, 3, pools)
+    record = {}
+    stats = serve.run([bs, cs], sessions, duration=0.5, record=record)
+    assert stats["ticks"] > 100 and stats["batches"] > 0
+    for key in ("100Hz", "60Hz"):
+        assert stats["latency"][key]["p99_ms"] < 50.0
+    # a sample of served results equals the same tick alone
+    for (i, k), r in list(record.items())[:6]:
+        ss = sessions[i]
+        env, model = (benv, bm) if ss.server == 0 else (cenv, cm)
+        a = _alone(lib, ctx, model, env, ss.n, ss.horizon, 3 * 1000 + i, i,
+                   ss.states[k % len(ss.states)], ss.user[k % len(ss.user)], k)
+        assert r["index"] == a["index"] and r["n_safe"] == a["n_safe"]
+    bs.free()
+    cs.free()
