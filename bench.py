@@ -57,7 +57,7 @@ SM_FP32_LANES = 128
 
 # DRAM bytes per tick-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum); valid only for the kernel source it was taken on.
-TRAFFIC = {"tick_kernel_sha1": "e3c00dbe8f403c0a60db79b076ebdb022c236c49", "bytes_per_launch": 24576}
+TRAFFIC = {"tick_kernel_sha1": "fb9b3614ea6b6bc564143bce9e8cce75f0a9addb", "bytes_per_launch": 24832}
 
 
 def kernel_sha1() -> str:
@@ -353,7 +353,7 @@ def run_gpu(args, rank, world):
     model.free()
     return dict(dev_time=dev_time, durs=durs, executed=executed, lat=lat, e2e_rate=e2e_rate,
                 wall=wall, clocks=clk, lanes=lanes, cands=cands, block=block, n_slots=n_slots,
-                residual=residual, n_fallback=int(n_fallback), trials=trials,
+                residual=residual, n_fallback=int(n_fallback), trials=trials, states=states,
                 sm_count=props.multi_processor_count,
                 gpu_name=props.name)
 
@@ -433,6 +433,45 @@ def run_learned(args):
     return out
 
 
+def run_serving(args, bot_states):
+    """256 concurrent sessions, half balance bot and half race car, N log-uniform in
+    1k..64k, H uniform in 20..100, ticks at 100 / 60 Hz with +-2 ms jitter, served
+    by one continuous-batching server per model (two streams), for a fixed wall
+    time.  Latency runs from a tick's scheduled arrival to its collected result."""
+    import torch
+    from paper_1906_02318_gb300 import mpmi as lib
+    from paper_1906_02318_gb300 import serve
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = lib.Context(dev.index)
+    x, u, xn = data.transitions("bot", FIT_SEED, FIT_COUNT)
+    bm, _ = lib.fit_model(ctx, "bot", x, u, xn)
+    lib.set_safety_set(bm, data.BOT_SAFE_LO, data.BOT_SAFE_HI)
+    x, u, xn = data.transitions("car", 3, 20000)
+    cm, _ = lib.fit_model(ctx, "car", x, u, xn)
+    track = data.track_polyline(3)
+    lib.set_safety_set(cm, data.CAR_SAFE_LO, data.CAR_SAFE_HI, 0.0, track,
+                       data.CAR_TRACK_HALF_WIDTH)
+    n_sess = args.serve_sessions
+    bs = lib.Server(ctx, bm, n_sess)
+    cs = lib.Server(ctx, cm, n_sess)
+    x0 = data.car_start_state(track, vx=13.0)
+    car_pool = x0[None, :] + data.states_in_box(4, 256, [-1.5, -1.5, -0.1, -3, -0.3, -0.2],
+                                                [1.5, 1.5, 0.1, 3, 0.3, 0.2])
+    meta = [(bs, plants.BOT_INPUT_LO, plants.BOT_INPUT_HI, 0.01),
+            (cs, plants.CAR_INPUT_LO, plants.CAR_INPUT_HI, 1.0 / 60.0)]
+    sessions = serve.make_sessions(meta, n_sess, 4, [bot_states, car_pool])
+    streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+    stats = serve.run([bs, cs], sessions, duration=args.serve_seconds, streams=streams)
+    stats.update(sessions=n_sess, mix="half balance bot (100 Hz), half race car (60 Hz)",
+                 n_range="log-uniform 1024..65536", h_range="uniform 20..100",
+                 launch="one persistent graph-replayed launch per batch and model")
+    bs.free()
+    cs.free()
+    bm.free()
+    cm.free()
+    return stats
+
+
 def max_over_ranks(values, world: int, device: str = "cpu"):
     """Element-wise maximum of per-rank timings (the slowest rank sets the job time)."""
     if world <= 1:
@@ -460,6 +499,9 @@ def main():
                     help="seconds of oracle work per host worker for cpu_baseline")
     ap.add_argument("--learned-ticks", type=int, default=300,
                     help="held-out ticks for the learned-vs-plain comparison (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0,
+                    help="wall time of the 256-session serving run (0 = skip)")
+    ap.add_argument("--serve-sessions", type=int, default=256)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -525,6 +567,8 @@ def main():
     }
     if rank == 0 and args.learned_ticks > 0:
         line["learned"] = run_learned(args)
+    if rank == 0 and args.serve_seconds > 0:
+        line["serving"] = run_serving(args, out["states"])
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)

@@ -2,9 +2,15 @@
 
 python -m paper_1906_02318_gb300.profile_tick --basis bot --n 16384 --horizon 50 --ticks 20
 
-Each tick is exactly one launch of the fused tick kernel; nothing else runs on
-the GPU after set-up except an optional L2 flush (one memset) before each tick.
-Prints the mean CUDA-event duration of the tick kernel and the executed steps.
+--mode plain (default): each tick is exactly one launch of the fused tick
+kernel; nothing else runs on the GPU after set-up except an optional L2 flush
+(one memset) before each tick.  Prints the mean CUDA-event duration and the
+executed steps.
+--mode screened (race car): each tick is one screened tick (score, compaction,
+exact rollout of the kept slots, fallback) with an untrained screener and the
+given --tau / --k.
+--mode serve: --ticks batches of --sessions requests (N log-uniform 1k..64k, H
+20..100) through one continuous-batching server of the chosen model.
 """
 from __future__ import annotations
 
@@ -34,6 +40,10 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--cands", type=int, default=0, help="candidates per thread (one lane)")
     ap.add_argument("--flush", action="store_true", help="write 256 MB before each tick")
+    ap.add_argument("--mode", choices=["plain", "screened", "serve"], default="plain")
+    ap.add_argument("--k", type=int, default=4096)
+    ap.add_argument("--tau", type=float, default=0.0)
+    ap.add_argument("--sessions", type=int, default=64)
     args = ap.parse_args()
 
     build.build()
@@ -56,8 +66,16 @@ def main():
                                  [1, 1, 0.05, 2, 0.2, 0.1])
         states = x0[None, :] + jit
     uhs = data.ou_user_input(2, args.ticks, 0.01, lo, hi)
+    if args.mode == "serve":
+        return serve_mode(args, ctx, model, lo, hi, states, uhs)
     sess = lib.Session(ctx, model, args.n, args.horizon, lo, hi, seed=2, lanes=args.lanes,
                        block=args.block, cands=args.cands)
+    scr = None
+    if args.mode == "screened":
+        if args.basis != "car":
+            raise SystemExit("--mode screened needs --basis car")
+        scr = lib.Screener(ctx, model, data.screener_init(5), max_batch=256,
+                           max_slots=args.n + 1)
     dev = torch.device("cuda")
     xs = torch.tensor(states, dtype=torch.float64, device=dev)
     us = torch.tensor(uhs, dtype=torch.float64, device=dev)
@@ -70,7 +88,11 @@ def main():
         if flush is not None:
             flush.zero_()
         e0[t].record(st)
-        lib.evaluate_candidates_device(sess, xs[t], us[t], res[t], tick=t, stream=st)
+        if args.mode == "screened":
+            lib.evaluate_screened(sess, scr, xs[t], us[t], res[t], k=args.k, tau=args.tau,
+                                  tick=t, stream=st)
+        else:
+            lib.evaluate_candidates_device(sess, xs[t], us[t], res[t], tick=t, stream=st)
         e1[t].record(st)
     torch.cuda.synchronize()
     ms = np.array([a.elapsed_time(b) for a, b in zip(e0, e1)])
@@ -84,6 +106,38 @@ def main():
           f"nominal={(args.n + 1) * args.horizon} "
           f"tflops={fl / (ms[1:].mean() * 1e-3 if len(ms) > 1 else ms[0] * 1e-3) / 1e12:.2f}")
     sess.close()
+    if scr is not None:
+        scr.free()
+    model.free()
+
+
+def serve_mode(args, ctx, model, lo, hi, states, uhs):
+    import torch
+
+    from paper_1906_02318_gb300 import mpmi as lib
+    srv = lib.Server(ctx, model, args.sessions)
+    rng = np.random.default_rng(4)
+    ns = np.exp(rng.uniform(np.log(1024), np.log(65536), args.sessions)).astype(int)
+    hs = rng.integers(20, 101, args.sessions)
+    slots = [srv.admit(int(n), int(h), lo, hi, seed=i, stream_id=i)
+             for i, (n, h) in enumerate(zip(ns, hs))]
+    st = torch.cuda.current_stream()
+    ms = []
+    for t in range(args.ticks):
+        idx = [i % len(states) for i in range(args.sessions)]
+        srv.submit(slots, states[idx], np.repeat(uhs[t:t + 1], args.sessions, axis=0),
+                   [t] * args.sessions)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        srv.launch(st)
+        e1.record(st)
+        srv.collect()
+        ms.append(e0.elapsed_time(e1))
+    steps = float(np.sum((ns + 1) * hs))
+    t = np.mean(ms[1:]) * 1e-3 if len(ms) > 1 else ms[0] * 1e-3
+    print(f"serve {args.basis} sessions={args.sessions} batches={args.ticks} "
+          f"mean_us={t * 1e6:.1f} steps_per_batch={steps:.0f} steps_per_s={steps / t:.3e}")
+    srv.free()
     model.free()
 
 
