@@ -10,12 +10,15 @@ it); the two meet only through the seeded inputs of the ``workloads`` package.
 Modules, each citing the passage it follows:
 
 * ``philox``   counter-based generator (Salmon et al., SC'11) for Alg. 2's samples
-* ``sampling`` candidate inputs xi ~ U^{M x N} (Alg. 2) and the equally spaced
-               grid of Sec. IV-B
+* ``sampling`` candidate inputs xi ~ U^{M x N} (Alg. 2), the equally spaced
+               grid of Sec. IV-B, and Alg. 2's per-step Gaussian noise z_i
+               (Box-Muller normals from the same generator)
 * ``basis``    lifted features Psi(x, u) of the learned linear model (Sec. IV-A)
 * ``fit``      least-squares fit of the lifted operator K (Sec. IV-A)
 * ``safety``   isSafe: geometric checks with an inflated barrier (Sec. V-C.1)
 * ``mpmi``     Alg. 2 (prediction, rejection, minimal-intervention argmin)
+* ``screener`` the learned candidate screener (not in the paper): features,
+               network, loss, gradients, Adam
 
 Parity unpinned (stated here and in the design notes): how well a fitted K
 predicts the true plant (it is a model; only the fit residual is reported), and

@@ -72,3 +72,68 @@ def grid_samples(n: int, lo, hi) -> np.ndarray:
         v = ((digit + 0.5) * (hi[j] - lo[j])) / g + lo[j]
         out[:, j] = v.astype(np.float32).astype(np.float64)
     return out
+
+
+# ---- Alg. 2's per-step Gaussian noise z_i -----------------------------------
+#
+# Alg. 2 adds white Gaussian noise z_i to every predicted state; the paper gives
+# neither its variance nor where it enters the lifted state.  Reading: after each
+# prediction step t (1..H) the first n_noise lifted coordinates (the state
+# read-out) get sigma_j * n_j with n_j standard normal, before that step's safety
+# test; the perturbed state is carried into the next step.  sigma = 0 is Alg. 2
+# without noise.
+#
+# Normals (Box & Muller, "A note on the generation of random normal deviates",
+# Ann. Math. Stat. 29, 1958): two uniform words (w_a, w_b) give
+#     u1 = ((w_a >> 8) + 1) 2^-24 in (0, 1],  u2 = (w_b >> 8) 2^-24 in [0, 1),
+#     r = sqrt(-2 ln u1),  n = (r cos(2 pi u2), r sin(2 pi u2)).
+# Words: Philox4x32-10 under the session's key with counter
+#     (slot, t mod 2^32, (t div 2^32 mod 2^16) + 2^16 step + 2^25 block, stream),
+# for a tick t below 2^48, step in 1..H and block b = 0, 1 (coordinates 4b..4b+3).
+# Because step >= 1 the third word is >= 2^16, so these counters never meet the
+# candidate counters (slot, t lo, t hi, stream) of any tick below 2^48.  Block b's
+# words (w0, w1, w2, w3) give coordinates 4b, 4b+1 from (w0, w1) and 4b+2, 4b+3
+# from (w2, w3).
+
+def box_muller(wa, wb):
+    """Two standard normals from two uint32 words (arrays), float64."""
+    wa = np.asarray(wa, dtype=np.uint32)
+    wb = np.asarray(wb, dtype=np.uint32)
+    u1 = ((wa >> np.uint32(8)).astype(np.float64) + 1.0) * 2.0 ** -24
+    u2 = (wb >> np.uint32(8)).astype(np.float64) * 2.0 ** -24
+    r = np.sqrt(-2.0 * np.log(u1))
+    return r * np.cos(2.0 * np.pi * u2), r * np.sin(2.0 * np.pi * u2)
+
+
+def noise_counter(slot, tick: int, step: int, block: int, stream: int):
+    """The Philox counter words of the noise for (slot, step, block) of a tick."""
+    tick = int(tick)
+    if not 0 <= tick < 2 ** 48:
+        raise ValueError("noise needs tick < 2^48")
+    slot = np.asarray(slot, dtype=np.uint64).astype(np.uint32)
+    c1 = np.uint32(tick & 0xFFFFFFFF)
+    c2 = np.uint32(((tick >> 32) & 0xFFFF) + (int(step) << 16) + (int(block) << 25))
+    c3 = np.uint32(int(stream) & 0xFFFFFFFF)
+    n = slot.shape[0]
+    return (slot, np.full(n, c1, np.uint32), np.full(n, c2, np.uint32),
+            np.full(n, c3, np.uint32))
+
+
+def gaussian_noise(seed: int, stream: int, tick: int, n_slots: int, H: int,
+                   n_noise: int) -> np.ndarray:
+    """(H, n_slots, n_noise) standard normals of a tick, float64 (n_noise <= 8)."""
+    if not 0 <= n_noise <= 8:
+        raise ValueError("noise covers at most 8 state coordinates")
+    out = np.zeros((H, n_slots, n_noise), dtype=np.float64)
+    slots = np.arange(n_slots)
+    k0 = int(seed) & 0xFFFFFFFF
+    k1 = (int(seed) >> 32) & 0xFFFFFFFF
+    for t in range(1, H + 1):
+        for b in range((n_noise + 3) // 4):
+            w = philox4x32(*noise_counter(slots, tick, t, b, stream), k0, k1)
+            n0, n1 = box_muller(w[0], w[1])
+            n2, n3 = box_muller(w[2], w[3])
+            for j, v in enumerate((n0, n1, n2, n3)):
+                if 4 * b + j < n_noise:
+                    out[t - 1, :, 4 * b + j] = v
+    return out
