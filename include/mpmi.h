@@ -195,6 +195,22 @@ void mpmi_session_close(mpmi_session* s);
  * launches with (any output pointer may be NULL). */
 int mpmi_session_launch_shape(const mpmi_session* s, int32_t* lanes, int32_t* cands,
                               int32_t* block);
+/* Alg. 2's per-step Gaussian noise z_i ("to account for inaccuracies in the
+ * dynamics model"; the paper gives no variance).  After every prediction step t
+ * the lifted state's first `count` coordinates (the state read-out, x_0 ..
+ * x_{count-1}) get sigma[j] * n_j, n_j standard normal, before step t's safety
+ * test; the perturbed state is carried into step t + 1.  The normals come from
+ * Philox4x32-10 under the session's seed with counter (slot, tick mod 2^32,
+ * (tick div 2^32 mod 2^16) + 2^16 t + 2^25 b, stream_id) for coordinates
+ * 4b..4b+3, mapped by Box-Muller (u1 = ((w0 >> 8) + 1) 2^-24, u2 = (w1 >> 8)
+ * 2^-24, n = sqrt(-2 ln u1)(cos 2 pi u2, sin 2 pi u2); words (w2, w3) give the
+ * next pair), so a tick's noise is a function of (seed, stream, tick, slot)
+ * alone.  sigma: count host doubles, finite and >= 0 (rounded to float32);
+ * count = 0 turns the noise off (the default).  Applies to every later tick of
+ * the session (host, device, trajectory and screened evaluations); ticks must
+ * then stay below 2^48.  MPMI_E_INVALID_ARG for count outside 0..nx or a tick
+ * in flight, MPMI_E_NONFINITE for a NaN/Inf sigma. */
+int mpmi_session_set_noise(mpmi_session* s, const double* sigma, int32_t count);
 
 /* ---- evaluate_candidates + select_input (Alg. 2) ------------------------ */
 /* Queues one tick on `stream`: copies x_t (nx doubles) and u_h (nu doubles) from

@@ -72,6 +72,9 @@ struct TickArgs {
   const int* n_list;
   const mpmi_result* skip_if_safe;
   unsigned long long result_flags;
+  // Alg. 2's per-step noise z_i: sigma per state coordinate (zero past n_noise)
+  float noise_sigma[MPMI_MAX_NX];
+  int n_noise;
 };
 
 }  // namespace mpmi
@@ -103,10 +106,12 @@ struct mpmi_session {
   const mpmi_model* model = nullptr;
   mpmi_session_config cfg{};
   int n_slots = 0, lanes = 1, cands = 1, block = 128, grid_g = 0;
-  // resident blocks on the device per launch kind (plain, trajectories, and both
-  // for the few-candidate shape) and the dynamic shared memory they assume
-  int max_grid[4] = {0, 0, 0, 0};
-  size_t grid_smem[4] = {0, 0, 0, 0};
+  // resident blocks on the device per launch kind (plain or trajectories, all
+  // slots or the few-candidate shape, with or without noise) and the dynamic
+  // shared memory they assume
+  // (index: trajectories + 2 few-candidate shape + 4 noise)
+  int max_grid[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  size_t grid_smem[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   mpmi::TickScratch* scratch_dev = nullptr;
   mpmi_result* result_dev = nullptr;
   double* in_dev = nullptr;        // x_t (8 doubles) then u_h (4 doubles)
@@ -114,6 +119,8 @@ struct mpmi_session {
   mpmi_result* result_host = nullptr;  // pinned
   cudaEvent_t done = nullptr;
   bool in_flight = false;
+  float noise_sigma[MPMI_MAX_NX] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int n_noise = 0;
   uint64_t bytes = 0;
 };
 

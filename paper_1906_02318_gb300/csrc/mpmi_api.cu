@@ -9,11 +9,12 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <string>
 #include <vector>
 
 #include "internal.h"
-#include "tick_kernel.cuh"
+#include "tick_dispatch.cuh"
 
 namespace mpmi {
 
@@ -58,55 +59,9 @@ static bool budget_ok(mpmi_ctx* ctx, uint64_t bytes) {
 }
 
 // ---- kernel dispatch -------------------------------------------------------
-struct TickKernel {
-  const void* fn = nullptr;
-  void (*launch)(const TickArgs&, int, int, size_t, cudaStream_t) = nullptr;
-  size_t k_smem = 0;  // bytes of K staged in shared memory
-};
-
-template <int KIND, int L, int C, bool KSMEM, bool TRAJ>
-static void launch_tick(const TickArgs& a, int grid, int block, size_t smem, cudaStream_t st) {
-  tick_kernel<KIND, L, C, KSMEM, TRAJ><<<grid, block, smem, st>>>(a);
-}
-
-template <int KIND, int L, int C, bool KSMEM, bool TRAJ>
-static TickKernel make_kernel() {
-  TickKernel k;
-  k.fn = reinterpret_cast<const void*>(&tick_kernel<KIND, L, C, KSMEM, TRAJ>);
-  k.launch = &launch_tick<KIND, L, C, KSMEM, TRAJ>;
-  k.k_smem = KSMEM ? (size_t)BasisTraits<KIND>::N * BasisTraits<KIND>::N * sizeof(float) : 0;
-  return k;
-}
-
-// Compiled launch shapes: (lanes, candidates per thread); the race car with one
-// lane keeps K in shared memory.
-template <int KIND, bool TRAJ>
-static TickKernel pick_shape(int lanes, int cands) {
-  if constexpr (KIND == kBot) {
-    if (lanes == 1 && cands == 1) return make_kernel<KIND, 1, 1, false, TRAJ>();
-    if (lanes == 1 && cands == 2) return make_kernel<KIND, 1, 2, false, TRAJ>();
-    if (lanes == 2 && cands == 1) return make_kernel<KIND, 2, 1, false, TRAJ>();
-    if (lanes == 4 && cands == 1) return make_kernel<KIND, 4, 1, false, TRAJ>();
-  } else if constexpr (KIND == kCar) {
-    if (lanes == 1 && cands == 1) return make_kernel<KIND, 1, 1, true, TRAJ>();
-    if (lanes == 1 && cands == 2) return make_kernel<KIND, 1, 2, true, TRAJ>();
-    if (lanes == 8 && cands == 1) return make_kernel<KIND, 8, 1, false, TRAJ>();
-    if (lanes == 16 && cands == 1) return make_kernel<KIND, 16, 1, false, TRAJ>();
-  } else {
-    if (lanes == 1 && cands == 1) return make_kernel<KIND, 1, 1, false, TRAJ>();
-  }
-  return TickKernel{};
-}
-
-static TickKernel pick_tick(int kind, int lanes, int cands, bool traj) {
-  switch (kind) {
-    case kBot: return traj ? pick_shape<kBot, true>(lanes, cands) : pick_shape<kBot, false>(lanes, cands);
-    case kCar: return traj ? pick_shape<kCar, true>(lanes, cands) : pick_shape<kCar, false>(lanes, cands);
-    case kLin11: return traj ? pick_shape<kLin11, true>(lanes, cands) : pick_shape<kLin11, false>(lanes, cands);
-    case kLin22: return traj ? pick_shape<kLin22, true>(lanes, cands) : pick_shape<kLin22, false>(lanes, cands);
-    case kLin41: return traj ? pick_shape<kLin41, true>(lanes, cands) : pick_shape<kLin41, false>(lanes, cands);
-  }
-  return TickKernel{};
+static TickKernel pick_tick(int kind, int lanes, int cands, bool traj, bool noise) {
+  return noise ? pick_tick_noise(kind, lanes, cands, traj)
+               : pick_variant<false>(kind, lanes, cands, traj);
 }
 
 // Default launch shape (lanes, candidates per thread, block): one lane per
@@ -148,6 +103,8 @@ TickArgs make_tick_args(const mpmi_session* s, uint64_t tick) {
   a.stream = s->cfg.stream_id;
   a.tick = tick;
   a.scratch = s->scratch_dev;
+  for (int j = 0; j < MPMI_MAX_NX; ++j) a.noise_sigma[j] = s->noise_sigma[j];
+  a.n_noise = s->n_noise;
   return a;
 }
 
@@ -167,10 +124,13 @@ int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, i
   const bool small = a.slot_list != nullptr && n_hint > 0 &&
                      (long long)n_hint * 8 <= (long long)s->ctx->sm_count * 512;
   if (small) small_shape(s->model->kind, &lanes, &cands, &block);
-  TickKernel k = pick_tick(s->model->kind, lanes, cands, traj);
+  const bool noise = a.n_noise > 0;
+  if (noise && a.tick >= (1ull << 48))
+    return fail(MPMI_E_INVALID_ARG, "ticks with noise must stay below 2^48");
+  TickKernel k = pick_tick(s->model->kind, lanes, cands, traj, noise);
   if (!k.fn) return fail(MPMI_E_UNSUPPORTED, "tick kernel not compiled for this launch shape");
   const size_t smem = k.k_smem + (a.safety.has_track ? (size_t)a.safety.track.blob_bytes : 0);
-  const int t = (traj ? 1 : 0) + (small ? 2 : 0);
+  const int t = (traj ? 1 : 0) + (small ? 2 : 0) + (noise ? 4 : 0);
   if (s->max_grid[t] == 0 || s->grid_smem[t] != smem) {
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -484,7 +444,7 @@ int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model, const mpmi_session
   }
   if (block % 32 != 0 || block < 32 || block > kMaxBlock)
     return fail(MPMI_E_INVALID_ARG, "session_open: block must be a multiple of 32 in 32..256");
-  if (!pick_tick(model->kind, lanes, cands, false).fn)
+  if (!pick_tick(model->kind, lanes, cands, false, false).fn)
     return fail(MPMI_E_UNSUPPORTED, "session_open: launch shape (lanes, candidates per thread) "
                                     "not compiled for this basis");
   const uint64_t bytes = sizeof(TickScratch) + sizeof(mpmi_result) + 16 * sizeof(double);
@@ -553,6 +513,22 @@ int mpmi_session_launch_shape(const mpmi_session* s, int32_t* lanes, int32_t* ca
   if (lanes) *lanes = s->lanes;
   if (cands) *cands = s->cands;
   if (block) *block = s->block;
+  return MPMI_OK;
+}
+
+int mpmi_session_set_noise(mpmi_session* s, const double* sigma, int32_t count) {
+  if (!s) return fail(MPMI_E_INVALID_ARG, "session is NULL");
+  if (s->in_flight)
+    return fail(MPMI_E_INVALID_ARG, "set_noise: a tick is in flight (call select_input first)");
+  if (count < 0 || count > s->model->nx)
+    return fail(MPMI_E_INVALID_ARG, "set_noise: count must be 0..the model's state dimension");
+  if (count > 0 && !sigma) return fail(MPMI_E_INVALID_ARG, "set_noise: sigma is NULL");
+  for (int j = 0; j < count; ++j) {
+    if (!std::isfinite(sigma[j])) return fail(MPMI_E_NONFINITE, "set_noise: sigma not finite");
+    if (sigma[j] < 0.0) return fail(MPMI_E_INVALID_ARG, "set_noise: sigma must be >= 0");
+  }
+  for (int j = 0; j < MPMI_MAX_NX; ++j) s->noise_sigma[j] = j < count ? (float)sigma[j] : 0.f;
+  s->n_noise = count;
   return MPMI_OK;
 }
 

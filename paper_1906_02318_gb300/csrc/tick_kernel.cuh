@@ -64,6 +64,42 @@ __device__ __forceinline__ void candidate_value(const P& a, int slot, const floa
   }
 }
 
+// Two standard normals from two Philox words (Box & Muller, Ann. Math. Stat. 29,
+// 1958): u1 = ((w_a >> 8) + 1) 2^-24 in (0, 1], u2 = (w_b >> 8) 2^-24 in [0, 1),
+// both exact in binary32; n = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
+  const float u1 = (float)((wa >> 8) + 1u) * 0x1p-24f;
+  const float u2 = (float)(wb >> 8) * 0x1p-24f;
+  const float r = sqrtf(-2.f * logf(u1));
+  float s, c;
+  sincospif(2.f * u2, &s, &c);
+  n0 = r * c;
+  n1 = r * s;
+}
+
+// Alg. 2's noise z_i after prediction step t of candidate `slot`: the state
+// coordinates j < n_noise get sigma_j n_j.  Block b (coordinates 4b..4b+3) is
+// one Philox call with counter (slot, tick lo, (tick hi mod 2^16) + 2^16 t +
+// 2^25 b, stream); its words pair as (w0, w1) -> 4b, 4b+1 and (w2, w3) -> 4b+2,
+// 4b+3.  Since t >= 1 these counters never meet a candidate counter.
+template <int NX, class P>
+__device__ __forceinline__ void add_noise(const P& a, int slot, int t, float* z) {
+  constexpr int NB = (NX + 3) / 4;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    if (4 * b < a.n_noise) {
+      const uint32_t c2 = (a.t_hi & 0xFFFFu) + ((uint32_t)t << 16) + ((uint32_t)b << 25);
+      const U32x4 w = philox4x32_10(U32x4{(uint32_t)slot, a.t_lo, c2, a.stream}, a.key0, a.key1);
+      float n[4];
+      box_muller(w.x, w.y, n[0], n[1]);
+      box_muller(w.z, w.w, n[2], n[3]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (4 * b + j < NX) z[4 * b + j] = __fmaf_rn(a.noise_sigma[4 * b + j], n[j], z[4 * b + j]);
+    }
+  }
+}
+
 // Input monomials p_k(xi) of the split lifting, float32.
 template <int KIND>
 __device__ __forceinline__ void monomials32(const float* xi, float* p) {
@@ -161,7 +197,7 @@ __device__ __forceinline__ void write_result(const P& a, unsigned long long k,
 // of a tick (Alg. 2 for each: sample, lift, predict with early exit, test,
 // score), folded into the caller's running key minimum and counts.  P is the
 // tick's parameter record (TickArgs, or a served session's record).
-template <int KIND, int L, int C, bool KSMEM, bool TRAJ, class P, class KR>
+template <int KIND, int L, int C, bool KSMEM, bool TRAJ, bool NOISE, class P, class KR>
 __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, int wt, int n_eval,
                                          const float* xs, const float* uh, float sn, float cs,
                                          const KR& kr, const float4* sK4, const TrackView& tv,
@@ -309,6 +345,11 @@ __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, in
         z[0][k] = v.x; z[0][k + 1] = v.y; z[0][k + 2] = v.z; z[0][k + 3] = v.w;
       }
     }
+    if constexpr (NOISE) {
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+        if (alive[c]) add_noise<NX>(a, slot[c], t, z[c]);
+    }
     bool any_alive = false;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -362,8 +403,10 @@ __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, in
 //   TRAJ     record every predicted z_t (parity checks);
 //   PARTIALS no-allocation variant: each block stores its partial (key,
 //            counts) in a.partials and the last block folds them, instead of
-//            atomics on a session's reduction record.
-template <int KIND, int L, int C, bool KSMEM, bool TRAJ, bool PARTIALS = false>
+//            atomics on a session's reduction record;
+//   NOISE    add Alg. 2's Gaussian noise z_i after every prediction step.
+template <int KIND, int L, int C, bool KSMEM, bool TRAJ, bool PARTIALS = false,
+          bool NOISE = false>
 __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__ TickArgs a) {
   using B = BasisTraits<KIND>;
   constexpr int N = B::N, NX = B::NX, NU = B::NU;
@@ -444,7 +487,7 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   constexpr int PER_WARP = GPW * C;  // candidate slots per warp-tile
   const int n_wtiles = (n_eval + PER_WARP - 1) / PER_WARP;
   for (int wt = blockIdx.x * wpb + warp; wt < n_wtiles; wt += gridDim.x * wpb)
-    run_tile<KIND, L, C, KSMEM, TRAJ>(a, a.safety, wt, n_eval, xs, uh, sn, cs, kr, sK4, tv,
+    run_tile<KIND, L, C, KSMEM, TRAJ, NOISE>(a, a.safety, wt, n_eval, xs, uh, sn, cs, kr, sK4, tv,
                                       &s_x[L > 1 ? warp : 0][0][0][0], best, n_safe, n_exec);
 
   // warp -> block -> grid reduction

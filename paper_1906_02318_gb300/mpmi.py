@@ -79,6 +79,7 @@ _SIGNATURES = {
     "mpmi_session_open": (c_i32, [c_vp, c_vp, ctypes.POINTER(SessionConfig),
                                   ctypes.POINTER(c_vp)]),
     "mpmi_session_close": (None, [c_vp]),
+    "mpmi_session_set_noise": (c_i32, [c_vp, P_dbl, c_i32]),
     "mpmi_session_launch_shape": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32),
                                           ctypes.POINTER(c_i32)]),
     "mpmi_evaluate_candidates": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
@@ -328,6 +329,13 @@ class Session:
         _check(self.ctx.lib.mpmi_session_launch_shape(self.handle, ctypes.byref(lanes),
                                                       ctypes.byref(cands), ctypes.byref(block)))
         return lanes.value, cands.value, block.value
+
+    def set_noise(self, sigma):
+        """mpmi_session_set_noise: Alg. 2's per-step Gaussian noise on the first
+        len(sigma) state coordinates (an empty sigma turns it off)."""
+        sig = np.ascontiguousarray(np.atleast_1d(np.asarray(sigma, dtype=np.float64)))
+        _check(self.ctx.lib.mpmi_session_set_noise(
+            self.handle, sig.ctypes.data_as(P_dbl), int(sig.size)))
 
     def close(self):
         if self.handle:
