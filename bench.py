@@ -472,6 +472,79 @@ def run_serving(args, bot_states):
     return stats
 
 
+def run_variants(args, bot_states):
+    """The paper's variants and the factorised ablation, device-resident at the
+    benchmark's sizes (L2 flushed before every tick): the balance bot (N = 16384,
+    H = 50) and the race car (N = 16384, H = 60) with the full rollout (Alg. 2),
+    with per-step noise z_i, with the equally spaced grid (bot, Sec. IV-B), and in
+    the factorised read-out form (exact in real arithmetic, not the method's own
+    rollout).  Rates count the steps the kernel executed (early exit)."""
+    import torch
+    from paper_1906_02318_gb300 import mpmi as lib
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = lib.Context(dev.index)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ticks = min(args.variant_ticks, len(bot_states))
+    x, u, xn = data.transitions("bot", FIT_SEED, FIT_COUNT)
+    bm, _ = lib.fit_model(ctx, "bot", x, u, xn)
+    lib.set_safety_set(bm, data.BOT_SAFE_LO, data.BOT_SAFE_HI)
+    x, u, xn = data.transitions("car", 3, 20000)
+    cm, _ = lib.fit_model(ctx, "car", x, u, xn)
+    track = data.track_polyline(3)
+    lib.set_safety_set(cm, data.CAR_SAFE_LO, data.CAR_SAFE_HI, 0.0, track,
+                       data.CAR_TRACK_HALF_WIDTH)
+    x0 = data.car_start_state(track, vx=12.0)
+    car_states = x0[None, :] + data.states_in_box(8, ticks, [-1.5, -1.5, -0.1, -3, -0.3, -0.2],
+                                                  [1.5, 1.5, 0.1, 3, 0.3, 0.2])
+    plans = {
+        "bot": (bm, plants.BOT_INPUT_LO, plants.BOT_INPUT_HI, HORIZON, bot_states[:ticks],
+                [0.005, 0.02, 0.005, 0.02]),
+        "car": (cm, plants.CAR_INPUT_LO, plants.CAR_INPUT_HI, 60, car_states,
+                [0.03, 0.03, 0.005, 0.1, 0.02, 0.01]),
+    }
+    out = {"N": N_SAMPLES, "ticks": ticks, "l2": "flushed before every tick", "runs": {}}
+    res = torch.zeros((ticks, lib.RESULT_BYTES), dtype=torch.uint8, device=dev)
+    for name, (model, lo, hi, H, states, sigma) in plans.items():
+        uhs = data.ou_user_input(9, ticks, 0.01, lo, hi)
+        xs = torch.tensor(np.asarray(states), dtype=torch.float64, device=dev)
+        us = torch.tensor(uhs, dtype=torch.float64, device=dev)
+        variants = [("full", {}), ("noise", {"noise": sigma}), ("factored", {"rollout": 1})]
+        if name == "bot":
+            variants.insert(2, ("grid", {"sampler": "grid"}))
+        runs = {}
+        for vname, opt in variants:
+            sess = lib.Session(ctx, model, N_SAMPLES, H, lo, hi, seed=11,
+                               sampler=opt.get("sampler", "uniform"))
+            if "noise" in opt:
+                sess.set_noise(opt["noise"])
+            if "rollout" in opt:
+                sess.set_rollout("factored")
+            for i in range(3):
+                lib.evaluate_candidates_device(sess, xs[i], us[i], res[i], tick=i)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(ticks)]
+            for i in range(ticks):
+                flush.zero_()
+                ev[i][0].record()
+                lib.evaluate_candidates_device(sess, xs[i], us[i], res[i], tick=100 + i)
+                ev[i][1].record()
+            torch.cuda.synchronize()
+            durs = np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3
+            rr = [lib.result_from_bytes(r, sess.nu) for r in res.cpu().numpy()]
+            executed = float(np.mean([r["executed_steps"] for r in rr]))
+            runs[vname] = {"mean_us": durs.mean() * 1e6, "p99_us": np.percentile(durs, 99) * 1e6,
+                           "executed_steps_per_tick": executed,
+                           "executed_steps_per_s": executed / durs.mean(),
+                           "nominal_steps_per_s": sess.n_slots * H / durs.mean(),
+                           "safe_fraction": float(np.mean([r["n_safe"] for r in rr])) / sess.n_slots}
+            sess.close()
+        out["runs"][name] = dict(H=H, sigma=sigma, **runs)
+    bm.free()
+    cm.free()
+    return out
+
+
 def max_over_ranks(values, world: int, device: str = "cpu"):
     """Element-wise maximum of per-rank timings (the slowest rank sets the job time)."""
     if world <= 1:
@@ -502,6 +575,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="wall time of the 256-session serving run (0 = skip)")
     ap.add_argument("--serve-sessions", type=int, default=256)
+    ap.add_argument("--variant-ticks", type=int, default=200,
+                    help="ticks per paper variant / factorised ablation (0 = skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -569,6 +644,8 @@ def main():
         line["learned"] = run_learned(args)
     if rank == 0 and args.serve_seconds > 0:
         line["serving"] = run_serving(args, out["states"])
+    if rank == 0 and args.variant_ticks > 0:
+        line["variants"] = run_variants(args, out["states"])
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)

@@ -48,6 +48,8 @@ extern "C" {
 #define MPMI_E_CUDA (-4)        /* a CUDA runtime call failed                 */
 #define MPMI_E_NOT_READY (-5)   /* select_input without an evaluate in flight */
 #define MPMI_E_UNSUPPORTED (-6) /* combination not compiled into the library  */
+#define MPMI_E_TIMEOUT (-7)     /* a bounded wait inside a kernel ran out (the
+                                   tick's result has status MPMI_TIMEOUT)      */
 
 /* ---- enums ------------------------------------------------------------- */
 /* Lifted bases (Sec. IV-A; the paper's own 6- and 26-function bases were chosen
@@ -65,6 +67,10 @@ extern "C" {
  * the case the paper leaves open: no candidate safe over the whole horizon). */
 #define MPMI_SAFE 0
 #define MPMI_FALLBACK 1
+/* Not a selection: a block of the tick kernel gave up waiting (about a second)
+ * for its shared-memory staging, skipped its candidates and flagged the tick;
+ * the other fields are not meaningful.  Never expected in normal operation. */
+#define MPMI_TIMEOUT 2
 
 /* Candidate sources (Alg. 2 draws xi ~ U^{M x N}; Sec. IV-B describes an
  * equally spaced discretisation; EXTERNAL reads caller-provided samples). */
@@ -129,7 +135,7 @@ typedef struct {
   double u_r[MPMI_MAX_NU];  /* selected input: u_h exactly when slot 0 (the user)
                                wins, else the candidate's float32 value           */
   int32_t index;            /* selected slot                                      */
-  int32_t status;           /* MPMI_SAFE or MPMI_FALLBACK                         */
+  int32_t status;           /* MPMI_SAFE, MPMI_FALLBACK (or MPMI_TIMEOUT)         */
   int32_t n_safe;           /* candidates safe over all H steps                   */
   int32_t ttv;              /* steps the selected candidate passed (H if safe)    */
   float cost;               /* ||u_r - u_h||^2 in float32                         */
@@ -212,6 +218,24 @@ int mpmi_session_launch_shape(const mpmi_session* s, int32_t* lanes, int32_t* ca
  * in flight, MPMI_E_NONFINITE for a NaN/Inf sigma. */
 int mpmi_session_set_noise(mpmi_session* s, const double* sigma, int32_t count);
 
+/* Rollout form of the session's ticks.  FULL (the default) predicts z <- K z as
+ * Alg. 2 does.  FACTORED is an ablation that is exact in real arithmetic: with
+ * the input held over the horizon (Sec. IV-A, VII-B) and the lifting affine in
+ * the input monomials p_k, z_0 = a(x_t) + sum_k p_k(xi) b_k(x_t), so each
+ * predicted state coordinate is e_j K^t a + sum_k p_k e_j K^t b_k.  Setting it
+ * computes the rows C K^t (t = 1..H, the n_x state rows) on the device once
+ * (H * n_x * n floats of device memory, counted against the budget); each tick
+ * then folds them with a(x_t), b_k(x_t) and tests only the coordinates the
+ * safety set bounds (and the position for a track), at (1 + P) FMAs per
+ * read-out per step instead of n^2.  Results agree with FULL up to rounding.
+ * Ticks of a FACTORED session return MPMI_E_UNSUPPORTED for trajectory
+ * recording and with noise switched on (the noise enters after K and does not
+ * factor).  MPMI_E_INVALID_ARG for an unknown mode or a tick in flight,
+ * MPMI_E_OOM beyond the budget.  Blocks until the rows are computed. */
+#define MPMI_ROLLOUT_FULL 0
+#define MPMI_ROLLOUT_FACTORED 1
+int mpmi_session_set_rollout(mpmi_session* s, int32_t mode);
+
 /* ---- evaluate_candidates + select_input (Alg. 2) ------------------------ */
 /* Queues one tick on `stream`: copies x_t (nx doubles) and u_h (nu doubles) from
  * host memory (through the session's pinned staging buffer), samples the
@@ -249,6 +273,16 @@ int mpmi_sample_candidates(mpmi_session* s, const double* u_h_dev,
  * trajectories: traj_dev (device float32, n_slots x (H + 1) x n) receives z_0 and
  * every predicted z_t the candidate reached (t <= min(ttv + 1, H)); entries past
  * a candidate's early exit are left untouched. */
+/* Test hook, not part of the method: with on != 0 every later tick of the
+ * session announces its shared-memory staging (K rows and the track grid) to
+ * the kernel's mbarrier but issues no copy, so each block's bounded wait runs
+ * out after about a second (twice), the blocks skip their candidates and the
+ * result comes back with status MPMI_TIMEOUT (select_input: MPMI_E_TIMEOUT).
+ * Exercises the wait limit without a fault; only shapes that stage shared
+ * memory (race car with K in shared memory or a track, factorised race car)
+ * are affected.  on = 0 restores normal ticks. */
+int mpmi_debug_withhold_staging(mpmi_session* s, int32_t on);
+
 int mpmi_debug_trajectories(mpmi_session* s, const double* x_t_dev,
                             const double* u_h_dev, const float* candidates_dev,
                             uint64_t tick, mpmi_result* result_dev,

@@ -40,7 +40,8 @@ struct TickScratch {
   unsigned long long key;     // min over candidates of the selection key
   unsigned long long counts;  // (n_safe << 40) + executed prediction steps
   unsigned int done;          // blocks finished
-  unsigned int pad[3];
+  unsigned int error;         // set by a block whose bounded staging wait ran out
+  unsigned int pad[2];
 };
 
 struct TickArgs {
@@ -75,6 +76,13 @@ struct TickArgs {
   // Alg. 2's per-step noise z_i: sigma per state coordinate (zero past n_noise)
   float noise_sigma[MPMI_MAX_NX];
   int n_noise;
+  // factorised rollout: rows C K^t (t = 1..H, n_x rows of n each) and the state
+  // coordinates the safety test reads (position first when a track is set)
+  const float* ck;
+  int ro_n;
+  int ro_idx[MPMI_MAX_NX];
+  // test hook: stage nothing, so the bounded staging wait runs out
+  int withhold_staging;
 };
 
 }  // namespace mpmi
@@ -121,6 +129,12 @@ struct mpmi_session {
   bool in_flight = false;
   float noise_sigma[MPMI_MAX_NX] = {0, 0, 0, 0, 0, 0, 0, 0};
   int n_noise = 0;
+  int rollout = MPMI_ROLLOUT_FULL;
+  float* ck_dev = nullptr;         // C K^t rows (factorised rollout)
+  uint64_t ck_bytes = 0;
+  int fact_grid = 0;               // resident blocks of the factorised kernel
+  size_t fact_smem = 0;
+  int withhold_staging = 0;        // test hook (mpmi_debug_withhold_staging)
   uint64_t bytes = 0;
 };
 
@@ -128,6 +142,9 @@ namespace mpmi {
 // tick launch helpers shared by the API and the screener (mpmi_api.cu)
 TickArgs make_tick_args(const mpmi_session* s, uint64_t tick);
 int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint);
+// factorised rollout (factored.cu)
+int compute_powers(int kind, const float* K, int H, float* out, cudaStream_t st);
+int launch_factored(mpmi_session* s, TickArgs& a, cudaStream_t st, int n_hint);
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
 // host helpers implemented in fit.cpp / track.cpp

@@ -105,6 +105,20 @@ TickArgs make_tick_args(const mpmi_session* s, uint64_t tick) {
   a.scratch = s->scratch_dev;
   for (int j = 0; j < MPMI_MAX_NX; ++j) a.noise_sigma[j] = s->noise_sigma[j];
   a.n_noise = s->n_noise;
+  a.withhold_staging = s->withhold_staging;
+  if (s->rollout == MPMI_ROLLOUT_FACTORED) {
+    // read-outs: the position when a track is set, then every bounded coordinate
+    a.ck = s->ck_dev;
+    const DevSafety& ds = m->dev_safety;
+    int r = 0;
+    if (ds.has_track) {
+      a.ro_idx[r++] = 0;
+      a.ro_idx[r++] = 1;
+    }
+    for (int j = ds.has_track ? 2 : 0; j < m->nx; ++j)
+      if (!isinf(ds.lo[j]) || !isinf(ds.hi[j])) a.ro_idx[r++] = j;
+    a.ro_n = r;
+  }
   return a;
 }
 
@@ -123,6 +137,11 @@ int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, i
   // a device-side list short enough that 8 lanes per candidate still fit one wave
   const bool small = a.slot_list != nullptr && n_hint > 0 &&
                      (long long)n_hint * 8 <= (long long)s->ctx->sm_count * 512;
+  if (s->rollout == MPMI_ROLLOUT_FACTORED) {
+    if (traj) return fail(MPMI_E_UNSUPPORTED, "the factorised rollout records no trajectories");
+    if (a.n_noise > 0) return fail(MPMI_E_UNSUPPORTED, "the factorised rollout has no noise");
+    return launch_factored(s, a, st, n_hint);
+  }
   if (small) small_shape(s->model->kind, &lanes, &cands, &block);
   const bool noise = a.n_noise > 0;
   if (noise && a.tick >= (1ull << 48))
@@ -132,7 +151,8 @@ int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, i
   const size_t smem = k.k_smem + (a.safety.has_track ? (size_t)a.safety.track.blob_bytes : 0);
   const int t = (traj ? 1 : 0) + (small ? 2 : 0) + (noise ? 4 : 0);
   if (s->max_grid[t] == 0 || s->grid_smem[t] != smem) {
-    if (smem > 48 * 1024) {
+    // static (lane exchange) plus dynamic shared memory may pass the 48 KB default
+    if (smem > 0) {
       cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(k.k_smem + kMaxTrackBytes));
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
@@ -497,6 +517,11 @@ void mpmi_session_close(mpmi_session* s) {
   if (!s) return;
   DeviceGuard guard(s->ctx->device);
   if (s->in_flight) cudaEventSynchronize(s->done);
+  if (s->ck_dev) {
+    cudaDeviceSynchronize();
+    cudaFree(s->ck_dev);
+    s->ctx->used -= s->ck_bytes;
+  }
   cudaFree(s->scratch_dev);
   cudaFree(s->result_dev);
   cudaFree(s->in_dev);
@@ -529,6 +554,49 @@ int mpmi_session_set_noise(mpmi_session* s, const double* sigma, int32_t count) 
   }
   for (int j = 0; j < MPMI_MAX_NX; ++j) s->noise_sigma[j] = j < count ? (float)sigma[j] : 0.f;
   s->n_noise = count;
+  return MPMI_OK;
+}
+
+int mpmi_session_set_rollout(mpmi_session* s, int32_t mode) {
+  if (!s) return fail(MPMI_E_INVALID_ARG, "session is NULL");
+  if (mode != MPMI_ROLLOUT_FULL && mode != MPMI_ROLLOUT_FACTORED)
+    return fail(MPMI_E_INVALID_ARG, "set_rollout: unknown mode");
+  if (s->in_flight)
+    return fail(MPMI_E_INVALID_ARG, "set_rollout: a tick is in flight (call select_input first)");
+  if (mode == s->rollout) return MPMI_OK;
+  mpmi_ctx* ctx = s->ctx;
+  DeviceGuard guard(ctx->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+  if (mode == MPMI_ROLLOUT_FULL) {
+    // device-resident ticks may still read the rows
+    MPMI_CUDA(cudaDeviceSynchronize(), "set_rollout: waiting for ticks in flight");
+    cudaFree(s->ck_dev);
+    ctx->used -= s->ck_bytes;
+    s->ck_dev = nullptr;
+    s->ck_bytes = 0;
+    s->rollout = mode;
+    return MPMI_OK;
+  }
+  const mpmi_model* m = s->model;
+  const uint64_t bytes = (uint64_t)s->cfg.horizon * m->nx * m->n * sizeof(float);
+  if (!budget_ok(ctx, bytes)) return fail(MPMI_E_OOM, "set_rollout: exceeds the memory budget");
+  float* ck = nullptr;
+  if (cudaMalloc(&ck, bytes) != cudaSuccess)
+    return fail(MPMI_E_OOM, "set_rollout: cudaMalloc failed");
+  int rc = compute_powers(m->kind, m->K32_dev, s->cfg.horizon, ck, 0);
+  if (rc == MPMI_OK) {
+    const cudaError_t e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) rc = cuda_fail(e, "set_rollout: powers of K");
+  }
+  if (rc != MPMI_OK) {
+    cudaFree(ck);
+    return rc;
+  }
+  s->ck_dev = ck;
+  s->ck_bytes = bytes;
+  ctx->used += bytes;
+  s->fact_grid = 0;
+  s->rollout = mode;
   return MPMI_OK;
 }
 
@@ -579,6 +647,15 @@ int mpmi_select_input(mpmi_session* s, mpmi_result* out) {
   MPMI_CUDA(cudaEventSynchronize(s->done), "waiting for the tick");
   s->in_flight = false;
   *out = *s->result_host;
+  if (out->status == MPMI_TIMEOUT)
+    return fail(MPMI_E_TIMEOUT, "select_input: a block of the tick kernel timed out staging "
+                                "shared memory; the result is not a selection");
+  return MPMI_OK;
+}
+
+int mpmi_debug_withhold_staging(mpmi_session* s, int32_t on) {
+  if (!s) return fail(MPMI_E_INVALID_ARG, "session is NULL");
+  s->withhold_staging = on ? 1 : 0;
   return MPMI_OK;
 }
 

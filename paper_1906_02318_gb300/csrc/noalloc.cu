@@ -78,7 +78,7 @@ template <int KIND, int L, bool KSMEM>
 static NoAllocKernel make_noalloc() {
   NoAllocKernel k;
   k.launch = &launch_noalloc<KIND, L, KSMEM>;
-  k.k_smem = KSMEM ? (size_t)BasisTraits<KIND>::N * BasisTraits<KIND>::N * sizeof(float) : 0;
+  k.k_smem = KSMEM ? KSmem<BasisTraits<KIND>::N>::BYTES : 0;
   return k;
 }
 

@@ -67,16 +67,13 @@ __global__ void __launch_bounds__(kMaxBlock) serve_kernel(const __grid_constant_
   constexpr int S = (N % 32 == 0) ? N + 4 : ((N % 4 == 0) ? N : N + (4 - N % 4));
   constexpr int NW = kMaxBlock / 32;
   constexpr int ANG = (KIND == kBot) ? 0 : ((KIND == kCar) ? 2 : -1);
-  constexpr int KWORDS = KSMEM ? (N * N) / 4 : 0;
+  constexpr int KWORDS = KSMEM ? KSmem<N>::WORDS : 0;
   extern __shared__ uint4 s_dyn[];
   __shared__ __align__(16) float s_x[(L > 1) ? NW : 1][2][GPW][S];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int q = lane % L;
 
-  if constexpr (KSMEM) {
-    const uint4* src = reinterpret_cast<const uint4*>(sa.K);
-    for (int i = tid; i < KWORDS; i += blockDim.x) s_dyn[i] = __ldg(&src[i]);
-  }
+  if constexpr (KSMEM) stage_k<N>(sa.K, s_dyn, tid, blockDim.x);
   TrackView tv{nullptr, nullptr, nullptr, nullptr};
   if constexpr (B::TRACK) {
     if (sa.safety.has_track) {
@@ -176,7 +173,7 @@ static ServeKernel make_serve() {
   ServeKernel k;
   k.fn = reinterpret_cast<const void*>(&serve_kernel<KIND, L, C, KSMEM>);
   k.launch = &launch_serve<KIND, L, C, KSMEM>;
-  k.k_smem = KSMEM ? (size_t)BasisTraits<KIND>::N * BasisTraits<KIND>::N * sizeof(float) : 0;
+  k.k_smem = KSMEM ? KSmem<BasisTraits<KIND>::N>::BYTES : 0;
   k.per_warp = 32 / L * C;
   return k;
 }
@@ -323,7 +320,7 @@ int mpmi_server_create(mpmi_ctx* ctx, const mpmi_model* model, int32_t max_sessi
     cudaMemset(s->table_dev[b], 0, s->table_bytes);
   }
   // persistent grid: every block resident at once
-  if (s->smem > 48 * 1024)
+  if (s->smem > 0)
     cudaFuncSetAttribute(kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern.fn, s->block, s->smem);

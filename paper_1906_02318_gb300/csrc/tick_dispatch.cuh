@@ -27,12 +27,13 @@ static TickKernel make_kernel() {
   TickKernel k;
   k.fn = reinterpret_cast<const void*>(&tick_kernel<KIND, L, C, KSMEM, TRAJ, false, NOISE>);
   k.launch = &launch_tick<KIND, L, C, KSMEM, TRAJ, NOISE>;
-  k.k_smem = KSMEM ? (size_t)BasisTraits<KIND>::N * BasisTraits<KIND>::N * sizeof(float) : 0;
+  k.k_smem = KSMEM ? KSmem<BasisTraits<KIND>::N>::BYTES : 0;
   return k;
 }
 
-// Compiled launch shapes: (lanes, candidates per thread); the race car with one
-// lane keeps K in shared memory.
+// Compiled launch shapes: (lanes, candidates per thread).  The race car keeps K
+// in shared memory with 1, 2 or 4 lanes per candidate and in registers with 8 or
+// 16; the other bases keep K in registers.
 template <int KIND, bool TRAJ, bool NOISE>
 static TickKernel pick_shape(int lanes, int cands) {
   if constexpr (KIND == kBot) {
@@ -43,6 +44,8 @@ static TickKernel pick_shape(int lanes, int cands) {
   } else if constexpr (KIND == kCar) {
     if (lanes == 1 && cands == 1) return make_kernel<KIND, 1, 1, true, TRAJ, NOISE>();
     if (lanes == 1 && cands == 2) return make_kernel<KIND, 1, 2, true, TRAJ, NOISE>();
+    if (lanes == 2 && cands == 1) return make_kernel<KIND, 2, 1, true, TRAJ, NOISE>();
+    if (lanes == 4 && cands == 1) return make_kernel<KIND, 4, 1, true, TRAJ, NOISE>();
     if (lanes == 8 && cands == 1) return make_kernel<KIND, 8, 1, false, TRAJ, NOISE>();
     if (lanes == 16 && cands == 1) return make_kernel<KIND, 16, 1, false, TRAJ, NOISE>();
   } else {

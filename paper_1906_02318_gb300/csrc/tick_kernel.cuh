@@ -29,6 +29,89 @@ namespace mpmi {
 constexpr int kMaxBlock = 256;
 constexpr unsigned kFull = 0xffffffffu;
 
+// ---- shared-memory staging by the bulk-copy engine (TMA, non-tensor form) ----
+// Thread 0 initialises an mbarrier, announces the byte count and issues
+// cp.async.bulk copies global -> shared that complete on it; every thread waits
+// on phase 0 before reading the staged data.  Each wait is bounded by
+// kWaitCycles SM clocks (about a second); a block whose wait runs out skips its
+// candidates and flags the tick instead of hanging.
+constexpr long long kWaitCycles = 1ll << 31;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void bar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// bytes: a multiple of 16; dst and src 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// true once phase `parity` of the barrier has completed, false after kWaitCycles
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+
+// Issues the copies of one staging (thread 0): K with padded rows (k_rows > 0,
+// row r of n floats to word r * s4) and then `blob_bytes` of blob.
+__device__ __forceinline__ void stage_issue(uint64_t* bar, uint4* dst, const float* K, int k_rows,
+                                            int k_cols, int s4, const uint4* blob, int blob_bytes,
+                                            bool withhold) {
+  const uint32_t row_bytes = (uint32_t)k_cols * 4u;
+  bar_expect(bar, (uint32_t)k_rows * row_bytes + (uint32_t)blob_bytes);
+  if (withhold) return;
+  for (int r = 0; r < k_rows; ++r) bulk_g2s(dst + r * s4, K + (size_t)r * k_cols, row_bytes, bar);
+  uint4* bd = dst + k_rows * s4;
+  for (int off = 0; off < blob_bytes; off += 32768) {
+    const int b = blob_bytes - off < 32768 ? blob_bytes - off : 32768;
+    bulk_g2s(reinterpret_cast<char*>(bd) + off, reinterpret_cast<const char*>(blob) + off,
+             (uint32_t)b, bar);
+  }
+}
+
+// K staged in shared memory (KSMEM shapes): row r starts at 16-byte word r * S4,
+// rows padded by four floats so that the L lanes of a group, which read L
+// different rows at once, fall into different banks.
+template <int N>
+struct KSmem {
+  static constexpr int S4 = (N + 4) / 4;    // 16-byte words per padded row
+  static constexpr int WORDS = N * S4;
+  static constexpr size_t BYTES = (size_t)WORDS * 16;
+};
+
+template <int N>
+__device__ __forceinline__ void stage_k(const float* K, uint4* dst, int tid, int nthreads) {
+  constexpr int W = N / 4;
+  const uint4* src = reinterpret_cast<const uint4*>(K);
+  for (int i = tid; i < N * W; i += nthreads) dst[(i / W) * KSmem<N>::S4 + i % W] = __ldg(&src[i]);
+}
+
 // Alg. 2 first step: the input held by candidate `slot`.
 template <int NU, class P>
 __device__ __forceinline__ void candidate_value(const P& a, int slot, const float* uh32,
@@ -146,13 +229,20 @@ __device__ __forceinline__ bool track_ok(const DevTrack& tr, const TrackView& v,
         ok = true;
       } else if (cls == kCellBoundary) {
         const int off = (int)((c >> 2) & 0x3FFFFFu), cnt = (int)(c >> 24);
-        for (int i = q; i < cnt; i += L) {
-          const int s = v.list[off + i];
-          const float4 sg = v.seg[s];
-          const float rx = px - sg.x, ry = py - sg.y;
-          const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * v.inv[s], 0.f), 1.f);
-          const float ex = rx - t * sg.z, ey = ry - t * sg.w;
-          if (ex * ex + ey * ey < tr.w2) {
+        // four independent segment tests per round (entries past the list end
+        // repeat its last entry); the OR over the list is unchanged
+        for (int i0 = q; i0 < cnt; i0 += 4 * L) {
+          bool hit = false;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int s = v.list[off + min(i0 + j * L, cnt - 1)];
+            const float4 sg = v.seg[s];
+            const float rx = px - sg.x, ry = py - sg.y;
+            const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * v.inv[s], 0.f), 1.f);
+            const float ex = rx - t * sg.z, ey = ry - t * sg.w;
+            hit = hit || (ex * ex + ey * ey < tr.w2);
+          }
+          if (hit) {
             ok = true;
             break;
           }
@@ -170,7 +260,8 @@ __device__ __forceinline__ bool track_ok(const DevTrack& tr, const TrackView& v,
 // Decode of the winning key into the tick's result record.
 template <int NU, class P>
 __device__ __forceinline__ void write_result(const P& a, unsigned long long k,
-                                             unsigned long long cnt, const float* uh) {
+                                             unsigned long long cnt, const float* uh,
+                                             bool timed_out = false) {
   const int pick = (int)(k & 0x7FFFFFull);
   const int hm = (int)(k >> 55);
   mpmi_result r;
@@ -182,7 +273,7 @@ __device__ __forceinline__ void write_result(const P& a, unsigned long long k,
   for (int j = 0; j < NU; ++j)
     r.u_r[j] = (a.include_user && pick == 0) ? a.u_h[j] : (double)xb[j];
   r.index = pick;
-  r.status = hm == 0 ? MPMI_SAFE : MPMI_FALLBACK;
+  r.status = timed_out ? MPMI_TIMEOUT : (hm == 0 ? MPMI_SAFE : MPMI_FALLBACK);
   r.n_safe = (int32_t)(cnt >> 40);
   r.ttv = a.horizon - hm;
   r.cost = __uint_as_float((unsigned int)((k >> 23) & 0xFFFFFFFFull));
@@ -262,7 +353,7 @@ __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, in
   }
 
   for (int t = 1; t <= H; ++t) {
-    if constexpr (KSMEM) {
+    if constexpr (KSMEM && L == 1) {
       // z <- K z with K read from shared memory (one broadcast LDS.128 feeds 4 C
       // FMAs).  The empty asm keeps the compiler from hoisting the loop-invariant
       // K loads out of the step loop (1024 values would not fit in registers).
@@ -275,7 +366,7 @@ __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, in
         for (int c = 0; c < C; ++c) av[c] = 0.f;
 #pragma unroll
         for (int k4 = 0; k4 < N / 4; ++k4) {
-          const float4 kv = sK4[r * (N / 4) + k4];
+          const float4 kv = sK4[r * KSmem<N>::S4 + k4];
 #pragma unroll
           for (int c = 0; c < C; ++c) {
             av[c] = __fmaf_rn(kv.x, z[c][4 * k4], av[c]);
@@ -314,22 +405,47 @@ __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, in
 #pragma unroll
         for (int j = 0; j < N; ++j) z[c][j] = zn[c][j];
     } else {
-      // L lanes per candidate: this lane's rows, then exchange through shared memory
+      // L lanes per candidate: this lane's rows, then exchange through shared
+      // memory.  K in registers: rows [qR, qR + R).  K in shared memory: rows
+      // q, q + L, ..., so the L rows read at once are consecutive padded rows in
+      // distinct banks.
       float zn[R];
+      if constexpr (KSMEM) {
+        asm volatile("" ::: "memory");
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float accv[ACC];
+        for (int r = 0; r < R; ++r) {
+          const float4* row = sK4 + (q + L * r) * KSmem<N>::S4;
+          float v = 0.f;
 #pragma unroll
-        for (int e = 0; e < ACC; ++e) accv[e] = 0.f;
+          for (int k4 = 0; k4 < N / 4; ++k4) {
+            const float4 kv = row[k4];
+            v = __fmaf_rn(kv.x, z[0][4 * k4], v);
+            v = __fmaf_rn(kv.y, z[0][4 * k4 + 1], v);
+            v = __fmaf_rn(kv.z, z[0][4 * k4 + 2], v);
+            v = __fmaf_rn(kv.w, z[0][4 * k4 + 3], v);
+          }
+          zn[r] = v;
+        }
+      } else {
 #pragma unroll
-        for (int k = 0; k < N; ++k) accv[k % ACC] = __fmaf_rn(kr[r][k], z[0][k], accv[k % ACC]);
-        float v = accv[0];
+        for (int r = 0; r < R; ++r) {
+          float accv[ACC];
 #pragma unroll
-        for (int e = 1; e < ACC; ++e) v += accv[e];
-        zn[r] = v;
+          for (int e = 0; e < ACC; ++e) accv[e] = 0.f;
+#pragma unroll
+          for (int k = 0; k < N; ++k)
+            accv[k % ACC] = __fmaf_rn(kr[r][k], z[0][k], accv[k % ACC]);
+          float v = accv[0];
+#pragma unroll
+          for (int e = 1; e < ACC; ++e) v += accv[e];
+          zn[r] = v;
+        }
       }
       float* buf = xbuf + ((t & 1) * GPW + g) * S;
-      if constexpr (R % 4 == 0) {
+      if constexpr (KSMEM) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[q + L * r] = zn[r];
+      } else if constexpr (R % 4 == 0) {
 #pragma unroll
         for (int r = 0; r < R; r += 4)
           *reinterpret_cast<float4*>(buf + q * R + r) =
@@ -394,6 +510,60 @@ __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, in
   }
 }
 
+// End of a tick launch: warp -> block -> grid reduction of the selection key
+// and the counts into the session's reduction record (one atomicMin/atomicAdd per
+// block); the block that finishes last decodes the result and resets the record.
+template <int NU, class P>
+__device__ __forceinline__ void session_epilogue(const P& a, unsigned long long best,
+                                                 unsigned int n_safe, unsigned int n_exec,
+                                                 const float* uh, bool failed = false) {
+  __shared__ unsigned long long s_key[kMaxBlock / 32];
+  __shared__ unsigned long long s_cnt[kMaxBlock / 32];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wpb = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(kFull, best, o);
+    best = other < best ? other : best;
+    n_exec += __shfl_xor_sync(kFull, n_exec, o);
+    n_safe += __shfl_xor_sync(kFull, n_safe, o);
+  }
+  if (lane == 0) {
+    s_key[warp] = best;
+    s_cnt[warp] = ((unsigned long long)n_safe << 40) + n_exec;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long bk = s_key[0], bc = s_cnt[0];
+    for (int w = 1; w < wpb; ++w) {
+      bk = s_key[w] < bk ? s_key[w] : bk;
+      bc += s_cnt[w];
+    }
+    TickScratch* sc = a.scratch;
+    atomicMin(&sc->key, bk);
+    atomicAdd(&sc->counts, bc);
+    if (failed) atomicOr(&sc->error, 1u);
+    __threadfence();
+    const unsigned int prev = atomicAdd(&sc->done, 1u);
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last && tid == 0) {
+    // last block: every other block's atomics are visible (fence + counter)
+    __threadfence();
+    TickScratch* sc = a.scratch;
+    const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&sc->key);
+    const unsigned long long cnt = *reinterpret_cast<volatile unsigned long long*>(&sc->counts);
+    const unsigned int err = *reinterpret_cast<volatile unsigned int*>(&sc->error);
+    write_result<NU>(a, k, cnt, uh, err != 0u);
+    sc->key = ~0ull;
+    sc->counts = 0ull;
+    sc->error = 0u;
+    sc->done = 0u;
+  }
+}
+
 // Template parameters of the tick kernel:
 //   L        lanes per candidate (K rows split across the lanes, see above);
 //   C        candidates per thread (L = 1 only): more independent FMA chains;
@@ -413,13 +583,13 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   static_assert(N % L == 0, "lanes must divide the lifted dimension");
   static_assert(32 % L == 0, "lanes must divide the warp");
   static_assert(C == 1 || L == 1, "several candidates per thread need L = 1");
-  static_assert(!KSMEM || (L == 1 && N % 4 == 0), "K in shared memory needs L = 1, n % 4 == 0");
+  static_assert(!KSMEM || N % 4 == 0, "K in shared memory needs n % 4 == 0");
   constexpr int R = N / L;              // rows of K per lane
   constexpr int GPW = 32 / L;           // candidate groups per warp
   constexpr int S = (N % 32 == 0) ? N + 4 : ((N % 4 == 0) ? N : N + (4 - N % 4));
   constexpr int NW = kMaxBlock / 32;
   constexpr int ANG = (KIND == kBot) ? 0 : ((KIND == kCar) ? 2 : -1);
-  constexpr int KWORDS = KSMEM ? (N * N) / 4 : 0;  // 16-byte words of K in shared memory
+  constexpr int KWORDS = KSMEM ? KSmem<N>::WORDS : 0;  // 16-byte words of K in shared memory
 
   extern __shared__ uint4 s_dyn[];  // [K (KSMEM)] [track blob (race car)]
   __shared__ __align__(16) float s_x[(L > 1) ? NW : 1][2][GPW][S];
@@ -434,17 +604,32 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   // number of candidates this launch evaluates (all slots, or a device-side list)
   const int n_eval = a.n_list ? *a.n_list : a.n_slots;
 
-  // stage K (KSMEM) and the track grid (race car) while the per-tick state is prepared
-  if constexpr (KSMEM) {
-    const uint4* src = reinterpret_cast<const uint4*>(a.K);
-    for (int i = tid; i < KWORDS; i += blockDim.x) s_dyn[i] = __ldg(&src[i]);
+  // stage K (KSMEM) and the track grid (race car) while the per-tick state is
+  // prepared: bulk copies on an mbarrier (plain loads in the no-allocation
+  // variant, whose K pointer comes from the caller with no alignment promise)
+  __shared__ uint64_t s_bar;
+  constexpr bool BULK = !PARTIALS;
+  const bool track_on = B::TRACK && a.safety.has_track;
+  const bool staging = KSMEM || track_on;
+  if constexpr (BULK) {
+    if (staging) {
+      if (tid == 0) bar_init(&s_bar);
+      __syncthreads();
+      if (tid == 0)
+        stage_issue(&s_bar, s_dyn, a.K, KSMEM ? N : 0, N, KSmem<N>::S4, a.safety.track.blob,
+                    track_on ? a.safety.track.blob_bytes : 0, a.withhold_staging != 0);
+    }
+  } else {
+    if constexpr (KSMEM) stage_k<N>(a.K, s_dyn, tid, blockDim.x);
+    if (track_on) {
+      const int words = a.safety.track.blob_bytes >> 4;
+      for (int i = tid; i < words; i += blockDim.x) s_dyn[KWORDS + i] = __ldg(&a.safety.track.blob[i]);
+    }
   }
   TrackView tv{nullptr, nullptr, nullptr, nullptr};
   if constexpr (B::TRACK) {
     if (a.safety.has_track) {
       uint4* dst = s_dyn + KWORDS;
-      const int words = a.safety.track.blob_bytes >> 4;
-      for (int i = tid; i < words; i += blockDim.x) dst[i] = __ldg(&a.safety.track.blob[i]);
       const char* base = reinterpret_cast<const char*>(dst);
       tv.cells = reinterpret_cast<const uint32_t*>(base);
       tv.list = reinterpret_cast<const uint16_t*>(base + a.safety.track.off_list);
@@ -479,18 +664,33 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
       }
     }
   }
-  if constexpr (KSMEM || B::TRACK) __syncthreads();
+  bool failed = false;
+  if constexpr (BULK) {
+    if (staging) {
+      // a wait that runs out is retried once (copies may still be in flight), then
+      // the whole block agrees to skip its candidates
+      bool ok = bar_wait(&s_bar, 0);
+      if (!ok) ok = bar_wait(&s_bar, 0);
+      failed = __syncthreads_or(!ok) != 0;
+    }
+  } else {
+    if constexpr (KSMEM || B::TRACK) __syncthreads();
+  }
 
   unsigned long long best = ~0ull;
   unsigned int n_safe = 0, n_exec = 0;
   const int wpb = blockDim.x >> 5;
   constexpr int PER_WARP = GPW * C;  // candidate slots per warp-tile
-  const int n_wtiles = (n_eval + PER_WARP - 1) / PER_WARP;
+  const int n_wtiles = failed ? 0 : (n_eval + PER_WARP - 1) / PER_WARP;
   for (int wt = blockIdx.x * wpb + warp; wt < n_wtiles; wt += gridDim.x * wpb)
     run_tile<KIND, L, C, KSMEM, TRAJ, NOISE>(a, a.safety, wt, n_eval, xs, uh, sn, cs, kr, sK4, tv,
                                       &s_x[L > 1 ? warp : 0][0][0][0], best, n_safe, n_exec);
 
-  // warp -> block -> grid reduction
+  if constexpr (!PARTIALS) {
+    session_epilogue<NU>(a, best, n_safe, n_exec, uh, failed);
+    return;
+  }
+  // warp -> block reduction, then per-block partials folded by the last block
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long other = __shfl_xor_sync(kFull, best, o);
@@ -503,7 +703,7 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
     s_cnt[warp] = ((unsigned long long)n_safe << 40) + n_exec;
   }
   __syncthreads();
-  if constexpr (PARTIALS) {
+  {
     unsigned long long* pk = a.partials;
     unsigned long long* pc = a.partials + a.partials_cap;
     unsigned long long* blocks_done = a.partials + 2 * a.partials_cap;
@@ -549,31 +749,6 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
       *blocks_done = 0ull;
     }
     return;
-  }
-  if (tid == 0) {
-    unsigned long long bk = s_key[0], bc = s_cnt[0];
-    for (int w = 1; w < wpb; ++w) {
-      bk = s_key[w] < bk ? s_key[w] : bk;
-      bc += s_cnt[w];
-    }
-    TickScratch* sc = a.scratch;
-    atomicMin(&sc->key, bk);
-    atomicAdd(&sc->counts, bc);
-    __threadfence();
-    const unsigned int prev = atomicAdd(&sc->done, 1u);
-    s_last = (prev == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (s_last && tid == 0) {
-    // last block: every other block's atomics are visible (fence + counter)
-    __threadfence();
-    TickScratch* sc = a.scratch;
-    const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&sc->key);
-    const unsigned long long cnt = *reinterpret_cast<volatile unsigned long long*>(&sc->counts);
-    write_result<NU>(a, k, cnt, uh);
-    sc->key = ~0ull;
-    sc->counts = 0ull;
-    sc->done = 0u;
   }
 }
 

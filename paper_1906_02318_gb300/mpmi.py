@@ -22,7 +22,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libmpmi.so")
 BASIS = {"bot": 0, "car": 1, "linear": 2}
 BASIS_DIMS = {"bot": (4, 1), "car": (6, 2)}
 SAMPLER = {"uniform": 0, "grid": 1, "external": 2}
-SAFE, FALLBACK = 0, 1
+ROLLOUT = {"full": 0, "factored": 1}
+SAFE, FALLBACK, TIMEOUT = 0, 1, 2
 MAX_NX, MAX_NU = 8, 4
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "NONFINITE", -4: "CUDA", -5: "NOT_READY",
           -6: "UNSUPPORTED"}
@@ -80,6 +81,8 @@ _SIGNATURES = {
                                   ctypes.POINTER(c_vp)]),
     "mpmi_session_close": (None, [c_vp]),
     "mpmi_session_set_noise": (c_i32, [c_vp, P_dbl, c_i32]),
+    "mpmi_session_set_rollout": (c_i32, [c_vp, c_i32]),
+    "mpmi_debug_withhold_staging": (c_i32, [c_vp, c_i32]),
     "mpmi_session_launch_shape": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32),
                                           ctypes.POINTER(c_i32)]),
     "mpmi_evaluate_candidates": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
@@ -336,6 +339,16 @@ class Session:
         sig = np.ascontiguousarray(np.atleast_1d(np.asarray(sigma, dtype=np.float64)))
         _check(self.ctx.lib.mpmi_session_set_noise(
             self.handle, sig.ctypes.data_as(P_dbl), int(sig.size)))
+
+    def set_rollout(self, mode: str):
+        """mpmi_session_set_rollout: "full" (z <- K z, Alg. 2) or "factored"
+        (read-outs from precomputed rows C K^t; an exact-in-real-arithmetic ablation)."""
+        _check(self.ctx.lib.mpmi_session_set_rollout(self.handle, ROLLOUT[mode]))
+
+    def withhold_staging(self, on: bool):
+        """mpmi_debug_withhold_staging: test hook that makes the kernel's bounded
+        staging wait run out (result status TIMEOUT)."""
+        _check(self.ctx.lib.mpmi_debug_withhold_staging(self.handle, int(bool(on))))
 
     def close(self):
         if self.handle:

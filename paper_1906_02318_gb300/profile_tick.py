@@ -11,6 +11,10 @@ exact rollout of the kept slots, fallback) with an untrained screener and the
 given --tau / --k.
 --mode serve: --ticks batches of --sessions requests (N log-uniform 1k..64k, H
 20..100) through one continuous-batching server of the chosen model.
+--rollout factored: plain ticks in the factorised read-out form (one launch of
+the factorised kernel per tick after the one-off powers of K).
+--noise s1,s2,..: Alg. 2's per-step noise with these standard deviations on the
+first state coordinates.
 """
 from __future__ import annotations
 
@@ -44,6 +48,8 @@ def main():
     ap.add_argument("--k", type=int, default=4096)
     ap.add_argument("--tau", type=float, default=0.0)
     ap.add_argument("--sessions", type=int, default=64)
+    ap.add_argument("--rollout", choices=["full", "factored"], default="full")
+    ap.add_argument("--noise", default="", help="comma-separated sigma per state coordinate")
     args = ap.parse_args()
 
     build.build()
@@ -70,6 +76,10 @@ def main():
         return serve_mode(args, ctx, model, lo, hi, states, uhs)
     sess = lib.Session(ctx, model, args.n, args.horizon, lo, hi, seed=2, lanes=args.lanes,
                        block=args.block, cands=args.cands)
+    if args.rollout != "full":
+        sess.set_rollout(args.rollout)
+    if args.noise:
+        sess.set_noise([float(v) for v in args.noise.split(",")])
     scr = None
     if args.mode == "screened":
         if args.basis != "car":

@@ -120,7 +120,7 @@ def test_noisy_bot_ticks(lib, ctx, bot, lanes, cands):
     assert changed > 0                                  # the noise matters at this sigma
 
 
-@pytest.mark.parametrize("lanes,cands", [(1, 1), (1, 2), (8, 1), (16, 1)])
+@pytest.mark.parametrize("lanes,cands", [(1, 1), (1, 2), (2, 1), (4, 1), (8, 1), (16, 1)])
 def test_noisy_car_ticks(lib, ctx, car, lanes, cands):
     env, model = car
     sigma = data.to_f32_exact(np.array([0.03, 0.03, 0.005, 0.1, 0.02, 0.01]))

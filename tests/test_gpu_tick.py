@@ -140,7 +140,7 @@ def test_bot_inflated_barrier(lib, ctx):
 
 
 # ------------------------------------------------------------------- race car
-@pytest.mark.parametrize("lanes,cands", [(1, 1), (1, 2), (8, 1), (16, 1)])
+@pytest.mark.parametrize("lanes,cands", [(1, 1), (1, 2), (2, 1), (4, 1), (8, 1), (16, 1)])
 def test_car_ticks(lib, ctx, car, lanes, cands):
     env, model = car
     x0 = data.car_start_state(env.track, vx=14.0)
@@ -370,8 +370,8 @@ def test_all_launch_shapes_agree_bit_for_bit(lib, ctx, bot, car, which):
     """Every compiled launch shape sums each row of K z in the same order, so the
     per-candidate outcomes and the selection are identical across shapes."""
     env, model = bot if which == "bot" else car
-    shapes = [(1, 1), (1, 2), (2, 1), (4, 1)] if which == "bot" else [(1, 1), (1, 2), (8, 1),
-                                                                        (16, 1)]
+    shapes = [(1, 1), (1, 2), (2, 1), (4, 1)] if which == "bot" else [(1, 1), (1, 2), (2, 1),
+                                                                        (4, 1), (8, 1), (16, 1)]
     H = 50 if which == "bot" else 60
     x_t = (np.array([0.3, 0.9, 1.2, 0.6]) if which == "bot"
            else data.car_start_state(env.track, vx=15.0) + np.array([1.0, -0.5, 0.05, 0, 0, 0]))
