@@ -35,6 +35,19 @@ BASES = {
 }
 
 
+# Features that depend on the input alone (and the constant).  With the input
+# held over the horizon (Sec. VII-B) a prediction step leaves them unchanged, so
+# their rows of K are unit rows (see ``fit``).
+HELD = {"bot": (4, 11), "car": (6, 7, 30, 31)}
+
+
+def held_features(basis: str, nx: int | None = None, nu: int | None = None):
+    """Indices of the held (input-only and constant) features of a basis."""
+    if basis == "linear":
+        return tuple(range(nx, nx + nu))
+    return HELD[basis]
+
+
 def dims(basis: str, nx: int | None = None, nu: int | None = None):
     """(n, nx, nu) of a basis; the linear basis takes nx, nu explicitly."""
     if basis == "linear":

@@ -11,13 +11,17 @@ i.e. with the lifted snapshots stacked as rows, X K^T ~= Y, solved here with the
 library least-squares routine in float64.  No regularisation, no sparsity
 selection (readings stated in the design notes).  Because the input is held over
 the horizon, each pure-input feature (u, delta, a, delta^2) and the constant
-appear unchanged in Y, so the matching rows of K are exact unit rows.
+appear unchanged in Y: their column of Y is a column of X, so the exact
+least-squares solution for their rows of K is the unit row (zero residual,
+unique when X has full column rank).  The routine returns it up to rounding
+(~1e-15); those rows are set to the exact unit rows, so a rollout carries the
+held features unchanged.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from .basis import lift
+from .basis import held_features, lift
 
 
 def fit_koopman(basis: str, x: np.ndarray, u: np.ndarray, x_next: np.ndarray):
@@ -26,7 +30,12 @@ def fit_koopman(basis: str, x: np.ndarray, u: np.ndarray, x_next: np.ndarray):
     Y = lift(basis, x_next, u)
     kt, *_ = np.linalg.lstsq(X, Y, rcond=None)
     K = kt.T.copy()
-    res = np.linalg.norm(X @ kt - Y) / np.linalg.norm(Y)
+    n = K.shape[0]
+    nx = np.atleast_2d(x).shape[1]
+    nu = np.atleast_2d(u).shape[1] if np.ndim(u) > 1 else 1
+    for j in held_features(basis, nx, nu):
+        K[j] = np.eye(n)[j]
+    res = np.linalg.norm(X @ K.T - Y) / np.linalg.norm(Y)
     return K, float(res)
 
 

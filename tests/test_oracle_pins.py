@@ -200,8 +200,19 @@ def test_fit_held_input_rows_are_unit_rows(kind, held):
     x, u, xn = data.transitions(kind, 1 if kind == "bot" else 3, 3000)
     K, res = fit.fit_koopman(kind, x, u, xn)
     n = K.shape[0]
+    assert basis.held_features(kind) == held
     for r in held:
-        assert np.abs(K[r] - np.eye(n)[r]).max() < 1e-12
+        assert np.array_equal(K[r], np.eye(n)[r])          # set exactly
+    # the unconstrained least-squares solution (normal equations, another
+    # routine) is the unit row up to rounding, and the other rows agree
+    X, Y = basis.lift(kind, x, u), basis.lift(kind, xn, u)
+    K_ne = np.linalg.solve(X.T @ X, X.T @ Y).T
+    for r in held:
+        assert np.abs(K_ne[r] - np.eye(n)[r]).max() < 1e-8
+    others = [r for r in range(n) if r not in held]
+    assert np.abs(K_ne[others] - K[others]).max() < 1e-6 * max(1.0, np.abs(K).max())
+    res_ne = np.linalg.norm(X @ K_ne.T - Y) / np.linalg.norm(Y)
+    assert abs(res - res_ne) < 1e-9
     assert 0 < res < 0.2
 
 
