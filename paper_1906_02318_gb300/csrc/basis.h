@@ -131,6 +131,17 @@ MPMI_HD void feature_split(int kind, int j, const T* x, T s, T c, T* a, T* b) {
   }
 }
 
+// Features that depend on the input alone (and the constant).  With the input
+// held over the horizon (Sec. VII-B) a prediction step leaves them unchanged:
+// their column of the fit target equals their regressor column, so their rows
+// of K are exact unit rows (the fit sets them; operators from callers are
+// checked), and a rollout need not recompute them.
+MPMI_HD constexpr bool held_feature(int kind, int j) {
+  return kind == kBot   ? (j == 4 || j == 11)
+         : kind == kCar ? (j == 6 || j == 7 || j == 30 || j == 31)
+                        : j >= (kind == kLin11 ? 1 : (kind == kLin22 ? 2 : 4));
+}
+
 // Index of the state coordinate whose sine/cosine the basis uses (-1: none).
 MPMI_HD int angle_index(int kind) { return kind == kBot ? 0 : (kind == kCar ? 2 : -1); }
 

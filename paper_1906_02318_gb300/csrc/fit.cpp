@@ -91,6 +91,11 @@ int fit_householder(int kind, const double* x, const double* u, const double* xn
     }
     for (int k = 0; k < n; ++k) (*K)[(size_t)c * n + k] = xs[k];
   }
+  // held input features: the exact solution of their rows is the unit row, which
+  // the back substitution returns up to rounding
+  for (int c = 0; c < n; ++c)
+    if (held_feature(kind, c))
+      for (int k = 0; k < n; ++k) (*K)[(size_t)c * n + k] = k == c ? 1.0 : 0.0;
   if (residual) {
     double num = 0.0, den = 0.0;
     for (int c = 0; c < n; ++c) {

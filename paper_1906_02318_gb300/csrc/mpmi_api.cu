@@ -326,6 +326,22 @@ int mpmi_model_from_operator(mpmi_ctx* ctx, const mpmi_basis_desc* basis, const 
   md->kind = kind;
   md->n = n; md->nx = nx; md->nu = nu; md->np = np;
   md->K64.assign(K, K + n * n);
+  // rows of held input features must be unit rows (the input is held over the
+  // horizon); rounding-level deviations are set exact, anything else is refused
+  for (int j = 0; j < n; ++j) {
+    if (!held_feature(kind, j)) continue;
+    for (int k = 0; k < n; ++k) {
+      const double want = k == j ? 1.0 : 0.0;
+      if (fabs(md->K64[(size_t)j * n + k] - want) > 1e-6) {
+        delete md;
+        return fail(MPMI_E_INVALID_ARG,
+                    "model_from_operator: row " + std::to_string(j) +
+                        " belongs to a held input feature and must be a unit row "
+                        "(the input is held over the horizon)");
+      }
+      md->K64[(size_t)j * n + k] = want;
+    }
+  }
   if ((rc = model_upload(ctx, md)) != MPMI_OK) {
     free_model_device(md);
     delete md;

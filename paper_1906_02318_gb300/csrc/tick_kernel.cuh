@@ -287,8 +287,12 @@ __device__ __forceinline__ void write_result(const P& a, unsigned long long k,
 // One warp-tile: the PER_WARP = 32 C / L candidate positions wt * PER_WARP ...
 // of a tick (Alg. 2 for each: sample, lift, predict with early exit, test,
 // score), folded into the caller's running key minimum and counts.  P is the
-// tick's parameter record (TickArgs, or a served session's record).
-template <int KIND, int L, int C, bool KSMEM, bool TRAJ, bool NOISE, class P, class KR>
+// tick's parameter record (TickArgs, or a served session's record).  HELD: the
+// operator's held-feature rows are exact unit rows (true for every model the
+// library built), so the one-lane shapes copy those coordinates instead of
+// recomputing them -- bit for bit the same z for finite states.
+template <int KIND, int L, int C, bool KSMEM, bool TRAJ, bool NOISE, bool HELD, class P,
+          class KR>
 __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, int wt, int n_eval,
                                          const float* xs, const float* uh, float sn, float cs,
                                          const KR& kr, const float4* sK4, const TrackView& tv,
@@ -361,6 +365,11 @@ __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, in
       float acc[C][N];
 #pragma unroll
       for (int r = 0; r < N; ++r) {
+        if (HELD && held_feature(KIND, r)) {  // unit row: the feature is held
+#pragma unroll
+          for (int c = 0; c < C; ++c) acc[c][r] = z[c][r];
+          continue;
+        }
         float av[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) av[c] = 0.f;
@@ -388,15 +397,13 @@ __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, in
       for (int c = 0; c < C; ++c) {
 #pragma unroll
         for (int r = 0; r < N; ++r) {
-          float accv[ACC];
+          if (HELD && held_feature(KIND, r)) {  // unit row: the feature is held
+            zn[c][r] = z[c][r];
+            continue;
+          }
+          float v = 0.f;
 #pragma unroll
-          for (int e = 0; e < ACC; ++e) accv[e] = 0.f;
-#pragma unroll
-          for (int k = 0; k < N; ++k)
-            accv[k % ACC] = __fmaf_rn(kr[r][k], z[c][k], accv[k % ACC]);
-          float v = accv[0];
-#pragma unroll
-          for (int e = 1; e < ACC; ++e) v += accv[e];
+          for (int k = 0; k < N; ++k) v = __fmaf_rn(kr[r][k], z[c][k], v);
           zn[c][r] = v;
         }
       }
@@ -437,7 +444,7 @@ __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, in
             accv[k % ACC] = __fmaf_rn(kr[r][k], z[0][k], accv[k % ACC]);
           float v = accv[0];
 #pragma unroll
-          for (int e = 1; e < ACC; ++e) v += accv[e];
+          for (int e = 1; e < ACC; ++e) v = __fadd_rn(v, accv[e]);
           zn[r] = v;
         }
       }
@@ -683,7 +690,7 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   constexpr int PER_WARP = GPW * C;  // candidate slots per warp-tile
   const int n_wtiles = failed ? 0 : (n_eval + PER_WARP - 1) / PER_WARP;
   for (int wt = blockIdx.x * wpb + warp; wt < n_wtiles; wt += gridDim.x * wpb)
-    run_tile<KIND, L, C, KSMEM, TRAJ, NOISE>(a, a.safety, wt, n_eval, xs, uh, sn, cs, kr, sK4, tv,
+    run_tile<KIND, L, C, KSMEM, TRAJ, NOISE, !PARTIALS>(a, a.safety, wt, n_eval, xs, uh, sn, cs, kr, sK4, tv,
                                       &s_x[L > 1 ? warp : 0][0][0][0], best, n_safe, n_exec);
 
   if constexpr (!PARTIALS) {

@@ -387,3 +387,21 @@ def test_all_launch_shapes_agree_bit_for_bit(lib, ctx, bot, car, which):
         assert np.array_equal(o["cost"], outs[0]["cost"])
         for k in ("index", "status", "n_safe", "executed_steps"):
             assert o["result"][k] == outs[0]["result"][k]
+
+
+def test_operator_held_rows_checked_and_set_exact(lib, ctx, bot):
+    """Rows of held input features (u and the constant for the balance bot) must
+    be unit rows: rounding-level deviations are set exact, others refused."""
+    env, _ = bot
+    K = env.K32.copy()
+    K[4, 2] += 1e-9
+    K[11, 11] -= 1e-9
+    m = lib.model_from_operator(ctx, "bot", K)
+    got = m.get_operator()
+    assert np.array_equal(got[4], np.eye(12)[4]) and np.array_equal(got[11], np.eye(12)[11])
+    assert np.array_equal(got[:4], K[:4])
+    m.free()
+    K[4, 2] += 1e-3
+    with pytest.raises(lib.MpmiError) as e:
+        lib.model_from_operator(ctx, "bot", K)
+    assert e.value.code == -1
