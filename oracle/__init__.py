@@ -14,7 +14,8 @@ Modules, each citing the passage it follows:
                grid of Sec. IV-B, and Alg. 2's per-step Gaussian noise z_i
                (Box-Muller normals from the same generator)
 * ``basis``    lifted features Psi(x, u) of the learned linear model (Sec. IV-A)
-* ``fit``      least-squares fit of the lifted operator K (Sec. IV-A)
+* ``fit``      least-squares fit of the lifted operator K (Sec. IV-A) and the
+               sparsity-promoting basis selection (Sec. IV-A, V-C.3)
 * ``safety``   isSafe: geometric checks with an inflated barrier (Sec. V-C.1)
 * ``mpmi``     Alg. 2 (prediction, rejection, minimal-intervention argmin)
 * ``screener`` the learned candidate screener (not in the paper): features,
