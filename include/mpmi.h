@@ -174,6 +174,27 @@ int mpmi_fit_model(mpmi_ctx* ctx, const mpmi_basis_desc* basis, const double* x,
 int mpmi_fit_operator(const mpmi_basis_desc* basis, const double* x, const double* u,
                       const double* x_next, int64_t m, double* K_out,
                       double* residual_out);
+
+/* Sparsity-promoting selection of the basis (Sec. IV-A and V-C.3 select the
+ * basis functions with sparsity-promoting DMD, Jovanovic et al. 2014; reading:
+ * its two stages applied to feature selection).  Stage 1 solves, by ADMM with
+ * penalty parameter rho for `iters` iterations,
+ *   min (1/m) ||A V - B||_F^2 + gamma sum_{j candidate} ||V[j, :]||_2
+ * with A, B the lifted regressors and targets scaled to unit RMS per column and
+ * one group per candidate feature (every feature but the state and the held
+ * input features); stage 2 refits K by least squares (Householder QR, float64)
+ * on the features whose group survived.  K_out (n x n row-major): zero column
+ * and zero row for every dropped feature, exact unit rows for held features, so
+ * mpmi_model_from_operator accepts it and the tick reads no dropped feature.
+ * support_out (n bytes, may be NULL): 1 = kept.  *residual_out (may be NULL):
+ * ||X K^T - Y||_F / ||Y||_F over the kept features.  gamma finite >= 0 (0 keeps
+ * every feature and equals mpmi_fit_operator up to rounding); rho finite > 0
+ * (1 is a good default); iters >= 1 (400 converges on the shipped bases).
+ * Pure host code.  INVALID_ARG / NONFINITE / UNSUPPORTED as mpmi_fit_operator. */
+int mpmi_fit_operator_sparse(const mpmi_basis_desc* basis, const double* x, const double* u,
+                             const double* x_next, int64_t m, double gamma, double rho,
+                             int32_t iters, double* K_out, uint8_t* support_out,
+                             double* residual_out);
 /* A model from a given operator K (host, n x n float64 row-major). */
 int mpmi_model_from_operator(mpmi_ctx* ctx, const mpmi_basis_desc* basis,
                              const double* K, mpmi_model** out);

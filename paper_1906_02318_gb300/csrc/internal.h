@@ -150,6 +150,9 @@ int fail(int code, const std::string& msg);
 // host helpers implemented in fit.cpp / track.cpp
 int fit_householder(int kind, const double* x, const double* u, const double* xn,
                     int64_t m, std::vector<double>* K, double* residual, std::string* err);
+int fit_sparse(int kind, const double* x, const double* u, const double* xn, int64_t m,
+               double gamma, double rho, int iters, std::vector<double>* K,
+               std::vector<unsigned char>* support, double* residual, std::string* err);
 struct TrackGrid {
   std::vector<uint32_t> cells;
   std::vector<uint16_t> list;

@@ -64,17 +64,35 @@ static TickKernel pick_tick(int kind, int lanes, int cands, bool traj, bool nois
                : pick_variant<false>(kind, lanes, cands, traj);
 }
 
-// Default launch shape (lanes, candidates per thread, block): one lane per
+// Default launch shape (lanes, candidates per thread, block).  A tick is one
+// warp's serial chain of H steps when the candidates fit the GPU several times
+// over, so few candidates take more lanes each (measured on GB300: race car
+// N = 1024..8192 with 8 lanes 35..70 us against 75 us with one; balance bot
+// N <= 4096 with 4 lanes 12.6 against 13.4..14.1 us).  Otherwise one lane per
 // candidate; the race car keeps K in shared memory and takes two candidates per
 // thread once there are enough candidates to fill the GPU; small grids use
 // 64-thread blocks so every SM gets work.
+static int default_block(int n_slots, int lanes, int cands, int sms) {
+  const long long threads = ((long long)n_slots * lanes + cands - 1) / cands;
+  return threads <= (long long)sms * 128 ? 64 : (threads <= (long long)sms * 256 ? 128 : 256);
+}
+
 static void default_shape(int kind, int n_slots, int sms, int* lanes, int* cands, int* block) {
+  if (kind == kCar && (long long)n_slots * 8 <= (long long)sms * 512) {
+    *lanes = 8;
+    *cands = 1;
+    *block = 128;
+    return;
+  }
+  if (kind == kBot && (long long)n_slots * 4 <= (long long)sms * 128) {
+    *lanes = 4;
+    *cands = 1;
+    *block = 128;
+    return;
+  }
   *lanes = 1;
   *cands = (kind == kCar && n_slots > 48 * 1024) ? 2 : 1;
-  if (*block == 0) {
-    const long long threads = ((long long)n_slots * *lanes + *cands - 1) / *cands;
-    *block = threads <= (long long)sms * 128 ? 64 : (threads <= (long long)sms * 256 ? 128 : 256);
-  }
+  *block = default_block(n_slots, *lanes, *cands, sms);
 }
 
 TickArgs make_tick_args(const mpmi_session* s, uint64_t tick) {
@@ -308,6 +326,40 @@ int mpmi_fit_operator(const mpmi_basis_desc* basis, const double* x, const doubl
   return MPMI_OK;
 }
 
+int mpmi_fit_operator_sparse(const mpmi_basis_desc* basis, const double* x, const double* u,
+                             const double* x_next, int64_t m, double gamma, double rho,
+                             int32_t iters, double* K_out, uint8_t* support_out,
+                             double* residual_out) {
+  if (!basis || !x || !u || !x_next || !K_out)
+    return fail(MPMI_E_INVALID_ARG, "fit_operator_sparse: NULL argument");
+  const int kind = basis_kind(basis->basis, basis->nx, basis->nu);
+  if (kind < 0) return fail(MPMI_E_UNSUPPORTED, "fit_operator_sparse: basis/dimensions not compiled");
+  if (!(gamma >= 0.0) || !std::isfinite(gamma))
+    return fail(MPMI_E_INVALID_ARG, "fit_operator_sparse: gamma must be finite and >= 0");
+  if (!(rho > 0.0) || !std::isfinite(rho))
+    return fail(MPMI_E_INVALID_ARG, "fit_operator_sparse: rho must be finite and > 0");
+  if (iters < 1) return fail(MPMI_E_INVALID_ARG, "fit_operator_sparse: iters must be >= 1");
+  int n, nx, nu, np;
+  kind_dims(kind, &n, &nx, &nu, &np);
+  if (m <= 0) return fail(MPMI_E_INVALID_ARG, "fit_operator_sparse: no transitions");
+  int rc;
+  if ((rc = check_finite(x, (int)(m * nx), "fit_operator_sparse: x")) != MPMI_OK) return rc;
+  if ((rc = check_finite(u, (int)(m * nu), "fit_operator_sparse: u")) != MPMI_OK) return rc;
+  if ((rc = check_finite(x_next, (int)(m * nx), "fit_operator_sparse: x_next")) != MPMI_OK)
+    return rc;
+  std::vector<double> K;
+  std::vector<unsigned char> sup;
+  std::string err;
+  double res = 0.0;
+  rc = fit_sparse(kind, x, u, x_next, m, gamma, rho, iters, &K, &sup, &res, &err);
+  if (rc != MPMI_OK) return fail(rc, err);
+  memcpy(K_out, K.data(), sizeof(double) * K.size());
+  if (support_out)
+    for (int j = 0; j < n; ++j) support_out[j] = sup[j];
+  if (residual_out) *residual_out = res;
+  return MPMI_OK;
+}
+
 int mpmi_model_from_operator(mpmi_ctx* ctx, const mpmi_basis_desc* basis, const double* K,
                              mpmi_model** out) {
   if (!ctx || !basis || !K || !out) return fail(MPMI_E_INVALID_ARG, "NULL argument");
@@ -471,12 +523,16 @@ int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model, const mpmi_session
     if (gg <= 0) return fail(MPMI_E_INVALID_ARG, "session_open: grid sampling needs N = G^M");
   }
   int lanes = cfg->lanes, cands = cfg->cands_per_thread, block = cfg->block;
-  {
-    int dl, dc, db = block;
+  if (lanes == 0 && cands > 1) lanes = 1;  // several candidates per thread need one lane
+  if (lanes == 0) {
+    int dl, dc, db;
     default_shape(model->kind, (int)slots, ctx->sm_count, &dl, &dc, &db);
-    if (lanes == 0) lanes = dl;
-    if (cands == 0) cands = lanes == 1 ? dc : 1;
+    lanes = dl;
+    if (cands == 0) cands = dc;
     if (block == 0) block = db;
+  } else {
+    if (cands == 0) cands = (lanes == 1 && model->kind == kCar && slots > 48 * 1024) ? 2 : 1;
+    if (block == 0) block = default_block((int)slots, lanes, cands, ctx->sm_count);
   }
   if (block % 32 != 0 || block < 32 || block > kMaxBlock)
     return fail(MPMI_E_INVALID_ARG, "session_open: block must be a multiple of 32 in 32..256");

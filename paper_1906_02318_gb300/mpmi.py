@@ -26,7 +26,7 @@ ROLLOUT = {"full": 0, "factored": 1}
 SAFE, FALLBACK, TIMEOUT = 0, 1, 2
 MAX_NX, MAX_NU = 8, 4
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "NONFINITE", -4: "CUDA", -5: "NOT_READY",
-          -6: "UNSUPPORTED"}
+          -6: "UNSUPPORTED", -7: "TIMEOUT"}
 
 c_i32, c_u32, c_i64, c_u64, c_dbl, c_vp = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64,
                                            ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p)
@@ -83,6 +83,8 @@ _SIGNATURES = {
     "mpmi_session_set_noise": (c_i32, [c_vp, P_dbl, c_i32]),
     "mpmi_session_set_rollout": (c_i32, [c_vp, c_i32]),
     "mpmi_debug_withhold_staging": (c_i32, [c_vp, c_i32]),
+    "mpmi_fit_operator_sparse": (c_i32, [ctypes.POINTER(BasisDesc), c_vp, c_vp, c_vp, c_i64,
+                                          c_dbl, c_dbl, c_i32, c_vp, c_vp, P_dbl]),
     "mpmi_session_launch_shape": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32),
                                           ctypes.POINTER(c_i32)]),
     "mpmi_evaluate_candidates": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
@@ -266,6 +268,26 @@ def fit_operator(basis: str, x, u, x_next, nx: int | None = None, nu: int | None
     _check(lib.mpmi_fit_operator(ctypes.byref(d), x.ctypes.data, u.ctypes.data, xn.ctypes.data,
                                  x.shape[0], K.ctypes.data, ctypes.byref(res)))
     return K, res.value
+
+
+def fit_operator_sparse(basis: str, x, u, x_next, gamma: float, rho: float = 1.0,
+                        iters: int = 400, nx: int | None = None, nu: int | None = None):
+    """mpmi_fit_operator_sparse: sparsity-promoting basis selection and refit on
+    the host; returns (K float64 n x n, support bool mask, residual)."""
+    lib = load()
+    d = _desc(basis, nx, nu)
+    x = _f64(x).reshape(-1, d.nx)
+    u = _f64(u).reshape(-1, d.nu)
+    xn = _f64(x_next).reshape(-1, d.nx)
+    n = d.nx + d.nu if basis == "linear" else {"bot": 12, "car": 32}[basis]
+    K = np.empty((n, n), dtype=np.float64)
+    sup = np.zeros(n, dtype=np.uint8)
+    res = ctypes.c_double()
+    _check(lib.mpmi_fit_operator_sparse(ctypes.byref(d), x.ctypes.data, u.ctypes.data,
+                                        xn.ctypes.data, x.shape[0], float(gamma), float(rho),
+                                        int(iters), K.ctypes.data, sup.ctypes.data,
+                                        ctypes.byref(res)))
+    return K, sup.astype(bool), res.value
 
 
 def model_from_operator(ctx: Context, basis: str, K, nx: int | None = None,

@@ -405,3 +405,23 @@ def test_operator_held_rows_checked_and_set_exact(lib, ctx, bot):
     with pytest.raises(lib.MpmiError) as e:
         lib.model_from_operator(ctx, "bot", K)
     assert e.value.code == -1
+
+
+def test_sparse_basis_model_ticks(lib, ctx):
+    """A model whose basis was selected by the sparsity-promoting fit (race car,
+    gamma = 1: 24 of 32 features kept) runs the same tick; parity with the
+    oracle's tick of the same operator."""
+    from oracle import fit as ofit
+    from parity import Env
+    x, u, xn = data.transitions("car", 3, 20000)
+    Ko, sup, _ = ofit.fit_koopman_sparse("car", x, u, xn, 1.0)
+    assert 0 < sup.sum() < 32
+    base = car_env()
+    env = Env("car", ofit.round_to_f32(Ko), base.spec, base.lo, base.hi, base.track)
+    model = gpu_model(lib, ctx, env)
+    x0 = data.car_start_state(env.track, vx=14.0)
+    for k, x_t in enumerate([x0, x0 + np.array([1.5, -1.0, 0.1, 4.0, 0.3, 0.2])]):
+        u_h = data.to_f32_exact(data.user_input_once(900 + k, env.lo, env.hi))
+        g, o = _tick(lib, ctx, env, model, x_t, u_h, 2047, 60, seed=5, tick=k)
+        assert compare(g, o, env, 60) <= 10
+    model.free()

@@ -51,7 +51,7 @@ def test_host_fit_matches_oracle(lib, kind, seed, m):
     assert abs(res - reso) <= 1e-9
     held = (4, 11) if kind == "bot" else (6, 7, 30, 31)
     for r in held:
-        assert np.abs(K[r] - np.eye(K.shape[0])[r]).max() < 1e-12
+        assert np.array_equal(K[r], np.eye(K.shape[0])[r])
 
 
 def test_host_fit_linear_closed_form(lib):
@@ -97,3 +97,28 @@ def test_context_without_gpu_fails_cleanly(lib):
 def test_missing_library_raises(lib, tmp_path):
     with pytest.raises(RuntimeError):
         lib.load(str(tmp_path / "nope.so"))
+
+
+@pytest.mark.parametrize("kind,seed,m,gamma", [("bot", 1, 5000, 0.02), ("bot", 1, 5000, 1.0),
+                                               ("car", 3, 20000, 1.0), ("car", 3, 20000, 0.0)])
+def test_host_sparse_fit_matches_oracle(lib, kind, seed, m, gamma):
+    """Sparsity-promoting basis selection: the host float64 implementation selects
+    the oracle's support and refits the same K."""
+    x, u, xn = data.transitions(kind, seed, m)
+    K, sup, res = lib.fit_operator_sparse(kind, x, u, xn, gamma)
+    Ko, supo, reso = ofit.fit_koopman_sparse(kind, x, u, xn, gamma)
+    assert sup.tolist() == supo.tolist()
+    assert np.abs(K - Ko).max() <= 1e-9 * np.abs(Ko).max()
+    assert abs(res - reso) <= 1e-9
+    if gamma > 0:
+        assert 0 < sup.sum() < K.shape[0]
+    assert not K[:, ~sup].any() and not K[~sup].any()
+
+
+def test_host_sparse_fit_errors(lib):
+    x, u, xn = data.transitions("bot", 1, 200)
+    for kw, code in ((dict(gamma=-1.0), -1), (dict(gamma=np.nan), -1), (dict(gamma=0.1, rho=0.0), -1),
+                     (dict(gamma=0.1, iters=0), -1)):
+        with pytest.raises(lib.MpmiError) as e:
+            lib.fit_operator_sparse("bot", x, u, xn, **kw)
+        assert e.value.code == code
