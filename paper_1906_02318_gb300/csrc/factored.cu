@@ -10,7 +10,8 @@
 // t = 1..H; per tick every block folds them with the split of the lifting at
 // x_t into the table V[t][r] = (e_r K^t a, e_r K^t b_1, ...), after which a
 // candidate-step costs (1 + P) FMAs per read-out coordinate instead of the n^2
-// of z <- K z.  Rounding differs from the full rollout.  The per-step noise of
+// of z <- K z, and the steps of a candidate no longer depend on each other: the
+// warp tests 32 of them at once.  Rounding differs from the full rollout.  The per-step noise of
 // Alg. 2 enters after K and does not factor, so noisy sessions cannot use this.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -20,7 +21,8 @@
 
 namespace mpmi {
 
-constexpr int kFactBlock = 64;
+constexpr int kFactBlock = 128;
+constexpr int kFactCands = 8;  // candidates per warp-tile (lanes 0..7 draw them)
 
 // Rows P_t = C K^t, t = 1..H: P_1 is the first NX rows of K and P_t = P_{t-1} K
 // (each entry one FMA chain over i = 0..n-1).  One block of NX * N threads;
@@ -140,10 +142,15 @@ __global__ void __launch_bounds__(256) factored_kernel(const __grid_constant__ T
   unsigned long long best = ~0ull;
   unsigned int n_safe = 0, n_exec = 0;
   const int wpb = blockDim.x >> 5;
-  const int n_wtiles = failed ? 0 : (n_eval + 31) >> 5;
+  // Time-parallel: the read-outs of different steps do not depend on each other,
+  // so a warp takes kFactCands candidates one after the other and tests 32 steps
+  // of a candidate at once (lane l: step t0 + l + 1); a ballot gives the first
+  // violation.
+  const int n_wtiles = failed ? 0 : (n_eval + kFactCands - 1) / kFactCands;
   for (int wt = blockIdx.x * wpb + warp; wt < n_wtiles; wt += gridDim.x * wpb) {
-    const int pos = wt * 32 + lane;
-    const bool valid = pos < n_eval;
+    // lanes 0..kFactCands-1 draw and score one candidate each
+    const int pos = wt * kFactCands + lane;
+    const bool valid = lane < kFactCands && pos < n_eval;
     const int slot = (valid && a.slot_list) ? a.slot_list[pos] : pos;
     float xi[NU];
     if (valid) {
@@ -160,44 +167,51 @@ __global__ void __launch_bounds__(256) factored_kernel(const __grid_constant__ T
     }
     float p[NP];
     monomials32<KIND>(xi, p);
-    int ttv = 0;
-    bool alive = valid;
-    for (int t = 1; t <= H; ++t) {
-      const float4* Vt = V + (t - 1) * ro_n;
-      bool ok = true;
-      float px = 0.f, py = 0.f;
+    int my_ttv = 0;
+    for (int c = 0; c < kFactCands; ++c) {
+      if (!__shfl_sync(kFull, (int)valid, c)) continue;  // uniform over the warp
+      float pc[NP];
 #pragma unroll
-      for (int r = 0; r < NX; ++r) {
-        if (r < ro_n) {
-          const float4 w = Vt[r];
-          float v = __fmaf_rn(p[0], w.y, w.x);
-          if constexpr (NP > 1) v = __fmaf_rn(p[1], w.z, v);
-          if constexpr (NP > 2) v = __fmaf_rn(p[2], w.w, v);
-          ok = ok && (v > lo[r]) && (v < hi[r]);
-          if (r == 0) px = v;
-          if (r == 1) py = v;
+      for (int k = 0; k < NP; ++k) pc[k] = __shfl_sync(kFull, p[k], c);
+      int ttv = H;
+      for (int t0 = 0; t0 < H; t0 += 32) {
+        const int t = t0 + lane + 1;
+        bool ok = true;
+        if (t <= H) {
+          const float4* Vt = V + (t - 1) * ro_n;
+          float px = 0.f, py = 0.f;
+#pragma unroll
+          for (int r = 0; r < NX; ++r) {
+            if (r < ro_n) {
+              const float4 w = Vt[r];
+              float v = __fmaf_rn(pc[0], w.y, w.x);
+              if constexpr (NP > 1) v = __fmaf_rn(pc[1], w.z, v);
+              if constexpr (NP > 2) v = __fmaf_rn(pc[2], w.w, v);
+              ok = ok && (v > lo[r]) && (v < hi[r]);
+              if (r == 0) px = v;
+              if (r == 1) py = v;
+            }
+          }
+          if constexpr (B::TRACK) {
+            if (track) ok = ok && track_ok<1>(a.safety.track, tv, px, py, 0, ok);
+          }
+        }
+        const unsigned bad = __ballot_sync(kFull, !ok);
+        if (bad) {
+          ttv = t0 + __ffs(bad) - 1;
+          break;
         }
       }
-      if constexpr (B::TRACK) {
-        if (track) {
-          const bool on_road = track_ok<1>(a.safety.track, tv, px, py, 0, alive && ok);
-          ok = ok && on_road;
-        }
-      }
-      if (alive) {
-        if (ok) ttv = t;
-        else alive = false;
-      }
-      if (!__any_sync(kFull, alive)) break;
+      if (lane == c) my_ttv = ttv;
     }
     if (valid) {
-      const unsigned long long key = ((unsigned long long)(H - ttv) << 55) |
+      const unsigned long long key = ((unsigned long long)(H - my_ttv) << 55) |
                                      ((unsigned long long)__float_as_uint(cost) << 23) |
                                      (unsigned long long)slot;
       best = key < best ? key : best;
-      n_exec += (unsigned int)min(ttv + 1, H);
-      n_safe += ttv == H;
-      if (a.ttv_out) a.ttv_out[slot] = ttv;
+      n_exec += (unsigned int)min(my_ttv + 1, H);
+      n_safe += my_ttv == H;
+      if (a.ttv_out) a.ttv_out[slot] = my_ttv;
       if (a.cost_out) a.cost_out[slot] = cost;
     }
   }
@@ -254,7 +268,7 @@ int launch_factored(mpmi_session* s, TickArgs& a, cudaStream_t st, int n_hint) {
     s->fact_smem = smem;
   }
   const int n_work = (n_hint > 0 && n_hint < s->n_slots) ? n_hint : s->n_slots;
-  const int n_wtiles = (n_work + 31) / 32;
+  const int n_wtiles = (n_work + kFactCands - 1) / kFactCands;
   int grid = (n_wtiles + kFactBlock / 32 - 1) / (kFactBlock / 32);
   if (grid > s->fact_grid) grid = s->fact_grid;
   if (grid < 1) grid = 1;
