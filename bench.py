@@ -57,7 +57,7 @@ SM_FP32_LANES = 128
 
 # DRAM bytes per tick-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum); valid only for the kernel source it was taken on.
-TRAFFIC = {"tick_kernel_sha1": "fb9b3614ea6b6bc564143bce9e8cce75f0a9addb", "bytes_per_launch": 24832}
+TRAFFIC = {"tick_kernel_sha1": "1ea7c0443ca570c0f45d2dedc048c1eba74a9bf5", "bytes_per_launch": 25856}
 
 
 def kernel_sha1() -> str:
