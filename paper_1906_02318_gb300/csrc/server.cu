@@ -138,11 +138,12 @@ __global__ void __launch_bounds__(kMaxBlock) serve_kernel(const __grid_constant_
       TickScratch* sc = st.scratch;
       atomicMin(&sc->key, best);
       atomicAdd(&sc->counts, ((unsigned long long)n_safe << 40) + n_exec);
-      __threadfence();
-      const unsigned int prev = atomicAdd(&sc->done, 1u);
+      // acquire-release on the tile counter orders this warp's atomics before the
+      // increment and lets the last warp see every other warp's
+      unsigned int prev;
+      asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&sc->done) : "memory");
       if (prev == (unsigned int)st.n_tiles - 1) {
         // this warp finished the session's last tile: decode and reset its record
-        __threadfence();
         const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&sc->key);
         const unsigned long long cnt =
             *reinterpret_cast<volatile unsigned long long*>(&sc->counts);

@@ -551,14 +551,14 @@ __device__ __forceinline__ void session_epilogue(const P& a, unsigned long long 
     atomicMin(&sc->key, bk);
     atomicAdd(&sc->counts, bc);
     if (failed) atomicOr(&sc->error, 1u);
-    __threadfence();
-    const unsigned int prev = atomicAdd(&sc->done, 1u);
+    // acquire-release on the block counter: this block's atomics above are
+    // visible before the increment, and the last block sees every other block's
+    unsigned int prev;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&sc->done) : "memory");
     s_last = (prev == gridDim.x - 1);
   }
   __syncthreads();
   if (s_last && tid == 0) {
-    // last block: every other block's atomics are visible (fence + counter)
-    __threadfence();
     TickScratch* sc = a.scratch;
     const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&sc->key);
     const unsigned long long cnt = *reinterpret_cast<volatile unsigned long long*>(&sc->counts);
