@@ -476,9 +476,10 @@ def run_variants(args, bot_states):
     """The paper's variants and the factorised ablation, device-resident at the
     benchmark's sizes (L2 flushed before every tick): the balance bot (N = 16384,
     H = 50) and the race car (N = 16384, H = 60) with the full rollout (Alg. 2),
-    with per-step noise z_i, with the equally spaced grid (bot, Sec. IV-B), and in
+    with per-step noise z_i, with the equally spaced grid (bot, Sec. IV-B), in
     the factorised read-out form (exact in real arithmetic, not the method's own
-    rollout).  Rates count the steps the kernel executed (early exit)."""
+    rollout) and, for the race car, with the rollout on the tensor cores.  Rates
+    count the steps the kernel executed (early exit)."""
     import torch
     from paper_1906_02318_gb300 import mpmi as lib
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -508,9 +509,11 @@ def run_variants(args, bot_states):
         uhs = data.ou_user_input(9, ticks, 0.01, lo, hi)
         xs = torch.tensor(np.asarray(states), dtype=torch.float64, device=dev)
         us = torch.tensor(uhs, dtype=torch.float64, device=dev)
-        variants = [("full", {}), ("noise", {"noise": sigma}), ("factored", {"rollout": 1})]
+        variants = [("full", {}), ("noise", {"noise": sigma}), ("factored", {"rollout": "factored"})]
         if name == "bot":
             variants.insert(2, ("grid", {"sampler": "grid"}))
+        else:
+            variants.append(("tensor", {"rollout": "tensor"}))
         runs = {}
         for vname, opt in variants:
             sess = lib.Session(ctx, model, N_SAMPLES, H, lo, hi, seed=11,
@@ -518,7 +521,7 @@ def run_variants(args, bot_states):
             if "noise" in opt:
                 sess.set_noise(opt["noise"])
             if "rollout" in opt:
-                sess.set_rollout("factored")
+                sess.set_rollout(opt["rollout"])
             for i in range(3):
                 lib.evaluate_candidates_device(sess, xs[i], us[i], res[i], tick=i)
             torch.cuda.synchronize()

@@ -134,6 +134,8 @@ struct mpmi_session {
   uint64_t ck_bytes = 0;
   int fact_grid = 0;               // resident blocks of the factorised kernel
   size_t fact_smem = 0;
+  int tc_grid[2] = {0, 0};         // resident CTAs of the tensor-core rollout (plain, traj)
+  size_t tc_smem[2] = {0, 0};
   int withhold_staging = 0;        // test hook (mpmi_debug_withhold_staging)
   uint64_t bytes = 0;
 };
@@ -145,6 +147,8 @@ int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, i
 // factorised rollout (factored.cu)
 int compute_powers(int kind, const float* K, int H, float* out, cudaStream_t st);
 int launch_factored(mpmi_session* s, TickArgs& a, cudaStream_t st, int n_hint);
+// tensor-core rollout (tensor.cu)
+int launch_tensor(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint);
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
 // host helpers implemented in fit.cpp / track.cpp

@@ -155,6 +155,11 @@ int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, i
   // a device-side list short enough that 8 lanes per candidate still fit one wave
   const bool small = a.slot_list != nullptr && n_hint > 0 &&
                      (long long)n_hint * 8 <= (long long)s->ctx->sm_count * 512;
+  if (s->rollout == MPMI_ROLLOUT_TENSOR) {
+    if (a.n_noise > 0 && a.tick >= (1ull << 48))
+      return fail(MPMI_E_INVALID_ARG, "ticks with noise must stay below 2^48");
+    return launch_tensor(s, a, traj, st, n_hint);
+  }
   if (s->rollout == MPMI_ROLLOUT_FACTORED) {
     if (traj) return fail(MPMI_E_UNSUPPORTED, "the factorised rollout records no trajectories");
     if (a.n_noise > 0) return fail(MPMI_E_UNSUPPORTED, "the factorised rollout has no noise");
@@ -631,15 +636,17 @@ int mpmi_session_set_noise(mpmi_session* s, const double* sigma, int32_t count) 
 
 int mpmi_session_set_rollout(mpmi_session* s, int32_t mode) {
   if (!s) return fail(MPMI_E_INVALID_ARG, "session is NULL");
-  if (mode != MPMI_ROLLOUT_FULL && mode != MPMI_ROLLOUT_FACTORED)
+  if (mode != MPMI_ROLLOUT_FULL && mode != MPMI_ROLLOUT_FACTORED && mode != MPMI_ROLLOUT_TENSOR)
     return fail(MPMI_E_INVALID_ARG, "set_rollout: unknown mode");
+  if (mode == MPMI_ROLLOUT_TENSOR && s->model->kind != kCar)
+    return fail(MPMI_E_UNSUPPORTED, "set_rollout: the tensor-core rollout is compiled for the race car");
   if (s->in_flight)
     return fail(MPMI_E_INVALID_ARG, "set_rollout: a tick is in flight (call select_input first)");
   if (mode == s->rollout) return MPMI_OK;
   mpmi_ctx* ctx = s->ctx;
   DeviceGuard guard(ctx->device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
-  if (mode == MPMI_ROLLOUT_FULL) {
+  if (mode == MPMI_ROLLOUT_FULL || mode == MPMI_ROLLOUT_TENSOR) {
     // device-resident ticks may still read the rows
     MPMI_CUDA(cudaDeviceSynchronize(), "set_rollout: waiting for ticks in flight");
     cudaFree(s->ck_dev);

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libmpmi.so")
 BASIS = {"bot": 0, "car": 1, "linear": 2}
 BASIS_DIMS = {"bot": (4, 1), "car": (6, 2)}
 SAMPLER = {"uniform": 0, "grid": 1, "external": 2}
-ROLLOUT = {"full": 0, "factored": 1}
+ROLLOUT = {"full": 0, "factored": 1, "tensor": 2}
 SAFE, FALLBACK, TIMEOUT = 0, 1, 2
 MAX_NX, MAX_NU = 8, 4
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "NONFINITE", -4: "CUDA", -5: "NOT_READY",
@@ -363,7 +363,8 @@ class Session:
             self.handle, sig.ctypes.data_as(P_dbl), int(sig.size)))
 
     def set_rollout(self, mode: str):
-        """mpmi_session_set_rollout: "full" (z <- K z, Alg. 2) or "factored"
+        """mpmi_session_set_rollout: "full" (z <- K z, Alg. 2, CUDA cores),
+        "tensor" (the same on tcgen05 tensor cores, race car) or "factored"
         (read-outs from precomputed rows C K^t; an exact-in-real-arithmetic ablation)."""
         _check(self.ctx.lib.mpmi_session_set_rollout(self.handle, ROLLOUT[mode]))
 

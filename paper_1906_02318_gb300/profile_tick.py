@@ -48,7 +48,7 @@ def main():
     ap.add_argument("--k", type=int, default=4096)
     ap.add_argument("--tau", type=float, default=0.0)
     ap.add_argument("--sessions", type=int, default=64)
-    ap.add_argument("--rollout", choices=["full", "factored"], default="full")
+    ap.add_argument("--rollout", choices=["full", "factored", "tensor"], default="full")
     ap.add_argument("--noise", default="", help="comma-separated sigma per state coordinate")
     args = ap.parse_args()
 
