@@ -57,7 +57,7 @@ SM_FP32_LANES = 128
 
 # DRAM bytes per tick-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum); valid only for the kernel source it was taken on.
-TRAFFIC = {"tick_kernel_sha1": "1ea7c0443ca570c0f45d2dedc048c1eba74a9bf5", "bytes_per_launch": 25856}
+TRAFFIC = {"tick_kernel_sha1": "8731985d3eb36342850da4898cdb4389b2257855", "bytes_per_launch": 25088}
 
 
 def kernel_sha1() -> str:
