@@ -268,10 +268,12 @@ int mpmi_session_set_noise(mpmi_session* s, const double* sigma, int32_t count);
 int mpmi_session_set_rollout(mpmi_session* s, int32_t mode);
 
 /* ---- evaluate_candidates + select_input (Alg. 2) ------------------------ */
-/* Queues one tick on `stream`: copies x_t (nx doubles) and u_h (nu doubles) from
- * host memory (through the session's pinned staging buffer), samples the
- * candidates (counter = tick), predicts, tests, scores and reduces them on the
- * GPU, and queues the device-to-host copy of the result.  Returns without waiting.
+/* Queues one tick on `stream`: copies x_t (nx doubles) and u_h (nu doubles) into
+ * the session's pinned staging buffer, samples the candidates (counter = tick),
+ * predicts, tests, scores and reduces them on the GPU, and brings the result back
+ * to pinned host memory.  Where the device can map host memory the kernel reads
+ * the staging buffer and writes the result over the host link directly
+ * (zero-copy); otherwise two asynchronous copies do it.  Returns without waiting.
  * candidates_dev: device N x M float32 samples for MPMI_SAMPLER_EXTERNAL, else
  * must be NULL.  NONFINITE if x_t or u_h holds NaN/Inf.  If a previous tick of
  * this session is still in flight, waits for it first. */
@@ -279,7 +281,11 @@ int mpmi_evaluate_candidates(mpmi_session* s, const double* x_t, const double* u
                              const float* candidates_dev, uint64_t tick,
                              void* stream);
 /* Waits for the tick queued by mpmi_evaluate_candidates and copies its outcome
- * to *out (host).  NOT_READY if no tick is in flight. */
+ * to *out (host).  With zero-copy ticks it returns as soon as the kernel has
+ * published the result (a completion word stored after it, polled for up to a
+ * second before falling back to the tick's CUDA event); the session's next
+ * launch is ordered behind the rest of that kernel on the GPU.  NOT_READY if no
+ * tick is in flight; TIMEOUT for a result with status MPMI_TIMEOUT. */
 int mpmi_select_input(mpmi_session* s, mpmi_result* out);
 
 /* Device-resident form of one tick (nothing is copied to or from the host and

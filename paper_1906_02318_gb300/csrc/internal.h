@@ -83,6 +83,10 @@ struct TickArgs {
   int ro_idx[MPMI_MAX_NX];
   // test hook: stage nothing, so the bounded staging wait runs out
   int withhold_staging;
+  // zero-copy host ticks: after the result, the decoding block stores seq here
+  // (pinned host memory) behind a system-scope fence
+  unsigned long long* seq_out;
+  unsigned long long seq;
 };
 
 }  // namespace mpmi
@@ -125,6 +129,16 @@ struct mpmi_session {
   double* in_dev = nullptr;        // x_t (8 doubles) then u_h (4 doubles)
   double* in_host = nullptr;       // pinned staging
   mpmi_result* result_host = nullptr;  // pinned
+  // device-side aliases of the pinned buffers (zero-copy host ticks)
+  double* in_map = nullptr;
+  mpmi_result* result_map = nullptr;
+  bool zero_copy = false;
+  unsigned long long* seq_host = nullptr;  // pinned; written by the device after a result
+  unsigned long long* seq_map = nullptr;
+  unsigned long long seq = 0;
+  // select_input returned on the completion word while the kernel may still be
+  // resetting the reduction record: the next launch waits for `done` first
+  bool tail_pending = false;
   cudaEvent_t done = nullptr;
   bool in_flight = false;
   float noise_sigma[MPMI_MAX_NX] = {0, 0, 0, 0, 0, 0, 0, 0};

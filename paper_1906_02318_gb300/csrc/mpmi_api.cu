@@ -9,6 +9,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -151,6 +153,12 @@ static void small_shape(int kind, int* lanes, int* cands, int* block) {
 }
 
 int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint) {
+  if (s->tail_pending) {
+    // the previous host tick's kernel may still be finishing: order behind it
+    const cudaError_t e = cudaStreamWaitEvent(st, s->done, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    s->tail_pending = false;
+  }
   int lanes = s->lanes, cands = s->cands, block = s->block;
   // a device-side list short enough that 8 lanes per candidate still fit one wave
   const bool small = a.slot_list != nullptr && n_hint > 0 &&
@@ -563,6 +571,7 @@ int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model, const mpmi_session
     cudaFree(s->in_dev);
     cudaFreeHost(s->in_host);
     cudaFreeHost(s->result_host);
+    cudaFreeHost(s->seq_host);
     if (s->done) cudaEventDestroy(s->done);
     delete s;
     return fail(code, msg);
@@ -576,6 +585,24 @@ int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model, const mpmi_session
     return cleanup(MPMI_E_OOM, "session_open: pinned allocation failed");
   if (cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) != cudaSuccess)
     return cleanup(MPMI_E_CUDA, "session_open: cudaEventCreate failed");
+  // host ticks read x_t, u_h from the pinned staging buffer and write the result
+  // into pinned memory directly (zero-copy over the host link) where the device
+  // can map host memory; otherwise they copy both ways
+  {
+    int can_map = 0;
+    if (cudaDeviceGetAttribute(&can_map, cudaDevAttrCanMapHostMemory, ctx->device) == cudaSuccess &&
+        can_map && cudaMallocHost(&s->seq_host, sizeof(unsigned long long)) == cudaSuccess &&
+        cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->in_map), s->in_host, 0) ==
+            cudaSuccess &&
+        cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->result_map), s->result_host, 0) ==
+            cudaSuccess &&
+        cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->seq_map), s->seq_host, 0) ==
+            cudaSuccess) {
+      s->zero_copy = true;
+      *s->seq_host = 0;
+    }
+    cudaGetLastError();
+  }
   TickScratch init;
   memset(&init, 0, sizeof(init));
   init.key = ~0ull;
@@ -593,7 +620,7 @@ int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model, const mpmi_session
 void mpmi_session_close(mpmi_session* s) {
   if (!s) return;
   DeviceGuard guard(s->ctx->device);
-  if (s->in_flight) cudaEventSynchronize(s->done);
+  if (s->in_flight || s->tail_pending) cudaEventSynchronize(s->done);
   if (s->ck_dev) {
     cudaDeviceSynchronize();
     cudaFree(s->ck_dev);
@@ -604,6 +631,7 @@ void mpmi_session_close(mpmi_session* s) {
   cudaFree(s->in_dev);
   cudaFreeHost(s->in_host);
   cudaFreeHost(s->result_host);
+  cudaFreeHost(s->seq_host);
   cudaEventDestroy(s->done);
   s->ctx->used -= s->bytes;
   delete s;
@@ -704,16 +732,26 @@ int mpmi_evaluate_candidates(mpmi_session* s, const double* x_t, const double* u
   }
   memcpy(s->in_host, x_t, sizeof(double) * m->nx);
   memcpy(s->in_host + 8, u_h, sizeof(double) * m->nu);
-  MPMI_CUDA(cudaMemcpyAsync(s->in_dev, s->in_host, 12 * sizeof(double), cudaMemcpyHostToDevice, st),
-            "copy x_t/u_h to the device");
   TickArgs a = make_tick_args(s, tick);
-  a.x_t = s->in_dev;
-  a.u_h = s->in_dev + 8;
   a.ext = candidates_dev;
-  a.result = s->result_dev;
-  if ((rc = launch_tick_args(s, a, false, st, 0)) != MPMI_OK) return rc;
-  MPMI_CUDA(cudaMemcpyAsync(s->result_host, s->result_dev, sizeof(mpmi_result),
-                            cudaMemcpyDeviceToHost, st), "copy the result to the host");
+  if (s->zero_copy) {
+    a.x_t = s->in_map;
+    a.u_h = s->in_map + 8;
+    a.result = s->result_map;
+    a.seq_out = s->seq_map;
+    a.seq = ++s->seq;
+    if ((rc = launch_tick_args(s, a, false, st, 0)) != MPMI_OK) return rc;
+  } else {
+    MPMI_CUDA(cudaMemcpyAsync(s->in_dev, s->in_host, 12 * sizeof(double),
+                              cudaMemcpyHostToDevice, st),
+              "copy x_t/u_h to the device");
+    a.x_t = s->in_dev;
+    a.u_h = s->in_dev + 8;
+    a.result = s->result_dev;
+    if ((rc = launch_tick_args(s, a, false, st, 0)) != MPMI_OK) return rc;
+    MPMI_CUDA(cudaMemcpyAsync(s->result_host, s->result_dev, sizeof(mpmi_result),
+                              cudaMemcpyDeviceToHost, st), "copy the result to the host");
+  }
   MPMI_CUDA(cudaEventRecord(s->done, st), "cudaEventRecord");
   s->in_flight = true;
   return MPMI_OK;
@@ -723,7 +761,26 @@ int mpmi_select_input(mpmi_session* s, mpmi_result* out) {
   if (!s || !out) return fail(MPMI_E_INVALID_ARG, "select_input: NULL argument");
   if (!s->in_flight) return fail(MPMI_E_NOT_READY, "select_input: no tick in flight");
   DeviceGuard guard(s->ctx->device);
-  MPMI_CUDA(cudaEventSynchronize(s->done), "waiting for the tick");
+  bool seen = false;
+  if (s->zero_copy) {
+    // the decoding block stores the tick's sequence number after the result
+    // (system-scope fence between): poll it for up to a second, then fall back
+    // to the event, which also reports a failed launch
+    const volatile unsigned long long* w = s->seq_host;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (unsigned long i = 0;; ++i) {
+      if (*w == s->seq) {
+        seen = true;
+        break;
+      }
+      if ((i & 1023) == 1023 &&
+          std::chrono::steady_clock::now() - t0 > std::chrono::seconds(1))
+        break;
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+  }
+  if (!seen) MPMI_CUDA(cudaEventSynchronize(s->done), "waiting for the tick");
+  s->tail_pending = seen;
   s->in_flight = false;
   *out = *s->result_host;
   if (out->status == MPMI_TIMEOUT)

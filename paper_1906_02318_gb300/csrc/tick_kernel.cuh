@@ -257,6 +257,16 @@ __device__ __forceinline__ bool track_ok(const DevTrack& tr, const TrackView& v,
   return ok;
 }
 
+// Parameter records that carry a completion word for zero-copy host ticks.
+template <class P, class = void>
+struct HasSeq {
+  static constexpr bool value = false;
+};
+template <class P>
+struct HasSeq<P, decltype((void)sizeof(((P*)nullptr)->seq_out), void())> {
+  static constexpr bool value = true;
+};
+
 // Decode of the winning key into the tick's result record.
 template <int NU, class P>
 __device__ __forceinline__ void write_result(const P& a, unsigned long long k,
@@ -282,6 +292,12 @@ __device__ __forceinline__ void write_result(const P& a, unsigned long long k,
   r.tick = a.tick;
   r.reserved = a.result_flags;
   *a.result = r;
+  if constexpr (HasSeq<P>::value) {
+    if (a.seq_out != nullptr) {  // the host polls this word instead of an event
+      __threadfence_system();
+      *reinterpret_cast<volatile unsigned long long*>(a.seq_out) = a.seq;
+    }
+  }
 }
 
 // One warp-tile: the PER_WARP = 32 C / L candidate positions wt * PER_WARP ...
