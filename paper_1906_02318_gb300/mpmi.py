@@ -25,6 +25,7 @@ SAMPLER = {"uniform": 0, "grid": 1, "external": 2}
 ROLLOUT = {"full": 0, "factored": 1, "tensor": 2}
 SAFE, FALLBACK, TIMEOUT = 0, 1, 2
 MAX_NX, MAX_NU = 8, 4
+MAX_HORIZON, MAX_SLOTS = 511, 8388607
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "NONFINITE", -4: "CUDA", -5: "NOT_READY",
           -6: "UNSUPPORTED", -7: "TIMEOUT"}
 
@@ -170,7 +171,8 @@ def _stream(stream):
 
 
 def _f64(a, n=None):
-    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
     if n is not None and a.size != n:
         raise ValueError(f"expected {n} values, got {a.size}")
     return a
@@ -347,6 +349,7 @@ class Session:
         self.n_slots = n_samples + int(include_user)
         self.nx, self.nu = model.nx, model.nu
         self.n = model.get_operator().shape[0]
+        self._result = Result()   # reused by select_input
 
     def launch_shape(self):
         """(lanes per candidate, candidates per thread, threads per block)."""
@@ -383,14 +386,18 @@ def evaluate_candidates(s: Session, x_t, u_h, candidates=None, tick: int = 0, st
     """mpmi_evaluate_candidates: queue one tick from host x_t / u_h (float64)."""
     x = _f64(x_t, s.nx)
     u = _f64(u_h, s.nu)
-    _check(s.ctx.lib.mpmi_evaluate_candidates(s.handle, x.ctypes.data, u.ctypes.data,
-                                              _ptr(candidates), tick, _stream(stream)))
+    rc = s.ctx.lib.mpmi_evaluate_candidates(s.handle, x.ctypes.data, u.ctypes.data,
+                                            _ptr(candidates), tick, _stream(stream))
+    if rc:
+        _check(rc)
 
 
 def select_input(s: Session) -> dict:
     """mpmi_select_input: wait for the queued tick and return its outcome."""
-    r = Result()
-    _check(s.ctx.lib.mpmi_select_input(s.handle, ctypes.byref(r)))
+    r = s._result
+    rc = s.ctx.lib.mpmi_select_input(s.handle, ctypes.byref(r))
+    if rc:
+        _check(rc)
     return result_dict(r, s.nu)
 
 

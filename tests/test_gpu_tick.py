@@ -425,3 +425,40 @@ def test_sparse_basis_model_ticks(lib, ctx):
         g, o = _tick(lib, ctx, env, model, x_t, u_h, 2047, 60, seed=5, tick=k)
         assert compare(g, o, env, 60) <= 10
     model.free()
+
+
+@pytest.mark.slow
+def test_maximum_slot_count(lib, ctx, bot):
+    """2^23 - 1 candidate slots (the key's 23-bit slot field full): the pick is the
+    lexicographic minimum of the GPU's own per-candidate outputs, sampled slots
+    (the last ones included) agree with the oracle, one more slot is refused."""
+    import torch
+    env, model = bot
+    N, H = lib.MAX_SLOTS - 1, 5
+    x_t = np.array([0.2, 0.6, -0.5, 0.3])
+    u_h = data.to_f32_exact(data.user_input_once(13, env.lo, env.hi))
+    sess = lib.Session(ctx, model, N, H, env.lo, env.hi, seed=17, stream_id=5)
+    g = run_gpu(lib, sess, x_t, u_h, tick=3)
+    sess.close()
+    ttv, cost, r = g["ttv"], g["cost"], g["result"]
+    assert r["n_slots"] == lib.MAX_SLOTS and ttv.size == lib.MAX_SLOTS
+    slots = np.arange(ttv.size)
+    order = np.lexsort((slots, cost.astype(np.float64), H - ttv))
+    assert r["index"] == int(order[0])
+    assert r["n_safe"] == int(np.count_nonzero(ttv == H))
+    assert r["executed_steps"] == int(np.minimum(ttv + 1, H).sum())
+    # sampled slots against the oracle (samples are slots 1..N)
+    samples = osamp.uniform_samples(17, 5, 3, N, env.lo, env.hi)
+    pick = np.unique(np.concatenate([np.arange(N - 64, N + 1), np.arange(1, 65),
+                                     np.random.default_rng(0).integers(1, N + 1, 256)]))
+    o = omp.tick(env.K32, env.basis, x_t, u_h, samples[pick - 1], H, env.spec,
+                 include_user=False, record=True)
+    assert np.allclose(cost[pick], o.cost, rtol=1e-6, atol=1e-12)
+    mism = np.nonzero(ttv[pick] != o.ttv)[0]
+    for i in mism:                                   # only at a safety boundary
+        s = int(min(ttv[pick[i]], o.ttv[i])) + 1
+        marg = float(osafe.margin(env.spec, o.traj[i, s][None, :])[0])
+        assert abs(marg) < 1e-4 * max(1.0, float(np.abs(o.traj[i, s]).max()))
+    with pytest.raises(lib.MpmiError) as e:
+        lib.Session(ctx, model, lib.MAX_SLOTS, H, env.lo, env.hi)
+    assert e.value.code == -1
