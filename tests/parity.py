@@ -50,12 +50,13 @@ def bot_env(seed: int = 1, m: int = 5000, inflation: float = 0.0) -> Env:
     return Env("bot", K, spec, plants.BOT_INPUT_LO, plants.BOT_INPUT_HI, None)
 
 
-def car_env(seed: int = 3, m: int = 20000, track_seed: int = 3) -> Env:
+def car_env(seed: int = 3, m: int = 20000, track_seed: int = 3,
+            inflation: float = 0.0) -> Env:
     x, u, xn = data.transitions("car", seed, m)
     K = ofit.round_to_f32(ofit.fit_koopman("car", x, u, xn)[0])
     track = data.track_polyline(track_seed)
     spec = osafe.SafetySpec(lo=data.CAR_SAFE_LO, hi=data.CAR_SAFE_HI, track=track,
-                            half_width=data.CAR_TRACK_HALF_WIDTH)
+                            half_width=data.CAR_TRACK_HALF_WIDTH, inflation=inflation)
     return Env("car", K, spec, plants.CAR_INPUT_LO, plants.CAR_INPUT_HI, track)
 
 

@@ -462,3 +462,27 @@ def test_maximum_slot_count(lib, ctx, bot):
     with pytest.raises(lib.MpmiError) as e:
         lib.Session(ctx, model, lib.MAX_SLOTS, H, env.lo, env.hi)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("inflation", [0.5, 1.5])
+@pytest.mark.parametrize("rollout", ["full", "tensor", "factored"])
+def test_car_inflated_barrier(lib, ctx, inflation, rollout):
+    """Sec. V-C.1's inflated barrier on the race car: the road narrows to w - iota
+    (the grid is rebuilt for it) and the box bounds tighten by iota; every rollout
+    form against the oracle."""
+    env = car_env(inflation=inflation)
+    model = gpu_model(lib, ctx, env)
+    x0 = data.car_start_state(env.track, vx=14.0)
+    for k, x_t in enumerate([x0, x0 + np.array([1.0, -0.8, 0.1, 3.0, 0.3, 0.2])]):
+        u_h = data.to_f32_exact(data.user_input_once(800 + k, env.lo, env.hi))
+        sess = lib.Session(ctx, model, 2047, 60, env.lo, env.hi, seed=6, stream_id=k)
+        sess.set_rollout(rollout)
+        g = run_gpu(lib, sess, x_t, u_h, tick=k, traj=rollout != "factored")
+        sess.close()
+        o = omp.tick(env.K32, "car", x_t, u_h, oracle_samples(env, 2047, 6, k, k), 60, env.spec,
+                     record=True)
+        assert compare(g, o, env, 60) <= 10
+        free = omp.tick(env.K32, "car", x_t, u_h, oracle_samples(env, 2047, 6, k, k), 60,
+                        car_env().spec)
+        assert free.n_safe >= o.n_safe          # a narrower road keeps fewer candidates
+    model.free()
