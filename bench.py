@@ -472,6 +472,73 @@ def run_serving(args, bot_states):
     return stats
 
 
+def run_car_loop(args):
+    """The race car in closed loop (N = 16384, H = 60, 60 Hz, 600 ticks, start on
+    the centre line at point 0 with vx = 10, OU user input, a trial restarting
+    from the start whenever the car leaves the road): host ticks through the C
+    ABI (latency, e2e rate), then the loop's states replayed device-resident
+    with the L2 flushed before each tick."""
+    import torch
+    from paper_1906_02318_gb300 import mpmi as lib
+    from paper_1906_02318_gb300.screener import car_in_safe_set
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = lib.Context(dev.index)
+    x, u, xn = data.transitions("car", 3, 20000)
+    model, _ = lib.fit_model(ctx, "car", x, u, xn)
+    track = data.track_polyline(3)
+    lib.set_safety_set(model, data.CAR_SAFE_LO, data.CAR_SAFE_HI, 0.0, track,
+                       data.CAR_TRACK_HALF_WIDTH)
+    lo, hi = plants.CAR_INPUT_LO, plants.CAR_INPUT_HI
+    ticks, N, H = args.car_ticks, 16384, 60
+    sess = lib.Session(ctx, model, N, H, lo, hi, seed=3)
+    x0 = data.car_start_state(track, vx=10.0)
+    uhs = data.to_f32_exact(data.ou_user_input(3, ticks, plants.CAR_DT, lo, hi))
+    stream = torch.cuda.current_stream(dev)
+    xt, states, lat = x0.copy(), np.empty((ticks, 6)), []
+    trials, fallback = 1, 0
+    for t in range(ticks):
+        states[t] = xt
+        t0 = time.perf_counter()
+        lib.evaluate_candidates(sess, xt, uhs[t], tick=t, stream=stream)
+        r = lib.select_input(sess)
+        lat.append(time.perf_counter() - t0)
+        fallback += r["status"] == lib.FALLBACK
+        xt = plants.bicycle_step(xt, r["u_r"])
+        if not car_in_safe_set(xt, track, data.CAR_TRACK_HALF_WIDTH, 25.0):
+            xt = x0.copy()
+            trials += 1
+    lat = np.array(lat[min(20, ticks // 10):])
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    xs = torch.tensor(states, dtype=torch.float64, device=dev)
+    us = torch.tensor(uhs, dtype=torch.float64, device=dev)
+    res = torch.zeros((ticks, lib.RESULT_BYTES), dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(ticks)]
+    for i in range(3):
+        lib.evaluate_candidates_device(sess, xs[i], us[i], res[i], tick=i)
+    for i in range(ticks):
+        flush.zero_()
+        ev[i][0].record()
+        lib.evaluate_candidates_device(sess, xs[i], us[i], res[i], tick=i)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    durs = np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3
+    executed = np.array([lib.result_from_bytes(b, 2)["executed_steps"] for b in res.cpu().numpy()])
+    lanes, cands, block = sess.launch_shape()
+    sess.close()
+    model.free()
+    return {"workload": "race car closed loop: N=16384 (+u_h), H=60, 60 Hz, 600 ticks",
+            "shape": {"lanes": lanes, "cands_per_thread": cands, "block": block},
+            "ticks": ticks, "trials": trials, "fallback_ticks": int(fallback),
+            "device_mean_us": durs.mean() * 1e6, "device_p99_us": np.percentile(durs, 99) * 1e6,
+            "rollout_steps_per_s": (N + 1) * H / durs.mean(),
+            "executed_steps_per_s": executed.mean() / durs.mean(),
+            "host_tick_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
+                             "p99": float(np.percentile(lat, 99) * 1e3), "deadline_ms": 1000 / 60,
+                             "misses": int(np.count_nonzero(lat > 1 / 60))},
+            "e2e_rollout_steps_per_s": (N + 1) * H * len(lat) / lat.sum()}
+
+
 def run_variants(args, bot_states):
     """The paper's variants and the factorised ablation, device-resident at the
     benchmark's sizes (L2 flushed before every tick): the balance bot (N = 16384,
@@ -580,6 +647,8 @@ def main():
     ap.add_argument("--serve-sessions", type=int, default=256)
     ap.add_argument("--variant-ticks", type=int, default=200,
                     help="ticks per paper variant / factorised ablation (0 = skip)")
+    ap.add_argument("--car-ticks", type=int, default=600,
+                    help="race-car closed-loop ticks (0 = skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -649,6 +718,8 @@ def main():
         line["serving"] = run_serving(args, out["states"])
     if rank == 0 and args.variant_ticks > 0:
         line["variants"] = run_variants(args, out["states"])
+    if rank == 0 and args.car_ticks > 0:
+        line["car_closed_loop"] = run_car_loop(args)
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)

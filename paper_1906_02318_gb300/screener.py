@@ -15,7 +15,10 @@ import numpy as np
 from . import mpmi as lib
 
 
-def _car_in_safe_set(x: np.ndarray, track: np.ndarray, half_width: float, vx_max: float) -> bool:
+def car_in_safe_set(x: np.ndarray, track: np.ndarray, half_width: float, vx_max: float) -> bool:
+    """Whether a simulated race-car state is still in the safe set (on the road and
+    below vx_max); leaving it ends a trial (Sec. V-B).  A plant-side check of the
+    closed loops, not part of a tick."""
     if not np.all(np.isfinite(x)) or x[3] >= vx_max:
         return False
     d = np.roll(track, -1, axis=0) - track
@@ -45,7 +48,7 @@ def collect_labels(session, screener, plant_step, x0, user_inputs, track, half_w
         lib.evaluate_candidates_device(session, xd, ud, res, tick=tick0 + t, ttv_dev=ttv[t])
         r = lib.result_from_bytes(res.cpu(), 2)
         x = plant_step(x, r["u_r"])
-        if not _car_in_safe_set(x, track, half_width, vx_max):
+        if not car_in_safe_set(x, track, half_width, vx_max):
             x = np.asarray(x0, dtype=np.float64).copy()
     targets = (ttv.to(torch.float32) / float(session.horizon)).reshape(-1)
     return feats.reshape(-1, 12), targets, xs
