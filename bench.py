@@ -222,6 +222,7 @@ def oracle_rate(K32, states, uhs, n, H, budget_s, workers, tick_ids):
                         [(K32, c, states, uhs, n, H, budget_s) for c in chunks if len(c)])
     steps = sum(s for s, _ in outs)
     t_max = max(t for _, t in outs)
+    oracle_rate.per_core = float(np.mean([s / t for s, t in outs if t > 0]))
     return steps / t_max, steps, t_max
 
 
@@ -736,6 +737,7 @@ def cpu_baseline(args):
     rate, steps, _ = oracle_rate(K32, states, uhs, N_SAMPLES, HORIZON, args.cpu_budget,
                                  workers, list(range(TICKS)))
     return {"value": rate, "unit": "rollout steps/s", "cores": workers, "kind": "oracle",
+            "per_core_value": oracle_rate.per_core,
             "sample": f"FP64 numpy oracle, {steps // ((N_SAMPLES + 1) * HORIZON)} full ticks "
                       f"(N=16384, H=50) across {workers} spawned single-threaded workers, "
                       f"~{args.cpu_budget:.0f} s each"}
@@ -753,14 +755,15 @@ def run_reference(args, cfg):
     ids = [i % TICKS for i in range(args.steps)]
     value, steps, wall = oracle_rate(K32, states, uhs, N_SAMPLES, HORIZON, 1e9, workers, ids)
     line = {"metric": "rollout steps/s (plain path) and p99 control-tick latency at N=16384",
-            "value": value, "unit": "rollout steps/s", "n_gpus": 0, "steps": args.steps,
+            "value": value, "unit": "rollout steps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg, "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "rollout steps/s", "cores": workers,
                              "kind": "oracle",
                              "sample": f"{args.steps} full ticks over {workers} spawned "
-                                       "single-threaded workers (slowest worker's time)"},
+                                       "single-threaded workers on the host cores, no GPU "
+                                       "(slowest worker's time)"},
             "e2e": {"value": value, "unit": "rollout steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
