@@ -320,6 +320,17 @@ int mpmi_sample_candidates(mpmi_session* s, const double* u_h_dev,
  * are affected.  on = 0 restores normal ticks. */
 int mpmi_debug_withhold_staging(mpmi_session* s, int32_t on);
 
+/* Host mirror of the race car's track test (Sec. V-C.1: unsafe off the road),
+ * for checking the grid the library builds without a GPU.  Builds the grid of
+ * the closed centre line track_xy (n_track vertices, row-major x, y) for the
+ * half width and answers, for each float32 point (x, y) of points (n_points x 2,
+ * host), whether it lies within the half width of the centre line, with the
+ * device's own cell lookup and listed-segment test in float32.  on_road: n_points
+ * bytes (host).  Pure host code.  INVALID_ARG for bad sizes, NONFINITE for a
+ * non-finite vertex, UNSUPPORTED if the grid does not fit shared memory. */
+int mpmi_debug_track_query(const double* track_xy, int32_t n_track, double half_width,
+                           const float* points, int64_t n_points, uint8_t* on_road);
+
 int mpmi_debug_trajectories(mpmi_session* s, const double* x_t_dev,
                             const double* u_h_dev, const float* candidates_dev,
                             uint64_t tick, mpmi_result* result_dev,

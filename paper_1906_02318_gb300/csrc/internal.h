@@ -183,4 +183,6 @@ struct TrackGrid {
 constexpr int kMaxTrackBytes = 96 * 1024;  // shared-memory budget of the grid
 int build_track_grid(const double* xy, int n, double half_width, TrackGrid* g,
                      std::string* err);
+int track_query_host(const double* xy, int n, double half_width, const float* pts, int64_t np,
+                     uint8_t* on_road, std::string* err);
 }  // namespace mpmi

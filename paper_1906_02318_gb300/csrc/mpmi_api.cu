@@ -373,6 +373,19 @@ int mpmi_fit_operator_sparse(const mpmi_basis_desc* basis, const double* x, cons
   return MPMI_OK;
 }
 
+int mpmi_debug_track_query(const double* track_xy, int32_t n_track, double half_width,
+                           const float* points, int64_t n_points, uint8_t* on_road) {
+  if (!track_xy || (n_points > 0 && (!points || !on_road)) || n_points < 0)
+    return fail(MPMI_E_INVALID_ARG, "debug_track_query: NULL argument or negative count");
+  if (n_track < 3 || n_track > MPMI_MAX_TRACK_VERTICES)
+    return fail(MPMI_E_INVALID_ARG, "debug_track_query: n_track out of range");
+  if (!(half_width > 0.0) || !std::isfinite(half_width))
+    return fail(MPMI_E_INVALID_ARG, "debug_track_query: half width must be > 0");
+  std::string err;
+  const int rc = track_query_host(track_xy, n_track, half_width, points, n_points, on_road, &err);
+  return rc == MPMI_OK ? MPMI_OK : fail(rc, err);
+}
+
 int mpmi_model_from_operator(mpmi_ctx* ctx, const mpmi_basis_desc* basis, const double* K,
                              mpmi_model** out) {
   if (!ctx || !basis || !K || !out) return fail(MPMI_E_INVALID_ARG, "NULL argument");

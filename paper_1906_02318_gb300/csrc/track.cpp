@@ -131,4 +131,46 @@ int build_track_grid(const double* xy, int n, double w, TrackGrid* g, std::strin
   return MPMI_E_UNSUPPORTED;
 }
 
+// Host mirror of the device's track test over a packed grid (the cell lookup
+// and the listed-segment test, in float32), for checking the grid builder on
+// machines without a GPU: on_road[i] = 1 iff point i is within the half width.
+int track_query_host(const double* xy, int n, double half_width, const float* pts, int64_t np,
+                     uint8_t* on_road, std::string* err) {
+  TrackGrid g;
+  const int rc = build_track_grid(xy, n, half_width, &g, err);
+  if (rc != MPMI_OK) return rc;
+  const uint8_t* base = g.blob.data();
+  const uint32_t* cells = reinterpret_cast<const uint32_t*>(base);
+  const uint16_t* list = reinterpret_cast<const uint16_t*>(base + g.off_list);
+  const float* seg = reinterpret_cast<const float*>(base + g.off_seg);
+  const float* inv = reinterpret_cast<const float*>(base + g.off_inv);
+  const float gx0 = (float)g.gx0, gy0 = (float)g.gy0, inv_h = (float)(1.0 / g.h);
+  const float w2 = (float)(half_width * half_width);
+  for (int64_t i = 0; i < np; ++i) {
+    const float px = pts[2 * i], py = pts[2 * i + 1];
+    bool ok = false;
+    const float fx = (px - gx0) * inv_h, fy = (py - gy0) * inv_h;
+    if (fx >= 0.f && fx < (float)g.gnx && fy >= 0.f && fy < (float)g.gny) {
+      const uint32_t c = cells[(int)fy * g.gnx + (int)fx];
+      const uint32_t cls = c & 3u;
+      if (cls == kCellInside) {
+        ok = true;
+      } else if (cls == kCellBoundary) {
+        const int off = (int)((c >> 2) & 0x3FFFFFu), cnt = (int)(c >> 24);
+        for (int k = 0; k < cnt && !ok; ++k) {
+          const int s = list[off + k];
+          const float* sg = seg + 4 * s;
+          const float rx = px - sg[0], ry = py - sg[1];
+          float t = (rx * sg[2] + ry * sg[3]) * inv[s];
+          t = t < 0.f ? 0.f : (t > 1.f ? 1.f : t);
+          const float ex = rx - t * sg[2], ey = ry - t * sg[3];
+          ok = ex * ex + ey * ey < w2;
+        }
+      }
+    }
+    on_road[i] = ok ? 1 : 0;
+  }
+  return MPMI_OK;
+}
+
 }  // namespace mpmi

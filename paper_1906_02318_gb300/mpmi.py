@@ -86,6 +86,7 @@ _SIGNATURES = {
     "mpmi_debug_withhold_staging": (c_i32, [c_vp, c_i32]),
     "mpmi_fit_operator_sparse": (c_i32, [ctypes.POINTER(BasisDesc), c_vp, c_vp, c_vp, c_i64,
                                           c_dbl, c_dbl, c_i32, c_vp, c_vp, P_dbl]),
+    "mpmi_debug_track_query": (c_i32, [P_dbl, c_i32, c_dbl, c_vp, c_i64, c_vp]),
     "mpmi_session_launch_shape": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32),
                                           ctypes.POINTER(c_i32)]),
     "mpmi_evaluate_candidates": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
@@ -290,6 +291,16 @@ def fit_operator_sparse(basis: str, x, u, x_next, gamma: float, rho: float = 1.0
                                         int(iters), K.ctypes.data, sup.ctypes.data,
                                         ctypes.byref(res)))
     return K, sup.astype(bool), res.value
+
+
+def debug_track_query(track_xy, half_width: float, points) -> np.ndarray:
+    """mpmi_debug_track_query: host mirror of the device's on-road test (bool per point)."""
+    tr = _f64(track_xy).reshape(-1, 2)
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.float32).reshape(-1, 2))
+    out = np.zeros(pts.shape[0], dtype=np.uint8)
+    _check(load().mpmi_debug_track_query(tr.ctypes.data_as(P_dbl), tr.shape[0], float(half_width),
+                                         pts.ctypes.data, pts.shape[0], out.ctypes.data))
+    return out.astype(bool)
 
 
 def model_from_operator(ctx: Context, basis: str, K, nx: int | None = None,
