@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kMaxBlock) serve_kernel(const __grid_constant_
     }
     unsigned long long best = ~0ull;
     unsigned int n_safe = 0, n_exec = 0;
-    run_tile<KIND, L, C, KSMEM, false, false, true>(st, sa.safety, gwt - st.tile_begin, st.n_slots, xs, uh,
+    run_tile<KIND, L, C, KSMEM, false, false, true>(st, dyn_of(st), sa.safety, gwt - st.tile_begin, st.n_slots, xs, uh,
                                        sn, cs, kr, sK4, tv, &s_x[L > 1 ? warp : 0][0][0][0],
                                        best, n_safe, n_exec);
 #pragma unroll

@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kTcM) tc_tick_kernel(const __grid_constant__ T
         for (int j = 0; j < N; ++j)
           if (!held_feature(KIND, j)) z[j] = zn[j];
       }
-      if (a.n_noise > 0 && alive) add_noise<NX>(a, slot, t, z);
+      if (a.n_noise > 0 && alive) add_noise<NX>(a, dyn_of(a), slot, t, z);
       if constexpr (TRAJ) {
         if (traj != nullptr && alive) {
 #pragma unroll

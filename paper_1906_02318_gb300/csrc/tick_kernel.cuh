@@ -112,10 +112,43 @@ __device__ __forceinline__ void stage_k(const float* K, uint4* dst, int tid, int
   for (int i = tid; i < N * W; i += nthreads) dst[(i / W) * KSmem<N>::S4 + i % W] = __ldg(&src[i]);
 }
 
-// Alg. 2 first step: the input held by candidate `slot`.
+// Parameter records that carry a completion word for zero-copy host ticks.
+template <class P, class = void>
+struct HasSeq {
+  static constexpr bool value = false;
+};
+template <class P>
+struct HasSeq<P, decltype((void)sizeof(((P*)nullptr)->seq_out), void())> {
+  static constexpr bool value = true;
+};
+
+// The values that change from tick to tick: the Philox counter words of the
+// tick, the tick itself, u_h (float64, device) and the completion number of a
+// zero-copy host tick.  Normally the launch's parameters; a persistent kernel
+// takes them from its command record.
+struct TickDyn {
+  uint32_t t_lo, t_hi;
+  unsigned long long tick, seq;
+  const double* u_h;
+};
+
+template <class P>
+__device__ __forceinline__ TickDyn dyn_of(const P& a) {
+  TickDyn d;
+  d.t_lo = a.t_lo;
+  d.t_hi = a.t_hi;
+  d.tick = a.tick;
+  d.u_h = a.u_h;
+  if constexpr (HasSeq<P>::value) d.seq = a.seq;
+  else d.seq = 0;
+  return d;
+}
+
+// Alg. 2 first step: the input held by candidate `slot` in the tick whose
+// counter words are (t_lo, t_hi).
 template <int NU, class P>
-__device__ __forceinline__ void candidate_value(const P& a, int slot, const float* uh32,
-                                                float* xi) {
+__device__ __forceinline__ void candidate_value(const P& a, uint32_t t_lo, uint32_t t_hi,
+                                                int slot, const float* uh32, float* xi) {
   if (a.include_user && slot == 0) {
 #pragma unroll
     for (int j = 0; j < NU; ++j) xi[j] = uh32[j];
@@ -123,7 +156,7 @@ __device__ __forceinline__ void candidate_value(const P& a, int slot, const floa
   }
   const int i = slot - a.include_user;
   if (a.sampler == MPMI_SAMPLER_UNIFORM) {
-    const U32x4 w = philox4x32_10(U32x4{(uint32_t)i, a.t_lo, a.t_hi, a.stream}, a.key0, a.key1);
+    const U32x4 w = philox4x32_10(U32x4{(uint32_t)i, t_lo, t_hi, a.stream}, a.key0, a.key1);
     const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
     for (int j = 0; j < NU; ++j) {
@@ -147,6 +180,12 @@ __device__ __forceinline__ void candidate_value(const P& a, int slot, const floa
   }
 }
 
+template <int NU, class P>
+__device__ __forceinline__ void candidate_value(const P& a, int slot, const float* uh32,
+                                                float* xi) {
+  candidate_value<NU>(a, a.t_lo, a.t_hi, slot, uh32, xi);
+}
+
 // Two standard normals from two Philox words (Box & Muller, Ann. Math. Stat. 29,
 // 1958): u1 = ((w_a >> 8) + 1) 2^-24 in (0, 1], u2 = (w_b >> 8) 2^-24 in [0, 1),
 // both exact in binary32; n = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
@@ -166,13 +205,13 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, 
 // 2^25 b, stream); its words pair as (w0, w1) -> 4b, 4b+1 and (w2, w3) -> 4b+2,
 // 4b+3.  Since t >= 1 these counters never meet a candidate counter.
 template <int NX, class P>
-__device__ __forceinline__ void add_noise(const P& a, int slot, int t, float* z) {
+__device__ __forceinline__ void add_noise(const P& a, TickDyn d, int slot, int t, float* z) {
   constexpr int NB = (NX + 3) / 4;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     if (4 * b < a.n_noise) {
-      const uint32_t c2 = (a.t_hi & 0xFFFFu) + ((uint32_t)t << 16) + ((uint32_t)b << 25);
-      const U32x4 w = philox4x32_10(U32x4{(uint32_t)slot, a.t_lo, c2, a.stream}, a.key0, a.key1);
+      const uint32_t c2 = (d.t_hi & 0xFFFFu) + ((uint32_t)t << 16) + ((uint32_t)b << 25);
+      const U32x4 w = philox4x32_10(U32x4{(uint32_t)slot, d.t_lo, c2, a.stream}, a.key0, a.key1);
       float n[4];
       box_muller(w.x, w.y, n[0], n[1]);
       box_muller(w.z, w.w, n[2], n[3]);
@@ -257,31 +296,21 @@ __device__ __forceinline__ bool track_ok(const DevTrack& tr, const TrackView& v,
   return ok;
 }
 
-// Parameter records that carry a completion word for zero-copy host ticks.
-template <class P, class = void>
-struct HasSeq {
-  static constexpr bool value = false;
-};
-template <class P>
-struct HasSeq<P, decltype((void)sizeof(((P*)nullptr)->seq_out), void())> {
-  static constexpr bool value = true;
-};
-
 // Decode of the winning key into the tick's result record.
 template <int NU, class P>
-__device__ __forceinline__ void write_result(const P& a, unsigned long long k,
+__device__ __forceinline__ void write_result(const P& a, TickDyn d, unsigned long long k,
                                              unsigned long long cnt, const float* uh,
                                              bool timed_out = false) {
   const int pick = (int)(k & 0x7FFFFFull);
   const int hm = (int)(k >> 55);
   mpmi_result r;
   float xb[NU];
-  candidate_value<NU>(a, pick, uh, xb);
+  candidate_value<NU>(a, d.t_lo, d.t_hi, pick, uh, xb);
 #pragma unroll
   for (int j = 0; j < MPMI_MAX_NU; ++j) r.u_r[j] = 0.0;
 #pragma unroll
   for (int j = 0; j < NU; ++j)
-    r.u_r[j] = (a.include_user && pick == 0) ? a.u_h[j] : (double)xb[j];
+    r.u_r[j] = (a.include_user && pick == 0) ? d.u_h[j] : (double)xb[j];
   r.index = pick;
   r.status = timed_out ? MPMI_TIMEOUT : (hm == 0 ? MPMI_SAFE : MPMI_FALLBACK);
   r.n_safe = (int32_t)(cnt >> 40);
@@ -289,15 +318,22 @@ __device__ __forceinline__ void write_result(const P& a, unsigned long long k,
   r.cost = __uint_as_float((unsigned int)((k >> 23) & 0xFFFFFFFFull));
   r.n_slots = a.n_list ? *a.n_list : a.n_slots;
   r.executed_steps = cnt & ((1ull << 40) - 1);
-  r.tick = a.tick;
+  r.tick = d.tick;
   r.reserved = a.result_flags;
   *a.result = r;
   if constexpr (HasSeq<P>::value) {
     if (a.seq_out != nullptr) {  // the host polls this word instead of an event
       __threadfence_system();
-      *reinterpret_cast<volatile unsigned long long*>(a.seq_out) = a.seq;
+      *reinterpret_cast<volatile unsigned long long*>(a.seq_out) = d.seq;
     }
   }
+}
+
+template <int NU, class P>
+__device__ __forceinline__ void write_result(const P& a, unsigned long long k,
+                                             unsigned long long cnt, const float* uh,
+                                             bool timed_out = false) {
+  write_result<NU>(a, dyn_of(a), k, cnt, uh, timed_out);
 }
 
 // One warp-tile: the PER_WARP = 32 C / L candidate positions wt * PER_WARP ...
@@ -309,7 +345,8 @@ __device__ __forceinline__ void write_result(const P& a, unsigned long long k,
 // recomputing them -- bit for bit the same z for finite states.
 template <int KIND, int L, int C, bool KSMEM, bool TRAJ, bool NOISE, bool HELD, class P,
           class KR>
-__device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, int wt, int n_eval,
+__device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety& safety,
+                                         int wt, int n_eval,
                                          const float* xs, const float* uh, float sn, float cs,
                                          const KR& kr, const float4* sK4, const TrackView& tv,
                                          float* xbuf, unsigned long long& best,
@@ -338,7 +375,7 @@ __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, in
     slot[c] = (valid[c] && a.slot_list) ? a.slot_list[pos] : pos;
     float xi[NU];
     if (valid[c]) {
-      candidate_value<NU>(a, slot[c], uh, xi);
+      candidate_value<NU>(a, d.t_lo, d.t_hi, slot[c], uh, xi);
     } else {
 #pragma unroll
       for (int j = 0; j < NU; ++j) xi[j] = uh[j];
@@ -487,7 +524,7 @@ __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, in
     if constexpr (NOISE) {
 #pragma unroll
       for (int c = 0; c < C; ++c)
-        if (alive[c]) add_noise<NX>(a, slot[c], t, z[c]);
+        if (alive[c]) add_noise<NX>(a, d, slot[c], t, z[c]);
     }
     bool any_alive = false;
 #pragma unroll
@@ -537,9 +574,10 @@ __device__ __forceinline__ void run_tile(const P& a, const DevSafety& safety, in
 // and the counts into the session's reduction record (one atomicMin/atomicAdd per
 // block); the block that finishes last decodes the result and resets the record.
 template <int NU, class P>
-__device__ __forceinline__ void session_epilogue(const P& a, unsigned long long best,
-                                                 unsigned int n_safe, unsigned int n_exec,
-                                                 const float* uh, bool failed = false) {
+__device__ __forceinline__ void session_epilogue(const P& a, TickDyn d,
+                                                 unsigned long long best, unsigned int n_safe,
+                                                 unsigned int n_exec, const float* uh,
+                                                 bool failed = false) {
   __shared__ unsigned long long s_key[kMaxBlock / 32];
   __shared__ unsigned long long s_cnt[kMaxBlock / 32];
   __shared__ int s_last;
@@ -579,12 +617,22 @@ __device__ __forceinline__ void session_epilogue(const P& a, unsigned long long 
     const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&sc->key);
     const unsigned long long cnt = *reinterpret_cast<volatile unsigned long long*>(&sc->counts);
     const unsigned int err = *reinterpret_cast<volatile unsigned int*>(&sc->error);
-    write_result<NU>(a, k, cnt, uh, err != 0u);
+    // reset the record before publishing: a persistent kernel's next tick may
+    // start as soon as the result is visible (the publish of a zero-copy tick
+    // sits behind a system-scope fence, which orders these stores too)
     sc->key = ~0ull;
     sc->counts = 0ull;
     sc->error = 0u;
     sc->done = 0u;
+    write_result<NU>(a, d, k, cnt, uh, err != 0u);
   }
+}
+
+template <int NU, class P>
+__device__ __forceinline__ void session_epilogue(const P& a, unsigned long long best,
+                                                 unsigned int n_safe, unsigned int n_exec,
+                                                 const float* uh, bool failed = false) {
+  session_epilogue<NU>(a, dyn_of(a), best, n_safe, n_exec, uh, failed);
 }
 
 // Template parameters of the tick kernel:
@@ -706,7 +754,7 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   constexpr int PER_WARP = GPW * C;  // candidate slots per warp-tile
   const int n_wtiles = failed ? 0 : (n_eval + PER_WARP - 1) / PER_WARP;
   for (int wt = blockIdx.x * wpb + warp; wt < n_wtiles; wt += gridDim.x * wpb)
-    run_tile<KIND, L, C, KSMEM, TRAJ, NOISE, !PARTIALS>(a, a.safety, wt, n_eval, xs, uh, sn, cs, kr, sK4, tv,
+    run_tile<KIND, L, C, KSMEM, TRAJ, NOISE, !PARTIALS>(a, dyn_of(a), a.safety, wt, n_eval, xs, uh, sn, cs, kr, sK4, tv,
                                       &s_x[L > 1 ? warp : 0][0][0][0], best, n_safe, n_exec);
 
   if constexpr (!PARTIALS) {
