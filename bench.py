@@ -14,8 +14,11 @@ test, cost, device-wide argmin and decode (every row of the hot path).
                (256 MB write) before every timed tick, CUDA events on the launch
                stream around each tick.
   e2e          the same metric through the host C-ABI call (evaluate_candidates +
-               select_input) driving the closed loop: per tick a host->device copy
-               of x_t/u_h from pinned memory and a device->host read of the result.
+               select_input) driving the closed loop, with persistent host ticks
+               (a resident kernel reads x_t/u_h from a pinned mailbox and writes the
+               result to pinned memory, every tick); e2e_launched: the same loop
+               with one kernel launch per tick.  Both loops must visit the same
+               states (persistent_loop_identical).
   roofline     FP32 CUDA-core (ALU) bound: algorithmic flops per tick (2 n^2 per
                executed prediction step + lifting + cost) / mean tick duration,
                against 152 SMs x 128 FP32 lanes x 2 flops x max SM clock.
@@ -274,27 +277,43 @@ def run_gpu(args, rank, world):
     # closed loop through the host C-ABI (e2e): W warm-up ticks, then timed ticks.
     # As in the paper's trials, a trial ends when the plant leaves the safe set
     # and the next one starts from x_0.
-    x_t = X0.copy()
-    states = np.empty((ticks, 4))
-    lat = []
-    n_fallback = 0
-    trials = 1
-    for t in range(ticks):
-        states[t] = x_t
-        t0 = time.perf_counter()
-        lib.evaluate_candidates(sess, x_t, uhs[t], tick=t, stream=stream)
-        r = lib.select_input(sess)
-        dt = time.perf_counter() - t0
-        if t >= args.warmup:
-            lat.append(dt)
-        n_fallback += r["status"] == lib.FALLBACK
-        x_t = plants.cartpole_step(x_t, r["u_r"])
-        inside = np.all(np.isfinite(x_t)) and np.all(x_t > data.BOT_SAFE_LO) and \
-            np.all(x_t < data.BOT_SAFE_HI)
-        if not inside:
-            x_t = X0.copy()
-            trials += 1
-    lat = np.array(lat)
+    def closed_loop():
+        x_t = X0.copy()
+        states = np.empty((ticks, 4))
+        lat = []
+        n_fallback = 0
+        trials = 1
+        for t in range(ticks):
+            states[t] = x_t
+            t0 = time.perf_counter()
+            lib.evaluate_candidates(sess, x_t, uhs[t], tick=t, stream=stream)
+            r = lib.select_input(sess)
+            dt = time.perf_counter() - t0
+            if t >= args.warmup:
+                lat.append(dt)
+            n_fallback += r["status"] == lib.FALLBACK
+            x_t = plants.cartpole_step(x_t, r["u_r"])
+            inside = np.all(np.isfinite(x_t)) and np.all(x_t > data.BOT_SAFE_LO) and \
+                np.all(x_t < data.BOT_SAFE_HI)
+            if not inside:
+                x_t = X0.copy()
+                trials += 1
+        return states, np.array(lat), n_fallback, trials
+
+    # launched host ticks (one kernel launch per tick, zero-copy inputs/result)
+    states, lat_launched, n_fallback, trials = closed_loop()
+    # the same loop with persistent host ticks (a resident kernel fed through a
+    # pinned mailbox); it must retrace the launched loop's states exactly
+    lat_persist, persist_note, persist_same = None, None, None
+    try:
+        sess.set_persistent(True)
+    except lib.MpmiError as e:
+        persist_note = f"persistent host ticks unavailable: {e}"
+    else:
+        states_p, lat_persist, _, _ = closed_loop()
+        sess.set_persistent(False)
+        persist_same = bool(np.array_equal(states_p, states))
+    lat = lat_persist if lat_persist is not None else lat_launched
     e2e_rate = n_slots * HORIZON * len(lat) / lat.sum()
 
     # device-resident ticks: inputs in HBM, L2 flushed before each timed tick
@@ -353,6 +372,8 @@ def run_gpu(args, rank, world):
     sess.close()
     model.free()
     return dict(dev_time=dev_time, durs=durs, executed=executed, lat=lat, e2e_rate=e2e_rate,
+                lat_launched=lat_launched, persistent=lat_persist is not None,
+                persist_note=persist_note, persist_same=persist_same,
                 wall=wall, clocks=clk, lanes=lanes, cands=cands, block=block, n_slots=n_slots,
                 residual=residual, n_fallback=int(n_fallback), trials=trials, states=states,
                 sm_count=props.multi_processor_count,
@@ -681,6 +702,15 @@ def main():
     value = job_throughput(world, K, n_step, t_max)
     e2e_value = job_throughput(world, len(out["lat"]), n_step, e2e_max)
 
+    if out["persistent"]:
+        # the resident kernel reads the mailbox (command word + 15 words) and writes
+        # the result record and the completion word
+        e2e_mode = "persistent host ticks (resident kernel, pinned mailbox)"
+        h2d, d2h = 16 * 8, 80 + 8
+    else:
+        e2e_mode = "launched host ticks (" + str(out["persist_note"]) + ")"
+        h2d, d2h = 12 * 8, 80 + 8
+
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = out["sm_count"] * SM_FP32_LANES * 2 * sm_max * 1e6 / 1e12
@@ -702,10 +732,19 @@ def main():
                        "p99": float(np.percentile(out["lat"], 99) * 1e3),
                        "deadline_ms": 10.0,
                        "misses": int(np.count_nonzero(out["lat"] > 0.010)),
-                       "what": "host-to-host C-ABI tick (evaluate_candidates + select_input)"},
+                       "what": "host-to-host C-ABI tick (evaluate_candidates + select_input), "
+                               + e2e_mode},
         "learned": None,
         "e2e": {"value": e2e_value, "unit": "rollout steps/s",
-                "h2d_bytes_per_step": 12 * 8, "d2h_bytes_per_step": 80},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "mode": e2e_mode},
+        "e2e_launched": {
+            "value": n_step * len(out["lat_launched"]) / float(out["lat_launched"].sum()),
+            "unit": "rollout steps/s",
+            "p50_ms": float(np.percentile(out["lat_launched"], 50) * 1e3),
+            "p99_ms": float(np.percentile(out["lat_launched"], 99) * 1e3),
+            "what": "one kernel launch per host tick; x_t/u_h read and the result written "
+                    "over the host link (zero-copy)"},
+        "persistent_loop_identical": out["persist_same"],
         "gpu_launches": K,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,

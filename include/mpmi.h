@@ -267,6 +267,29 @@ int mpmi_session_set_noise(mpmi_session* s, const double* sigma, int32_t count);
 #define MPMI_ROLLOUT_TENSOR 2
 int mpmi_session_set_rollout(mpmi_session* s, int32_t mode);
 
+/* Persistent host ticks (not part of the method; the tick itself is Alg. 2
+ * unchanged).  With on != 0, host ticks (mpmi_evaluate_candidates) of the FULL
+ * rollout without noise and with a built-in sampler run in one kernel that stays
+ * resident on the device between ticks: it stages K and the track grid once and
+ * then waits on a mailbox in pinned host memory; each host tick writes x_t, u_h
+ * and the tick into the mailbox and publishes its sequence number with one
+ * system-scope compare-and-swap, and select_input waits for the completion word
+ * as for zero-copy ticks.  No CUDA call is made per tick.  Results are
+ * bit-identical to the launched tick of the same session.
+ *   idle_ms: the kernel exits after this long without a command (0 = 1000 ms;
+ *     at most 60000); the next host tick relaunches it.  Every wait inside the
+ *     kernel is bounded by it.
+ *   Other ticks of the session (device-resident, trajectories, screened ticks,
+ *   ticks with noise or another rollout) first stop the resident kernel and run
+ *   as launches; the next host tick restarts it.  on = 0 stops it (after any
+ *   tick in flight has been published) and returns to launched host ticks.
+ * The resident kernel holds the blocks one tick needs (cooperative launch, on a
+ * stream of its own) and one polling thread per block while idle.
+ * MPMI_E_UNSUPPORTED where the device cannot map host memory, has no native
+ * host-memory atomics or cooperative launch, or the session's launch shape has
+ * no persistent form; MPMI_E_INVALID_ARG for idle_ms outside 0..60000 or NaN. */
+int mpmi_session_set_persistent(mpmi_session* s, int32_t on, double idle_ms);
+
 /* ---- evaluate_candidates + select_input (Alg. 2) ------------------------ */
 /* Queues one tick on `stream`: copies x_t (nx doubles) and u_h (nu doubles) into
  * the session's pinned staging buffer, samples the candidates (counter = tick),
@@ -276,7 +299,9 @@ int mpmi_session_set_rollout(mpmi_session* s, int32_t mode);
  * (zero-copy); otherwise two asynchronous copies do it.  Returns without waiting.
  * candidates_dev: device N x M float32 samples for MPMI_SAMPLER_EXTERNAL, else
  * must be NULL.  NONFINITE if x_t or u_h holds NaN/Inf.  If a previous tick of
- * this session is still in flight, waits for it first. */
+ * this session is still in flight, waits for it first.  In persistent mode
+ * (mpmi_session_set_persistent) the tick is handed to the resident kernel through
+ * the mailbox and `stream` is not used. */
 int mpmi_evaluate_candidates(mpmi_session* s, const double* x_t, const double* u_h,
                              const float* candidates_dev, uint64_t tick,
                              void* stream);
@@ -284,8 +309,11 @@ int mpmi_evaluate_candidates(mpmi_session* s, const double* x_t, const double* u
  * to *out (host).  With zero-copy ticks it returns as soon as the kernel has
  * published the result (a completion word stored after it, polled for up to a
  * second before falling back to the tick's CUDA event); the session's next
- * launch is ordered behind the rest of that kernel on the GPU.  NOT_READY if no
- * tick is in flight; TIMEOUT for a result with status MPMI_TIMEOUT. */
+ * launch is ordered behind the rest of that kernel on the GPU.  A tick handed to
+ * a resident kernel (mpmi_session_set_persistent) is waited for on the same word
+ * for the idle limit plus a second; then the kernel is stopped (it finishes the
+ * tick first) and TIMEOUT is returned if still nothing was published.  NOT_READY
+ * if no tick is in flight; TIMEOUT for a result with status MPMI_TIMEOUT. */
 int mpmi_select_input(mpmi_session* s, mpmi_result* out);
 
 /* Device-resident form of one tick (nothing is copied to or from the host and

@@ -89,6 +89,25 @@ struct TickArgs {
   unsigned long long seq;
 };
 
+// Persistent host ticks: the mailbox (pinned host memory) and its device copy
+// are kCmdWords 64-bit words: [0] command number, [1] tick, [2, 10) x_t,
+// [10, 14) u_h (doubles); word kCmdHalt of the device copy is block 0's halt
+// flag.  Flags in the mailbox's word 0: kCmdStop (host: halt once the pending
+// command is done), kCmdExit (kernel: exited after the idle limit).
+constexpr int kCmdWords = 16;
+constexpr int kCmdPayload = 14;  // words 0 .. 13
+constexpr int kCmdHalt = 14;
+constexpr unsigned long long kCmdStop = 1ull << 63;
+constexpr unsigned long long kCmdExit = 1ull << 62;
+constexpr unsigned long long kCmdSeqMask = kCmdExit - 1;
+
+struct PersistArgs {
+  unsigned long long* mbox;  // device alias of the pinned mailbox
+  unsigned long long* cmd;   // device copy that blocks other than 0 read
+  unsigned long long start_seq;  // commands numbered above this one are new
+  unsigned long long idle_ns;    // exit after this long without a command
+};
+
 }  // namespace mpmi
 
 // ---- host handles ----------------------------------------------------------
@@ -151,6 +170,17 @@ struct mpmi_session {
   int tc_grid[2] = {0, 0};         // resident CTAs of the tensor-core rollout (plain, traj)
   size_t tc_smem[2] = {0, 0};
   int withhold_staging = 0;        // test hook (mpmi_debug_withhold_staging)
+  // persistent host ticks (persistent.cu)
+  bool persist = false;            // requested by mpmi_session_set_persistent
+  bool persist_running = false;    // a resident kernel may be waiting on the mailbox
+  bool persist_posted = false;     // the tick in flight went through the mailbox
+  unsigned long long persist_idle_ns = 0;
+  unsigned long long* mbox_host = nullptr;  // pinned, kCmdWords words
+  unsigned long long* mbox_map = nullptr;
+  unsigned long long* cmd_dev = nullptr;    // kCmdWords words
+  unsigned long long cmd_init[mpmi::kCmdWords] = {};  // source of the copy that resets it
+  cudaStream_t persist_stream = nullptr;
+  cudaEvent_t persist_done = nullptr;
   uint64_t bytes = 0;
 };
 
@@ -161,6 +191,9 @@ int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, i
 // factorised rollout (factored.cu)
 int compute_powers(int kind, const float* K, int H, float* out, cudaStream_t st);
 int launch_factored(mpmi_session* s, TickArgs& a, cudaStream_t st, int n_hint);
+// persistent host ticks (persistent.cu)
+bool persist_supported(int kind, int lanes, int cands);
+int launch_persistent(mpmi_session* s, const TickArgs& a, const PersistArgs& p);
 // tensor-core rollout (tensor.cu)
 int launch_tensor(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint);
 void set_error(const std::string& msg);

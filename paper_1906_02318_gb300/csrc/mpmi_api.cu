@@ -152,7 +152,105 @@ static void small_shape(int kind, int* lanes, int* cands, int* block) {
   *lanes = kind == kCar ? 8 : (kind == kBot ? 4 : 1);
 }
 
+// ---- persistent host ticks ----------------------------------------------------
+// The resident kernel (persistent.cu) takes commands from the session's mailbox.
+// Word 0 holds the number of the last command posted; the host posts command q
+// by a compare-and-swap from q - 1, which fails only if the kernel has marked
+// the word as exited after its idle limit (then the host waits for the exit and
+// relaunches).  A stop request is a flag or-ed into the word; the kernel still
+// finishes a command posted before it.
+
+// Stops the resident kernel, if any, and waits for it to exit.
+static int persist_stop(mpmi_session* s) {
+  if (!s->persist_running) return MPMI_OK;
+  __atomic_fetch_or(&s->mbox_host[0], kCmdStop, __ATOMIC_SEQ_CST);
+  s->persist_running = false;
+  MPMI_CUDA(cudaEventSynchronize(s->persist_done), "waiting for the resident tick kernel to stop");
+  return MPMI_OK;
+}
+
+// Launches the resident kernel; commands numbered above `start` are new to it.
+static int persist_start(mpmi_session* s, cudaStream_t st, unsigned long long start) {
+  MPMI_CUDA(cudaEventSynchronize(s->persist_done), "waiting for the previous resident kernel");
+  __atomic_store_n(&s->mbox_host[0], start, __ATOMIC_SEQ_CST);
+  for (int j = 0; j < kCmdWords; ++j) s->cmd_init[j] = 0;
+  s->cmd_init[0] = start;
+  MPMI_CUDA(cudaMemcpyAsync(s->cmd_dev, s->cmd_init, sizeof(s->cmd_init),
+                            cudaMemcpyHostToDevice, s->persist_stream),
+            "initialising the resident kernel's command copy");
+  // order behind a launched tick that may still be finishing and behind earlier
+  // work on the caller's stream
+  if (s->tail_pending) {
+    MPMI_CUDA(cudaStreamWaitEvent(s->persist_stream, s->done, 0), "cudaStreamWaitEvent");
+    s->tail_pending = false;
+  }
+  MPMI_CUDA(cudaEventRecord(s->done, st), "cudaEventRecord");
+  MPMI_CUDA(cudaStreamWaitEvent(s->persist_stream, s->done, 0), "cudaStreamWaitEvent");
+  TickArgs a = make_tick_args(s, 0);
+  a.result = s->result_map;
+  a.seq_out = s->seq_map;
+  PersistArgs p;
+  p.mbox = s->mbox_map;
+  p.cmd = s->cmd_dev;
+  p.start_seq = start;
+  p.idle_ns = s->persist_idle_ns;
+  const int rc = launch_persistent(s, a, p);
+  if (rc != MPMI_OK) return rc;
+  MPMI_CUDA(cudaEventRecord(s->persist_done, s->persist_stream), "cudaEventRecord");
+  s->persist_running = true;
+  return MPMI_OK;
+}
+
+// Posts command `seq` (mailbox words 1.. already written), relaunching the
+// resident kernel where it is not running.
+static int persist_post(mpmi_session* s, cudaStream_t st, unsigned long long seq) {
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    if (!s->persist_running) {
+      const int rc = persist_start(s, st, seq - 1);
+      if (rc != MPMI_OK) return rc;
+    }
+    unsigned long long expect = seq - 1;
+    if (__atomic_compare_exchange_n(&s->mbox_host[0], &expect, seq, false, __ATOMIC_SEQ_CST,
+                                    __ATOMIC_SEQ_CST))
+      return MPMI_OK;
+    // the kernel exited after its idle limit just before the command
+    s->persist_running = false;
+  }
+  return fail(MPMI_E_CUDA, "persistent tick: the resident kernel keeps exiting before a command");
+}
+
+// Waits for the completion word of the tick in flight (zero-copy ticks): true
+// once it holds the tick's number, false after `limit`.
+static bool poll_published(const mpmi_session* s, std::chrono::nanoseconds limit) {
+  const volatile unsigned long long* w = s->seq_host;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (unsigned long i = 0;; ++i) {
+    if (*w == s->seq) {
+      std::atomic_thread_fence(std::memory_order_acquire);
+      return true;
+    }
+    if ((i & 1023) == 1023 && std::chrono::steady_clock::now() - t0 > limit) return false;
+  }
+}
+
+// The result of a tick posted to the resident kernel: polls for the idle limit
+// plus a second, then stops the kernel (which finishes the command first) and
+// looks once more.
+static int persist_wait(mpmi_session* s) {
+  if (poll_published(s, std::chrono::nanoseconds(s->persist_idle_ns) + std::chrono::seconds(1)))
+    return MPMI_OK;
+  const int rc = persist_stop(s);
+  if (poll_published(s, std::chrono::nanoseconds(0))) return MPMI_OK;
+  if (rc != MPMI_OK) return rc;
+  return fail(MPMI_E_TIMEOUT, "persistent tick: no result within the idle limit plus a second");
+}
+
 int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint) {
+  // a launched tick shares the session's reduction record with the resident kernel
+  if (s->persist_running) {
+    const int rc = persist_stop(s);
+    if (rc != MPMI_OK) return rc;
+  }
   if (s->tail_pending) {
     // the previous host tick's kernel may still be finishing: order behind it
     const cudaError_t e = cudaStreamWaitEvent(st, s->done, 0);
@@ -633,6 +731,7 @@ int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model, const mpmi_session
 void mpmi_session_close(mpmi_session* s) {
   if (!s) return;
   DeviceGuard guard(s->ctx->device);
+  persist_stop(s);
   if (s->in_flight || s->tail_pending) cudaEventSynchronize(s->done);
   if (s->ck_dev) {
     cudaDeviceSynchronize();
@@ -646,6 +745,10 @@ void mpmi_session_close(mpmi_session* s) {
   cudaFreeHost(s->result_host);
   cudaFreeHost(s->seq_host);
   cudaEventDestroy(s->done);
+  if (s->mbox_host) cudaFreeHost(s->mbox_host);
+  if (s->cmd_dev) cudaFree(s->cmd_dev);
+  if (s->persist_stream) cudaStreamDestroy(s->persist_stream);
+  if (s->persist_done) cudaEventDestroy(s->persist_done);
   s->ctx->used -= s->bytes;
   delete s;
 }
@@ -687,6 +790,8 @@ int mpmi_session_set_rollout(mpmi_session* s, int32_t mode) {
   mpmi_ctx* ctx = s->ctx;
   DeviceGuard guard(ctx->device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+  const int prc = persist_stop(s);  // the device-wide waits below would wait for it
+  if (prc != MPMI_OK) return prc;
   if (mode == MPMI_ROLLOUT_FULL || mode == MPMI_ROLLOUT_TENSOR) {
     // device-resident ticks may still read the rows
     MPMI_CUDA(cudaDeviceSynchronize(), "set_rollout: waiting for ticks in flight");
@@ -720,6 +825,67 @@ int mpmi_session_set_rollout(mpmi_session* s, int32_t mode) {
   return MPMI_OK;
 }
 
+int mpmi_session_set_persistent(mpmi_session* s, int32_t on, double idle_ms) {
+  if (!s) return fail(MPMI_E_INVALID_ARG, "session is NULL");
+  if (!(idle_ms == 0.0 || (idle_ms >= 1.0 && idle_ms <= 60000.0)))
+    return fail(MPMI_E_INVALID_ARG, "set_persistent: idle_ms must be 0 or in 1..60000");
+  DeviceGuard guard(s->ctx->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+  if (!on) {
+    s->persist = false;
+    return persist_stop(s);  // a command in flight is finished and published first
+  }
+  if (!s->zero_copy)
+    return fail(MPMI_E_UNSUPPORTED, "set_persistent: the device cannot map host memory");
+  int atomics = 0, coop = 0;
+  if (cudaDeviceGetAttribute(&atomics, cudaDevAttrHostNativeAtomicSupported, s->ctx->device) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MPMI_E_CUDA, "set_persistent: device attributes");
+  }
+  if (!atomics)
+    return fail(MPMI_E_UNSUPPORTED, "set_persistent: no native atomics on host memory");
+  if (!coop) return fail(MPMI_E_UNSUPPORTED, "set_persistent: no cooperative launch");
+  if (!persist_supported(s->model->kind, s->lanes, s->cands))
+    return fail(MPMI_E_UNSUPPORTED, "set_persistent: no persistent form of this launch shape");
+  if (!s->mbox_host) {
+    const size_t bytes = kCmdWords * sizeof(unsigned long long);
+    if (!budget_ok(s->ctx, bytes)) return fail(MPMI_E_OOM, "set_persistent: exceeds the memory budget");
+    bool ok = cudaMallocHost(&s->mbox_host, bytes) == cudaSuccess &&
+              cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->mbox_map), s->mbox_host, 0) ==
+                  cudaSuccess &&
+              cudaMalloc(&s->cmd_dev, bytes) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&s->persist_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&s->persist_done, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      if (s->mbox_host) cudaFreeHost(s->mbox_host);
+      if (s->cmd_dev) cudaFree(s->cmd_dev);
+      if (s->persist_stream) cudaStreamDestroy(s->persist_stream);
+      if (s->persist_done) cudaEventDestroy(s->persist_done);
+      s->mbox_host = nullptr;
+      s->mbox_map = nullptr;
+      s->cmd_dev = nullptr;
+      s->persist_stream = nullptr;
+      s->persist_done = nullptr;
+      return fail(MPMI_E_OOM, "set_persistent: allocating the mailbox failed");
+    }
+    memset(s->mbox_host, 0, bytes);
+    s->bytes += bytes;
+    s->ctx->used += bytes;
+  }
+  const unsigned long long idle_ns =
+      (unsigned long long)((idle_ms == 0.0 ? 1000.0 : idle_ms) * 1e6);
+  if (s->persist_running && idle_ns != s->persist_idle_ns) {
+    const int rc = persist_stop(s);  // the next tick relaunches with the new limit
+    if (rc != MPMI_OK) return rc;
+  }
+  s->persist_idle_ns = idle_ns;
+  s->persist = true;
+  return MPMI_OK;
+}
+
 static int check_ext(const mpmi_session* s, const float* candidates_dev) {
   if (s->cfg.sampler == MPMI_SAMPLER_EXTERNAL && s->cfg.n_samples > 0 && !candidates_dev)
     return fail(MPMI_E_INVALID_ARG, "EXTERNAL sampler needs candidates_dev");
@@ -740,8 +906,29 @@ int mpmi_evaluate_candidates(mpmi_session* s, const double* x_t, const double* u
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
   if (s->in_flight) {
-    MPMI_CUDA(cudaEventSynchronize(s->done), "waiting for the previous tick");
+    if (s->persist_posted) {
+      if ((rc = persist_wait(s)) != MPMI_OK) return rc;
+    } else {
+      MPMI_CUDA(cudaEventSynchronize(s->done), "waiting for the previous tick");
+    }
     s->in_flight = false;
+    s->persist_posted = false;
+  }
+  if (s->persist && s->rollout == MPMI_ROLLOUT_FULL && s->n_noise == 0 &&
+      s->cfg.sampler != MPMI_SAMPLER_EXTERNAL) {
+    // hand the tick to the resident kernel: mailbox words, then the number
+    unsigned long long* mb = s->mbox_host;
+    double xw[MPMI_MAX_NX] = {0, 0, 0, 0, 0, 0, 0, 0}, uw[MPMI_MAX_NU] = {0, 0, 0, 0};
+    memcpy(xw, x_t, sizeof(double) * m->nx);
+    memcpy(uw, u_h, sizeof(double) * m->nu);
+    mb[1] = tick;
+    memcpy(mb + 2, xw, sizeof(xw));
+    memcpy(mb + 10, uw, sizeof(uw));
+    if ((rc = persist_post(s, st, s->seq + 1)) != MPMI_OK) return rc;
+    ++s->seq;
+    s->persist_posted = true;
+    s->in_flight = true;
+    return MPMI_OK;
   }
   memcpy(s->in_host, x_t, sizeof(double) * m->nx);
   memcpy(s->in_host + 8, u_h, sizeof(double) * m->nu);
@@ -774,6 +961,17 @@ int mpmi_select_input(mpmi_session* s, mpmi_result* out) {
   if (!s || !out) return fail(MPMI_E_INVALID_ARG, "select_input: NULL argument");
   if (!s->in_flight) return fail(MPMI_E_NOT_READY, "select_input: no tick in flight");
   DeviceGuard guard(s->ctx->device);
+  if (s->persist_posted) {
+    const int rc = persist_wait(s);
+    s->in_flight = false;
+    s->persist_posted = false;
+    if (rc != MPMI_OK) return rc;
+    *out = *s->result_host;
+    if (out->status == MPMI_TIMEOUT)
+      return fail(MPMI_E_TIMEOUT, "select_input: a block of the resident tick kernel timed out "
+                                  "staging shared memory; the result is not a selection");
+    return MPMI_OK;
+  }
   bool seen = false;
   if (s->zero_copy) {
     // the decoding block stores the tick's sequence number after the result
@@ -805,7 +1003,9 @@ int mpmi_select_input(mpmi_session* s, mpmi_result* out) {
 int mpmi_debug_withhold_staging(mpmi_session* s, int32_t on) {
   if (!s) return fail(MPMI_E_INVALID_ARG, "session is NULL");
   s->withhold_staging = on ? 1 : 0;
-  return MPMI_OK;
+  // a resident kernel keeps the staging it started with: the next tick relaunches
+  DeviceGuard guard(s->ctx->device);
+  return persist_stop(s);
 }
 
 static int evaluate_device(mpmi_session* s, const double* x_t_dev, const double* u_h_dev,

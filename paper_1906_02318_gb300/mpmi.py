@@ -83,6 +83,7 @@ _SIGNATURES = {
     "mpmi_session_close": (None, [c_vp]),
     "mpmi_session_set_noise": (c_i32, [c_vp, P_dbl, c_i32]),
     "mpmi_session_set_rollout": (c_i32, [c_vp, c_i32]),
+    "mpmi_session_set_persistent": (c_i32, [c_vp, c_i32, c_dbl]),
     "mpmi_debug_withhold_staging": (c_i32, [c_vp, c_i32]),
     "mpmi_fit_operator_sparse": (c_i32, [ctypes.POINTER(BasisDesc), c_vp, c_vp, c_vp, c_i64,
                                           c_dbl, c_dbl, c_i32, c_vp, c_vp, P_dbl]),
@@ -381,6 +382,12 @@ class Session:
         "tensor" (the same on tcgen05 tensor cores, race car) or "factored"
         (read-outs from precomputed rows C K^t; an exact-in-real-arithmetic ablation)."""
         _check(self.ctx.lib.mpmi_session_set_rollout(self.handle, ROLLOUT[mode]))
+
+    def set_persistent(self, on: bool = True, idle_ms: float = 0.0):
+        """mpmi_session_set_persistent: host ticks run in a resident kernel fed
+        through a pinned mailbox (idle_ms: exit after that long without a tick;
+        0 = one second)."""
+        _check(self.ctx.lib.mpmi_session_set_persistent(self.handle, int(bool(on)), float(idle_ms)))
 
     def withhold_staging(self, on: bool):
         """mpmi_debug_withhold_staging: test hook that makes the kernel's bounded
