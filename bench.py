@@ -304,15 +304,16 @@ def run_gpu(args, rank, world):
     states, lat_launched, n_fallback, trials = closed_loop()
     # the same loop with persistent host ticks (a resident kernel fed through a
     # pinned mailbox); it must retrace the launched loop's states exactly
-    lat_persist, persist_note, persist_same = None, None, None
-    try:
-        sess.set_persistent(True)
-    except lib.MpmiError as e:
-        persist_note = f"persistent host ticks unavailable: {e}"
-    else:
-        states_p, lat_persist, _, _ = closed_loop()
-        sess.set_persistent(False)
-        persist_same = bool(np.array_equal(states_p, states))
+    lat_persist, persist_note, persist_same = None, "launched host ticks requested", None
+    if not args.launched_host_ticks:
+        try:
+            sess.set_persistent(True)
+        except lib.MpmiError as e:
+            persist_note = f"persistent host ticks unavailable: {e}"
+        else:
+            states_p, lat_persist, _, _ = closed_loop()
+            sess.set_persistent(False)
+            persist_same = bool(np.array_equal(states_p, states))
     lat = lat_persist if lat_persist is not None else lat_launched
     e2e_rate = n_slots * HORIZON * len(lat) / lat.sum()
 
@@ -516,20 +517,36 @@ def run_car_loop(args):
     x0 = data.car_start_state(track, vx=10.0)
     uhs = data.to_f32_exact(data.ou_user_input(3, ticks, plants.CAR_DT, lo, hi))
     stream = torch.cuda.current_stream(dev)
-    xt, states, lat = x0.copy(), np.empty((ticks, 6)), []
-    trials, fallback = 1, 0
-    for t in range(ticks):
-        states[t] = xt
-        t0 = time.perf_counter()
-        lib.evaluate_candidates(sess, xt, uhs[t], tick=t, stream=stream)
-        r = lib.select_input(sess)
-        lat.append(time.perf_counter() - t0)
-        fallback += r["status"] == lib.FALLBACK
-        xt = plants.bicycle_step(xt, r["u_r"])
-        if not car_in_safe_set(xt, track, data.CAR_TRACK_HALF_WIDTH, 25.0):
-            xt = x0.copy()
-            trials += 1
-    lat = np.array(lat[min(20, ticks // 10):])
+
+    def closed_loop():
+        xt, states, lat = x0.copy(), np.empty((ticks, 6)), []
+        trials, fallback = 1, 0
+        for t in range(ticks):
+            states[t] = xt
+            t0 = time.perf_counter()
+            lib.evaluate_candidates(sess, xt, uhs[t], tick=t, stream=stream)
+            r = lib.select_input(sess)
+            lat.append(time.perf_counter() - t0)
+            fallback += r["status"] == lib.FALLBACK
+            xt = plants.bicycle_step(xt, r["u_r"])
+            if not car_in_safe_set(xt, track, data.CAR_TRACK_HALF_WIDTH, 25.0):
+                xt = x0.copy()
+                trials += 1
+        return states, np.array(lat[min(20, ticks // 10):]), trials, fallback
+
+    # launched host ticks, then the same loop with persistent host ticks
+    states, lat_launched, trials, fallback = closed_loop()
+    lat, mode, same = lat_launched, "launched host ticks (requested)", None
+    if not args.launched_host_ticks:
+        try:
+            sess.set_persistent(True)
+        except lib.MpmiError as e:
+            mode = f"launched host ticks (persistent unavailable: {e})"
+        else:
+            states_p, lat, _, _ = closed_loop()
+            sess.set_persistent(False)
+            mode = "persistent host ticks (resident kernel, pinned mailbox)"
+            same = bool(np.array_equal(states_p, states))
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     xs = torch.tensor(states, dtype=torch.float64, device=dev)
     us = torch.tensor(uhs, dtype=torch.float64, device=dev)
@@ -557,8 +574,11 @@ def run_car_loop(args):
             "executed_steps_per_s": executed.mean() / durs.mean(),
             "host_tick_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
                              "p99": float(np.percentile(lat, 99) * 1e3), "deadline_ms": 1000 / 60,
-                             "misses": int(np.count_nonzero(lat > 1 / 60))},
-            "e2e_rollout_steps_per_s": (N + 1) * H * len(lat) / lat.sum()}
+                             "misses": int(np.count_nonzero(lat > 1 / 60)), "mode": mode},
+            "e2e_rollout_steps_per_s": (N + 1) * H * len(lat) / lat.sum(),
+            "launched_host_tick_ms": {"p50": float(np.percentile(lat_launched, 50) * 1e3),
+                                      "p99": float(np.percentile(lat_launched, 99) * 1e3)},
+            "persistent_loop_identical": same}
 
 
 def run_variants(args, bot_states):
@@ -671,6 +691,10 @@ def main():
                     help="ticks per paper variant / factorised ablation (0 = skip)")
     ap.add_argument("--car-ticks", type=int, default=600,
                     help="race-car closed-loop ticks (0 = skip)")
+    ap.add_argument("--launched-host-ticks", action="store_true",
+                    help="host ticks as one launch each only (no resident kernel; for runs "
+                         "under a profiler, which serialises launches and would leave a "
+                         "resident kernel waiting on a mailbox that cannot be written)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -91,7 +91,7 @@ _SIGNATURES = {
     "mpmi_session_launch_shape": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32),
                                           ctypes.POINTER(c_i32)]),
     "mpmi_evaluate_candidates": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
-    "mpmi_select_input": (c_i32, [c_vp, ctypes.POINTER(Result)]),
+    "mpmi_select_input": (c_i32, [c_vp, c_vp]),
     "mpmi_evaluate_candidates_device": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp, c_vp,
                                                 c_vp, c_vp]),
     "mpmi_sample_candidates": (c_i32, [c_vp, c_vp, c_vp, c_u64, c_vp, c_vp]),
@@ -362,6 +362,12 @@ class Session:
         self.nx, self.nu = model.nx, model.nu
         self.n = model.get_operator().shape[0]
         self._result = Result()   # reused by select_input
+        self._result_ptr = ctypes.addressof(self._result)
+        self._u_r = np.frombuffer(self._result, dtype=np.float64, count=MAX_NU)
+        # x_t / u_h staging for host ticks (the library copies them during the call)
+        self._in = np.zeros(MAX_NX + MAX_NU)
+        self._x_ptr = self._in.ctypes.data
+        self._u_ptr = self._x_ptr + 8 * MAX_NX
 
     def launch_shape(self):
         """(lanes per candidate, candidates per thread, threads per block)."""
@@ -402,9 +408,10 @@ class Session:
 
 def evaluate_candidates(s: Session, x_t, u_h, candidates=None, tick: int = 0, stream=None):
     """mpmi_evaluate_candidates: queue one tick from host x_t / u_h (float64)."""
-    x = _f64(x_t, s.nx)
-    u = _f64(u_h, s.nu)
-    rc = s.ctx.lib.mpmi_evaluate_candidates(s.handle, x.ctypes.data, u.ctypes.data,
+    buf = s._in
+    buf[:s.nx] = _f64(x_t, s.nx)
+    buf[MAX_NX:MAX_NX + s.nu] = _f64(u_h, s.nu)
+    rc = s.ctx.lib.mpmi_evaluate_candidates(s.handle, s._x_ptr, s._u_ptr,
                                             _ptr(candidates), tick, _stream(stream))
     if rc:
         _check(rc)
@@ -413,10 +420,12 @@ def evaluate_candidates(s: Session, x_t, u_h, candidates=None, tick: int = 0, st
 def select_input(s: Session) -> dict:
     """mpmi_select_input: wait for the queued tick and return its outcome."""
     r = s._result
-    rc = s.ctx.lib.mpmi_select_input(s.handle, ctypes.byref(r))
+    rc = s.ctx.lib.mpmi_select_input(s.handle, s._result_ptr)
     if rc:
         _check(rc)
-    return result_dict(r, s.nu)
+    return dict(u_r=s._u_r[:s.nu].copy(), index=r.index, status=r.status, n_safe=r.n_safe,
+                ttv=r.ttv, cost=r.cost, n_slots=r.n_slots, executed_steps=r.executed_steps,
+                tick=r.tick, flags=r.reserved)
 
 
 def evaluate_candidates_device(s: Session, x_t_dev, u_h_dev, result_dev, candidates=None,
