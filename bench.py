@@ -60,7 +60,7 @@ SM_FP32_LANES = 128
 
 # DRAM bytes per tick-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum); valid only for the kernel source it was taken on.
-TRAFFIC = {"tick_kernel_sha1": "25d7b081e9ef59cdc83db10fa9bdf0e8f894039d", "bytes_per_launch": 25344}
+TRAFFIC = {"tick_kernel_sha1": "af5f4c194dbd102e25f607496fdcb04b8be34dba", "bytes_per_launch": 25088}
 
 
 def kernel_sha1() -> str:
