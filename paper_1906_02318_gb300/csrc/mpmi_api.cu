@@ -69,17 +69,25 @@ static TickKernel pick_tick(int kind, int lanes, int cands, bool traj, bool nois
 // Default launch shape (lanes, candidates per thread, block).  A tick is one
 // warp's serial chain of H steps when the candidates fit the GPU several times
 // over, so few candidates take more lanes each (measured on GB300: race car
-// N = 1024..8192 with 8 lanes 35..70 us against 75 us with one; balance bot
+// N = 1024..8192 with 8 lanes 31..70 us against 75 us with one; balance bot
 // N <= 4096 with 4 lanes 12.6 against 13.4..14.1 us).  Otherwise one lane per
 // candidate; the race car keeps K in shared memory and takes two candidates per
-// thread once there are enough candidates to fill the GPU; small grids use
-// 64-thread blocks so every SM gets work.
-static int default_block(int n_slots, int lanes, int cands, int sms) {
-  const long long threads = ((long long)n_slots * lanes + cands - 1) / cands;
-  return threads <= (long long)sms * 128 ? 64 : (threads <= (long long)sms * 256 ? 128 : 256);
-}
+// thread once there are enough candidates to fill the GPU.  Blocks of 128
+// threads (one warp per SM sub-partition per block) measured never slower than
+// 64 or 256 (bot N = 8192..65536, race car N = 16384..65536; 256 concentrates two
+// warps on a sub-partition while SMs stay idle at N = 16384: 17.0 / 137 us
+// against 13.6 / 82 us), and fewer blocks stage K and the track grid fewer times.
+constexpr int kDefaultBlock = 128;
 
 static void default_shape(int kind, int n_slots, int sms, int* lanes, int* cands, int* block) {
+  if (kind == kCar && (long long)n_slots * 16 <= (long long)sms * 128) {
+    // at most one warp per SM sub-partition even with 16 lanes per candidate
+    // (N = 1024: 28.1 us against 31.0 us with 8 lanes)
+    *lanes = 16;
+    *cands = 1;
+    *block = 128;
+    return;
+  }
   if (kind == kCar && (long long)n_slots * 8 <= (long long)sms * 512) {
     *lanes = 8;
     *cands = 1;
@@ -94,7 +102,7 @@ static void default_shape(int kind, int n_slots, int sms, int* lanes, int* cands
   }
   *lanes = 1;
   *cands = (kind == kCar && n_slots > 48 * 1024) ? 2 : 1;
-  *block = default_block(n_slots, *lanes, *cands, sms);
+  *block = kDefaultBlock;
 }
 
 TickArgs make_tick_args(const mpmi_session* s, uint64_t tick) {
@@ -656,7 +664,7 @@ int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model, const mpmi_session
     if (block == 0) block = db;
   } else {
     if (cands == 0) cands = (lanes == 1 && model->kind == kCar && slots > 48 * 1024) ? 2 : 1;
-    if (block == 0) block = default_block((int)slots, lanes, cands, ctx->sm_count);
+    if (block == 0) block = kDefaultBlock;
   }
   if (block % 32 != 0 || block < 32 || block > kMaxBlock)
     return fail(MPMI_E_INVALID_ARG, "session_open: block must be a multiple of 32 in 32..256");

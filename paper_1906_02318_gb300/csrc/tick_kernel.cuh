@@ -240,7 +240,7 @@ template <int NX>
 __device__ __forceinline__ bool box_ok(const DevSafety& s, const float* z) {
   bool ok = true;
 #pragma unroll
-  for (int j = 0; j < NX; ++j) ok = ok && (z[j] > s.lo[j]) && (z[j] < s.hi[j]);
+  for (int j = 0; j < NX; ++j) ok = ok & (z[j] > s.lo[j]) & (z[j] < s.hi[j]);
   return ok;
 }
 
@@ -253,7 +253,9 @@ struct TrackView {
 };
 
 // isSafe on the track part, shared by the L lanes of a group: lane q tests list
-// entries q, q + L, ... (nearest first, stops at the first hit); the group ORs.
+// entries q, q + L, ... (nearest first, stops at the first hit); the group ORs
+// through one warp vote.  Non-short-circuit boolean operators keep the tests
+// independent (fewer dependent branches on the step's critical path).
 template <int L>
 __device__ __forceinline__ bool track_ok(const DevTrack& tr, const TrackView& v, float px,
                                          float py, int q, bool active) {
@@ -261,7 +263,7 @@ __device__ __forceinline__ bool track_ok(const DevTrack& tr, const TrackView& v,
   if (active) {
     const float fx = (px - tr.gx0) * tr.inv_h;
     const float fy = (py - tr.gy0) * tr.inv_h;
-    if (fx >= 0.f && fx < (float)tr.gnx && fy >= 0.f && fy < (float)tr.gny) {
+    if ((fx >= 0.f) & (fx < (float)tr.gnx) & (fy >= 0.f) & (fy < (float)tr.gny)) {
       const uint32_t c = v.cells[(int)fy * tr.gnx + (int)fx];
       const uint32_t cls = c & 3u;
       if (cls == kCellInside) {
@@ -279,7 +281,7 @@ __device__ __forceinline__ bool track_ok(const DevTrack& tr, const TrackView& v,
             const float rx = px - sg.x, ry = py - sg.y;
             const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * v.inv[s], 0.f), 1.f);
             const float ex = rx - t * sg.z, ey = ry - t * sg.w;
-            hit = hit || (ex * ex + ey * ey < tr.w2);
+            hit = hit | (ex * ex + ey * ey < tr.w2);
           }
           if (hit) {
             ok = true;
@@ -290,8 +292,10 @@ __device__ __forceinline__ bool track_ok(const DevTrack& tr, const TrackView& v,
     }
   }
   if constexpr (L > 1) {
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) ok = ok | (__shfl_xor_sync(kFull, (int)ok, o) != 0);
+    // OR over the group's L lanes: one warp vote, then the group's bits
+    const unsigned int votes = __ballot_sync(kFull, ok);
+    const int base = (int)(threadIdx.x & 31) & ~(L - 1);
+    ok = ((votes >> base) & ((L == 32) ? kFull : ((1u << L) - 1u))) != 0u;
   }
   return ok;
 }
