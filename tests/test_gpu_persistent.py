@@ -285,6 +285,65 @@ def test_withheld_staging_in_the_resident_kernel(lib, ctx, car):
     sess.close()
 
 
+@pytest.mark.parametrize("case", ["bot_grid", "bot_no_user", "car_inflated", "linear_22",
+                                  "bot_max_horizon", "car_ragged"])
+def test_resident_ticks_across_session_kinds(lib, ctx, bot, car, case):
+    """Samplers, the user slot, the inflated barrier, the linear bases, the longest
+    horizon and ragged slot counts: resident ticks equal launched ticks."""
+    models = []
+    if case == "bot_grid":
+        env, model = bot
+        kw = dict(n=4096, H=50, sampler="grid")
+    elif case == "bot_no_user":
+        env, model = bot
+        kw = dict(n=3000, H=40, include_user=False)
+    elif case == "car_inflated":
+        env = car_env(inflation=0.5)
+        model = gpu_model(lib, ctx, env)
+        models.append(model)
+        kw = dict(n=2500, H=60)
+    elif case == "linear_22":
+        K = np.array([[1.0, 0.0, 0.05, 0.0], [0.0, 1.0, 0.0, 0.05],
+                      [0.0, 0.0, 1.0, 0.0], [0.0, 0.0, 0.0, 1.0]])
+        model = lib.model_from_operator(ctx, "linear", K, nx=2, nu=2)
+        lib.set_safety_set(model, [-1.0, -1.0], [1.0, 1.0])
+        models.append(model)
+        env = None
+        kw = dict(n=5000, H=80)
+    elif case == "bot_max_horizon":
+        env, model = bot
+        kw = dict(n=1000, H=511)
+    else:
+        env, model = car
+        kw = dict(n=16384 + 77, H=60)
+    lo = env.lo if env is not None else [-1.0, -1.0]
+    hi = env.hi if env is not None else [1.0, 1.0]
+    n, H = kw.pop("n"), kw.pop("H")
+    rng = np.random.default_rng(7)
+    cases = []
+    for k in range(6):
+        if env is None:
+            x = rng.uniform(-0.8, 0.8, 2)
+            u = data.to_f32_exact(rng.uniform(-1.0, 1.0, 2))
+        else:
+            x, u = _inputs(env, "bot" if env.basis == "bot" else "car", 10 + k)
+        cases.append((x, u, 40 + 3 * k))
+    plain = lib.Session(ctx, model, n, H, lo, hi, seed=13, **kw)
+    want = []
+    for x, u, t in cases:
+        lib.evaluate_candidates(plain, x, u, tick=t)
+        want.append(lib.select_input(plain))
+    plain.close()
+    sess = lib.Session(ctx, model, n, H, lo, hi, seed=13, **kw)
+    _persistent(lib, sess)
+    for (x, u, t), w in zip(cases, want):
+        lib.evaluate_candidates(sess, x, u, tick=t)
+        _same(lib.select_input(sess), w)
+    sess.close()
+    for m in models:
+        m.free()
+
+
 def test_argument_checks(lib, ctx, bot):
     env, model = bot
     sess = lib.Session(ctx, model, 100, 10, env.lo, env.hi)
