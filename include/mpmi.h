@@ -258,9 +258,10 @@ int mpmi_session_set_noise(mpmi_session* s, const double* sigma, int32_t count);
 /* TENSOR (race car only): the same z <- K z as FULL, computed for tiles of 128
  * candidates as one matrix product per step on the tcgen05 tensor cores (Sec.
  * IV-A: a batch of predictions is one matrix-matrix product).  Each float32
- * operand is split into two TF32 parts and the product taken as hi*hi + hi*lo +
- * lo*hi with float32 accumulation in tensor memory (error of the order of
- * float32 rounding); held features are restored exactly after every step.
+ * operand is split into two TF32 parts and the product taken as hi*hi + lo*hi
+ * (one float32 accumulator in tensor memory) plus hi*lo (a second one), the two
+ * added in float32 (error of the order of float32 rounding); held features are
+ * restored exactly after every step.
  * Results agree with the float64 reference under the same tolerance as FULL but
  * are not bit-identical to it.  Supports trajectories, noise and screened
  * ticks; no extra device memory.  MPMI_E_UNSUPPORTED for other bases. */

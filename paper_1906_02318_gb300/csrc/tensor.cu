@@ -8,13 +8,15 @@
 //   1. thread i writes its z as two TF32 rows (hi = rna(z), lo = rna(z - hi)) into
 //      the K-major shared-memory tiles A_hi, A_lo (8-row x 16-byte core
 //      matrices, no swizzle);
-//   2. one thread issues tcgen05.mma kind::tf32 (M = 128, N = 32, K = 8) for
-//      the three products A_hi K_hi + A_hi K_lo + A_lo K_hi over the four K
-//      blocks, all into one float32 accumulator in TMEM, and commits to an
+//   2. one thread issues tcgen05.mma kind::tf32 over the four K blocks of 8:
+//      A_hi [K_hi; K_lo]^T (N = 64, the K_lo tile directly follows K_hi, so one
+//      operand covers both) into accumulator columns 0..63, then A_lo K_hi^T
+//      (N = 32) into columns 0..31 -- eight MMAs in all -- and commits to an
 //      mbarrier;
-//   3. every thread reads its row of the accumulator back with tcgen05.ld,
-//      restores the held features exactly (their rows of K are unit rows),
-//      adds the noise z_i if enabled, and runs the safety test.
+//   3. every thread reads its row of both column halves back with tcgen05.ld,
+//      adds them (A_hi K_hi^T + A_lo K_hi^T + A_hi K_lo^T), restores the held
+//      features exactly (their rows of K are unit rows), adds the noise z_i if
+//      enabled, and runs the safety test.
 // Dropping lo*lo leaves an error of the order of float32 rounding (measured:
 // 4e-7 relative per product against float64, 1e-5 after 60 steps like the
 // float32 FMA chain), so results agree with the oracle under the same
@@ -52,14 +54,18 @@ __device__ __forceinline__ uint64_t mat_desc(uint32_t saddr, uint32_t lbo, uint3
 
 // Instruction descriptor, kind::tf32: D float32, A and B TF32, both K-major,
 // N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) |
-                                ((uint32_t)(kTcM >> 4) << 24);
+constexpr uint32_t idesc_tf32(uint32_t n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
+constexpr uint32_t kIdescTf32 = idesc_tf32(32);
+constexpr uint32_t kIdescTf32N64 = idesc_tf32(64);
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-      "l"(ad), "l"(bd), "r"(kIdescTf32), "r"(acc)
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
 }
 
@@ -121,7 +127,7 @@ __global__ void __launch_bounds__(kTcM) tc_tick_kernel(const __grid_constant__ T
     s_fail = 0;
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
                      smem_u32(&s_tmem))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -235,14 +241,16 @@ __global__ void __launch_bounds__(kTcM) tc_tick_kernel(const __grid_constant__ T
       tc_fence_after();
       // (2) Z K^T as hi*hi + hi*lo + lo*hi over the four K blocks of 8
       if (tid == 0) {
-        const uint32_t as[3] = {a_hi, a_hi, a_lo};
-        const uint32_t bs[3] = {b_hi, b_lo, b_hi};
+        // columns 0..31: A_hi K_hi^T + A_lo K_hi^T; columns 32..63: A_hi K_lo^T (B rows
+        // 32..63 are the K_lo tile, which directly follows K_hi)
 #pragma unroll
-        for (int term = 0; term < 3; ++term)
+        for (int kb = 0; kb < N / 8; ++kb)
+          mma_tf32(tmem, mat_desc(a_hi + kb * 256, 128, 1024), mat_desc(b_hi + kb * 256, 128, 1024),
+                   kIdescTf32N64, kb ? 1u : 0u);
 #pragma unroll
-          for (int kb = 0; kb < N / 8; ++kb)
-            mma_tf32(tmem, mat_desc(as[term] + kb * 256, 128, 1024),
-                     mat_desc(bs[term] + kb * 256, 128, 1024), (term | kb) ? 1u : 0u);
+        for (int kb = 0; kb < N / 8; ++kb)
+          mma_tf32(tmem, mat_desc(a_lo + kb * 256, 128, 1024), mat_desc(b_hi + kb * 256, 128, 1024),
+                   kIdescTf32, 1u);
         asm volatile(
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&s_bar_mma))
@@ -255,11 +263,12 @@ __global__ void __launch_bounds__(kTcM) tc_tick_kernel(const __grid_constant__ T
       tc_fence_after();
       // (3) the new z: the accumulator row, held features restored exactly
       if (done) {
-        float zn[N];
+        float zn[N], zl[N];
         tmem_ld32(taddr, zn);
+        tmem_ld32(taddr + 32, zl);
 #pragma unroll
         for (int j = 0; j < N; ++j)
-          if (!held_feature(KIND, j)) z[j] = zn[j];
+          if (!held_feature(KIND, j)) z[j] = __fadd_rn(zn[j], zl[j]);
       }
       if (a.n_noise > 0 && alive) add_noise<NX>(a, dyn_of(a), slot, t, z);
       if constexpr (TRAJ) {
@@ -303,7 +312,7 @@ __global__ void __launch_bounds__(kTcM) tc_tick_kernel(const __grid_constant__ T
   __syncthreads();
   tc_fence_after();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
   session_epilogue<NU>(a, best, n_safe, n_exec, uh, failed);
 }
 
