@@ -284,8 +284,11 @@ int mpmi_session_set_rollout(mpmi_session* s, int32_t mode);
  *   ticks with noise or another rollout) first stop the resident kernel and run
  *   as launches; the next host tick restarts it.  on = 0 stops it (after any
  *   tick in flight has been published) and returns to launched host ticks.
- * The resident kernel holds the blocks one tick needs (cooperative launch, on a
- * stream of its own) and one polling thread per block while idle.
+ * The resident kernel holds at most one block per SM (cooperative launch, on a
+ * stream of its own) and one polling thread per block while idle; other work on
+ * the device gets the remaining resources until the idle limit or a stop.  The
+ * resident grids of several persistent sessions must fit beside each other: a
+ * grid that cannot start waits until another one exits.
  * MPMI_E_UNSUPPORTED where the device cannot map host memory, has no native
  * host-memory atomics or cooperative launch, or the session's launch shape has
  * no persistent form; MPMI_E_INVALID_ARG for idle_ms outside 0..60000 or NaN. */

@@ -265,6 +265,10 @@ int launch_persistent(mpmi_session* s, const TickArgs& a, const PersistArgs& pa)
   const int per_warp = 32 / s->lanes * s->cands;
   const int n_wtiles = (s->n_slots + per_warp - 1) / per_warp;
   int grid = (n_wtiles + wpb - 1) / wpb;
+  // at most one block per SM (warps stride over the warp-tiles), so that a
+  // resident grid leaves room beside it for other kernels and other sessions'
+  // resident grids
+  if (grid > s->ctx->sm_count) grid = s->ctx->sm_count;
   if (grid > nb * s->ctx->sm_count) grid = nb * s->ctx->sm_count;
   if (grid < 1) grid = 1;
   // every block must be resident at once (they wait on block 0's relay)
