@@ -54,6 +54,8 @@ TICKS = 1000
 FIT_SEED, FIT_COUNT = 1, 5000
 LOOP_SEED = 2
 X0 = np.array([0.05, 0.0, 0.0, 0.0])
+CAR_SEED, CAR_TRACK_SEED, CAR_FIT_COUNT = 3, 3, 20000
+CAR_ORACLE_N = 4096  # candidates per oracle tick in the race car's CPU sample
 LIFTED_N = 12
 FLUSH_BYTES = 256 << 20
 SM_FP32_LANES = 128
@@ -195,34 +197,40 @@ class ClockSampler:
 def _oracle_worker(args):
     """Spawned worker: oracle ticks over the given tick indices until the time
     budget runs out.  Returns (rollout steps, seconds)."""
-    (K32, ticks, states, uhs, n, H, budget) = args
+    (basis, K32, ticks, states, uhs, n, H, budget) = args
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
     sys.path.insert(0, ROOT)
     from oracle import mpmi as omp
     from oracle import safety as osafe
     from oracle import sampling as osamp
-    spec = osafe.SafetySpec(lo=data.BOT_SAFE_LO, hi=data.BOT_SAFE_HI)
+    if basis == "bot":
+        spec = osafe.SafetySpec(lo=data.BOT_SAFE_LO, hi=data.BOT_SAFE_HI)
+        lo, hi, seed = plants.BOT_INPUT_LO, plants.BOT_INPUT_HI, LOOP_SEED
+    else:
+        spec = osafe.SafetySpec(lo=data.CAR_SAFE_LO, hi=data.CAR_SAFE_HI,
+                                track=data.track_polyline(CAR_TRACK_SEED),
+                                half_width=data.CAR_TRACK_HALF_WIDTH)
+        lo, hi, seed = plants.CAR_INPUT_LO, plants.CAR_INPUT_HI, CAR_SEED
     steps = 0
     t0 = time.perf_counter()
     for t in ticks:
-        s = osamp.uniform_samples(LOOP_SEED, 0, int(t), n, plants.BOT_INPUT_LO,
-                                  plants.BOT_INPUT_HI)
-        omp.tick(K32, "bot", states[t], uhs[t], s, H, spec)
+        s = osamp.uniform_samples(seed, 0, int(t), n, lo, hi)
+        omp.tick(K32, basis, states[t], uhs[t], s, H, spec)
         steps += (n + 1) * H
         if time.perf_counter() - t0 > budget:
             break
     return steps, time.perf_counter() - t0
 
 
-def oracle_rate(K32, states, uhs, n, H, budget_s, workers, tick_ids):
+def oracle_rate(K32, states, uhs, n, H, budget_s, workers, tick_ids, basis="bot"):
     """Rollout steps/s of the oracle on `workers` spawned processes."""
     import multiprocessing as mp
     chunks = [tick_ids[w::workers] for w in range(workers)]
     ctx = mp.get_context("spawn")
     with ctx.Pool(workers) as pool:
         outs = pool.map(_oracle_worker,
-                        [(K32, c, states, uhs, n, H, budget_s) for c in chunks if len(c)])
+                        [(basis, K32, c, states, uhs, n, H, budget_s) for c in chunks if len(c)])
     steps = sum(s for s, _ in outs)
     t_max = max(t for _, t in outs)
     oracle_rate.per_core = float(np.mean([s / t for s, t in outs if t > 0]))
@@ -392,9 +400,9 @@ def run_learned(args):
     from paper_1906_02318_gb300 import screener as drv
     dev = torch.device("cuda", torch.cuda.current_device())
     ctx = lib.Context(dev.index)
-    x, u, xn = data.transitions("car", 3, 20000)
+    x, u, xn = data.transitions("car", CAR_SEED, CAR_FIT_COUNT)
     model, _ = lib.fit_model(ctx, "car", x, u, xn)
-    track = data.track_polyline(3)
+    track = data.track_polyline(CAR_TRACK_SEED)
     lib.set_safety_set(model, data.CAR_SAFE_LO, data.CAR_SAFE_HI, 0.0, track,
                        data.CAR_TRACK_HALF_WIDTH)
     lo, hi = plants.CAR_INPUT_LO, plants.CAR_INPUT_HI
@@ -506,16 +514,16 @@ def run_car_loop(args):
     from paper_1906_02318_gb300.screener import car_in_safe_set
     dev = torch.device("cuda", torch.cuda.current_device())
     ctx = lib.Context(dev.index)
-    x, u, xn = data.transitions("car", 3, 20000)
+    x, u, xn = data.transitions("car", CAR_SEED, CAR_FIT_COUNT)
     model, _ = lib.fit_model(ctx, "car", x, u, xn)
-    track = data.track_polyline(3)
+    track = data.track_polyline(CAR_TRACK_SEED)
     lib.set_safety_set(model, data.CAR_SAFE_LO, data.CAR_SAFE_HI, 0.0, track,
                        data.CAR_TRACK_HALF_WIDTH)
     lo, hi = plants.CAR_INPUT_LO, plants.CAR_INPUT_HI
     ticks, N, H = args.car_ticks, 16384, 60
-    sess = lib.Session(ctx, model, N, H, lo, hi, seed=3)
+    sess = lib.Session(ctx, model, N, H, lo, hi, seed=CAR_SEED)
     x0 = data.car_start_state(track, vx=10.0)
-    uhs = data.to_f32_exact(data.ou_user_input(3, ticks, plants.CAR_DT, lo, hi))
+    uhs = data.to_f32_exact(data.ou_user_input(CAR_SEED, ticks, plants.CAR_DT, lo, hi))
     stream = torch.cuda.current_stream(dev)
 
     def closed_loop():
@@ -566,6 +574,14 @@ def run_car_loop(args):
     lanes, cands, block = sess.launch_shape()
     sess.close()
     model.free()
+    # the float64 oracle on the host cores, beside it: one tick of CAR_ORACLE_N
+    # candidates per worker, on the loop's first states
+    from oracle import fit as ofit
+    K32 = ofit.round_to_f32(ofit.fit_koopman("car", x, u, xn)[0])
+    workers = max(1, min(16, os.cpu_count() or 1))
+    o_rate, o_steps, o_t = oracle_rate(K32, states, uhs, CAR_ORACLE_N, H, 0.0, workers,
+                                       list(range(min(workers, ticks))), basis="car")
+    rate = (N + 1) * H / durs.mean()
     return {"workload": "race car closed loop: N=16384 (+u_h), H=60, 60 Hz, 600 ticks",
             "shape": {"lanes": lanes, "cands_per_thread": cands, "block": block},
             "ticks": ticks, "trials": trials, "fallback_ticks": int(fallback),
@@ -578,7 +594,14 @@ def run_car_loop(args):
             "e2e_rollout_steps_per_s": (N + 1) * H * len(lat) / lat.sum(),
             "launched_host_tick_ms": {"p50": float(np.percentile(lat_launched, 50) * 1e3),
                                       "p99": float(np.percentile(lat_launched, 99) * 1e3)},
-            "persistent_loop_identical": same}
+            "persistent_loop_identical": same,
+            "cpu_oracle": {"value": o_rate, "unit": "rollout steps/s", "cores": workers,
+                           "kind": "oracle", "per_core_value": oracle_rate.per_core,
+                           "sample": f"FP64 numpy oracle, {o_steps // ((CAR_ORACLE_N + 1) * H)} "
+                                     f"ticks of N={CAR_ORACLE_N} (H=60, track test against all "
+                                     f"segments), one per spawned single-threaded worker, "
+                                     f"{o_t:.1f} s"},
+            "gpu_over_oracle": rate / o_rate}
 
 
 def run_variants(args, bot_states):
