@@ -405,6 +405,14 @@ class Session:
             self.ctx.lib.mpmi_session_close(self.handle)
             self.handle = None
 
+    def __del__(self):
+        # a session holds its context, so the context outlives it; closing also
+        # stops a resident tick kernel instead of leaving it to its idle limit
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 def evaluate_candidates(s: Session, x_t, u_h, candidates=None, tick: int = 0, stream=None):
     """mpmi_evaluate_candidates: queue one tick from host x_t / u_h (float64)."""
