@@ -323,10 +323,17 @@ def test_memory_budget_admission(lib):
     small = lib.Context(0, mem_budget=2048)
     model = gpu_model(lib, small, env)
     s1 = lib.Session(small, model, 100, 10, env.lo, env.hi)
+    held = []  # open sessions keep their memory (a dropped session is closed)
     with pytest.raises(lib.MpmiError) as e:
         for _ in range(20):
-            lib.Session(small, model, 100, 10, env.lo, env.hi)
+            held.append(lib.Session(small, model, 100, 10, env.lo, env.hi))
     assert e.value.code == -2
+    used = small.memory_in_use()
+    for s in held:
+        s.close()
+    assert small.memory_in_use() < used
+    # room again once sessions are closed
+    lib.Session(small, model, 100, 10, env.lo, env.hi).close()
     s1.close()
 
 
