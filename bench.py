@@ -365,6 +365,9 @@ def run_gpu(args, rank, world):
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
     durs = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)]) * 1e-3
+    # the device's FP32 FMA rate measured by the library's own FMA loop (context
+    # for the roofline, whose peak is the nominal unit count x maximum clock)
+    ffma_tflops = lib.measure_fp32_peak(dev.index, 0.5)
     dev_time = float(durs.sum())
     res = results.cpu().numpy()
     executed = []
@@ -385,6 +388,7 @@ def run_gpu(args, rank, world):
                 persist_note=persist_note, persist_same=persist_same,
                 wall=wall, clocks=clk, lanes=lanes, cands=cands, block=block, n_slots=n_slots,
                 residual=residual, n_fallback=int(n_fallback), trials=trials, states=states,
+                ffma_tflops=ffma_tflops,
                 sm_count=props.multi_processor_count,
                 gpu_name=props.name)
 
@@ -795,7 +799,9 @@ def main():
         "gpu_launches": K,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                     "peak_basis": f"{out['sm_count']} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
+                     "peak_basis": f"{out['sm_count']} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                     "ffma_loop_tflops": out["ffma_tflops"],
+                     "frac_of_ffma_loop": achieved / out["ffma_tflops"]},
         "clocks": out["clocks"],
         "fallback_ticks": out["n_fallback"], "trials": out["trials"],
     }

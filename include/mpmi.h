@@ -363,6 +363,14 @@ int mpmi_debug_withhold_staging(mpmi_session* s, int32_t on);
 int mpmi_debug_track_query(const double* track_xy, int32_t n_track, double half_width,
                            const float* points, int64_t n_points, uint8_t* on_road);
 
+/* Measured FP32 FMA throughput of CUDA device `device` (not part of the method;
+ * the denominator of the tick kernels' ALU roofline): every resident warp runs
+ * eight independent FMA chains for about `seconds` (0 < seconds <= 10); the
+ * flops over the launch's CUDA-event time, in TFLOP/s, go to *tflops_out (host).
+ * The rate is the one at the clocks the device ran at.  Blocks until done.
+ * INVALID_ARG for a NULL output or seconds out of range, CUDA/OOM on failure. */
+int mpmi_measure_fp32_peak(int32_t device, double seconds, double* tflops_out);
+
 int mpmi_debug_trajectories(mpmi_session* s, const double* x_t_dev,
                             const double* u_h_dev, const float* candidates_dev,
                             uint64_t tick, mpmi_result* result_dev,

@@ -25,7 +25,7 @@ LIB = os.path.join(LIBDIR, "libmpmi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", f"-I{INCLUDE}",
           f"-I{CSRC}"]
-UNITS = ["mpmi_api.cu", "tick_noise.cu", "factored.cu", "tensor.cu", "persistent.cu", "noalloc.cu", "screener.cu", "server.cu", "fit.cpp", "track.cpp"]
+UNITS = ["mpmi_api.cu", "tick_noise.cu", "factored.cu", "tensor.cu", "persistent.cu", "noalloc.cu", "screener.cu", "server.cu", "measure.cu", "fit.cpp", "track.cpp"]
 
 
 def nvcc() -> str:

@@ -84,6 +84,7 @@ _SIGNATURES = {
     "mpmi_session_set_noise": (c_i32, [c_vp, P_dbl, c_i32]),
     "mpmi_session_set_rollout": (c_i32, [c_vp, c_i32]),
     "mpmi_session_set_persistent": (c_i32, [c_vp, c_i32, c_dbl]),
+    "mpmi_measure_fp32_peak": (c_i32, [c_i32, c_dbl, P_dbl]),
     "mpmi_debug_withhold_staging": (c_i32, [c_vp, c_i32]),
     "mpmi_fit_operator_sparse": (c_i32, [ctypes.POINTER(BasisDesc), c_vp, c_vp, c_vp, c_i64,
                                           c_dbl, c_dbl, c_i32, c_vp, c_vp, P_dbl]),
@@ -412,6 +413,13 @@ class Session:
             self.close()
         except Exception:
             pass
+
+
+def measure_fp32_peak(device: int = 0, seconds: float = 0.5) -> float:
+    """mpmi_measure_fp32_peak: the device's FP32 FMA throughput in TFLOP/s."""
+    out = c_dbl()
+    _check(load().mpmi_measure_fp32_peak(device, float(seconds), ctypes.byref(out)))
+    return out.value
 
 
 def evaluate_candidates(s: Session, x_t, u_h, candidates=None, tick: int = 0, stream=None):
