@@ -61,8 +61,10 @@ FLUSH_BYTES = 256 << 20
 SM_FP32_LANES = 128
 
 # DRAM bytes per tick-kernel launch from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum); valid only for the kernel source it was taken on.
-TRAFFIC = {"tick_kernel_sha1": "f2ae689b6154f2e45b47bc70620163931e2556dc", "bytes_per_launch": 25088}
+# dram__bytes_write.sum); valid only for the kernel source and launch shape
+# (lanes, candidates per thread, block) it was taken on.
+TRAFFIC = {"tick_kernel_sha1": "f2ae689b6154f2e45b47bc70620163931e2556dc", "bytes_per_launch": 25088,
+           "shape": (1, 1, 128)}
 
 
 def kernel_sha1() -> str:
@@ -268,13 +270,18 @@ def run_gpu(args, rank, world):
     model, residual = lib.fit_model(ctx, "bot", x, u, xn)
     lib.set_safety_set(model, data.BOT_SAFE_LO, data.BOT_SAFE_HI)
     seed = LOOP_SEED + 1000 * rank
+    ticks = max(TICKS, args.warmup + args.steps)
+    uhs = data.ou_user_input(seed, ticks, plants.BOT_DT, plants.BOT_INPUT_LO,
+                             plants.BOT_INPUT_HI)
+    # the library's autotuner picks the launch shape for this configuration (any
+    # shape gives bit-identical results); the session below takes its choice
+    tuned = lib.tune_launch_shape(ctx, model, N_SAMPLES, HORIZON, plants.BOT_INPUT_LO,
+                                  plants.BOT_INPUT_HI, X0, uhs[0], reps=30, seed=seed,
+                                  stream_id=rank)
     sess = lib.Session(ctx, model, N_SAMPLES, HORIZON, plants.BOT_INPUT_LO,
                        plants.BOT_INPUT_HI, seed=seed, stream_id=rank)
     lanes, cands, block = sess.launch_shape()
     n_slots = sess.n_slots
-    ticks = max(TICKS, args.warmup + args.steps)
-    uhs = data.ou_user_input(seed, ticks, plants.BOT_DT, plants.BOT_INPUT_LO,
-                             plants.BOT_INPUT_HI)
     stream = torch.cuda.current_stream(dev)
     gpu_id = None
     try:
@@ -388,7 +395,7 @@ def run_gpu(args, rank, world):
                 persist_note=persist_note, persist_same=persist_same,
                 wall=wall, clocks=clk, lanes=lanes, cands=cands, block=block, n_slots=n_slots,
                 residual=residual, n_fallback=int(n_fallback), trials=trials, states=states,
-                ffma_tflops=ffma_tflops,
+                ffma_tflops=ffma_tflops, tuned=tuned,
                 sm_count=props.multi_processor_count,
                 gpu_name=props.name)
 
@@ -495,11 +502,23 @@ def run_serving(args, bot_states):
     meta = [(bs, plants.BOT_INPUT_LO, plants.BOT_INPUT_HI, 0.01),
             (cs, plants.CAR_INPUT_LO, plants.CAR_INPUT_HI, 1.0 / 60.0)]
     sessions = serve.make_sessions(meta, n_sess, 4, [bot_states, car_pool])
+    # the servers' autotuner: every compiled serve shape and block size on a small
+    # batch like the mix's typical one (three sessions of the model)
+    tuned = {}
+    for m, (srv, lo, hi, _) in enumerate(meta):
+        mine = [ss for ss in sessions if ss.server == m][:3]
+        reqs = [(ss.n, ss.horizon, lo, hi, 90 + i, 900 + i) for i, ss in enumerate(mine)]
+        xs = np.stack([ss.states[0] for ss in mine])
+        us = np.stack([ss.user[0] for ss in mine])
+        r = srv.tune(reqs, xs, us, reps=5)
+        tuned["bot" if m == 0 else "car"] = {k: r[k] for k in ("lanes", "cands", "block",
+                                                                 "n_tried", "us", "default_us")}
     streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
     stats = serve.run([bs, cs], sessions, duration=args.serve_seconds, streams=streams)
     stats.update(sessions=n_sess, mix="half balance bot (100 Hz), half race car (60 Hz)",
                  n_range="log-uniform 1024..65536", h_range="uniform 20..100",
-                 launch="one persistent graph-replayed launch per batch and model")
+                 launch="one persistent graph-replayed launch per batch and model",
+                 autotuned=tuned)
     bs.free()
     cs.free()
     bm.free()
@@ -525,9 +544,10 @@ def run_car_loop(args):
                        data.CAR_TRACK_HALF_WIDTH)
     lo, hi = plants.CAR_INPUT_LO, plants.CAR_INPUT_HI
     ticks, N, H = args.car_ticks, 16384, 60
-    sess = lib.Session(ctx, model, N, H, lo, hi, seed=CAR_SEED)
     x0 = data.car_start_state(track, vx=10.0)
     uhs = data.to_f32_exact(data.ou_user_input(CAR_SEED, ticks, plants.CAR_DT, lo, hi))
+    tuned = lib.tune_launch_shape(ctx, model, N, H, lo, hi, x0, uhs[0], reps=20, seed=CAR_SEED)
+    sess = lib.Session(ctx, model, N, H, lo, hi, seed=CAR_SEED)
     stream = torch.cuda.current_stream(dev)
 
     def closed_loop():
@@ -587,7 +607,9 @@ def run_car_loop(args):
                                        list(range(min(workers, ticks))), basis="car")
     rate = (N + 1) * H / durs.mean()
     return {"workload": "race car closed loop: N=16384 (+u_h), H=60, 60 Hz, 600 ticks",
-            "shape": {"lanes": lanes, "cands_per_thread": cands, "block": block},
+            "shape": {"lanes": lanes, "cands_per_thread": cands, "block": block,
+                      "autotuned": {"n_tried": tuned["n_tried"], "winner_us": tuned["us"],
+                                    "default_shape_us": tuned["default_us"]}},
             "ticks": ticks, "trials": trials, "fallback_ticks": int(fallback),
             "device_mean_us": durs.mean() * 1e6, "device_p99_us": np.percentile(durs, 99) * 1e6,
             "rollout_steps_per_s": (N + 1) * H / durs.mean(),
@@ -769,7 +791,9 @@ def main():
     flops_per_tick = (float(out["executed"].mean()) * 2 * LIFTED_N ** 2
                       + out["n_slots"] * (2 * LIFTED_N * 1 + 2))
     achieved = flops_per_tick / mean_dur / 1e12
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["tick_kernel_sha1"] == kernel_sha1() else None
+    traffic = (TRAFFIC["bytes_per_launch"]
+               if TRAFFIC["tick_kernel_sha1"] == kernel_sha1()
+               and TRAFFIC["shape"] == (out["lanes"], out["cands"], out["block"]) else None)
 
     line = {
         "metric": "rollout steps/s (plain path) and p99 control-tick latency at N=16384",
@@ -777,6 +801,10 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_max / K * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(cfg, lanes=out["lanes"], cands_per_thread=out["cands"], block=out["block"],
+                       autotuned={"n_tried": out["tuned"]["n_tried"],
+                                  "winner_us": out["tuned"]["us"],
+                                  "default_shape_us": out["tuned"]["default_us"],
+                                  "what": "warm device ticks, median of 30 per shape"},
                        parallelism=f"replicas{world}" if world > 1 else "single"),
         "executed_steps_per_s": world * float(out["executed"].sum()) / t_max,
         "latency_ms": {"p50": float(np.percentile(out["lat"], 50) * 1e3),

@@ -222,6 +222,33 @@ void mpmi_session_close(mpmi_session* s);
  * launches with (any output pointer may be NULL). */
 int mpmi_session_launch_shape(const mpmi_session* s, int32_t* lanes, int32_t* cands,
                               int32_t* block);
+
+/* ---- launch-shape autotuner --------------------------------------------- */
+/* Outcome of one tuning run: the fastest shape and its median tick time. */
+typedef struct {
+  int32_t lanes;     /* lanes per candidate                                    */
+  int32_t cands;     /* candidates per thread                                  */
+  int32_t block;     /* threads per block                                      */
+  int32_t n_tried;   /* shapes measured                                        */
+  double us;         /* median device time per tick of the winner (microseconds) */
+  double default_us; /* the same for the library's default shape               */
+} mpmi_tune_result;
+
+/* Times every compiled launch shape (lanes per candidate x candidates per thread)
+ * at 64, 128 and 256 threads per block for one tick configuration -- the model,
+ * cfg's N, H, sampler and user slot (cfg's lanes, cands_per_thread and block are
+ * ignored) -- from the host state x_t (nx doubles) and input u_h (nu doubles):
+ * two warm-up ticks, then `reps` device-resident ticks (1..1000) each timed with
+ * CUDA events, median per shape.  The winner is returned in *out and recorded in
+ * the context: a later mpmi_session_open with lanes, cands_per_thread and block
+ * all 0 and the same (basis, N + include_user, H) uses it instead of the built-in
+ * rule.  Every shape computes bit-identical results, so tuning changes speed
+ * only.  Opens and closes temporary sessions (device memory within the budget);
+ * blocks until done.  INVALID_ARG / NONFINITE as for session_open and
+ * evaluate_candidates, OOM beyond the budget. */
+int mpmi_tune_launch_shape(mpmi_ctx* ctx, const mpmi_model* model,
+                           const mpmi_session_config* cfg, const double* x_t,
+                           const double* u_h, int32_t reps, mpmi_tune_result* out);
 /* Alg. 2's per-step Gaussian noise z_i ("to account for inaccuracies in the
  * dynamics model"; the paper gives no variance).  After every prediction step t
  * the lifted state's first `count` coordinates (the state read-out, x_0 ..
@@ -412,6 +439,19 @@ int mpmi_server_poll(mpmi_server* s, int32_t* done);
 /* Waits for the batch in flight and copies its results (host, in submission
  * order) with the sessions they belong to; *n_out = number of results. */
 int mpmi_server_collect(mpmi_server* s, mpmi_result* out, int32_t* slots_out, int32_t* n_out);
+/* Autotunes the server's launch shape for a request mix: for every compiled
+ * shape of the model's basis (lanes per candidate x candidates per thread) at 64,
+ * 128 and 256 threads per block, serves `reps` batches (1..100, after one
+ * warm-up batch) of the n requests described by cfgs[n] (session configurations,
+ * admitted on temporary slots and released again), x_t (n x nx) and u_h (n x nu)
+ * through the server's own submit / launch / collect path, timing each graph
+ * launch with CUDA events; the shape with the lowest median batch time is kept
+ * for all later batches and returned in *out (default_us: the server's initial
+ * shape).  Results are bit-identical across shapes.  NOT_READY while a batch is
+ * staged or in flight, OOM without n free slots. */
+int mpmi_server_tune(mpmi_server* s, int32_t n, const mpmi_session_config* cfgs,
+                     const double* x_t, const double* u_h, int32_t reps,
+                     mpmi_tune_result* out);
 
 /* ---- learned candidate screener (not in the paper) ----------------------- */
 /* A small network (12 -> 128 -> 128 -> 1, tanh-form GELU, sigmoid output) that

@@ -116,6 +116,11 @@ struct mpmi_ctx {
   uint64_t budget = 0;
   uint64_t used = 0;
   int sm_count = 0;
+  // launch shapes chosen by the autotuner, keyed by (basis, slots, horizon)
+  struct TunedShape {
+    int kind, n_slots, horizon, lanes, cands, block;
+  };
+  std::vector<TunedShape> tuned;
 };
 
 struct mpmi_model {

@@ -9,6 +9,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -655,6 +656,16 @@ int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model, const mpmi_session
     if (gg <= 0) return fail(MPMI_E_INVALID_ARG, "session_open: grid sampling needs N = G^M");
   }
   int lanes = cfg->lanes, cands = cfg->cands_per_thread, block = cfg->block;
+  if (lanes == 0 && cands == 0 && block == 0) {
+    // a shape the autotuner measured for this configuration, if any
+    for (const auto& t : ctx->tuned)
+      if (t.kind == model->kind && t.n_slots == (int)slots && t.horizon == cfg->horizon) {
+        lanes = t.lanes;
+        cands = t.cands;
+        block = t.block;
+        break;
+      }
+  }
   if (lanes == 0 && cands > 1) lanes = 1;  // several candidates per thread need one lane
   if (lanes == 0) {
     int dl, dc, db;
@@ -1050,6 +1061,122 @@ int mpmi_debug_trajectories(mpmi_session* s, const double* x_t_dev, const double
   if (!traj_dev) return fail(MPMI_E_INVALID_ARG, "debug_trajectories: traj_dev is NULL");
   return evaluate_device(s, x_t_dev, u_h_dev, candidates_dev, tick, result_dev, ttv_dev,
                          cost_dev, traj_dev, stream);
+}
+
+int mpmi_tune_launch_shape(mpmi_ctx* ctx, const mpmi_model* model,
+                           const mpmi_session_config* cfg, const double* x_t,
+                           const double* u_h, int32_t reps, mpmi_tune_result* out) {
+  if (!ctx || !model || !cfg || !x_t || !u_h || !out)
+    return fail(MPMI_E_INVALID_ARG, "tune_launch_shape: NULL argument");
+  if (reps < 1 || reps > 1000)
+    return fail(MPMI_E_INVALID_ARG, "tune_launch_shape: reps must be in 1..1000");
+  if (cfg->sampler == MPMI_SAMPLER_EXTERNAL)
+    return fail(MPMI_E_UNSUPPORTED, "tune_launch_shape: tune with a built-in sampler");
+  int rc;
+  if ((rc = check_finite(x_t, model->nx, "x_t")) != MPMI_OK) return rc;
+  if ((rc = check_finite(u_h, model->nu, "u_h")) != MPMI_OK) return rc;
+  DeviceGuard guard(ctx->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
+  const long long slots = (long long)cfg->n_samples + cfg->include_user;
+  int dl = 0, dc = 0, db = 0;
+  default_shape(model->kind, (int)slots, ctx->sm_count, &dl, &dc, &db);
+  double* in_dev = nullptr;
+  mpmi_result* res_dev = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(in_dev);
+    cudaFree(res_dev);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  double in_host[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  memcpy(in_host, x_t, sizeof(double) * model->nx);
+  memcpy(in_host + 8, u_h, sizeof(double) * model->nu);
+  if (cudaMalloc(&in_dev, sizeof(in_host)) != cudaSuccess ||
+      cudaMalloc(&res_dev, sizeof(mpmi_result)) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+      cudaMemcpy(in_dev, in_host, sizeof(in_host), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cleanup();
+    return fail(MPMI_E_OOM, "tune_launch_shape: device buffers");
+  }
+  mpmi_tune_result best;
+  memset(&best, 0, sizeof(best));
+  best.us = INFINITY;
+  best.default_us = NAN;
+  std::vector<float> t(reps);
+  static const int kLanes[] = {1, 2, 4, 8, 16, 32};
+  static const int kBlocks[] = {64, 128, 256};
+  for (int lanes : kLanes) {
+    for (int cands = 1; cands <= 2; ++cands) {
+      if (!pick_tick(model->kind, lanes, cands, false, false).fn) continue;
+      for (int block : kBlocks) {
+        mpmi_session_config c = *cfg;
+        c.lanes = lanes;
+        c.cands_per_thread = cands;
+        c.block = block;
+        mpmi_session* s = nullptr;
+        rc = mpmi_session_open(ctx, model, &c, &s);
+        if (rc == MPMI_E_UNSUPPORTED) continue;  // not resident with this block
+        if (rc != MPMI_OK) {
+          cleanup();
+          return rc;
+        }
+        for (int r = -2; r < reps && rc == MPMI_OK; ++r) {
+          TickArgs a = make_tick_args(s, (uint64_t)(r + 2));
+          a.x_t = in_dev;
+          a.u_h = in_dev + 8;
+          a.result = res_dev;
+          if (r >= 0) cudaEventRecord(e0, 0);
+          rc = launch_tick_args(s, a, false, 0, 0);
+          if (rc != MPMI_OK) break;
+          if (r >= 0) {
+            cudaEventRecord(e1, 0);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+              rc = fail(MPMI_E_CUDA, "tune_launch_shape: timing a tick");
+              break;
+            }
+            t[r] = ms;
+          }
+        }
+        mpmi_session_close(s);
+        if (rc == MPMI_E_UNSUPPORTED) {  // this block size cannot be resident: skip it
+          rc = MPMI_OK;
+          continue;
+        }
+        if (rc != MPMI_OK) {
+          cleanup();
+          return rc;
+        }
+        std::vector<float> sorted(t);
+        std::sort(sorted.begin(), sorted.end());
+        const double us = 1e3 * sorted[reps / 2];
+        best.n_tried += 1;
+        if (lanes == dl && cands == dc && block == db) best.default_us = us;
+        if (us < best.us) {
+          best.us = us;
+          best.lanes = lanes;
+          best.cands = cands;
+          best.block = block;
+        }
+      }
+    }
+  }
+  cleanup();
+  if (best.n_tried == 0) return fail(MPMI_E_UNSUPPORTED, "tune_launch_shape: no shape runs");
+  bool replaced = false;
+  for (auto& e : ctx->tuned)
+    if (e.kind == model->kind && e.n_slots == (int)slots && e.horizon == cfg->horizon) {
+      e.lanes = best.lanes;
+      e.cands = best.cands;
+      e.block = best.block;
+      replaced = true;
+    }
+  if (!replaced)
+    ctx->tuned.push_back({model->kind, (int)slots, cfg->horizon, best.lanes, best.cands, best.block});
+  *out = best;
+  return MPMI_OK;
 }
 
 int mpmi_sample_candidates(mpmi_session* s, const double* u_h_dev, const float* candidates_dev,

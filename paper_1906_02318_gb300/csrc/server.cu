@@ -17,6 +17,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -60,7 +61,7 @@ struct ServeArgs {
 };
 
 template <int KIND, int L, int C, bool KSMEM>
-__global__ void __launch_bounds__(kMaxBlock) serve_kernel(const __grid_constant__ ServeArgs sa) {
+__global__ void __launch_bounds__(kMaxBlock, 1) serve_kernel(const __grid_constant__ ServeArgs sa) {
   using B = BasisTraits<KIND>;
   constexpr int N = B::N, NX = B::NX, NU = B::NU;
   constexpr int R = N / L, GPW = 32 / L;
@@ -162,6 +163,7 @@ struct ServeKernel {
   void (*launch)(const ServeArgs&, int, int, size_t, cudaStream_t) = nullptr;
   size_t k_smem = 0;
   int per_warp = 32;
+  int lanes = 1, cands = 1;
 };
 
 template <int KIND, int L, int C, bool KSMEM>
@@ -176,20 +178,32 @@ static ServeKernel make_serve() {
   k.launch = &launch_serve<KIND, L, C, KSMEM>;
   k.k_smem = KSMEM ? KSmem<BasisTraits<KIND>::N>::BYTES : 0;
   k.per_warp = 32 / L * C;
+  k.lanes = L;
+  k.cands = C;
   return k;
 }
 
-// One candidate per thread: the balance bot keeps K in registers, the race car in
-// shared memory (the shapes the single-session tick uses by default).
-static ServeKernel pick_serve(int kind) {
+// The server's shapes per basis; the first is the initial one (one candidate per
+// thread: the balance bot keeps K in registers, the race car in shared memory, as
+// the single-session tick does by default), the others are for the autotuner.
+static std::vector<ServeKernel> serve_shapes(int kind) {
   switch (kind) {
-    case kBot: return make_serve<kBot, 1, 1, false>();
-    case kCar: return make_serve<kCar, 1, 1, true>();
-    case kLin11: return make_serve<kLin11, 1, 1, false>();
-    case kLin22: return make_serve<kLin22, 1, 1, false>();
-    case kLin41: return make_serve<kLin41, 1, 1, false>();
+    case kBot:
+      return {make_serve<kBot, 1, 1, false>(), make_serve<kBot, 1, 2, false>(),
+              make_serve<kBot, 2, 1, false>(), make_serve<kBot, 4, 1, false>()};
+    case kCar:
+      return {make_serve<kCar, 1, 1, true>(), make_serve<kCar, 1, 2, true>(),
+              make_serve<kCar, 8, 1, false>()};
+    case kLin11: return {make_serve<kLin11, 1, 1, false>()};
+    case kLin22: return {make_serve<kLin22, 1, 1, false>()};
+    case kLin41: return {make_serve<kLin41, 1, 1, false>()};
   }
-  return ServeKernel{};
+  return {};
+}
+
+static ServeKernel pick_serve(int kind) {
+  const std::vector<ServeKernel> v = serve_shapes(kind);
+  return v.empty() ? ServeKernel{} : v[0];
 }
 
 }  // namespace mpmi
@@ -497,6 +511,141 @@ int mpmi_server_collect(mpmi_server* s, mpmi_result* out, int32_t* slots_out, in
   s->table_host[b]->n_requests = 0;
   s->table_host[b]->total_tiles = 0;
   s->in_flight = -1;
+  return MPMI_OK;
+}
+
+}  // extern "C"
+
+namespace mpmi {
+
+// Switches the server to launch shape k with `block` threads per block and
+// re-captures both batch graphs.  UNSUPPORTED if the shape cannot be resident.
+static int server_set_shape(mpmi_server* s, const ServeKernel& k, int block) {
+  const size_t smem =
+      k.k_smem + (s->model->dev_safety.has_track ? (size_t)s->model->dev_safety.track.blob_bytes : 0);
+  if (smem > 0 &&
+      cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return fail(MPMI_E_UNSUPPORTED, "server: shape cannot take its shared memory");
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.fn, block, smem) != cudaSuccess ||
+      nb < 1) {
+    cudaGetLastError();
+    return fail(MPMI_E_UNSUPPORTED, "server: shape cannot be resident");
+  }
+  s->kern = k;
+  s->block = block;
+  s->smem = smem;
+  s->grid = nb * s->ctx->sm_count;
+  for (int b = 0; b < 2; ++b) {
+    if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
+    s->graph[b] = nullptr;
+    const int rc = build_graph(s, b);
+    if (rc != MPMI_OK) return rc;
+  }
+  return MPMI_OK;
+}
+
+}  // namespace mpmi
+
+extern "C" {
+
+int mpmi_server_tune(mpmi_server* s, int32_t n, const mpmi_session_config* cfgs,
+                     const double* x_t, const double* u_h, int32_t reps,
+                     mpmi_tune_result* out) {
+  if (!s || !cfgs || !x_t || !u_h || !out || n < 1)
+    return fail(MPMI_E_INVALID_ARG, "server_tune: NULL argument or n < 1");
+  if (reps < 1 || reps > 100) return fail(MPMI_E_INVALID_ARG, "server_tune: reps must be in 1..100");
+  if (s->in_flight >= 0 || s->table_host[s->stage]->n_requests > 0)
+    return fail(MPMI_E_NOT_READY, "server_tune: a batch is staged or in flight");
+  std::vector<int32_t> slots;
+  auto release_all = [&]() {
+    for (int32_t sl : slots) mpmi_server_release(s, sl);
+  };
+  for (int i = 0; i < n; ++i) {
+    int32_t sl = -1;
+    const int rc = mpmi_server_admit(s, &cfgs[i], &sl);
+    if (rc != MPMI_OK) {
+      release_all();
+      return rc;
+    }
+    slots.push_back(sl);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    release_all();
+    return fail(MPMI_E_CUDA, "server_tune: events");
+  }
+  std::vector<mpmi_result> res(n);
+  std::vector<int32_t> got(n);
+  std::vector<uint64_t> ticks(n);
+  std::vector<float> t(reps);
+  const ServeKernel initial = s->kern;
+  const int initial_block = s->block;
+  ServeKernel best_k = initial;
+  int best_block = initial_block;
+  mpmi_tune_result best;
+  memset(&best, 0, sizeof(best));
+  best.us = INFINITY;
+  best.default_us = NAN;
+  int rc = MPMI_OK;
+  static const int kBlocks[] = {64, 128, 256};
+  for (const ServeKernel& k : serve_shapes(s->model->kind)) {
+    for (int block : kBlocks) {
+      rc = server_set_shape(s, k, block);
+      if (rc == MPMI_E_UNSUPPORTED) {
+        rc = MPMI_OK;
+        continue;
+      }
+      if (rc != MPMI_OK) break;
+      for (int r = -1; r < reps && rc == MPMI_OK; ++r) {
+        for (int i = 0; i < n; ++i) ticks[i] = (uint64_t)(r + 1) * (uint64_t)n + (uint64_t)i;
+        rc = mpmi_server_submit(s, n, slots.data(), x_t, u_h, ticks.data());
+        if (rc != MPMI_OK) break;
+        int32_t launched = 0, n_out = 0;
+        cudaEventRecord(e0, 0);
+        rc = mpmi_server_launch(s, nullptr, &launched);
+        cudaEventRecord(e1, 0);
+        if (rc != MPMI_OK) break;
+        rc = mpmi_server_collect(s, res.data(), got.data(), &n_out);
+        if (rc != MPMI_OK) break;
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          rc = fail(MPMI_E_CUDA, "server_tune: timing a batch");
+          break;
+        }
+        if (r >= 0) t[r] = ms;
+      }
+      if (rc != MPMI_OK) break;
+      std::vector<float> sorted(t);
+      std::sort(sorted.begin(), sorted.end());
+      const double us = 1e3 * sorted[reps / 2];
+      best.n_tried += 1;
+      if (k.fn == initial.fn && block == initial_block) best.default_us = us;
+      if (us < best.us) {
+        best.us = us;
+        best_k = k;
+        best_block = block;
+      }
+    }
+    if (rc != MPMI_OK) break;
+  }
+  // keep the winner (or go back to the initial shape after a failure)
+  const int rc2 = rc == MPMI_OK ? server_set_shape(s, best_k, best_block)
+                                : server_set_shape(s, initial, initial_block);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  release_all();
+  if (rc != MPMI_OK) return rc;
+  if (rc2 != MPMI_OK) return rc2;
+  best.lanes = best_k.lanes;
+  best.cands = best_k.cands;
+  best.block = best_block;
+  *out = best;
   return MPMI_OK;
 }
 

@@ -45,6 +45,11 @@ class SafetySpecC(ctypes.Structure):
                 ("track_half_width", c_dbl)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("lanes", c_i32), ("cands", c_i32), ("block", c_i32), ("n_tried", c_i32),
+                ("us", c_dbl), ("default_us", c_dbl)]
+
+
 class SessionConfig(ctypes.Structure):
     _fields_ = [("n_samples", c_i32), ("horizon", c_i32), ("include_user", c_i32),
                 ("sampler", c_i32), ("input_lo", c_dbl * MAX_NU), ("input_hi", c_dbl * MAX_NU),
@@ -85,6 +90,10 @@ _SIGNATURES = {
     "mpmi_session_set_rollout": (c_i32, [c_vp, c_i32]),
     "mpmi_session_set_persistent": (c_i32, [c_vp, c_i32, c_dbl]),
     "mpmi_measure_fp32_peak": (c_i32, [c_i32, c_dbl, P_dbl]),
+    "mpmi_tune_launch_shape": (c_i32, [c_vp, c_vp, ctypes.POINTER(SessionConfig), c_vp, c_vp,
+                                       c_i32, ctypes.POINTER(TuneResult)]),
+    "mpmi_server_tune": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, c_i32,
+                                 ctypes.POINTER(TuneResult)]),
     "mpmi_debug_withhold_staging": (c_i32, [c_vp, c_i32]),
     "mpmi_fit_operator_sparse": (c_i32, [ctypes.POINTER(BasisDesc), c_vp, c_vp, c_vp, c_i64,
                                           c_dbl, c_dbl, c_i32, c_vp, c_vp, P_dbl]),
@@ -337,6 +346,39 @@ def set_safety_set(model: Model, lo, hi, inflation: float = 0.0, track=None,
     del keep
 
 
+def _session_config(n_samples, horizon, input_lo, input_hi, include_user=True,
+                    sampler="uniform", seed=0, stream_id=0, lanes=0, block=0, cands=0):
+    cfg = SessionConfig()
+    cfg.n_samples, cfg.horizon = n_samples, horizon
+    cfg.include_user = int(include_user)
+    cfg.sampler = SAMPLER[sampler]
+    lo, hi = _f64(input_lo), _f64(input_hi)
+    for j in range(MAX_NU):
+        cfg.input_lo[j] = lo[j] if j < lo.size else 0.0
+        cfg.input_hi[j] = hi[j] if j < hi.size else 1.0
+    cfg.seed, cfg.stream_id, cfg.lanes, cfg.block = seed, stream_id, lanes, block
+    cfg.cands_per_thread = cands
+    return cfg
+
+
+def tune_launch_shape(ctx: Context, model: Model, n_samples: int, horizon: int, input_lo,
+                      input_hi, x_t, u_h, reps: int = 20, include_user: bool = True,
+                      sampler: str = "uniform", seed: int = 0, stream_id: int = 0) -> dict:
+    """mpmi_tune_launch_shape: time every compiled launch shape for this tick
+    configuration; the winner is used by later sessions opened with the library's
+    choice of shape (results are bit-identical across shapes)."""
+    cfg = _session_config(n_samples, horizon, input_lo, input_hi, include_user, sampler, seed,
+                          stream_id)
+    x = _f64(x_t, model.nx)
+    u = _f64(u_h, model.nu)
+    r = TuneResult()
+    _check(ctx.lib.mpmi_tune_launch_shape(ctx.handle, model.handle, ctypes.byref(cfg),
+                                          x.ctypes.data, u.ctypes.data, int(reps),
+                                          ctypes.byref(r)))
+    return dict(lanes=r.lanes, cands=r.cands, block=r.block, n_tried=r.n_tried, us=r.us,
+                default_us=r.default_us)
+
+
 class Session:
     """mpmi_session_open: one controller with fixed N and H."""
 
@@ -344,16 +386,8 @@ class Session:
                  input_lo, input_hi, include_user: bool = True, sampler: str = "uniform",
                  seed: int = 0, stream_id: int = 0, lanes: int = 0, block: int = 0,
                  cands: int = 0):
-        cfg = SessionConfig()
-        cfg.n_samples, cfg.horizon = n_samples, horizon
-        cfg.include_user = int(include_user)
-        cfg.sampler = SAMPLER[sampler]
-        lo, hi = _f64(input_lo), _f64(input_hi)
-        for j in range(MAX_NU):
-            cfg.input_lo[j] = lo[j] if j < lo.size else 0.0
-            cfg.input_hi[j] = hi[j] if j < hi.size else 1.0
-        cfg.seed, cfg.stream_id, cfg.lanes, cfg.block = seed, stream_id, lanes, block
-        cfg.cands_per_thread = cands
+        cfg = _session_config(n_samples, horizon, input_lo, input_hi, include_user, sampler,
+                              seed, stream_id, lanes, block, cands)
         h = c_vp()
         _check(ctx.lib.mpmi_session_open(ctx.handle, model.handle, ctypes.byref(cfg),
                                          ctypes.byref(h)))
@@ -641,6 +675,22 @@ class Server:
         _check(self.ctx.lib.mpmi_server_collect(self.handle, self._res, self._slots.ctypes.data,
                                                 ctypes.byref(n)))
         return [(int(self._slots[i]), result_dict(self._res[i], self.nu)) for i in range(n.value)]
+
+    def tune(self, requests, x_t, u_h, reps: int = 10) -> dict:
+        """mpmi_server_tune: pick the fastest launch shape for a request mix.
+        requests: [(n_samples, horizon, input_lo, input_hi, seed, stream_id), ...];
+        x_t (n x nx), u_h (n x nu)."""
+        n = len(requests)
+        cfgs = (SessionConfig * n)()
+        for i, (ns, hz, lo, hi, seed, sid) in enumerate(requests):
+            cfgs[i] = _session_config(ns, hz, lo, hi, True, "uniform", seed, sid)
+        x = _f64(x_t).reshape(n, self.nx)
+        u = _f64(u_h).reshape(n, self.nu)
+        r = TuneResult()
+        _check(self.ctx.lib.mpmi_server_tune(self.handle, n, cfgs, x.ctypes.data, u.ctypes.data,
+                                             int(reps), ctypes.byref(r)))
+        return dict(lanes=r.lanes, cands=r.cands, block=r.block, n_tried=r.n_tried, us=r.us,
+                    default_us=r.default_us)
 
     def free(self):
         if self.handle:

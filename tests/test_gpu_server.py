@@ -154,3 +154,44 @@ def test_short_serving_run(lib, ctx):
         assert r["index"] == a["index"] and r["n_safe"] == a["n_safe"]
     bs.free()
     cs.free()
+
+
+@pytest.mark.parametrize("which,n_shapes", [("bot", 4), ("car", 3)])
+def test_tuned_server_results_equal_alone(lib, ctx, which, n_shapes):
+    """The server's autotuner tries every compiled serve shape at three block
+    sizes on a request mix, keeps the fastest, and served results stay
+    bit-identical to the same ticks alone."""
+    env = bot_env() if which == "bot" else car_env()
+    model = gpu_model(lib, ctx, env)
+    srv = lib.Server(ctx, model, max_sessions=16)
+    specs = [(1023, 20), (4096, 60), (16384, 50), (2000, 100)]
+    xs = _states(env, which, len(specs), 5)
+    us = data.to_f32_exact(np.random.default_rng(3).uniform(env.lo, env.hi,
+                                                            (len(specs), len(env.lo))))
+    reqs = [(n, H, env.lo, env.hi, 200 + i, i) for i, (n, H) in enumerate(specs)]
+    r = srv.tune(reqs, xs, us, reps=3)
+    assert 1 <= r["n_tried"] <= 3 * n_shapes
+    assert r["us"] <= r["default_us"]
+    assert r["block"] in (64, 128, 256)
+    slots = [srv.admit(n, H, env.lo, env.hi, seed=200 + i, stream_id=i)
+             for i, (n, H) in enumerate(specs)]
+    srv.submit(slots, xs, us, [7 + i for i in range(len(specs))])
+    # tuning needs an empty stage
+    with pytest.raises(lib.MpmiError) as e:
+        srv.tune(reqs, xs, us, reps=3)
+    assert e.value.code == -5
+    assert srv.launch() == len(specs)
+    got = dict(srv.collect())
+    for i, (n, H) in enumerate(specs):
+        want = _alone(lib, ctx, model, env, n, H, 200 + i, i, xs[i], us[i], 7 + i)
+        res = got[slots[i]]
+        for k in ("index", "status", "n_safe", "ttv", "executed_steps", "tick"):
+            assert res[k] == want[k], (i, k)
+        assert np.array_equal(res["u_r"], want["u_r"])
+    with pytest.raises(lib.MpmiError) as e:
+        srv.tune(reqs, xs, us, reps=0)
+    assert e.value.code == -1
+    for sl in slots:
+        srv.release(sl)
+    srv.free()
+    model.free()
