@@ -63,8 +63,8 @@ SM_FP32_LANES = 128
 # DRAM bytes per tick-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum); valid only for the kernel source and launch shape
 # (lanes, candidates per thread, block) it was taken on.
-TRAFFIC = {"tick_kernel_sha1": "f2ae689b6154f2e45b47bc70620163931e2556dc", "bytes_per_launch": 25088,
-           "shape": (1, 1, 128)}
+TRAFFIC = {"tick_kernel_sha1": "f67a2ce7b56e058f52428fdcb7347ba31bf0b15e",
+           "bytes_per_launch": {(1, 1, 128): 25344, (1, 1, 64): 25344}}
 
 
 def kernel_sha1() -> str:
@@ -791,9 +791,8 @@ def main():
     flops_per_tick = (float(out["executed"].mean()) * 2 * LIFTED_N ** 2
                       + out["n_slots"] * (2 * LIFTED_N * 1 + 2))
     achieved = flops_per_tick / mean_dur / 1e12
-    traffic = (TRAFFIC["bytes_per_launch"]
-               if TRAFFIC["tick_kernel_sha1"] == kernel_sha1()
-               and TRAFFIC["shape"] == (out["lanes"], out["cands"], out["block"]) else None)
+    traffic = (TRAFFIC["bytes_per_launch"].get((out["lanes"], out["cands"], out["block"]))
+               if TRAFFIC["tick_kernel_sha1"] == kernel_sha1() else None)
 
     line = {
         "metric": "rollout steps/s (plain path) and p99 control-tick latency at N=16384",

@@ -111,6 +111,7 @@ TickArgs make_tick_args(const mpmi_session* s, uint64_t tick) {
   TickArgs a;
   memset(&a, 0, sizeof(a));
   a.K = m->K32_dev;
+  a.Ks = m->K32_dev + (size_t)m->n * m->n;
   a.safety = m->dev_safety;
   a.kind = m->kind;
   a.n_samples = s->cfg.n_samples;
@@ -338,11 +339,17 @@ static void free_model_device(mpmi_model* m) {
   m->track_dev = nullptr;
 }
 
+// K in float32 twice: row-major, then with each row's columns in staging order
+// (the layout the shared-memory shapes copy in one piece).
 static int model_upload(mpmi_ctx* ctx, mpmi_model* m) {
-  const size_t bytes = sizeof(float) * m->n * m->n;
+  const size_t nn = (size_t)m->n * m->n;
+  const size_t bytes = sizeof(float) * 2 * nn;
   if (!budget_ok(ctx, bytes)) return fail(MPMI_E_OOM, "model exceeds the memory budget");
-  std::vector<float> k32(m->n * m->n);
-  for (size_t i = 0; i < k32.size(); ++i) k32[i] = (float)m->K64[i];
+  std::vector<float> k32(2 * nn);
+  for (size_t i = 0; i < nn; ++i) k32[i] = (float)m->K64[i];
+  for (int r = 0; r < m->n; ++r)
+    for (int p = 0; p < m->n; ++p)
+      k32[nn + (size_t)r * m->n + p] = (float)m->K64[(size_t)r * m->n + staged_col(m->kind, m->n, p)];
   if (cudaMalloc(&m->K32_dev, bytes) != cudaSuccess)
     return fail(MPMI_E_OOM, "cudaMalloc of K failed");
   MPMI_CUDA(cudaMemcpy(m->K32_dev, k32.data(), bytes, cudaMemcpyHostToDevice), "upload K");
@@ -1153,8 +1160,10 @@ int mpmi_tune_launch_shape(mpmi_ctx* ctx, const mpmi_model* model,
         std::sort(sorted.begin(), sorted.end());
         const double us = 1e3 * sorted[reps / 2];
         best.n_tried += 1;
-        if (lanes == dl && cands == dc && block == db) best.default_us = us;
-        if (us < best.us) {
+        const bool is_default = lanes == dl && cands == dc && block == db;
+        if (is_default) best.default_us = us;
+        // event times are quantised: a tie goes to the default shape
+        if (us < best.us || (us == best.us && is_default)) {
           best.us = us;
           best.lanes = lanes;
           best.cands = cands;

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kMaxBlock)
     if (tid == 0) bar_init(&s_bar);
     __syncthreads();
     if (tid == 0)
-      stage_issue(&s_bar, s_dyn, a.K, KSMEM ? N : 0, N, KSmem<N>::S4, a.safety.track.blob,
+      stage_issue(&s_bar, s_dyn, a.Ks, KSMEM ? N : 0, N, KSmem<N>::S4, a.safety.track.blob,
                   track_on ? a.safety.track.blob_bytes : 0, a.withhold_staging != 0);
   }
   TrackView tv{nullptr, nullptr, nullptr, nullptr};
@@ -257,13 +257,23 @@ int launch_persistent(mpmi_session* s, const TickArgs& a, const PersistArgs& pa)
                                                (int)(k.k_smem + kMaxTrackBytes));
     if (e != cudaSuccess) return fail(MPMI_E_CUDA, "cudaFuncSetAttribute (persistent)");
   }
-  int nb = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.fn, s->block, smem);
-  if (e != cudaSuccess || nb < 1)
-    return fail(MPMI_E_UNSUPPORTED, "persistent tick cannot be resident");
-  const int wpb = s->block / 32;
   const int per_warp = 32 / s->lanes * s->cands;
   const int n_wtiles = (s->n_slots + per_warp - 1) / per_warp;
+  // at most one block per SM (below), so the block is widened from the session's
+  // until those blocks cover every warp-tile at once; the block size changes no
+  // result (the reduction is a minimum and integer sums)
+  int block = s->block;
+  const int want_wpb = (n_wtiles + s->ctx->sm_count - 1) / s->ctx->sm_count;
+  while (block < kMaxBlock && block / 32 < want_wpb) block += 32;
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.fn, block, smem);
+  if (e != cudaSuccess || nb < 1) {
+    block = s->block;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.fn, block, smem);
+  }
+  if (e != cudaSuccess || nb < 1)
+    return fail(MPMI_E_UNSUPPORTED, "persistent tick cannot be resident");
+  const int wpb = block / 32;
   int grid = (n_wtiles + wpb - 1) / wpb;
   // at most one block per SM (warps stride over the warp-tiles), so that a
   // resident grid leaves room beside it for other kernels and other sessions'
@@ -273,7 +283,7 @@ int launch_persistent(mpmi_session* s, const TickArgs& a, const PersistArgs& pa)
   if (grid < 1) grid = 1;
   // every block must be resident at once (they wait on block 0's relay)
   void* args[] = {const_cast<TickArgs*>(&a), const_cast<PersistArgs*>(&pa)};
-  e = cudaLaunchCooperativeKernel(k.fn, dim3(grid), dim3(s->block), args, smem, s->persist_stream);
+  e = cudaLaunchCooperativeKernel(k.fn, dim3(grid), dim3(block), args, smem, s->persist_stream);
   if (e != cudaSuccess)
     return fail(MPMI_E_CUDA, std::string("persistent tick launch: ") + cudaGetErrorString(e));
   return MPMI_OK;

@@ -97,7 +97,9 @@ __device__ __forceinline__ void stage_issue(uint64_t* bar, uint4* dst, const flo
 
 // K staged in shared memory (KSMEM shapes): row r starts at 16-byte word r * S4,
 // rows padded by four floats so that the L lanes of a group, which read L
-// different rows at once, fall into different banks.
+// different rows at once, fall into different banks.  Within a row the columns
+// are in staging order (staged_col): the free columns ascending, then the held
+// ones ascending, so a prediction step reads only the free columns' words.
 template <int N>
 struct KSmem {
   static constexpr int S4 = (N + 4) / 4;    // 16-byte words per padded row
@@ -105,11 +107,56 @@ struct KSmem {
   static constexpr size_t BYTES = (size_t)WORDS * 16;
 };
 
+// Number of free (not held) columns of a basis.
+MPMI_HD constexpr int free_cols(int kind, int n) {
+  int nf = 0;
+  for (int k = 0; k < n; ++k) nf += held_feature(kind, k) ? 0 : 1;
+  return nf;
+}
+
+// Column of K at position p of a row in staging order, in closed form so that
+// the unrolled step loops index z with constants (checked against held_feature
+// below).  Bot: held 4, 11; race car: held 6, 7, 30, 31; linear bases: the held
+// inputs already come last.
+MPMI_HD constexpr int staged_col(int kind, int n, int p) {
+  return kind == kBot   ? (p < 4 ? p : (p < 10 ? p + 1 : (p == 10 ? 4 : 11)))
+         : kind == kCar ? (p < 6 ? p : (p < 28 ? p + 2 : (p < 30 ? p - 22 : p)))
+                        : (n > 0 ? p : -1);
+}
+
+// staged_col lists the free columns ascending, then the held ones ascending.
+constexpr bool staged_order_ok(int kind, int n) {
+  const int nf = free_cols(kind, n);
+  for (int p = 0; p < n; ++p) {
+    const int c = staged_col(kind, n, p);
+    if (c < 0 || c >= n || held_feature(kind, c) != (p >= nf)) return false;
+    if (p > 0 && p != nf && staged_col(kind, n, p - 1) >= c) return false;
+  }
+  return true;
+}
+static_assert(staged_order_ok(kBot, 12) && staged_order_ok(kCar, 32) &&
+                  staged_order_ok(kLin11, 2) && staged_order_ok(kLin22, 4) &&
+                  staged_order_ok(kLin41, 5),
+              "staging order");
+
+// K already in staging order (the model's staging copy) into padded rows.
 template <int N>
-__device__ __forceinline__ void stage_k(const float* K, uint4* dst, int tid, int nthreads) {
+__device__ __forceinline__ void stage_k(const float* Ks, uint4* dst, int tid, int nthreads) {
   constexpr int W = N / 4;
-  const uint4* src = reinterpret_cast<const uint4*>(K);
+  const uint4* src = reinterpret_cast<const uint4*>(Ks);
   for (int i = tid; i < N * W; i += nthreads) dst[(i / W) * KSmem<N>::S4 + i % W] = __ldg(&src[i]);
+}
+
+// K in row-major column order (a caller's buffer) into padded rows in staging
+// order, one float at a time.
+template <int KIND>
+__device__ __forceinline__ void stage_k_gather(const float* K, uint4* dst, int tid, int nthreads) {
+  constexpr int N = BasisTraits<KIND>::N;
+  float* d = reinterpret_cast<float*>(dst);
+  for (int i = tid; i < N * N; i += nthreads) {
+    const int r = i / N, p = i % N;
+    d[r * 4 * KSmem<N>::S4 + p] = __ldg(K + r * N + staged_col(KIND, N, p));
+  }
 }
 
 // Parameter records that carry a completion word for zero-copy host ticks.
@@ -340,6 +387,17 @@ __device__ __forceinline__ void write_result(const P& a, unsigned long long k,
   write_result<NU>(a, dyn_of(a), k, cnt, uh, timed_out);
 }
 
+// One word (positions 4 w .. 4 w + 3) of a row of K in staging order: its part of
+// the FMA chain of that row of K z.
+template <int KIND>
+__device__ __forceinline__ void fma_word(const float4 kv, const float* z, int w, float& v) {
+  constexpr int N = BasisTraits<KIND>::N;
+  v = __fmaf_rn(kv.x, z[staged_col(KIND, N, 4 * w)], v);
+  v = __fmaf_rn(kv.y, z[staged_col(KIND, N, 4 * w + 1)], v);
+  v = __fmaf_rn(kv.z, z[staged_col(KIND, N, 4 * w + 2)], v);
+  v = __fmaf_rn(kv.w, z[staged_col(KIND, N, 4 * w + 3)], v);
+}
+
 // One warp-tile: the PER_WARP = 32 C / L candidate positions wt * PER_WARP ...
 // of a tick (Alg. 2 for each: sample, lift, predict with early exit, test,
 // score), folded into the caller's running key minimum and counts.  P is the
@@ -347,6 +405,13 @@ __device__ __forceinline__ void write_result(const P& a, unsigned long long k,
 // operator's held-feature rows are exact unit rows (true for every model the
 // library built), so the one-lane shapes copy those coordinates instead of
 // recomputing them -- bit for bit the same z for finite states.
+//
+// Row order of z <- K z: every shape sums row r as one FMA chain, first over the
+// held columns (ascending), then over the others (ascending).  With HELD the held
+// coordinates of z stay at their lifted values for the whole horizon (the input
+// is held, Sec. VII-B), so the first part of the chain is the same number at
+// every step: it is summed once per candidate (hc) and each step continues the
+// chain from it -- the same rounding as summing it every step.
 template <int KIND, int L, int C, bool KSMEM, bool TRAJ, bool NOISE, bool HELD, class P,
           class KR>
 __device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety& safety,
@@ -360,9 +425,11 @@ __device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety&
   constexpr int R = N / L;
   constexpr int GPW = 32 / L;
   constexpr int S = (N % 32 == 0) ? N + 4 : ((N % 4 == 0) ? N : N + (4 - N % 4));
-  // Every launch shape sums each row of K z in the same order (one FMA chain over
-  // k = 0..n-1), so all shapes produce bit-identical trajectories and decisions.
-  constexpr int ACC = 1;
+  constexpr int NF = free_cols(KIND, N);  // free columns: staged words [0, NF / 4)
+  static_assert(!KSMEM || NF % 4 == 0, "K in shared memory needs whole words of free columns");
+  // Every launch shape sums each row of K z in the same order (one FMA chain,
+  // held columns first; see above), so all shapes produce bit-identical
+  // trajectories and decisions.
   constexpr int PER_WARP = GPW * C;
   const int lane = threadIdx.x & 31, q = lane % L, g = lane / L;
   const int H = a.horizon;
@@ -413,6 +480,30 @@ __device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety&
     alive[c] = valid[c];
   }
 
+  // the held columns' share of each row this lane computes (HELD only)
+  constexpr int HR = (L == 1) ? N : R;  // rows per candidate held in hc
+  float hc[HELD ? C : 1][HELD ? HR : 1];
+  if constexpr (HELD) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+#pragma unroll
+      for (int r = 0; r < HR; ++r) {
+        if (L == 1 && held_feature(KIND, r)) continue;  // copied, never summed
+        float v = 0.f;
+        if constexpr (KSMEM) {
+          const float4* row = sK4 + ((L == 1) ? r : (q + L * r)) * KSmem<N>::S4;
+#pragma unroll
+          for (int w = NF / 4; w < N / 4; ++w) fma_word<KIND>(row[w], z[c], w, v);
+        } else {
+#pragma unroll
+          for (int k = 0; k < N; ++k)
+            if (held_feature(KIND, k)) v = __fmaf_rn(kr[r][k], z[c][k], v);
+        }
+        hc[c][r] = v;
+      }
+    }
+  }
+
   for (int t = 1; t <= H; ++t) {
     if constexpr (KSMEM && L == 1) {
       // z <- K z with K read from shared memory (one broadcast LDS.128 feeds 4 C
@@ -428,18 +519,24 @@ __device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety&
           continue;
         }
         float av[C];
+        if constexpr (HELD) {
 #pragma unroll
-        for (int c = 0; c < C; ++c) av[c] = 0.f;
+          for (int c = 0; c < C; ++c) av[c] = hc[c][r];
+        } else {
 #pragma unroll
-        for (int k4 = 0; k4 < N / 4; ++k4) {
-          const float4 kv = sK4[r * KSmem<N>::S4 + k4];
+          for (int c = 0; c < C; ++c) av[c] = 0.f;
 #pragma unroll
-          for (int c = 0; c < C; ++c) {
-            av[c] = __fmaf_rn(kv.x, z[c][4 * k4], av[c]);
-            av[c] = __fmaf_rn(kv.y, z[c][4 * k4 + 1], av[c]);
-            av[c] = __fmaf_rn(kv.z, z[c][4 * k4 + 2], av[c]);
-            av[c] = __fmaf_rn(kv.w, z[c][4 * k4 + 3], av[c]);
+          for (int w = NF / 4; w < N / 4; ++w) {
+            const float4 kv = sK4[r * KSmem<N>::S4 + w];
+#pragma unroll
+            for (int c = 0; c < C; ++c) fma_word<KIND>(kv, z[c], w, av[c]);
           }
+        }
+#pragma unroll
+        for (int w = 0; w < NF / 4; ++w) {
+          const float4 kv = sK4[r * KSmem<N>::S4 + w];
+#pragma unroll
+          for (int c = 0; c < C; ++c) fma_word<KIND>(kv, z[c], w, av[c]);
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[c][r] = av[c];
@@ -459,8 +556,16 @@ __device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety&
             continue;
           }
           float v = 0.f;
+          if constexpr (HELD) {
+            v = hc[c][r];
+          } else {
 #pragma unroll
-          for (int k = 0; k < N; ++k) v = __fmaf_rn(kr[r][k], z[c][k], v);
+            for (int k = 0; k < N; ++k)
+              if (held_feature(KIND, k)) v = __fmaf_rn(kr[r][k], z[c][k], v);
+          }
+#pragma unroll
+          for (int k = 0; k < N; ++k)
+            if (!held_feature(KIND, k)) v = __fmaf_rn(kr[r][k], z[c][k], v);
           zn[c][r] = v;
         }
       }
@@ -480,28 +585,30 @@ __device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety&
         for (int r = 0; r < R; ++r) {
           const float4* row = sK4 + (q + L * r) * KSmem<N>::S4;
           float v = 0.f;
+          if constexpr (HELD) {
+            v = hc[0][r];
+          } else {
 #pragma unroll
-          for (int k4 = 0; k4 < N / 4; ++k4) {
-            const float4 kv = row[k4];
-            v = __fmaf_rn(kv.x, z[0][4 * k4], v);
-            v = __fmaf_rn(kv.y, z[0][4 * k4 + 1], v);
-            v = __fmaf_rn(kv.z, z[0][4 * k4 + 2], v);
-            v = __fmaf_rn(kv.w, z[0][4 * k4 + 3], v);
+            for (int w = NF / 4; w < N / 4; ++w) fma_word<KIND>(row[w], z[0], w, v);
           }
+#pragma unroll
+          for (int w = 0; w < NF / 4; ++w) fma_word<KIND>(row[w], z[0], w, v);
           zn[r] = v;
         }
       } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          float accv[ACC];
+          float v = 0.f;
+          if constexpr (HELD) {
+            v = hc[0][r];
+          } else {
 #pragma unroll
-          for (int e = 0; e < ACC; ++e) accv[e] = 0.f;
+            for (int k = 0; k < N; ++k)
+              if (held_feature(KIND, k)) v = __fmaf_rn(kr[r][k], z[0][k], v);
+          }
 #pragma unroll
           for (int k = 0; k < N; ++k)
-            accv[k % ACC] = __fmaf_rn(kr[r][k], z[0][k], accv[k % ACC]);
-          float v = accv[0];
-#pragma unroll
-          for (int e = 1; e < ACC; ++e) v = __fadd_rn(v, accv[e]);
+            if (!held_feature(KIND, k)) v = __fmaf_rn(kr[r][k], z[0][k], v);
           zn[r] = v;
         }
       }
@@ -666,7 +773,7 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   constexpr int ANG = (KIND == kBot) ? 0 : ((KIND == kCar) ? 2 : -1);
   constexpr int KWORDS = KSMEM ? KSmem<N>::WORDS : 0;  // 16-byte words of K in shared memory
 
-  extern __shared__ uint4 s_dyn[];  // [K (KSMEM)] [track blob (race car)]
+  extern __shared__ uint4 s_dyn[];  // [K in staging order (KSMEM)] [track blob (race car)]
   __shared__ __align__(16) float s_x[(L > 1) ? NW : 1][2][GPW][S];
   __shared__ unsigned long long s_key[NW];
   __shared__ unsigned long long s_cnt[NW];
@@ -691,11 +798,11 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
       if (tid == 0) bar_init(&s_bar);
       __syncthreads();
       if (tid == 0)
-        stage_issue(&s_bar, s_dyn, a.K, KSMEM ? N : 0, N, KSmem<N>::S4, a.safety.track.blob,
+        stage_issue(&s_bar, s_dyn, a.Ks, KSMEM ? N : 0, N, KSmem<N>::S4, a.safety.track.blob,
                     track_on ? a.safety.track.blob_bytes : 0, a.withhold_staging != 0);
     }
   } else {
-    if constexpr (KSMEM) stage_k<N>(a.K, s_dyn, tid, blockDim.x);
+    if constexpr (KSMEM) stage_k_gather<KIND>(a.K, s_dyn, tid, blockDim.x);
     if (track_on) {
       const int words = a.safety.track.blob_bytes >> 4;
       for (int i = tid; i < words; i += blockDim.x) s_dyn[KWORDS + i] = __ldg(&a.safety.track.blob[i]);

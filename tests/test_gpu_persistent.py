@@ -101,6 +101,30 @@ def test_resident_ticks_equal_launched_ticks(lib, ctx, bot, car, which, N, H):
     res.close()
 
 
+@pytest.mark.parametrize("which,N,H", [("bot", 16384, 50), ("car", 16384, 60)])
+def test_resident_ticks_with_a_narrow_block(lib, ctx, bot, car, which, N, H):
+    """A session with 64-thread blocks: the resident grid (one block per SM)
+    widens its blocks until it covers every warp-tile at once; the results stay
+    those of the launched ticks with 64-thread blocks."""
+    env, model = bot if which == "bot" else car
+    plain = lib.Session(ctx, model, N, H, env.lo, env.hi, seed=23, block=64)
+    res = lib.Session(ctx, model, N, H, env.lo, env.hi, seed=23, block=64)
+    assert plain.launch_shape()[2] == 64
+    ticks = [500 + 3 * k for k in range(12)]
+    want = []
+    for k, tick in enumerate(ticks):
+        x, u = _inputs(env, which, k)
+        lib.evaluate_candidates(plain, x, u, tick=tick)
+        want.append(lib.select_input(plain))
+    plain.close()
+    _persistent(lib, res)
+    for k, tick in enumerate(ticks):
+        x, u = _inputs(env, which, k)
+        lib.evaluate_candidates(res, x, u, tick=tick)
+        _same(lib.select_input(res), want[k])
+    res.close()
+
+
 @pytest.mark.parametrize("which", ["bot", "car"])
 def test_resident_tick_against_the_oracle(lib, ctx, bot, car, which):
     env, model = bot if which == "bot" else car
