@@ -781,6 +781,12 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int q = lane % L;
+  // The session's reduction record is usually cold in L2 (other work ran since
+  // the last tick): start fetching it now, so that the epilogue's atomics do
+  // not wait for HBM on the tick's critical path.
+  if constexpr (!PARTIALS) {
+    if (tid == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.scratch));
+  }
   // a fallback launch has nothing to do when the screened result is already safe
   if (a.skip_if_safe != nullptr && a.skip_if_safe->status == MPMI_SAFE) return;
   // number of candidates this launch evaluates (all slots, or a device-side list)
@@ -870,67 +876,66 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
 
   if constexpr (!PARTIALS) {
     session_epilogue<NU>(a, best, n_safe, n_exec, uh, failed);
-    return;
-  }
-  // warp -> block reduction, then per-block partials folded by the last block
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long other = __shfl_xor_sync(kFull, best, o);
-    best = other < best ? other : best;
-    n_exec += __shfl_xor_sync(kFull, n_exec, o);
-    n_safe += __shfl_xor_sync(kFull, n_safe, o);
-  }
-  if (lane == 0) {
-    s_key[warp] = best;
-    s_cnt[warp] = ((unsigned long long)n_safe << 40) + n_exec;
-  }
-  __syncthreads();
-  {
-    unsigned long long* pk = a.partials;
-    unsigned long long* pc = a.partials + a.partials_cap;
-    unsigned long long* blocks_done = a.partials + 2 * a.partials_cap;
-    if (tid == 0) {
-      unsigned long long bk = s_key[0], bc = s_cnt[0];
-      for (int w = 1; w < wpb; ++w) {
-        bk = s_key[w] < bk ? s_key[w] : bk;
-        bc += s_cnt[w];
-      }
-      pk[blockIdx.x] = bk;
-      pc[blockIdx.x] = bc;
-      __threadfence();
-      const unsigned long long prev = atomicAdd(blocks_done, 1ull);
-      s_last = (prev == (unsigned long long)gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    unsigned long long k = ~0ull, cc = 0ull;
-    for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
-      const unsigned long long kb = *reinterpret_cast<volatile unsigned long long*>(pk + b);
-      k = kb < k ? kb : k;
-      cc += *reinterpret_cast<volatile unsigned long long*>(pc + b);
-    }
+  } else {
+    // warp -> block reduction, then per-block partials folded by the last block
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long other = __shfl_xor_sync(kFull, k, o);
-      k = other < k ? other : k;
-      cc += __shfl_xor_sync(kFull, cc, o);
+      const unsigned long long other = __shfl_xor_sync(kFull, best, o);
+      best = other < best ? other : best;
+      n_exec += __shfl_xor_sync(kFull, n_exec, o);
+      n_safe += __shfl_xor_sync(kFull, n_safe, o);
     }
-    __syncthreads();
     if (lane == 0) {
-      s_key[warp] = k;
-      s_cnt[warp] = cc;
+      s_key[warp] = best;
+      s_cnt[warp] = ((unsigned long long)n_safe << 40) + n_exec;
     }
     __syncthreads();
-    if (tid == 0) {
-      for (int w = 1; w < wpb; ++w) {
-        k = s_key[w] < k ? s_key[w] : k;
-        cc += s_cnt[w];
+    {
+      unsigned long long* pk = a.partials;
+      unsigned long long* pc = a.partials + a.partials_cap;
+      unsigned long long* blocks_done = a.partials + 2 * a.partials_cap;
+      if (tid == 0) {
+        unsigned long long bk = s_key[0], bc = s_cnt[0];
+        for (int w = 1; w < wpb; ++w) {
+          bk = s_key[w] < bk ? s_key[w] : bk;
+          bc += s_cnt[w];
+        }
+        pk[blockIdx.x] = bk;
+        pc[blockIdx.x] = bc;
+        __threadfence();
+        const unsigned long long prev = atomicAdd(blocks_done, 1ull);
+        s_last = (prev == (unsigned long long)gridDim.x - 1);
       }
-      write_result<NU>(a, k, cc, uh);
-      *blocks_done = 0ull;
+      __syncthreads();
+      if (!s_last) return;
+      __threadfence();
+      unsigned long long k = ~0ull, cc = 0ull;
+      for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+        const unsigned long long kb = *reinterpret_cast<volatile unsigned long long*>(pk + b);
+        k = kb < k ? kb : k;
+        cc += *reinterpret_cast<volatile unsigned long long*>(pc + b);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(kFull, k, o);
+        k = other < k ? other : k;
+        cc += __shfl_xor_sync(kFull, cc, o);
+      }
+      __syncthreads();
+      if (lane == 0) {
+        s_key[warp] = k;
+        s_cnt[warp] = cc;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        for (int w = 1; w < wpb; ++w) {
+          k = s_key[w] < k ? s_key[w] : k;
+          cc += s_cnt[w];
+        }
+        write_result<NU>(a, k, cc, uh);
+        *blocks_done = 0ull;
+      }
     }
-    return;
   }
 }
 
