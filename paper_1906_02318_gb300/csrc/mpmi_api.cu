@@ -1089,19 +1089,23 @@ int mpmi_tune_launch_shape(mpmi_ctx* ctx, const mpmi_model* model,
   default_shape(model->kind, (int)slots, ctx->sm_count, &dl, &dc, &db);
   double* in_dev = nullptr;
   mpmi_result* res_dev = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // one start and one end event per timed tick: the ticks are queued back to back
+  // and read after one synchronisation, so a tick's time never includes the
+  // host's launch of the next one
+  std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
   auto cleanup = [&]() {
     cudaFree(in_dev);
     cudaFree(res_dev);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
   };
   double in_host[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   memcpy(in_host, x_t, sizeof(double) * model->nx);
   memcpy(in_host + 8, u_h, sizeof(double) * model->nu);
-  if (cudaMalloc(&in_dev, sizeof(in_host)) != cudaSuccess ||
+  bool events_ok = true;
+  for (cudaEvent_t& e : ev) events_ok = events_ok && cudaEventCreate(&e) == cudaSuccess;
+  if (!events_ok || cudaMalloc(&in_dev, sizeof(in_host)) != cudaSuccess ||
       cudaMalloc(&res_dev, sizeof(mpmi_result)) != cudaSuccess ||
-      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
       cudaMemcpy(in_dev, in_host, sizeof(in_host), cudaMemcpyHostToDevice) != cudaSuccess) {
     cleanup();
     return fail(MPMI_E_OOM, "tune_launch_shape: device buffers");
@@ -1133,19 +1137,17 @@ int mpmi_tune_launch_shape(mpmi_ctx* ctx, const mpmi_model* model,
           a.x_t = in_dev;
           a.u_h = in_dev + 8;
           a.result = res_dev;
-          if (r >= 0) cudaEventRecord(e0, 0);
+          if (r >= 0) cudaEventRecord(ev[2 * r], 0);
           rc = launch_tick_args(s, a, false, 0, 0);
           if (rc != MPMI_OK) break;
-          if (r >= 0) {
-            cudaEventRecord(e1, 0);
-            float ms = 0.f;
-            if (cudaEventSynchronize(e1) != cudaSuccess ||
-                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          if (r >= 0) cudaEventRecord(ev[2 * r + 1], 0);
+        }
+        if (rc == MPMI_OK) {
+          if (cudaEventSynchronize(ev[2 * (size_t)reps - 1]) != cudaSuccess)
+            rc = fail(MPMI_E_CUDA, "tune_launch_shape: timing the ticks");
+          for (int r = 0; r < reps && rc == MPMI_OK; ++r)
+            if (cudaEventElapsedTime(&t[r], ev[2 * r], ev[2 * r + 1]) != cudaSuccess)
               rc = fail(MPMI_E_CUDA, "tune_launch_shape: timing a tick");
-              break;
-            }
-            t[r] = ms;
-          }
         }
         mpmi_session_close(s);
         if (rc == MPMI_E_UNSUPPORTED) {  // this block size cannot be resident: skip it

@@ -32,31 +32,48 @@ def _same(a, b):
     assert a["cost"] == b["cost"]
 
 
-@pytest.mark.parametrize("lanes", [1, 4])
-def test_noalloc_matches_session_path_twice(lib, lanes):
+@pytest.mark.parametrize("basis,lanes", [("bot", 1), ("bot", 4), ("car", 1), ("car", 8)])
+def test_noalloc_matches_session_path_twice(lib, basis, lanes):
+    """The race car runs with its box bounds only (a track needs a preprocessed
+    grid, which this entry point does not take); with one lane its K is staged
+    in shared memory from the caller's row-major buffer."""
     import torch
-    x, u, xn = data.transitions("bot", 1, 5000)
-    K, _ = lib.fit_operator("bot", x, u, xn)
+    if basis == "bot":
+        x, u, xn = data.transitions("bot", 1, 5000)
+        safe_lo, safe_hi = data.BOT_SAFE_LO, data.BOT_SAFE_HI
+        lo, hi = plants.BOT_INPUT_LO, plants.BOT_INPUT_HI
+        states = [np.array([0.05, 0.0, 0.0, 0.0]), np.array([0.3, 0.8, 1.1, 0.5])]
+        uhs = [np.array([0.25]), np.array([-0.75])]
+        N, H = 16384, 50
+    else:
+        x, u, xn = data.transitions("car", 3, 20000)
+        safe_lo, safe_hi = data.CAR_SAFE_LO, data.CAR_SAFE_HI
+        lo, hi = plants.CAR_INPUT_LO, plants.CAR_INPUT_HI
+        states = [np.array([0.0, 0.0, 0.3, 18.0, 0.5, 0.1]),
+                  np.array([5.0, -3.0, 1.2, 23.0, -0.8, 0.4])]
+        uhs = [np.array([0.1, 0.5]), np.array([-0.3, 0.9])]
+        N, H = 16384, 60
+    nu = len(uhs[0])
+    K, _ = lib.fit_operator(basis, x, u, xn)
     ctx = lib.Context(0)
-    model = lib.model_from_operator(ctx, "bot", K)
-    lib.set_safety_set(model, data.BOT_SAFE_LO, data.BOT_SAFE_HI)
-    N, H, seed = 16384, 50, 7
-    lo, hi = plants.BOT_INPUT_LO, plants.BOT_INPUT_HI
+    model = lib.model_from_operator(ctx, basis, K)
+    lib.set_safety_set(model, safe_lo, safe_hi)
+    seed = 7
     sess = lib.Session(ctx, model, N, H, lo, hi, seed=seed, lanes=lanes)
     dev = torch.device("cuda")
     K_dev = torch.tensor(K, dtype=torch.float32, device=dev)   # caller-owned buffers
-    states = [np.array([0.05, 0.0, 0.0, 0.0]), np.array([0.3, 0.8, 1.1, 0.5])]
-    uhs = [np.array([0.25]), np.array([-0.75])]
     for call, (x_t, u_h) in enumerate(zip(states, uhs)):
         xt = torch.tensor(x_t, dtype=torch.float64, device=dev)
         uh = torch.tensor(u_h, dtype=torch.float64, device=dev)
         ref = torch.zeros(lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
         out = torch.zeros(lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
         lib.evaluate_candidates_device(sess, xt, uh, ref, tick=call)
-        lib.evaluate_candidates_noalloc("bot", K_dev, data.BOT_SAFE_LO, data.BOT_SAFE_HI, N, H,
-                                        lo, hi, xt, uh, out, seed=seed, lanes=lanes, tick=call)
+        # 256-thread blocks keep 8 lanes per candidate within the scratch's 1024 blocks
+        lib.evaluate_candidates_noalloc(basis, K_dev, safe_lo, safe_hi, N, H,
+                                        lo, hi, xt, uh, out, seed=seed, lanes=lanes,
+                                        block=256 if lanes >= 8 else 0, tick=call)
         torch.cuda.synchronize()
-        _same(lib.result_from_bytes(out.cpu(), 1), lib.result_from_bytes(ref.cpu(), 1))
+        _same(lib.result_from_bytes(out.cpu(), nu), lib.result_from_bytes(ref.cpu(), nu))
     sess.close()
     model.free()
 
