@@ -1,7 +1,8 @@
 // Learned candidate screener (not in the paper): training kernels (float32),
-// tensor-core inference (bfloat16 mma.sync, float32 accumulation), per-tick track
-// features, and the screened tick (score -> threshold -> compaction -> exact
-// rollout on the kept slots -> on-device fallback to the full evaluation).
+// tensor-core inference (tcgen05, bfloat16 operands, float32 accumulation in
+// TMEM), per-tick track features, and the screened tick (score -> threshold ->
+// compaction -> exact rollout on the kept slots -> on-device fallback to the full
+// evaluation).
 //
 // Network: 12 -> 128 -> 128 -> 1, GELU in its tanh form (Hendrycks & Gimpel),
 // sigmoid output trained on ttv / H with the mean squared error and Adam.
@@ -14,26 +15,37 @@
 #include <vector>
 
 #include "internal.h"
+#include "tcgen05.cuh"
 #include "tick_kernel.cuh"
 
 namespace mpmi {
 
-constexpr int kH = 128, kIn = 12, kInP = 16, kW2S = 136;
+constexpr int kH = 128, kIn = 12, kInP = 16;
 constexpr int oW1 = 0, ob1 = kH * kIn, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, ow3 = ob2 + kH,
               ob3 = ow3 + kH, kP = ob3 + 1;
 static_assert(kP == MPMI_SCREENER_PARAMS, "packed weight layout");
 constexpr int kBins = 2048;  // histogram of (predicted unsafe, cost) keys: key >> 21
 constexpr float kGeluC = 0.7978845608028654f, kGeluA = 0.044715f;
 
-// bfloat16 inference copy of the weights (W1 padded to 16 inputs, W2 rows padded to
-// 136 so the B-fragment loads of a warp hit 32 different banks)
+// bfloat16 inference copy of the weights, laid out as the tensor cores' B operands:
+// K-major tiles of 8-row x 16-byte core matrices without swizzle (bf_off), row j
+// = unit j of the layer, K = its inputs (layer 1 padded from 12 to 16).  Staged
+// verbatim into shared memory by every scoring block.
 struct InferW {
-  __nv_bfloat16 W1[kH * kInP];
-  __nv_bfloat16 W2[kH * kW2S];
+  __nv_bfloat16 W1[kH * kInP];  // 128 x 16: 2 core matrices per 8-row group
+  __nv_bfloat16 W2[kH * kH];    // 128 x 128: 16 core matrices per 8-row group
   float b1[kH], b2[kH], w3[kH];
   float b3, pad[3];
 };
 static_assert(sizeof(InferW) % 16 == 0, "InferW is staged with 16-byte copies");
+
+// Byte offset of element (row, k) in a K-major bfloat16 tile with kc 8-element
+// chunks per row: core matrix (row / 8, k / 8) holds 8 rows x 16 bytes; the
+// chunks of a row group lie 128 B apart (the descriptor's leading byte offset),
+// the row groups kc * 128 B apart (its stride byte offset).
+__host__ __device__ constexpr uint32_t bf_off(int row, int k, int kc) {
+  return (uint32_t)((((row >> 3) * kc + (k >> 3)) * 128) + (row & 7) * 16 + (k & 7) * 2);
+}
 
 struct ScreenScratch {
   unsigned int hist[kBins];
@@ -195,13 +207,17 @@ __global__ void adam(float* P, const float* g, float* m, float* v, float lr, flo
 
 __global__ void to_infer(const float* P, InferW* w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned char* w1 = reinterpret_cast<unsigned char*>(w->W1);
+  unsigned char* w2 = reinterpret_cast<unsigned char*>(w->W2);
   if (i < kH * kInP) {
     const int j = i / kInP, k = i % kInP;
-    w->W1[i] = __float2bfloat16_rn(k < kIn ? P[oW1 + j * kIn + k] : 0.f);
+    *reinterpret_cast<__nv_bfloat16*>(w1 + bf_off(j, k, kInP / 8)) =
+        __float2bfloat16_rn(k < kIn ? P[oW1 + j * kIn + k] : 0.f);
   }
-  if (i < kH * kW2S) {
-    const int j = i / kW2S, k = i % kW2S;
-    w->W2[i] = __float2bfloat16_rn(k < kH ? P[oW2 + j * kH + k] : 0.f);
+  if (i < kH * kH) {
+    const int j = i / kH, k = i % kH;
+    *reinterpret_cast<__nv_bfloat16*>(w2 + bf_off(j, k, kH / 8)) =
+        __float2bfloat16_rn(P[oW2 + j * kH + k]);
   }
   if (i < kH) {
     w->b1[i] = P[ob1 + i];
@@ -212,18 +228,30 @@ __global__ void to_infer(const float* P, InferW* w) {
 }
 
 // ---------------------------------------------------------------- inference (tensor cores)
+// One CTA of 128 threads scores a tile of 128 rows on the 5th-generation tensor
+// cores: thread i = row i = TMEM lane i.
+//   1. thread i writes its 12 inputs (bfloat16, padded to 16) as row i of the
+//      K-major tile A1;
+//   2. one thread issues tcgen05.mma kind::f16 (M = N = 128, K = 16): A1 W1^T into
+//      128 TMEM columns, and commits to an mbarrier;
+//   3. thread i reads its row back (tcgen05.ld), adds b1, applies GELU and writes
+//      the 128 hidden values as row i of the bfloat16 tile A2 (K = 128);
+//   4. one thread issues eight K = 16 MMAs, A2 W2^T, into the same columns;
+//   5. thread i reads its row, adds b2, applies GELU, takes the dot product with
+//      w3, adds b3 and the sigmoid.
+// The weights' rounding to bfloat16 and the float32 accumulation are those of
+// the network's inference form; GELU uses the hardware tanh approximation.
+constexpr int kTileRows = 128;
+constexpr uint32_t kOffA1 = 38912;                 // after the staged InferW (38,416 B)
+constexpr uint32_t kOffA2 = kOffA1 + kTileRows * kInP * 2;
+constexpr int kScoreSmem = (int)(kOffA2 + kTileRows * kH * 2);  // 75,776 B
+static_assert(sizeof(InferW) <= kOffA1 && kOffA1 % 1024 == 0 && kOffA2 % 1024 == 0,
+              "shared-memory layout of a scoring block");
+constexpr int kTmemCols = 128;
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 __device__ __forceinline__ float tanh_approx(float x) {
@@ -236,95 +264,167 @@ __device__ __forceinline__ float gelu_fast(float z) {
   return 0.5f * z * (1.f + tanh_approx(kGeluC * (z + kGeluA * z * z * z)));
 }
 
-// Scores 16 rows (one mma M tile) per call.  Lane l holds rows g = l / 4 and g + 8
-// (f0, f1: their 12 inputs) and receives their sigmoid outputs in *y0, *y1 (valid
-// in lanes with l % 4 == 0).  Weights in shared memory (sw).
-__device__ __forceinline__ void mlp_tile(const InferW* sw, const float* f0, const float* f1,
-                                         float* y0, float* y1) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-  uint32_t a[4];
-  auto in = [&](const float* f, int k) { return k < kIn ? f[k] : 0.f; };
-  a[0] = pack_bf16(in(f0, 2 * q), in(f0, 2 * q + 1));
-  a[1] = pack_bf16(in(f1, 2 * q), in(f1, 2 * q + 1));
-  a[2] = pack_bf16(in(f0, 8 + 2 * q), in(f0, 9 + 2 * q));
-  a[3] = pack_bf16(in(f1, 8 + 2 * q), in(f1, 9 + 2 * q));
-  // layer 1: 16 n-tiles of 8 hidden units, one k step (16 padded inputs)
-  float c1[16][4];
-  const uint32_t* W1w = reinterpret_cast<const uint32_t*>(sw->W1);
-#pragma unroll
-  for (int nt = 0; nt < 16; ++nt) {
-    const int col = 8 * nt + 2 * q;
-    c1[nt][0] = sw->b1[col];
-    c1[nt][1] = sw->b1[col + 1];
-    c1[nt][2] = sw->b1[col];
-    c1[nt][3] = sw->b1[col + 1];
-    const int n = 8 * nt + g;
-    mma16816(c1[nt], a, W1w[(n * kInP + 2 * q) >> 1], W1w[(n * kInP + 8 + 2 * q) >> 1]);
-  }
-  // GELU, then the accumulator tiles become layer 2's A fragments
-  uint32_t a2[8][4];
-#pragma unroll
-  for (int kt = 0; kt < 8; ++kt) {
-    a2[kt][0] = pack_bf16(gelu_fast(c1[2 * kt][0]), gelu_fast(c1[2 * kt][1]));
-    a2[kt][1] = pack_bf16(gelu_fast(c1[2 * kt][2]), gelu_fast(c1[2 * kt][3]));
-    a2[kt][2] = pack_bf16(gelu_fast(c1[2 * kt + 1][0]), gelu_fast(c1[2 * kt + 1][1]));
-    a2[kt][3] = pack_bf16(gelu_fast(c1[2 * kt + 1][2]), gelu_fast(c1[2 * kt + 1][3]));
-  }
-  // layer 2 and the output unit
-  const uint32_t* W2w = reinterpret_cast<const uint32_t*>(sw->W2);
-  float p0 = 0.f, p1 = 0.f;
-#pragma unroll
-  for (int nt = 0; nt < 16; ++nt) {
-    const int col = 8 * nt + 2 * q;
-    float c[4] = {sw->b2[col], sw->b2[col + 1], sw->b2[col], sw->b2[col + 1]};
-    const int n = 8 * nt + g;
-#pragma unroll
-    for (int kt = 0; kt < 8; ++kt)
-      mma16816(c, a2[kt], W2w[(n * kW2S + 16 * kt + 2 * q) >> 1],
-               W2w[(n * kW2S + 16 * kt + 8 + 2 * q) >> 1]);
-    const float w0 = sw->w3[col], w1 = sw->w3[col + 1];
-    p0 = fmaf(w0, gelu_fast(c[0]), fmaf(w1, gelu_fast(c[1]), p0));
-    p1 = fmaf(w0, gelu_fast(c[2]), fmaf(w1, gelu_fast(c[3]), p1));
-  }
-  p0 += __shfl_xor_sync(0xffffffffu, p0, 1);
-  p0 += __shfl_xor_sync(0xffffffffu, p0, 2);
-  p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
-  p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
-  *y0 = 1.f / (1.f + __expf(-(p0 + sw->b3)));
-  *y1 = 1.f / (1.f + __expf(-(p1 + sw->b3)));
+// Instruction descriptor, kind::f16: D float32, A and B bfloat16, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24 (M = N = 128).
+constexpr uint32_t kIdescBf16 =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kTileRows >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(kIdescBf16), "r"(acc)
+      : "memory");
 }
 
-__device__ void stage_weights(const InferW* w, InferW* sw) {
-  const uint4* src = reinterpret_cast<const uint4*>(w);
-  uint4* dst = reinterpret_cast<uint4*>(sw);
-  for (int i = threadIdx.x; i < (int)(sizeof(InferW) / 16); i += blockDim.x) dst[i] = src[i];
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
 }
 
-// Scores arbitrary feature rows (batch x 12).
-__global__ void __launch_bounds__(128) score_rows(const InferW* w, const float* feats, int B,
-                                                  float* out) {
-  extern __shared__ uint4 s_dyn[];
-  InferW* sw = reinterpret_cast<InferW*>(s_dyn);
-  stage_weights(w, sw);
+// Generic-proxy writes to shared memory become visible to the tensor cores, and
+// every thread's earlier tcgen05 reads are ordered before the next MMA.
+__device__ __forceinline__ void tc_handoff() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
   __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
-  const int tiles = (B + 15) / 16;
-  for (int t = blockIdx.x * wpb + warp; t < tiles; t += gridDim.x * wpb) {
-    const int r0 = 16 * t + g, r1 = r0 + 8;
-    float f0[kIn], f1[kIn];
+  tc_fence_after();
+}
+
+// Waits for the MMAs committed to `bar` (phase `phase`), bounded; the CTA agrees.
+__device__ __forceinline__ bool mma_wait(uint64_t* bar, uint32_t phase) {
+  bool ok = bar_wait(bar, phase);
+  if (!ok) ok = bar_wait(bar, phase);
+  const bool all = __syncthreads_and(ok) != 0;
+  tc_fence_after();
+  return all;
+}
+
+// Per scoring block: TMEM for the accumulator and the mbarrier of the MMAs.
+struct ScoreCtx {
+  unsigned char* smem;  // staged InferW | A1 | A2
+  uint32_t tmem;
+  uint64_t* bar;
+  uint32_t phase;
+  bool ok;
+};
+
+// Stages the weights and allocates the accumulator (all threads; ends synced).
+__device__ void score_begin(const InferW* w, unsigned char* smem, uint64_t* bar,
+                            uint32_t* s_tmem, ScoreCtx* c) {
+  const uint4* src = reinterpret_cast<const uint4*>(w);
+  uint4* dst = reinterpret_cast<uint4*>(smem);
+  for (int i = threadIdx.x; i < (int)(sizeof(InferW) / 16); i += blockDim.x) dst[i] = __ldg(&src[i]);
+  if (threadIdx.x == 0) bar_init(bar);
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(s_tmem)), "n"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  c->smem = smem;
+  c->tmem = *s_tmem;
+  c->bar = bar;
+  c->phase = 0;
+  c->ok = true;
+}
+
+// Frees the accumulator (all threads, after the last tile).
+__device__ void score_end(const ScoreCtx& c) {
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c.tmem),
+                 "n"(kTmemCols)
+                 : "memory");
+}
+
+// The network's output for this thread's row of the tile (inputs f[0..12));
+// called by all 128 threads of the block.  After a wait that runs out the block
+// stops using the tensor cores (c->ok = false) and every row scores 1.
+__device__ float score_tile(ScoreCtx* c, const float* f) {
+  if (!c->ok) return 1.f;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char* a1 = c->smem + kOffA1;
+  unsigned char* a2 = c->smem + kOffA2;
+  const InferW* sw = reinterpret_cast<const InferW*>(c->smem);
+  *reinterpret_cast<uint4*>(a1 + bf_off(tid, 0, kInP / 8)) =
+      make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]),
+                 pack_bf16(f[6], f[7]));
+  *reinterpret_cast<uint4*>(a1 + bf_off(tid, 8, kInP / 8)) =
+      make_uint4(pack_bf16(f[8], f[9]), pack_bf16(f[10], f[11]), 0u, 0u);
+  tc_handoff();
+  const uint32_t sa1 = smem_u32(a1), sa2 = smem_u32(a2);
+  const uint32_t sw1 = smem_u32(sw->W1), sw2 = smem_u32(sw->W2);
+  if (tid == 0) {
+    mma_bf16(c->tmem, mat_desc(sa1, 128, 256), mat_desc(sw1, 128, 256), 0u);
+    mma_commit(c->bar);
+  }
+  c->ok = mma_wait(c->bar, c->phase);
+  c->phase ^= 1u;
+  if (!c->ok) return 1.f;
+  const uint32_t taddr = c->tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-    for (int k = 0; k < kIn; ++k) {
-      f0[k] = r0 < B ? feats[(size_t)r0 * kIn + k] : 0.f;
-      f1[k] = r1 < B ? feats[(size_t)r1 * kIn + k] : 0.f;
-    }
-    float y0, y1;
-    mlp_tile(sw, f0, f1, &y0, &y1);
-    if (q == 0) {
-      if (r0 < B) out[r0] = y0;
-      if (r1 < B) out[r1] = y1;
+  for (int q = 0; q < kH / 32; ++q) {
+    float h[32];
+    tmem_ld32(taddr + 32 * q, h);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int j = 32 * q + 8 * m;
+      float g[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) g[e] = gelu_fast(h[8 * m + e] + sw->b1[j + e]);
+      *reinterpret_cast<uint4*>(a2 + bf_off(tid, j, kH / 8)) =
+          make_uint4(pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]),
+                     pack_bf16(g[6], g[7]));
     }
   }
+  tc_handoff();
+  if (tid == 0) {
+#pragma unroll
+    for (int kb = 0; kb < kH / 16; ++kb)
+      mma_bf16(c->tmem, mat_desc(sa2 + kb * 256, 128, 2048), mat_desc(sw2 + kb * 256, 128, 2048),
+               kb ? 1u : 0u);
+    mma_commit(c->bar);
+  }
+  c->ok = mma_wait(c->bar, c->phase);
+  c->phase ^= 1u;
+  if (!c->ok) return 1.f;
+  float p = 0.f;
+#pragma unroll
+  for (int q = 0; q < kH / 32; ++q) {
+    float h[32];
+    tmem_ld32(taddr + 32 * q, h);
+#pragma unroll
+    for (int e = 0; e < 32; ++e) p = fmaf(sw->w3[32 * q + e], gelu_fast(h[e] + sw->b2[32 * q + e]), p);
+  }
+  return 1.f / (1.f + __expf(-(p + sw->b3)));
+}
+
+// Scores arbitrary feature rows (batch x 12), 128 rows per block and tile.
+__global__ void __launch_bounds__(kTileRows) score_rows(const InferW* w, const float* feats, int B,
+                                                        float* out) {
+  extern __shared__ __align__(1024) unsigned char s_score[];
+  __shared__ uint64_t s_bar;
+  __shared__ uint32_t s_tmem;
+  ScoreCtx c;
+  score_begin(w, s_score, &s_bar, &s_tmem, &c);
+  const int tiles = (B + kTileRows - 1) / kTileRows;
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int r = t * kTileRows + (int)threadIdx.x;
+    float f[kIn];
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) f[k] = r < B ? feats[(size_t)r * kIn + k] : 0.f;
+    const float y = score_tile(&c, f);
+    if (r < B) out[r] = c.ok ? y : __int_as_float(0x7fc00000);  // NaN: the wait ran out
+  }
+  score_end(c);
 }
 
 // ---------------------------------------------------------------- track features
@@ -424,55 +524,11 @@ __global__ void slot_features(TickArgs a, FeatureSrc fs, float* out) {
 }
 
 // ---------------------------------------------------------------- screened tick
-// Scores every slot, writes its key ((score < tau) << 31 | cost bits >> 1; slot 0,
-// the user's input, gets key 0 so it is always kept) and builds the histogram of
-// key >> 21.  The last block finds the smallest bin where k slots are reached,
-// clears the histogram and the list counter for the next tick.
-__global__ void __launch_bounds__(128) screen_score(TickArgs a, FeatureSrc fs, const InferW* w,
-                                                   float tau, int k, unsigned int* keys,
-                                                   ScreenScratch* ss) {
-  extern __shared__ uint4 s_dyn[];
-  InferW* sw = reinterpret_cast<InferW*>(s_dyn);
-  __shared__ unsigned int s_hist[kBins];
-  __shared__ float s_feat[12];
+// End of a scoring launch (every thread of the block): this block's histogram
+// into the tick's, and the last block finds the smallest bin where k slots are
+// reached, then clears the histogram and the list counter for the next tick.
+__device__ void screen_finish(unsigned int* s_hist, int k, ScreenScratch* ss) {
   __shared__ int s_last;
-  for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
-  if (tau > 0.f) stage_weights(w, sw);
-  block_tick_features(fs, a.x_t, s_feat);  // ends with __syncthreads
-  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
-  float uh[2] = {__double2float_rn(a.u_h[0]), __double2float_rn(a.u_h[1])};
-  const int tiles = (a.n_slots + 15) / 16;
-  for (int t = blockIdx.x * wpb + warp; t < tiles; t += gridDim.x * wpb) {
-    const int r0 = 16 * t + g, r1 = r0 + 8;
-    float f0[kIn], f1[kIn], x0[2], x1[2];
-    candidate_value<2>(a, r0 < a.n_slots ? r0 : 0, uh, x0);
-    candidate_value<2>(a, r1 < a.n_slots ? r1 : 0, uh, x1);
-#pragma unroll
-    for (int m = 0; m < 10; ++m) f0[m] = f1[m] = s_feat[m];
-    f0[10] = x0[0] / 0.4f;
-    f0[11] = x0[1];
-    f1[10] = x1[0] / 0.4f;
-    f1[11] = x1[1];
-    float y0 = 1.f, y1 = 1.f;
-    if (tau > 0.f) mlp_tile(sw, f0, f1, &y0, &y1);  // tau <= 0: cost order only
-    if (q == 0) {
-      const int rr[2] = {r0, r1};
-      const float yy[2] = {y0, y1};
-      const float* xx[2] = {x0, x1};
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int r = rr[e];
-        if (r >= a.n_slots) continue;
-        const float d0 = __fsub_rn(xx[e][0], uh[0]), d1 = __fsub_rn(xx[e][1], uh[1]);
-        const float cost = __fmaf_rn(d1, d1, __fmul_rn(d0, d0));
-        unsigned int key = (yy[e] < tau ? 0x80000000u : 0u) | (__float_as_uint(cost) >> 1);
-        if (a.include_user && r == 0) key = 0u;
-        keys[r] = key;
-        atomicAdd(&s_hist[key >> 21], 1u);
-      }
-    }
-  }
   __syncthreads();
   for (int i = threadIdx.x; i < kBins; i += blockDim.x)
     if (s_hist[i]) atomicAdd(&ss->hist[i], s_hist[i]);
@@ -536,6 +592,86 @@ __global__ void __launch_bounds__(128) screen_score(TickArgs a, FeatureSrc fs, c
     ss->done = 0;
   }
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) ss->hist[i] = 0;
+}
+
+// Scores every slot with the network (tau > 0), 128 slots per block and tile,
+// writes its key ((score < tau) << 31 | cost bits >> 1; slot 0, the user's
+// input, gets key 0 so it is always kept) and builds the histogram of key >> 21
+// (screen_finish).
+__global__ void __launch_bounds__(kTileRows) screen_score(TickArgs a, FeatureSrc fs,
+                                                          const InferW* w, float tau, int k,
+                                                          unsigned int* keys, ScreenScratch* ss) {
+  extern __shared__ __align__(1024) unsigned char s_score[];
+  __shared__ unsigned int s_hist[kBins];
+  __shared__ float s_feat[12];
+  __shared__ uint64_t s_bar;
+  __shared__ uint32_t s_tmem;
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
+  ScoreCtx c;
+  score_begin(w, s_score, &s_bar, &s_tmem, &c);
+  block_tick_features(fs, a.x_t, s_feat);  // ends with __syncthreads
+  float uh[2] = {__double2float_rn(a.u_h[0]), __double2float_rn(a.u_h[1])};
+  const int tiles = (a.n_slots + kTileRows - 1) / kTileRows;
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int r = t * kTileRows + (int)threadIdx.x;
+    float f[kIn], x[2];
+    candidate_value<2>(a, r < a.n_slots ? r : 0, uh, x);
+#pragma unroll
+    for (int m = 0; m < 10; ++m) f[m] = s_feat[m];
+    f[10] = x[0] / 0.4f;
+    f[11] = x[1];
+    const float y = score_tile(&c, f);
+    const bool live = r < a.n_slots;
+    unsigned int key = 0u;
+    if (live) {
+      const float d0 = __fsub_rn(x[0], uh[0]), d1 = __fsub_rn(x[1], uh[1]);
+      const float cost = __fmaf_rn(d1, d1, __fmul_rn(d0, d0));
+      key = (y < tau ? 0x80000000u : 0u) | (__float_as_uint(cost) >> 1);
+      if (a.include_user && r == 0) key = 0u;
+      keys[r] = key;
+    }
+    // one shared-memory atomic per distinct bin of the warp (neighbouring slots'
+    // costs share few bins)
+    const unsigned int bin = live ? key >> 21 : 0xFFFFFFFFu;
+    const unsigned int same = __match_any_sync(kFull, bin);
+    if (live && (threadIdx.x & 31) == (unsigned int)(__ffs(same) - 1))
+      atomicAdd(&s_hist[bin], (unsigned int)__popc(same));
+  }
+  score_end(c);
+  screen_finish(s_hist, k, ss);
+}
+
+// Cost order alone (tau <= 0; no network): warps take 16-slot tiles, lanes
+// l and l + 4 k of a group compute the same two slots and one lane per slot
+// writes its key (a small kernel keeps the instruction footprint of this path low).
+__global__ void __launch_bounds__(128) screen_cost(TickArgs a, FeatureSrc fs, int k,
+                                                  unsigned int* keys, ScreenScratch* ss) {
+  __shared__ unsigned int s_hist[kBins];
+  __shared__ float s_feat[12];
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
+  block_tick_features(fs, a.x_t, s_feat);  // ends with __syncthreads
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  float uh[2] = {__double2float_rn(a.u_h[0]), __double2float_rn(a.u_h[1])};
+  const int tiles = (a.n_slots + 15) / 16;
+  for (int t = blockIdx.x * wpb + warp; t < tiles; t += gridDim.x * wpb) {
+    if (q != 0) continue;
+    const int rr[2] = {16 * t + g, 16 * t + g + 8};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int r = rr[e];
+      if (r >= a.n_slots) continue;
+      float x[2];
+      candidate_value<2>(a, r, uh, x);
+      const float d0 = __fsub_rn(x[0], uh[0]), d1 = __fsub_rn(x[1], uh[1]);
+      const float cost = __fmaf_rn(d1, d1, __fmul_rn(d0, d0));
+      unsigned int key = __float_as_uint(cost) >> 1;
+      if (a.include_user && r == 0) key = 0u;
+      keys[r] = key;
+      atomicAdd(&s_hist[key >> 21], 1u);
+    }
+  }
+  screen_finish(s_hist, k, ss);
 }
 
 // Keeps the slots whose key bin is at or below the threshold (warp-aggregated append).
@@ -627,7 +763,7 @@ static std::vector<float> lookahead(const std::vector<double>& xy) {
 
 static int refresh_infer(mpmi_screener* s, cudaStream_t st) {
   if (!s->stale) return MPMI_OK;
-  to_infer<<<(kH * kW2S + 255) / 256, 256, 0, st>>>(s->params, s->infer);
+  to_infer<<<(kH * kH + 255) / 256, 256, 0, st>>>(s->params, s->infer);
   SCR_CUDA(cudaGetLastError(), "to_infer launch");
   s->stale = false;
   return MPMI_OK;
@@ -716,7 +852,7 @@ int mpmi_screener_create(mpmi_ctx* ctx, const mpmi_model* model, const float* we
          cudaMemset(s->ss, 0, sizeof(ScreenScratch)) == cudaSuccess;
   if (ok) {
     const int fwd = kP * sizeof(float), bwd = (kH * kH + kH) * sizeof(float);
-    const int inf = (int)sizeof(InferW);
+    const int inf = kScoreSmem;
     ok = cudaFuncSetAttribute(mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd) ==
              cudaSuccess &&
          cudaFuncSetAttribute(mlp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd) ==
@@ -824,10 +960,11 @@ int mpmi_screener_score(mpmi_screener* s, const float* feats, int32_t batch, flo
   cudaStream_t st = (cudaStream_t)stream;
   int rc = refresh_infer(s, st);
   if (rc != MPMI_OK) return rc;
-  const int tiles = (batch + 15) / 16;
-  int blocks = (tiles + 3) / 4;
-  if (blocks > 4 * s->ctx->sm_count) blocks = 4 * s->ctx->sm_count;
-  score_rows<<<blocks, 128, sizeof(InferW), st>>>(s->infer, feats, batch, scores);
+  // one 128-row tile per block and step, at most two blocks per SM (each holds
+  // 128 TMEM columns)
+  const int tiles = (batch + kTileRows - 1) / kTileRows;
+  const int blocks = tiles < 2 * s->ctx->sm_count ? tiles : 2 * s->ctx->sm_count;
+  score_rows<<<blocks, kTileRows, kScoreSmem, st>>>(s->infer, feats, batch, scores);
   SCR_CUDA(cudaGetLastError(), "score_rows launch");
   return MPMI_OK;
 }
@@ -851,11 +988,19 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
   a.x_t = x_t_dev;
   a.u_h = u_h_dev;
   a.result = result_dev;
-  const int tiles = (session->n_slots + 15) / 16;
-  int blocks = (tiles + 3) / 4;
-  if (blocks > 2 * s->ctx->sm_count) blocks = 2 * s->ctx->sm_count;
-  screen_score<<<blocks, 128, sizeof(InferW), st>>>(a, feature_src(s), s->infer, tau, k, s->keys,
-                                                    s->ss);
+  // at most two blocks per SM: with the network each holds 128 TMEM columns and
+  // the staged weights; more blocks would only repeat the per-tick features
+  if (tau > 0.f) {
+    const int tiles = (session->n_slots + kTileRows - 1) / kTileRows;
+    const int blocks = tiles < 2 * s->ctx->sm_count ? tiles : 2 * s->ctx->sm_count;
+    screen_score<<<blocks, kTileRows, kScoreSmem, st>>>(a, feature_src(s), s->infer, tau, k,
+                                                        s->keys, s->ss);
+  } else {
+    const int tiles = (session->n_slots + 15) / 16;
+    int blocks = (tiles + 3) / 4;
+    if (blocks > 2 * s->ctx->sm_count) blocks = 2 * s->ctx->sm_count;
+    screen_cost<<<blocks, 128, 0, st>>>(a, feature_src(s), k, s->keys, s->ss);
+  }
   int cb = (session->n_slots + 255) / 256;
   if (cb > 4 * s->ctx->sm_count) cb = 4 * s->ctx->sm_count;
   screen_compact<<<cb, 256, 0, st>>>(s->keys, session->n_slots, s->ss, s->list);

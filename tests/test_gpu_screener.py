@@ -212,6 +212,42 @@ def test_screened_tick_invariants(lib, setup, k, tau):
             assert a["status"] == lib.SAFE and cost[a["index"]] <= cost[b["index"]]
 
 
+def test_screen_score_network_matches_reference(lib, setup):
+    """The network inside the screened tick (tensor cores) against the float64
+    network on the same slot features: with tau at the median reference score,
+    every kept slot but the user's is predicted safe, and the cheapest slots that
+    the reference scores clearly safe are all kept (margin 0.05 for the bfloat16
+    inference)."""
+    import torch
+    ctx, env, model, scr, w0 = setup
+    w = {key: v.copy() for key, v in w0.items()}
+    w["b1"] = np.random.default_rng(4).normal(0, 0.3, 128)
+    w["w3"] = 4.0 * w["w3"]  # spread the outputs (reference std ~0.09)
+    scr.set_weights(w)
+    N, k, tick = 8000, 512, 77
+    x = _states(env, 2, 9)[2]
+    u_h = data.to_f32_exact(data.user_input_once(61, env.lo, env.hi))
+    sess = lib.Session(ctx, model, N, 60, env.lo, env.hi, seed=7)
+    feats = torch.zeros((N + 1, 12), dtype=torch.float32, device="cuda")
+    scr.features(sess, torch.tensor(x, dtype=torch.float64, device="cuda"),
+                 torch.tensor(u_h, dtype=torch.float64, device="cuda"), feats, tick=tick)
+    torch.cuda.synchronize()
+    sess.close()
+    y = osc.forward({key: data.to_f32_exact(v) for key, v in w.items()},
+                    feats.cpu().numpy().astype(np.float64))["y"]
+    tau = float(np.median(y[1:]))
+    a, b, ttv, cost, lst = _plain_and_screened(lib, ctx, env, model, scr, x, u_h, N, k, tau,
+                                               tick)
+    kept = lst[lst != 0]
+    assert len(kept) >= k - 1
+    assert np.all(y[kept] >= tau - 0.05)
+    sure = np.flatnonzero(y >= tau + 0.05)
+    sure = sure[sure != 0]
+    assert len(sure) > 1000
+    cheapest = sure[np.argsort(cost[sure], kind="stable")[:64]]
+    assert set(cheapest.tolist()) <= set(lst.tolist())
+
+
 def test_training_reduces_loss(lib, setup):
     from paper_1906_02318_gb300 import screener as drv
     ctx, env, model, scr, w0 = setup
