@@ -228,20 +228,25 @@ __global__ void to_infer(const float* P, InferW* w) {
 }
 
 // ---------------------------------------------------------------- inference (tensor cores)
-// One CTA of 128 threads scores a tile of 128 rows on the 5th-generation tensor
-// cores: thread i = row i = TMEM lane i.
-//   1. thread i writes its 12 inputs (bfloat16, padded to 16) as row i of the
-//      K-major tile A1;
+// One CTA of 256 threads scores a tile of 128 rows on the 5th-generation tensor
+// cores.  Warps w and w + 4 read TMEM lanes 32 (w % 4) .. + 31, so row i of the
+// tile (TMEM lane i) has two threads: the first half of the block takes inputs
+// 0..7 and accumulator columns 0..63 of each row, the second half inputs 8..15
+// and columns 64..127.
+//   1. each thread writes its 8 inputs (bfloat16; 12 inputs padded to 16) into row
+//      i of the K-major tile A1;
 //   2. one thread issues tcgen05.mma kind::f16 (M = N = 128, K = 16): A1 W1^T into
 //      128 TMEM columns, and commits to an mbarrier;
-//   3. thread i reads its row back (tcgen05.ld), adds b1, applies GELU and writes
-//      the 128 hidden values as row i of the bfloat16 tile A2 (K = 128);
+//   3. each thread reads its 64 columns of row i back (tcgen05.ld), adds b1,
+//      applies GELU and writes them into row i of the bfloat16 tile A2 (K = 128);
 //   4. one thread issues eight K = 16 MMAs, A2 W2^T, into the same columns;
-//   5. thread i reads its row, adds b2, applies GELU, takes the dot product with
-//      w3, adds b3 and the sigmoid.
+//   5. each thread reads its 64 columns, adds b2, applies GELU and takes the dot
+//      product with its half of w3; the two halves are added in order, then b3
+//      and the sigmoid.
 // The weights' rounding to bfloat16 and the float32 accumulation are those of
 // the network's inference form; GELU uses the hardware tanh approximation.
 constexpr int kTileRows = 128;
+constexpr int kScoreThreads = 2 * kTileRows;
 constexpr uint32_t kOffA1 = 38912;                 // after the staged InferW (38,416 B)
 constexpr uint32_t kOffA2 = kOffA1 + kTileRows * kInP * 2;
 constexpr int kScoreSmem = (int)(kOffA2 + kTileRows * kH * 2);  // 75,776 B
@@ -311,6 +316,12 @@ struct ScoreCtx {
   bool ok;
 };
 
+// Row of the tile (TMEM lane) and half of the row's columns this thread takes.
+__device__ __forceinline__ int score_row() {
+  return (int)(((threadIdx.x >> 5) & 3) * 32 + (threadIdx.x & 31));
+}
+__device__ __forceinline__ int score_half() { return (int)(threadIdx.x >> 7); }
+
 // Stages the weights and allocates the accumulator (all threads; ends synced).
 __device__ void score_begin(const InferW* w, unsigned char* smem, uint64_t* bar,
                             uint32_t* s_tmem, ScoreCtx* c) {
@@ -345,48 +356,50 @@ __device__ void score_end(const ScoreCtx& c) {
                  : "memory");
 }
 
-// The network's output for this thread's row of the tile (inputs f[0..12));
-// called by all 128 threads of the block.  After a wait that runs out the block
-// stops using the tensor cores (c->ok = false) and every row scores 1.
-__device__ float score_tile(ScoreCtx* c, const float* f) {
+// The network's output for this thread's row of the tile; f8 holds the row's
+// inputs 8 h .. 8 h + 7 (h = score_half(); inputs 12..15 are zero).  Called by
+// all 256 threads of the block; both threads of a row get the output.  After a
+// wait that runs out the block stops using the tensor cores (c->ok = false) and
+// every row scores 1.
+__device__ float score_tile(ScoreCtx* c, const float* f8) {
+  __shared__ float s_part[2][kTileRows];
   if (!c->ok) return 1.f;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int warp = (int)(threadIdx.x >> 5), row = score_row(), h = score_half();
   unsigned char* a1 = c->smem + kOffA1;
   unsigned char* a2 = c->smem + kOffA2;
   const InferW* sw = reinterpret_cast<const InferW*>(c->smem);
-  *reinterpret_cast<uint4*>(a1 + bf_off(tid, 0, kInP / 8)) =
-      make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]),
-                 pack_bf16(f[6], f[7]));
-  *reinterpret_cast<uint4*>(a1 + bf_off(tid, 8, kInP / 8)) =
-      make_uint4(pack_bf16(f[8], f[9]), pack_bf16(f[10], f[11]), 0u, 0u);
+  *reinterpret_cast<uint4*>(a1 + bf_off(row, 8 * h, kInP / 8)) =
+      make_uint4(pack_bf16(f8[0], f8[1]), pack_bf16(f8[2], f8[3]), pack_bf16(f8[4], f8[5]),
+                 pack_bf16(f8[6], f8[7]));
   tc_handoff();
   const uint32_t sa1 = smem_u32(a1), sa2 = smem_u32(a2);
   const uint32_t sw1 = smem_u32(sw->W1), sw2 = smem_u32(sw->W2);
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     mma_bf16(c->tmem, mat_desc(sa1, 128, 256), mat_desc(sw1, 128, 256), 0u);
     mma_commit(c->bar);
   }
   c->ok = mma_wait(c->bar, c->phase);
   c->phase ^= 1u;
   if (!c->ok) return 1.f;
-  const uint32_t taddr = c->tmem + ((uint32_t)(warp * 32) << 16);
+  const int col0 = 64 * h;
+  const uint32_t taddr = c->tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)col0;
 #pragma unroll
-  for (int q = 0; q < kH / 32; ++q) {
-    float h[32];
-    tmem_ld32(taddr + 32 * q, h);
+  for (int q = 0; q < 2; ++q) {
+    float v[32];
+    tmem_ld32(taddr + 32 * q, v);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      const int j = 32 * q + 8 * m;
+      const int j = col0 + 32 * q + 8 * m;
       float g[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) g[e] = gelu_fast(h[8 * m + e] + sw->b1[j + e]);
-      *reinterpret_cast<uint4*>(a2 + bf_off(tid, j, kH / 8)) =
+      for (int e = 0; e < 8; ++e) g[e] = gelu_fast(v[8 * m + e] + sw->b1[j + e]);
+      *reinterpret_cast<uint4*>(a2 + bf_off(row, j, kH / 8)) =
           make_uint4(pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]),
                      pack_bf16(g[6], g[7]));
     }
   }
   tc_handoff();
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
 #pragma unroll
     for (int kb = 0; kb < kH / 16; ++kb)
       mma_bf16(c->tmem, mat_desc(sa2 + kb * 256, 128, 2048), mat_desc(sw2 + kb * 256, 128, 2048),
@@ -398,31 +411,42 @@ __device__ float score_tile(ScoreCtx* c, const float* f) {
   if (!c->ok) return 1.f;
   float p = 0.f;
 #pragma unroll
-  for (int q = 0; q < kH / 32; ++q) {
-    float h[32];
-    tmem_ld32(taddr + 32 * q, h);
+  for (int q = 0; q < 2; ++q) {
+    float v[32];
+    tmem_ld32(taddr + 32 * q, v);
 #pragma unroll
-    for (int e = 0; e < 32; ++e) p = fmaf(sw->w3[32 * q + e], gelu_fast(h[e] + sw->b2[32 * q + e]), p);
+    for (int e = 0; e < 32; ++e) {
+      const int j = col0 + 32 * q + e;
+      p = fmaf(sw->w3[j], gelu_fast(v[e] + sw->b2[j]), p);
+    }
   }
-  return 1.f / (1.f + __expf(-(p + sw->b3)));
+  s_part[h][row] = p;
+  __syncthreads();
+  const float y = 1.f / (1.f + __expf(-((s_part[0][row] + s_part[1][row]) + sw->b3)));
+  __syncthreads();  // s_part is rewritten by the next tile
+  return y;
 }
 
 // Scores arbitrary feature rows (batch x 12), 128 rows per block and tile.
-__global__ void __launch_bounds__(kTileRows) score_rows(const InferW* w, const float* feats, int B,
-                                                        float* out) {
+__global__ void __launch_bounds__(kScoreThreads) score_rows(const InferW* w, const float* feats,
+                                                            int B, float* out) {
   extern __shared__ __align__(1024) unsigned char s_score[];
   __shared__ uint64_t s_bar;
   __shared__ uint32_t s_tmem;
   ScoreCtx c;
   score_begin(w, s_score, &s_bar, &s_tmem, &c);
+  const int row = score_row(), h = score_half();
   const int tiles = (B + kTileRows - 1) / kTileRows;
   for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int r = t * kTileRows + (int)threadIdx.x;
-    float f[kIn];
+    const int r = t * kTileRows + row;
+    float f8[8];
 #pragma unroll
-    for (int k = 0; k < kIn; ++k) f[k] = r < B ? feats[(size_t)r * kIn + k] : 0.f;
-    const float y = score_tile(&c, f);
-    if (r < B) out[r] = c.ok ? y : __int_as_float(0x7fc00000);  // NaN: the wait ran out
+    for (int e = 0; e < 8; ++e) {
+      const int k = 8 * h + e;
+      f8[e] = (r < B && k < kIn) ? feats[(size_t)r * kIn + k] : 0.f;
+    }
+    const float y = score_tile(&c, f8);
+    if (h == 0 && r < B) out[r] = c.ok ? y : __int_as_float(0x7fc00000);  // NaN: the wait ran out
   }
   score_end(c);
 }
@@ -598,7 +622,7 @@ __device__ void screen_finish(unsigned int* s_hist, int k, ScreenScratch* ss) {
 // writes its key ((score < tau) << 31 | cost bits >> 1; slot 0, the user's
 // input, gets key 0 so it is always kept) and builds the histogram of key >> 21
 // (screen_finish).
-__global__ void __launch_bounds__(kTileRows) screen_score(TickArgs a, FeatureSrc fs,
+__global__ void __launch_bounds__(kScoreThreads) screen_score(TickArgs a, FeatureSrc fs,
                                                           const InferW* w, float tau, int k,
                                                           unsigned int* keys, ScreenScratch* ss) {
   extern __shared__ __align__(1024) unsigned char s_score[];
@@ -611,31 +635,43 @@ __global__ void __launch_bounds__(kTileRows) screen_score(TickArgs a, FeatureSrc
   score_begin(w, s_score, &s_bar, &s_tmem, &c);
   block_tick_features(fs, a.x_t, s_feat);  // ends with __syncthreads
   float uh[2] = {__double2float_rn(a.u_h[0]), __double2float_rn(a.u_h[1])};
+  // the first half of the block feeds the per-tick inputs 0..7; the second half
+  // inputs 8..11 (two per-tick, the candidate's two) and writes the keys
+  const int row = score_row(), h = score_half();
   const int tiles = (a.n_slots + kTileRows - 1) / kTileRows;
   for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int r = t * kTileRows + (int)threadIdx.x;
-    float f[kIn], x[2];
-    candidate_value<2>(a, r < a.n_slots ? r : 0, uh, x);
-#pragma unroll
-    for (int m = 0; m < 10; ++m) f[m] = s_feat[m];
-    f[10] = x[0] / 0.4f;
-    f[11] = x[1];
-    const float y = score_tile(&c, f);
+    const int r = t * kTileRows + row;
     const bool live = r < a.n_slots;
-    unsigned int key = 0u;
-    if (live) {
-      const float d0 = __fsub_rn(x[0], uh[0]), d1 = __fsub_rn(x[1], uh[1]);
-      const float cost = __fmaf_rn(d1, d1, __fmul_rn(d0, d0));
-      key = (y < tau ? 0x80000000u : 0u) | (__float_as_uint(cost) >> 1);
-      if (a.include_user && r == 0) key = 0u;
-      keys[r] = key;
+    float f8[8], x[2] = {0.f, 0.f};
+    if (h == 0) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) f8[m] = s_feat[m];
+    } else {
+      candidate_value<2>(a, live ? r : 0, uh, x);
+      f8[0] = s_feat[8];
+      f8[1] = s_feat[9];
+      f8[2] = x[0] / 0.4f;
+      f8[3] = x[1];
+#pragma unroll
+      for (int m = 4; m < 8; ++m) f8[m] = 0.f;
     }
-    // one shared-memory atomic per distinct bin of the warp (neighbouring slots'
-    // costs share few bins)
-    const unsigned int bin = live ? key >> 21 : 0xFFFFFFFFu;
-    const unsigned int same = __match_any_sync(kFull, bin);
-    if (live && (threadIdx.x & 31) == (unsigned int)(__ffs(same) - 1))
-      atomicAdd(&s_hist[bin], (unsigned int)__popc(same));
+    const float y = score_tile(&c, f8);
+    if (h == 1) {  // whole warps
+      unsigned int key = 0u;
+      if (live) {
+        const float d0 = __fsub_rn(x[0], uh[0]), d1 = __fsub_rn(x[1], uh[1]);
+        const float cost = __fmaf_rn(d1, d1, __fmul_rn(d0, d0));
+        key = (y < tau ? 0x80000000u : 0u) | (__float_as_uint(cost) >> 1);
+        if (a.include_user && r == 0) key = 0u;
+        keys[r] = key;
+      }
+      // one shared-memory atomic per distinct bin of the warp (neighbouring slots'
+      // costs share few bins)
+      const unsigned int bin = live ? key >> 21 : 0xFFFFFFFFu;
+      const unsigned int same = __match_any_sync(kFull, bin);
+      if (live && (threadIdx.x & 31) == (unsigned int)(__ffs(same) - 1))
+        atomicAdd(&s_hist[bin], (unsigned int)__popc(same));
+    }
   }
   score_end(c);
   screen_finish(s_hist, k, ss);
@@ -964,7 +1000,7 @@ int mpmi_screener_score(mpmi_screener* s, const float* feats, int32_t batch, flo
   // 128 TMEM columns)
   const int tiles = (batch + kTileRows - 1) / kTileRows;
   const int blocks = tiles < 2 * s->ctx->sm_count ? tiles : 2 * s->ctx->sm_count;
-  score_rows<<<blocks, kTileRows, kScoreSmem, st>>>(s->infer, feats, batch, scores);
+  score_rows<<<blocks, kScoreThreads, kScoreSmem, st>>>(s->infer, feats, batch, scores);
   SCR_CUDA(cudaGetLastError(), "score_rows launch");
   return MPMI_OK;
 }
@@ -993,8 +1029,8 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
   if (tau > 0.f) {
     const int tiles = (session->n_slots + kTileRows - 1) / kTileRows;
     const int blocks = tiles < 2 * s->ctx->sm_count ? tiles : 2 * s->ctx->sm_count;
-    screen_score<<<blocks, kTileRows, kScoreSmem, st>>>(a, feature_src(s), s->infer, tau, k,
-                                                        s->keys, s->ss);
+    screen_score<<<blocks, kScoreThreads, kScoreSmem, st>>>(a, feature_src(s), s->infer, tau, k,
+                                                            s->keys, s->ss);
   } else {
     const int tiles = (session->n_slots + 15) / 16;
     int blocks = (tiles + 3) / 4;
