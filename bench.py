@@ -30,6 +30,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -46,6 +47,21 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 from workloads import data, plants  # noqa: E402
+
+
+class NoGC:
+    """Python's cyclic garbage collector off for a timed host loop (collected
+    once before), so that a collection pause of the interpreter is not taken for
+    a slow tick."""
+
+    def __enter__(self):
+        gc.collect()
+        self.was = gc.isenabled()
+        gc.disable()
+
+    def __exit__(self, *exc):
+        if self.was:
+            gc.enable()
 
 # ---- workload constants -----------------------------------------------------
 N_SAMPLES = 16384
@@ -316,7 +332,8 @@ def run_gpu(args, rank, world):
         return states, np.array(lat), n_fallback, trials
 
     # launched host ticks (one kernel launch per tick, zero-copy inputs/result)
-    states, lat_launched, n_fallback, trials = closed_loop()
+    with NoGC():
+        states, lat_launched, n_fallback, trials = closed_loop()
     # the same loop with persistent host ticks (a resident kernel fed through a
     # pinned mailbox); it must retrace the launched loop's states exactly
     lat_persist, persist_note, persist_same = None, "launched host ticks requested", None
@@ -326,7 +343,8 @@ def run_gpu(args, rank, world):
         except lib.MpmiError as e:
             persist_note = f"persistent host ticks unavailable: {e}"
         else:
-            states_p, lat_persist, _, _ = closed_loop()
+            with NoGC():
+                states_p, lat_persist, _, _ = closed_loop()
             sess.set_persistent(False)
             persist_same = bool(np.array_equal(states_p, states))
     lat = lat_persist if lat_persist is not None else lat_launched
@@ -514,7 +532,8 @@ def run_serving(args, bot_states):
         tuned["bot" if m == 0 else "car"] = {k: r[k] for k in ("lanes", "cands", "block",
                                                                  "n_tried", "us", "default_us")}
     streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
-    stats = serve.run([bs, cs], sessions, duration=args.serve_seconds, streams=streams)
+    with NoGC():
+        stats = serve.run([bs, cs], sessions, duration=args.serve_seconds, streams=streams)
     stats.update(sessions=n_sess, mix="half balance bot (100 Hz), half race car (60 Hz)",
                  n_range="log-uniform 1024..65536", h_range="uniform 20..100",
                  launch="one persistent graph-replayed launch per batch and model",
@@ -567,7 +586,8 @@ def run_car_loop(args):
         return states, np.array(lat[min(20, ticks // 10):]), trials, fallback
 
     # launched host ticks, then the same loop with persistent host ticks
-    states, lat_launched, trials, fallback = closed_loop()
+    with NoGC():
+        states, lat_launched, trials, fallback = closed_loop()
     lat, mode, same = lat_launched, "launched host ticks (requested)", None
     if not args.launched_host_ticks:
         try:
@@ -575,7 +595,8 @@ def run_car_loop(args):
         except lib.MpmiError as e:
             mode = f"launched host ticks (persistent unavailable: {e})"
         else:
-            states_p, lat, _, _ = closed_loop()
+            with NoGC():
+                states_p, lat, _, _ = closed_loop()
             sess.set_persistent(False)
             mode = "persistent host ticks (resident kernel, pinned mailbox)"
             same = bool(np.array_equal(states_p, states))
