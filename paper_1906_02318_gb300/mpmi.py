@@ -234,6 +234,7 @@ class Model:
 
     def __init__(self, ctx: Context, handle, basis: str, nx: int, nu: int):
         self.ctx, self.handle, self.basis, self.nx, self.nu = ctx, handle, basis, nx, nu
+        self.safety = None  # the last set_safety_set arguments (for checkpoints)
 
     def get_operator(self) -> np.ndarray:
         n = c_i32()
@@ -343,6 +344,9 @@ def set_safety_set(model: Model, lo, hi, inflation: float = 0.0, track=None,
         spec.track_x, spec.track_y = 0, 1
         spec.track_half_width = half_width
     _check(model.ctx.lib.mpmi_set_safety_set(model.handle, ctypes.byref(spec)))
+    model.safety = dict(lo=lo.copy(), hi=hi.copy(), inflation=float(inflation),
+                        track=None if keep is None else keep.copy(),
+                        half_width=float(half_width))
     del keep
 
 
@@ -392,6 +396,14 @@ class Session:
         _check(ctx.lib.mpmi_session_open(ctx.handle, model.handle, ctypes.byref(cfg),
                                          ctypes.byref(h)))
         self.ctx, self.model, self.handle = ctx, model, h
+        # the opening arguments, the noise and the rollout form (for checkpoints)
+        self.config = dict(n_samples=int(n_samples), horizon=int(horizon),
+                           input_lo=_f64(input_lo).copy(), input_hi=_f64(input_hi).copy(),
+                           include_user=bool(include_user), sampler=sampler, seed=int(seed),
+                           stream_id=int(stream_id), lanes=int(lanes), block=int(block),
+                           cands=int(cands))
+        self.noise = np.zeros(0)
+        self.rollout = "full"
         self.n_samples, self.horizon, self.include_user = n_samples, horizon, bool(include_user)
         self.n_slots = n_samples + int(include_user)
         self.nx, self.nu = model.nx, model.nu
@@ -417,12 +429,14 @@ class Session:
         sig = np.ascontiguousarray(np.atleast_1d(np.asarray(sigma, dtype=np.float64)))
         _check(self.ctx.lib.mpmi_session_set_noise(
             self.handle, sig.ctypes.data_as(P_dbl), int(sig.size)))
+        self.noise = sig.copy()
 
     def set_rollout(self, mode: str):
         """mpmi_session_set_rollout: "full" (z <- K z, Alg. 2, CUDA cores),
         "tensor" (the same on tcgen05 tensor cores, race car) or "factored"
         (read-outs from precomputed rows C K^t; an exact-in-real-arithmetic ablation)."""
         _check(self.ctx.lib.mpmi_session_set_rollout(self.handle, ROLLOUT[mode]))
+        self.rollout = mode
 
     def set_persistent(self, on: bool = True, idle_ms: float = 0.0):
         """mpmi_session_set_persistent: host ticks run in a resident kernel fed
