@@ -30,7 +30,6 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 from __future__ import annotations
 
 import argparse
-import gc
 import hashlib
 import json
 import os
@@ -47,21 +46,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 from workloads import data, plants  # noqa: E402
-
-
-class NoGC:
-    """Python's cyclic garbage collector off for a timed host loop (collected
-    once before), so that a collection pause of the interpreter is not taken for
-    a slow tick."""
-
-    def __enter__(self):
-        gc.collect()
-        self.was = gc.isenabled()
-        gc.disable()
-
-    def __exit__(self, *exc):
-        if self.was:
-            gc.enable()
+from paper_1906_02318_gb300 import metrics  # noqa: E402
 
 # ---- workload constants -----------------------------------------------------
 N_SAMPLES = 16384
@@ -308,7 +293,7 @@ def run_gpu(args, rank, world):
     # closed loop through the host C-ABI (e2e): W warm-up ticks, then timed ticks.
     # As in the paper's trials, a trial ends when the plant leaves the safe set
     # and the next one starts from x_0.
-    def closed_loop():
+    def closed_loop(recs=None):
         x_t = X0.copy()
         states = np.empty((ticks, 4))
         lat = []
@@ -326,14 +311,17 @@ def run_gpu(args, rank, world):
             x_t = plants.cartpole_step(x_t, r["u_r"])
             inside = np.all(np.isfinite(x_t)) and np.all(x_t > data.BOT_SAFE_LO) and \
                 np.all(x_t < data.BOT_SAFE_HI)
+            if recs is not None and t >= args.warmup:
+                recs.append(metrics.tick_record(r, uhs[t], t, trials - 1, N_SAMPLES,
+                                                latency_s=dt, failed=not inside))
             if not inside:
                 x_t = X0.copy()
                 trials += 1
         return states, np.array(lat), n_fallback, trials
 
     # launched host ticks (one kernel launch per tick, zero-copy inputs/result)
-    with NoGC():
-        states, lat_launched, n_fallback, trials = closed_loop()
+    recs_launched, recs_persist = [], []
+    states, lat_launched, n_fallback, trials = closed_loop(recs_launched)
     # the same loop with persistent host ticks (a resident kernel fed through a
     # pinned mailbox); it must retrace the launched loop's states exactly
     lat_persist, persist_note, persist_same = None, "launched host ticks requested", None
@@ -343,12 +331,15 @@ def run_gpu(args, rank, world):
         except lib.MpmiError as e:
             persist_note = f"persistent host ticks unavailable: {e}"
         else:
-            with NoGC():
-                states_p, lat_persist, _, _ = closed_loop()
+            states_p, lat_persist, _, _ = closed_loop(recs_persist)
             sess.set_persistent(False)
             persist_same = bool(np.array_equal(states_p, states))
     lat = lat_persist if lat_persist is not None else lat_launched
     e2e_rate = n_slots * HORIZON * len(lat) / lat.sum()
+    # the paper's run metrics (Sec. VI, Table I) over the timed closed loop
+    paper_metrics = metrics.summarize(recs_persist if lat_persist is not None else recs_launched,
+                                      plants.BOT_DT)
+    paper_metrics["eq2_bound"] = 2.0 / (2 * N_SAMPLES)  # lambda*(U) / (2N), 1-D input box
 
     # device-resident ticks: inputs in HBM, L2 flushed before each timed tick
     xs = torch.tensor(states, dtype=torch.float64, device=dev)
@@ -413,6 +404,7 @@ def run_gpu(args, rank, world):
                 persist_note=persist_note, persist_same=persist_same,
                 wall=wall, clocks=clk, lanes=lanes, cands=cands, block=block, n_slots=n_slots,
                 residual=residual, n_fallback=int(n_fallback), trials=trials, states=states,
+                paper_metrics=paper_metrics,
                 ffma_tflops=ffma_tflops, tuned=tuned,
                 sm_count=props.multi_processor_count,
                 gpu_name=props.name)
@@ -532,8 +524,7 @@ def run_serving(args, bot_states):
         tuned["bot" if m == 0 else "car"] = {k: r[k] for k in ("lanes", "cands", "block",
                                                                  "n_tried", "us", "default_us")}
     streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
-    with NoGC():
-        stats = serve.run([bs, cs], sessions, duration=args.serve_seconds, streams=streams)
+    stats = serve.run([bs, cs], sessions, duration=args.serve_seconds, streams=streams)
     stats.update(sessions=n_sess, mix="half balance bot (100 Hz), half race car (60 Hz)",
                  n_range="log-uniform 1024..65536", h_range="uniform 20..100",
                  launch="one persistent graph-replayed launch per batch and model",
@@ -569,7 +560,7 @@ def run_car_loop(args):
     sess = lib.Session(ctx, model, N, H, lo, hi, seed=CAR_SEED)
     stream = torch.cuda.current_stream(dev)
 
-    def closed_loop():
+    def closed_loop(recs=None):
         xt, states, lat = x0.copy(), np.empty((ticks, 6)), []
         trials, fallback = 1, 0
         for t in range(ticks):
@@ -580,14 +571,18 @@ def run_car_loop(args):
             lat.append(time.perf_counter() - t0)
             fallback += r["status"] == lib.FALLBACK
             xt = plants.bicycle_step(xt, r["u_r"])
-            if not car_in_safe_set(xt, track, data.CAR_TRACK_HALF_WIDTH, 25.0):
+            inside = car_in_safe_set(xt, track, data.CAR_TRACK_HALF_WIDTH, 25.0)
+            if recs is not None and t >= min(20, ticks // 10):
+                recs.append(metrics.tick_record(r, uhs[t], t, trials - 1, N,
+                                                latency_s=lat[-1], failed=not inside))
+            if not inside:
                 xt = x0.copy()
                 trials += 1
         return states, np.array(lat[min(20, ticks // 10):]), trials, fallback
 
     # launched host ticks, then the same loop with persistent host ticks
-    with NoGC():
-        states, lat_launched, trials, fallback = closed_loop()
+    recs_l, recs_p = [], []
+    states, lat_launched, trials, fallback = closed_loop(recs_l)
     lat, mode, same = lat_launched, "launched host ticks (requested)", None
     if not args.launched_host_ticks:
         try:
@@ -595,8 +590,7 @@ def run_car_loop(args):
         except lib.MpmiError as e:
             mode = f"launched host ticks (persistent unavailable: {e})"
         else:
-            with NoGC():
-                states_p, lat, _, _ = closed_loop()
+            states_p, lat, _, _ = closed_loop(recs_p)
             sess.set_persistent(False)
             mode = "persistent host ticks (resident kernel, pinned mailbox)"
             same = bool(np.array_equal(states_p, states))
@@ -632,6 +626,7 @@ def run_car_loop(args):
                       "autotuned": {"n_tried": tuned["n_tried"], "winner_us": tuned["us"],
                                     "default_shape_us": tuned["default_us"]}},
             "ticks": ticks, "trials": trials, "fallback_ticks": int(fallback),
+            "paper_metrics": metrics.summarize(recs_p if recs_p else recs_l, plants.CAR_DT),
             "device_mean_us": durs.mean() * 1e6, "device_p99_us": np.percentile(durs, 99) * 1e6,
             "rollout_steps_per_s": (N + 1) * H / durs.mean(),
             "executed_steps_per_s": executed.mean() / durs.mean(),
@@ -852,6 +847,7 @@ def main():
                      "frac_of_ffma_loop": achieved / out["ffma_tflops"]},
         "clocks": out["clocks"],
         "fallback_ticks": out["n_fallback"], "trials": out["trials"],
+        "paper_metrics": out["paper_metrics"],
     }
     if rank == 0 and args.learned_ticks > 0:
         line["learned"] = run_learned(args)
