@@ -390,6 +390,17 @@ int mpmi_debug_withhold_staging(mpmi_session* s, int32_t on);
 int mpmi_debug_track_query(const double* track_xy, int32_t n_track, double half_width,
                            const float* points, int64_t n_points, uint8_t* on_road);
 
+/* Test hook for Alg. 2's sampling step: the generator the candidates come from is
+ * Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11).  For each of n records of
+ * six uint32 words (counter c0 c1 c2 c3, key k0 k1; records_dev, device, n x 6)
+ * writes the four output words of the device's generator to words_dev (device,
+ * n x 4 uint32), so the device function can be checked against the published
+ * known-answer vectors.  Buffers 4-byte aligned and caller-owned.  Asynchronous
+ * on `stream`.  INVALID_ARG for NULL buffers, misalignment or n outside
+ * [0, 2^30]; CUDA if the launch fails. */
+int mpmi_debug_philox(const uint32_t* records_dev, int64_t n, uint32_t* words_dev,
+                      void* stream);
+
 /* Measured FP32 FMA throughput of CUDA device `device` (not part of the method;
  * the denominator of the tick kernels' ALU roofline): every resident warp runs
  * eight independent FMA chains for about `seconds` (0 < seconds <= 10); the
@@ -524,7 +535,8 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
  * the same tick as mpmi_evaluate_candidates_device without a session and calls
  * no cudaMalloc, cudaFree or other allocating routine.
  *   basis          the lifted basis (as for mpmi_model_from_operator)
- *   K_dev          device, n x n float32 row-major operator (caller-owned)
+ *   K_dev          device, n x n float32 row-major operator (caller-owned),
+ *                  16-byte aligned
  *   spec           host; per-coordinate box and inflation only: track_xy must be
  *                  NULL (a track needs the grid a model allocates)
  *   cfg            host; N, H, include_user, sampler (UNIFORM or EXTERNAL),
@@ -538,7 +550,12 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
  * MPMI_E_INVALID_ARG and a message giving the limit.  All calls share that array:
  * calls whose kernels overlap on the GPU race and must not be issued (keep them on
  * one stream).  The first call on each device looks up the array's address; make
- * it before any stream capture begins.  Returns without waiting. */
+ * it before any stream capture begins, and do not cudaDeviceReset a device the
+ * library is in use on (the looked-up address dies with the module).
+ * Alignment: K_dev must be 16-byte aligned (the register-resident launch shapes
+ * read it as float4), x_t_dev, u_h_dev and result_dev 8-byte aligned,
+ * candidates_dev 4-byte aligned; otherwise MPMI_E_INVALID_ARG before any CUDA
+ * call.  Returns without waiting. */
 int mpmi_evaluate_candidates_noalloc(const mpmi_basis_desc* basis, const float* K_dev,
                                      const mpmi_safety_spec* spec,
                                      const mpmi_session_config* cfg, const double* x_t_dev,

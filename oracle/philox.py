@@ -14,10 +14,11 @@ Definition used (4 words of 32 bits, 2 key words, 10 rounds):
   * M0 = 0xD2511F53, M1 = 0xCD9E8D57, W0 = 0x9E3779B9 (golden ratio),
     W1 = 0xBB67AE85 (sqrt(3) - 1).
 
-Pins: the generator's bit pattern cannot be checked against the paper's
-known-answer vectors (not available here); tests pin the property the method
-needs (uniform, independent words, full avalanche on counter and key) and the
-64-bit product split against Python integers.
+Pins: the published known-answer vectors of Philox4x32-10 (Random123, the
+library that accompanies the SC'11 paper; tests/golden/philox4x32_10_kat.json)
+fix the whole bit pattern; tests also pin the one- and two-round forms, the
+64-bit product split against Python integers and the statistical properties the
+method needs (uniform, independent words, full avalanche on counter and key).
 """
 from __future__ import annotations
 

@@ -358,6 +358,20 @@ static int model_upload(mpmi_ctx* ctx, mpmi_model* m) {
   return MPMI_OK;
 }
 
+// Test hook: the raw Philox4x32-10 words of n (counter, key) records, each six
+// words c0 c1 c2 c3 k0 k1, through the same device function the sampler uses.
+static __global__ void philox_words_kernel(const uint32_t* __restrict__ in, int64_t n,
+                                           uint32_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t* r = in + 6 * i;
+  const U32x4 w = philox4x32_10(U32x4{r[0], r[1], r[2], r[3]}, r[4], r[5]);
+  out[4 * i + 0] = w.x;
+  out[4 * i + 1] = w.y;
+  out[4 * i + 2] = w.z;
+  out[4 * i + 3] = w.w;
+}
+
 }  // namespace mpmi
 
 using namespace mpmi;
@@ -1211,6 +1225,23 @@ int mpmi_sample_candidates(mpmi_session* s, const double* u_h_dev, const float* 
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "sample kernel launch");
+  return MPMI_OK;
+}
+
+int mpmi_debug_philox(const uint32_t* records_dev, int64_t n, uint32_t* words_dev,
+                      void* stream) {
+  if (n < 0 || n > (int64_t(1) << 30))
+    return fail(MPMI_E_INVALID_ARG, "debug_philox: n out of range");
+  if (n == 0) return MPMI_OK;
+  if (!records_dev || !words_dev) return fail(MPMI_E_INVALID_ARG, "debug_philox: NULL argument");
+  if ((reinterpret_cast<uintptr_t>(records_dev) | reinterpret_cast<uintptr_t>(words_dev)) & 3)
+    return fail(MPMI_E_INVALID_ARG, "debug_philox: buffers must be 4-byte aligned");
+  const int block = 256;
+  const int64_t grid = (n + block - 1) / block;
+  philox_words_kernel<<<(unsigned)grid, block, 0, (cudaStream_t)stream>>>(records_dev, n,
+                                                                            words_dev);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "philox kernel launch");
   return MPMI_OK;
 }
 

@@ -26,7 +26,13 @@
 //
 // Set-up: the first call on each device looks up the array's device address
 // with cudaGetSymbolAddress, with that device current, and caches it.  Make the
-// first call on a device before any stream capture begins.
+// first call on a device before any stream capture begins.  A cudaDeviceReset
+// destroys the module and with it the cached address: do not reset a device
+// while the library is in use on it.
+//
+// Alignment: K_dev 16 bytes (read as float4 by the register-resident shapes),
+// x_t_dev, u_h_dev and result_dev 8 bytes, candidates_dev 4 bytes; a misaligned
+// buffer is refused before any CUDA call.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -111,6 +117,20 @@ extern "C" int mpmi_evaluate_candidates_noalloc(
     const float* candidates_dev, uint64_t tick, mpmi_result* result_dev, void* stream) {
   if (!basis || !K_dev || !spec || !cfg || !x_t_dev || !u_h_dev || !result_dev)
     return fail(MPMI_E_INVALID_ARG, "evaluate_candidates_noalloc: NULL argument");
+  // The register-resident shapes read K as float4 and the kernel reads x_t, u_h
+  // and writes the result as 8-byte words: a misaligned caller buffer would be a
+  // misaligned-address fault on the device, so refuse it here, before any CUDA call.
+  if (reinterpret_cast<uintptr_t>(K_dev) & 15)
+    return fail(MPMI_E_INVALID_ARG,
+                "evaluate_candidates_noalloc: K_dev must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(x_t_dev) | reinterpret_cast<uintptr_t>(u_h_dev) |
+       reinterpret_cast<uintptr_t>(result_dev)) & 7)
+    return fail(MPMI_E_INVALID_ARG,
+                "evaluate_candidates_noalloc: x_t_dev, u_h_dev and result_dev must be 8-byte "
+                "aligned");
+  if (reinterpret_cast<uintptr_t>(candidates_dev) & 3)
+    return fail(MPMI_E_INVALID_ARG,
+                "evaluate_candidates_noalloc: candidates_dev must be 4-byte aligned");
   const int kind = basis_kind(basis->basis, basis->nx, basis->nu);
   if (kind < 0) return fail(MPMI_E_UNSUPPORTED, "evaluate_candidates_noalloc: basis not compiled");
   int n, nx, nu, np;

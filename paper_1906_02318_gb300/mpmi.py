@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libmpmi.so")
 
 BASIS = {"bot": 0, "car": 1, "linear": 2}
 BASIS_DIMS = {"bot": (4, 1), "car": (6, 2)}
+BASIS_SIZE = {"bot": 12, "car": 32}   # lifted dimension n; the linear basis has nx + nu
 SAMPLER = {"uniform": 0, "grid": 1, "external": 2}
 ROLLOUT = {"full": 0, "factored": 1, "tensor": 2}
 SAFE, FALLBACK, TIMEOUT = 0, 1, 2
@@ -98,6 +99,7 @@ _SIGNATURES = {
     "mpmi_fit_operator_sparse": (c_i32, [ctypes.POINTER(BasisDesc), c_vp, c_vp, c_vp, c_i64,
                                           c_dbl, c_dbl, c_i32, c_vp, c_vp, P_dbl]),
     "mpmi_debug_track_query": (c_i32, [P_dbl, c_i32, c_dbl, c_vp, c_i64, c_vp]),
+    "mpmi_debug_philox": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
     "mpmi_session_launch_shape": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32),
                                           ctypes.POINTER(c_i32)]),
     "mpmi_evaluate_candidates": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_vp]),
@@ -180,6 +182,25 @@ def _stream(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _require(t, name, itemsize, min_numel, dtype=None):
+    """Check a caller's CUDA tensor before its address crosses the C ABI: on the
+    current device, contiguous, of the element size (and dtype) the entry point
+    reads, with at least min_numel elements."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor")
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: must live on the current CUDA device")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if t.element_size() != itemsize:
+        raise TypeError(f"{name}: expected {itemsize}-byte elements, got {t.dtype}")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name}: needs at least {min_numel} elements, has {t.numel()}")
 
 
 def _f64(a, n=None):
@@ -507,6 +528,17 @@ def sample_candidates(s: Session, out_dev, u_h_dev=None, candidates=None, tick: 
                                             _ptr(out_dev), _stream(stream)))
 
 
+def debug_philox(records_dev, words_dev, stream=None):
+    """mpmi_debug_philox: raw Philox4x32-10 words of the device generator.
+    records_dev: int32/uint32 CUDA tensor (n, 6) = c0 c1 c2 c3 k0 k1;
+    words_dev: (n, 4) of the same 4-byte type."""
+    import torch
+    n = records_dev.shape[0]
+    _require(records_dev, "records_dev", 4, 6 * n)
+    _require(words_dev, "words_dev", 4, 4 * n)
+    _check(load().mpmi_debug_philox(_ptr(records_dev), n, _ptr(words_dev), _stream(stream)))
+
+
 def debug_trajectories(s: Session, x_t_dev, u_h_dev, result_dev, traj_dev, candidates=None,
                        tick: int = 0, ttv_dev=None, cost_dev=None, stream=None):
     """mpmi_debug_trajectories: a tick that also records every predicted z_t."""
@@ -540,6 +572,17 @@ def evaluate_candidates_noalloc(basis: str, K_dev, lo, hi, n_samples: int, horiz
         cfg.input_lo[j] = ilo[j] if j < ilo.size else 0.0
         cfg.input_hi[j] = ihi[j] if j < ihi.size else 1.0
     cfg.seed, cfg.stream_id, cfg.lanes, cfg.block = seed, stream_id, lanes, block
+    import torch
+    n = BASIS_SIZE[basis] if basis in BASIS_SIZE else d.nx + d.nu
+    _require(K_dev, "K_dev", 4, n * n, torch.float32)
+    if K_dev.numel() != n * n:
+        raise ValueError(f"K_dev: expected {n} x {n} values, got {K_dev.numel()}")
+    _require(x_t_dev, "x_t_dev", 8, d.nx, torch.float64)
+    _require(u_h_dev, "u_h_dev", 8, d.nu, torch.float64)
+    _require(result_dev, "result_dev", result_dev.element_size(),
+             -(-RESULT_BYTES // result_dev.element_size()))
+    if candidates is not None:
+        _require(candidates, "candidates", 4, n_samples * d.nu, torch.float32)
     _check(lib.mpmi_evaluate_candidates_noalloc(
         ctypes.byref(d), _ptr(K_dev), ctypes.byref(spec), ctypes.byref(cfg), _ptr(x_t_dev),
         _ptr(u_h_dev), _ptr(candidates), tick, _ptr(result_dev), _stream(stream)))

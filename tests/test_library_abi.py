@@ -122,3 +122,33 @@ def test_host_sparse_fit_errors(lib):
         with pytest.raises(lib.MpmiError) as e:
             lib.fit_operator_sparse("bot", x, u, xn, **kw)
         assert e.value.code == code
+
+
+def test_noalloc_refuses_misaligned_buffers_before_any_cuda_call(lib):
+    """mpmi_evaluate_candidates_noalloc reads K as float4 in its register-resident
+    shapes: a K pointer that is not 16-byte aligned (a view such as buf[1:]) is
+    refused on the host.  The pointers below are never dereferenced: the check
+    comes before any CUDA call, so this runs without a GPU."""
+    so = lib.load()
+    d = lib.BasisDesc(lib.BASIS["bot"], 4, 1)
+    spec = lib.SafetySpecC()
+    for j in range(lib.MAX_NX):
+        spec.state_lo[j], spec.state_hi[j] = -1.0, 1.0
+    cfg = lib.SessionConfig()
+    cfg.n_samples, cfg.horizon, cfg.include_user = 1024, 20, 1
+    cfg.input_lo[0], cfg.input_hi[0] = -1.0, 1.0
+    base = 0x7f0000000000
+    ok8, ok16 = base + 0x100, base + 0x200
+
+    def call(K, xt=ok8, uh=ok8, res=ok8, cand=None):
+        return so.mpmi_evaluate_candidates_noalloc(
+            ctypes.byref(d), ctypes.c_void_p(K), ctypes.byref(spec), ctypes.byref(cfg),
+            ctypes.c_void_p(xt), ctypes.c_void_p(uh),
+            None if cand is None else ctypes.c_void_p(cand), 0, ctypes.c_void_p(res), None)
+
+    for off in (4, 8, 12):
+        assert call(ok16 + off) == -1
+        assert "16-byte" in so.mpmi_last_error().decode()
+    assert call(ok16, xt=ok8 + 4) == -1 and "8-byte" in so.mpmi_last_error().decode()
+    assert call(ok16, res=ok8 + 4) == -1 and "8-byte" in so.mpmi_last_error().decode()
+    assert call(ok16, cand=ok8 + 2) == -1 and "4-byte" in so.mpmi_last_error().decode()

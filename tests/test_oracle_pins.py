@@ -32,6 +32,25 @@ def test_mulhilo_matches_python_integers():
             assert h == p >> 32 and l == p & 0xFFFFFFFF
 
 
+def _philox_kat():
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.json")) as f:
+        cases = json.load(f)["cases"]
+    return [([int(w, 16) for w in c["counter"]], [int(w, 16) for w in c["key"]],
+             [int(w, 16) for w in c["expected"]]) for c in cases]
+
+
+def test_philox_known_answer_vectors():
+    # The published known answers fix the whole generator: the multipliers, the
+    # round function's word order, the Weyl key schedule and the round count.
+    for ctr, key, want in _philox_kat():
+        got = philox.philox4x32(*ctr, *key)
+        assert [int(v) for v in got] == want
+    # nine or eleven rounds miss every vector
+    for rounds in (9, 11):
+        for ctr, key, want in _philox_kat():
+            assert [int(v) for v in philox.philox4x32(*ctr, *key, rounds=rounds)] != want
+
+
 def test_philox_single_round_zero_counter_is_key_placement():
     # With a zero counter both products vanish, so one round leaves only the key
     # words in positions 0 and 2 (definition of the round function).
