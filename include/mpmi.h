@@ -510,21 +510,26 @@ int mpmi_screener_train_step(mpmi_screener* s, const float* features_dev,
  * bfloat16 weights and activations on tensor cores with float32 accumulation. */
 int mpmi_screener_score(mpmi_screener* s, const float* features_dev, int32_t batch,
                         float* scores_dev, void* stream);
-/* A screened tick: score every slot of the session's tick, keep the slots whose
- * (score < tau, cost) key falls at or below the histogram bin where k slots are
- * reached (slot 0, the user's input, is always kept), run the exact rollout on
- * those, and -- on the device, with no host round trip -- fall back to the full
- * evaluation when none of them is safe.  result_dev's reserved word carries
- * flags: bit 0 the screened set was evaluated, bit 1 the full evaluation ran.
- * list_dev (optional, n_slots int32) receives the screened slots and
- * n_list_dev (optional, one int32) their number.  tau <= 0 skips the network and
- * keeps the k cheapest slots: an exact cost-ordered search (the kept slots either
- * contain the least-cost safe candidate or are all cheaper than it and unsafe,
- * which triggers the full evaluation). */
+/* A screened tick (exact): roll out a prefix of the tick's cost order (least
+ * ||xi - u_h||^2 first), cut between two cost bins (the float32 exponent and the
+ * top three mantissa bits of the cost), so that every slot left out costs more
+ * than every slot kept.  The prefix is the shortest one holding at least k slots
+ * and, with the network (tau > 0), at least m slots the network predicts safe
+ * (score >= tau); tau <= 0 skips the network (the k cheapest slots, the exact
+ * cost-ordered search).  The kept slots go through the exact rollout; if none of
+ * them is safe and they are not every slot, the full evaluation runs on the
+ * device with no host round trip.  Either the kept slots contain the least-cost
+ * safe candidate of the whole tick or they are all unsafe, so the selection is
+ * always the exhaustive one: the network decides only how far down the cost
+ * order the tick goes.  result_dev's reserved word carries flags: bit 0 the
+ * screened set was evaluated, bit 1 the full evaluation ran; executed_steps
+ * counts the steps of both launches, n_slots the slots of the last.  list_dev
+ * (optional, n_slots int32) receives the kept slots and n_list_dev (optional,
+ * one int32) their number.  INVALID_ARG for k < 1, or m < 1 with tau > 0. */
 int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double* x_t_dev,
                            const double* u_h_dev, uint64_t tick, int32_t k, float tau,
-                           mpmi_result* result_dev, int32_t* list_dev, int32_t* n_list_dev,
-                           void* stream);
+                           int32_t m, mpmi_result* result_dev, int32_t* list_dev,
+                           int32_t* n_list_dev, void* stream);
 
 /* ---- a tick that allocates nothing -------------------------------------- */
 /* The paper has no counterpart to this entry point; it serves callers that may

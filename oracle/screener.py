@@ -5,7 +5,9 @@ time to violation ttv / H of Alg. 2's prediction, so that only the most
 promising candidates need the exact rollout.  This module is the plain
 statement of what the CUDA screener computes: its input features, the network
 (12 -> 128 -> 128 -> 1, GELU, sigmoid output), the squared-error loss, the
-backward pass by the chain rule, one Adam step, and the screening rule.
+backward pass by the chain rule, one Adam step, and the screening rule (which
+slots a screened tick rolls out exactly: a prefix of the cost order whose length
+the network sets, so that the selection is always the exhaustive one).
 
 The hidden activation is GELU in its tanh form (Hendrycks & Gimpel 2016).
 
@@ -160,9 +162,38 @@ def adam_step(params: dict, grads: dict, state: dict, step: int, lr: float = 1e-
 
 
 # ------------------------------------------------------------------ screening rule
-def screen(scores: np.ndarray, cost: np.ndarray, k: int, tau: float) -> np.ndarray:
-    """Slots of the k candidates with the smallest (predicted unsafe, cost, slot):
-    predicted-safe (score >= tau) candidates first, each group by cost."""
-    slot = np.arange(len(scores))
-    order = np.lexsort((slot, cost, (scores < tau).astype(np.int64)))
-    return order[:k]
+BIN_SHIFT = 20  # cost bins: float32 exponent and the top three mantissa bits
+
+
+def cost_bin(cost) -> np.ndarray:
+    """Bin of a candidate's cost (>= 0) in the screened tick: the bits of the
+    cost as a float32 shifted right by BIN_SHIFT.  For non-negative floats the bit
+    pattern is monotone in the value, so bins never invert the cost order."""
+    c = np.ascontiguousarray(np.asarray(cost, dtype=np.float32))
+    return (c.view(np.uint32) >> np.uint32(BIN_SHIFT)).astype(np.int64)
+
+
+def screen(scores: np.ndarray, cost: np.ndarray, k: int, tau: float, m: int = 1) -> np.ndarray:
+    """Slots a screened tick rolls out, ascending: the shortest prefix of the cost
+    order, cut between cost bins, that holds at least k slots and -- when tau > 0
+    -- at least m slots the network predicts safe (score >= tau); every slot when
+    no prefix does.  Every slot left out costs more than every slot kept."""
+    b = cost_bin(cost)
+    safe = np.asarray(scores) >= tau
+    for edge in np.unique(b):  # ascending
+        inside = b <= edge
+        if inside.sum() >= k and (tau <= 0 or np.count_nonzero(inside & safe) >= m):
+            return np.flatnonzero(inside)
+    return np.arange(len(b))
+
+
+def screened_selection(ttv: np.ndarray, cost: np.ndarray, kept: np.ndarray, H: int) -> int:
+    """Slot a screened tick selects from the exact rollout of the kept slots: the
+    least (cost, slot) safe kept slot; when none is safe, the full evaluation's
+    choice over all slots (least (H - ttv, cost, slot))."""
+    kept = np.asarray(kept)
+    safe = kept[np.asarray(ttv)[kept] == H]
+    if len(safe):
+        return int(safe[np.lexsort((safe, np.asarray(cost)[safe]))[0]])
+    slot = np.arange(len(ttv))
+    return int(np.lexsort((slot, cost, H - np.asarray(ttv)))[0])

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) factored_kernel(const __grid_constant__ T
   __shared__ float s_f[N][4];  // split of the lifting at x_t: a_j, b_1j, b_2j, b_3j
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (a.skip_if_safe != nullptr && a.skip_if_safe->status == MPMI_SAFE) return;
+  if (fallback_not_needed(a)) return;
   const int n_eval = a.n_list ? *a.n_list : a.n_slots;
   const int H = a.horizon, ro_n = a.ro_n;
 

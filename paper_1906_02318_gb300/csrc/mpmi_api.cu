@@ -268,9 +268,11 @@ int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, i
     s->tail_pending = false;
   }
   int lanes = s->lanes, cands = s->cands, block = s->block;
-  // a device-side list short enough that 8 lanes per candidate still fit one wave
-  const bool small = a.slot_list != nullptr && n_hint > 0 &&
-                     (long long)n_hint * 8 <= (long long)s->ctx->sm_count * 512;
+  // a device-side list short enough that 8 lanes per candidate still fit one wave;
+  // n_hint < 0: a list of unknown length (grid for every slot, idle blocks leave)
+  const bool small = a.slot_list != nullptr &&
+                     (n_hint < 0 || (n_hint > 0 && (long long)n_hint * 8 <=
+                                                       (long long)s->ctx->sm_count * 512));
   if (s->rollout == MPMI_ROLLOUT_TENSOR) {
     if (a.n_noise > 0 && a.tick >= (1ull << 48))
       return fail(MPMI_E_INVALID_ARG, "ticks with noise must stay below 2^48");

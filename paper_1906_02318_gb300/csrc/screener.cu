@@ -24,7 +24,10 @@ constexpr int kH = 128, kIn = 12, kInP = 16;
 constexpr int oW1 = 0, ob1 = kH * kIn, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, ow3 = ob2 + kH,
               ob3 = ow3 + kH, kP = ob3 + 1;
 static_assert(kP == MPMI_SCREENER_PARAMS, "packed weight layout");
-constexpr int kBins = 2048;  // histogram of (predicted unsafe, cost) keys: key >> 21
+// histograms of the screened tick over cost bins: float32 bits of a cost >= 0
+// shifted right by kBinShift (sign 0, exponent, three mantissa bits) < kBins
+constexpr int kBins = 2048;
+constexpr int kBinShift = 20;
 constexpr float kGeluC = 0.7978845608028654f, kGeluA = 0.044715f;
 
 // bfloat16 inference copy of the weights, laid out as the tensor cores' B operands:
@@ -48,7 +51,8 @@ __host__ __device__ constexpr uint32_t bf_off(int row, int k, int kc) {
 }
 
 struct ScreenScratch {
-  unsigned int hist[kBins];
+  unsigned int hist[kBins];       // all slots per cost bin
+  unsigned int hist_safe[kBins];  // predicted-safe slots per cost bin
   unsigned int done;  // score blocks finished
   int bstar;          // threshold bin
   int n_list;         // kept slots
@@ -548,28 +552,21 @@ __global__ void slot_features(TickArgs a, FeatureSrc fs, float* out) {
 }
 
 // ---------------------------------------------------------------- screened tick
-// End of a scoring launch (every thread of the block): this block's histogram
-// into the tick's, and the last block finds the smallest bin where k slots are
-// reached, then clears the histogram and the list counter for the next tick.
-__device__ void screen_finish(unsigned int* s_hist, int k, ScreenScratch* ss) {
-  __shared__ int s_last;
-  __syncthreads();
-  for (int i = threadIdx.x; i < kBins; i += blockDim.x)
-    if (s_hist[i]) atomicAdd(&ss->hist[i], s_hist[i]);
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(&ss->done, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  // last block: find the first bin where the inclusive count reaches k.  The
-  // histogram is copied to shared memory, each thread sums a run of bins, the run
-  // sums are scanned, and the thread whose run crosses k walks it.
+// Which slots a screened tick rolls out: a prefix of the cost order, cut between
+// two cost bins (bin = float32 bits of the cost >> kBinShift: the exponent and
+// the top three mantissa bits, monotone in the cost), so that every slot left
+// out costs strictly more than every slot kept.  The prefix is the shortest one
+// that holds at least k slots and -- with the network (tau > 0) -- at least m
+// slots the network predicts safe (score >= tau).  Whatever the scores, the kept
+// slots either contain the least-cost safe candidate of the whole tick or are all
+// unsafe (then the full evaluation runs): the selection is always the exhaustive
+// one.  The network only decides how far down the cost order to go.
+
+// One histogram: the first bin at which the inclusive count reaches `target`, or
+// kBins - 1 if it never does (whole block; s_hist in shared memory).
+__device__ int first_bin_reaching(const unsigned int* s_hist, unsigned int target,
+                                  unsigned int* s_run, int* s_bin) {
   constexpr int kRun = kBins / 128;
-  for (int i = threadIdx.x; i < kBins; i += blockDim.x)
-    s_hist[i] = *reinterpret_cast<volatile unsigned int*>(&ss->hist[i]);
-  __shared__ unsigned int s_run[128];
-  __syncthreads();
   unsigned int run = 0;
   if (threadIdx.x < 128)
     for (int i = 0; i < kRun; ++i) run += s_hist[threadIdx.x * kRun + i];
@@ -596,41 +593,90 @@ __device__ void screen_finish(unsigned int* s_hist, int k, ScreenScratch* ss) {
       before += v[j];
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) ss->bstar = kBins - 1;  // fewer than k slots in total: keep all
+  if (threadIdx.x == 0) *s_bin = kBins - 1;  // never reached: keep everything
   __syncthreads();
   if (threadIdx.x < 128) {
     unsigned int cum = s_run[threadIdx.x];
-    if (cum < (unsigned int)k) {
+    if (cum < target) {
       for (int i = 0; i < kRun; ++i) {
         cum += s_hist[threadIdx.x * kRun + i];
-        if (cum >= (unsigned int)k) {
-          ss->bstar = threadIdx.x * kRun + i;  // the only run that crosses k
+        if (cum >= target) {
+          *s_bin = threadIdx.x * kRun + i;  // the only run that crosses the target
           break;
         }
       }
     }
   }
+  __syncthreads();
+  const int b = *s_bin;
+  __syncthreads();
+  return b;
+}
+
+// End of a scoring launch (every thread of the block): this block's histograms
+// into the tick's; the last block finds the threshold bin (the larger of the bin
+// reaching k slots and, with s_safe, the bin reaching m predicted-safe slots),
+// then clears the histograms and the list counter for the next tick.
+__device__ void screen_finish(unsigned int* s_all, unsigned int* s_safe, int k, int m,
+                              ScreenScratch* ss) {
+  __shared__ int s_last, s_bin;
+  __shared__ unsigned int s_run[128];
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x) {
+    if (s_all[i]) atomicAdd(&ss->hist[i], s_all[i]);
+    if (s_safe && s_safe[i]) atomicAdd(&ss->hist_safe[i], s_safe[i]);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&ss->done, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x) {
+    s_all[i] = *reinterpret_cast<volatile unsigned int*>(&ss->hist[i]);
+    if (s_safe) s_safe[i] = *reinterpret_cast<volatile unsigned int*>(&ss->hist_safe[i]);
+  }
+  __syncthreads();
+  int b = first_bin_reaching(s_all, (unsigned int)k, s_run, &s_bin);
+  if (s_safe) {
+    const int bs = first_bin_reaching(s_safe, (unsigned int)m, s_run, &s_bin);
+    b = bs > b ? bs : b;
+  }
   if (threadIdx.x == 0) {
+    ss->bstar = b;
     ss->n_list = 0;
     ss->done = 0;
   }
-  for (int i = threadIdx.x; i < kBins; i += blockDim.x) ss->hist[i] = 0;
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x) {
+    ss->hist[i] = 0;
+    ss->hist_safe[i] = 0;
+  }
+}
+
+// Cost of a candidate against the user's input: the same float32 operations as
+// the rollout's cost (so a kept slot's bin follows its selection cost).
+__device__ __forceinline__ float screen_cost_of(const float* x, const float* uh) {
+  const float d0 = __fsub_rn(x[0], uh[0]), d1 = __fsub_rn(x[1], uh[1]);
+  return __fmaf_rn(d1, d1, __fmul_rn(d0, d0));
 }
 
 // Scores every slot with the network (tau > 0), 128 slots per block and tile,
-// writes its key ((score < tau) << 31 | cost bits >> 1; slot 0, the user's
-// input, gets key 0 so it is always kept) and builds the histogram of key >> 21
-// (screen_finish).
+// writes its key (the cost's float32 bits) and builds the histograms of all slots
+// and of the predicted-safe slots over the cost bins (screen_finish).
 __global__ void __launch_bounds__(kScoreThreads) screen_score(TickArgs a, FeatureSrc fs,
                                                           const InferW* w, float tau, int k,
-                                                          unsigned int* keys, ScreenScratch* ss) {
+                                                          int m, unsigned int* keys,
+                                                          ScreenScratch* ss) {
   extern __shared__ __align__(1024) unsigned char s_score[];
   __shared__ unsigned int s_hist[kBins];
+  __shared__ unsigned int s_hsafe[kBins];
   __shared__ float s_feat[12];
   __shared__ uint64_t s_bar;
   __shared__ uint32_t s_tmem;
-  for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
+  for (int i = threadIdx.x; i < kBins; i += blockDim.x) {
+    s_hist[i] = 0;
+    s_hsafe[i] = 0;
+  }
   ScoreCtx c;
   score_begin(w, s_score, &s_bar, &s_tmem, &c);
   block_tick_features(fs, a.x_t, s_feat);  // ends with __syncthreads
@@ -645,7 +691,7 @@ __global__ void __launch_bounds__(kScoreThreads) screen_score(TickArgs a, Featur
     float f8[8], x[2] = {0.f, 0.f};
     if (h == 0) {
 #pragma unroll
-      for (int m = 0; m < 8; ++m) f8[m] = s_feat[m];
+      for (int mm = 0; mm < 8; ++mm) f8[mm] = s_feat[mm];
     } else {
       candidate_value<2>(a, live ? r : 0, uh, x);
       f8[0] = s_feat[8];
@@ -653,39 +699,40 @@ __global__ void __launch_bounds__(kScoreThreads) screen_score(TickArgs a, Featur
       f8[2] = x[0] / 0.4f;
       f8[3] = x[1];
 #pragma unroll
-      for (int m = 4; m < 8; ++m) f8[m] = 0.f;
+      for (int mm = 4; mm < 8; ++mm) f8[mm] = 0.f;
     }
     const float y = score_tile(&c, f8);
     if (h == 1) {  // whole warps
       unsigned int key = 0u;
       if (live) {
-        const float d0 = __fsub_rn(x[0], uh[0]), d1 = __fsub_rn(x[1], uh[1]);
-        const float cost = __fmaf_rn(d1, d1, __fmul_rn(d0, d0));
-        key = (y < tau ? 0x80000000u : 0u) | (__float_as_uint(cost) >> 1);
-        if (a.include_user && r == 0) key = 0u;
+        key = __float_as_uint(screen_cost_of(x, uh));
         keys[r] = key;
       }
       // one shared-memory atomic per distinct bin of the warp (neighbouring slots'
-      // costs share few bins)
-      const unsigned int bin = live ? key >> 21 : 0xFFFFFFFFu;
+      // costs share few bins), for all slots and for the predicted-safe ones
+      const unsigned int bin = live ? key >> kBinShift : 0xFFFFFFFFu;
       const unsigned int same = __match_any_sync(kFull, bin);
       if (live && (threadIdx.x & 31) == (unsigned int)(__ffs(same) - 1))
         atomicAdd(&s_hist[bin], (unsigned int)__popc(same));
+      const bool safe = live && y >= tau;
+      const unsigned int sbin = safe ? bin : 0xFFFFFFFFu;
+      const unsigned int ssame = __match_any_sync(kFull, sbin);
+      if (safe && (threadIdx.x & 31) == (unsigned int)(__ffs(ssame) - 1))
+        atomicAdd(&s_hsafe[bin], (unsigned int)__popc(ssame));
     }
   }
   score_end(c);
-  screen_finish(s_hist, k, ss);
+  screen_finish(s_hist, s_hsafe, k, m, ss);
 }
 
 // Cost order alone (tau <= 0; no network): warps take 16-slot tiles, lanes
 // l and l + 4 k of a group compute the same two slots and one lane per slot
 // writes its key (a small kernel keeps the instruction footprint of this path low).
-__global__ void __launch_bounds__(128) screen_cost(TickArgs a, FeatureSrc fs, int k,
-                                                  unsigned int* keys, ScreenScratch* ss) {
+__global__ void __launch_bounds__(128) screen_cost(TickArgs a, int k, unsigned int* keys,
+                                                  ScreenScratch* ss) {
   __shared__ unsigned int s_hist[kBins];
-  __shared__ float s_feat[12];
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
-  block_tick_features(fs, a.x_t, s_feat);  // ends with __syncthreads
+  __syncthreads();
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
   float uh[2] = {__double2float_rn(a.u_h[0]), __double2float_rn(a.u_h[1])};
@@ -699,18 +746,15 @@ __global__ void __launch_bounds__(128) screen_cost(TickArgs a, FeatureSrc fs, in
       if (r >= a.n_slots) continue;
       float x[2];
       candidate_value<2>(a, r, uh, x);
-      const float d0 = __fsub_rn(x[0], uh[0]), d1 = __fsub_rn(x[1], uh[1]);
-      const float cost = __fmaf_rn(d1, d1, __fmul_rn(d0, d0));
-      unsigned int key = __float_as_uint(cost) >> 1;
-      if (a.include_user && r == 0) key = 0u;
+      const unsigned int key = __float_as_uint(screen_cost_of(x, uh));
       keys[r] = key;
-      atomicAdd(&s_hist[key >> 21], 1u);
+      atomicAdd(&s_hist[key >> kBinShift], 1u);
     }
   }
-  screen_finish(s_hist, k, ss);
+  screen_finish(s_hist, nullptr, k, 0, ss);
 }
 
-// Keeps the slots whose key bin is at or below the threshold (warp-aggregated append).
+// Keeps the slots whose cost bin is at or below the threshold (warp-aggregated append).
 __global__ void screen_compact(const unsigned int* keys, int n_slots, ScreenScratch* ss,
                                int* list) {
   const int bstar = ss->bstar;
@@ -718,7 +762,7 @@ __global__ void screen_compact(const unsigned int* keys, int n_slots, ScreenScra
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_slots;
        base += gridDim.x * blockDim.x) {
     const int slot = base + lane;
-    const bool keep = slot < n_slots && (int)(keys[slot] >> 21) <= bstar;
+    const bool keep = slot < n_slots && (int)(keys[slot] >> kBinShift) <= bstar;
     const unsigned int m = __ballot_sync(0xffffffffu, keep);
     int at = 0;
     if (lane == 0 && m) at = atomicAdd(&ss->n_list, __popc(m));
@@ -1007,8 +1051,8 @@ int mpmi_screener_score(mpmi_screener* s, const float* feats, int32_t batch, flo
 
 int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double* x_t_dev,
                            const double* u_h_dev, uint64_t tick, int32_t k, float tau,
-                           mpmi_result* result_dev, int32_t* list_dev, int32_t* n_list_dev,
-                           void* stream) {
+                           int32_t m, mpmi_result* result_dev, int32_t* list_dev,
+                           int32_t* n_list_dev, void* stream) {
   if (!session || !s || !x_t_dev || !u_h_dev || !result_dev)
     return fail(MPMI_E_INVALID_ARG, "evaluate_screened: NULL argument");
   if (session->model != s->model) return fail(MPMI_E_INVALID_ARG, "screener: another model");
@@ -1017,6 +1061,8 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
   if (session->n_slots > s->max_slots)
     return fail(MPMI_E_INVALID_ARG, "evaluate_screened: session has more slots than max_slots");
   if (k < 1) return fail(MPMI_E_INVALID_ARG, "evaluate_screened: k must be >= 1");
+  if (tau > 0.f && m < 1)
+    return fail(MPMI_E_INVALID_ARG, "evaluate_screened: m must be >= 1 with the network");
   cudaStream_t st = (cudaStream_t)stream;
   int rc = refresh_infer(s, st);
   if (rc != MPMI_OK) return rc;
@@ -1030,23 +1076,23 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
     const int tiles = (session->n_slots + kTileRows - 1) / kTileRows;
     const int blocks = tiles < 2 * s->ctx->sm_count ? tiles : 2 * s->ctx->sm_count;
     screen_score<<<blocks, kScoreThreads, kScoreSmem, st>>>(a, feature_src(s), s->infer, tau, k,
-                                                            s->keys, s->ss);
+                                                            m, s->keys, s->ss);
   } else {
     const int tiles = (session->n_slots + 15) / 16;
     int blocks = (tiles + 3) / 4;
     if (blocks > 2 * s->ctx->sm_count) blocks = 2 * s->ctx->sm_count;
-    screen_cost<<<blocks, 128, 0, st>>>(a, feature_src(s), k, s->keys, s->ss);
+    screen_cost<<<blocks, 128, 0, st>>>(a, k, s->keys, s->ss);
   }
   int cb = (session->n_slots + 255) / 256;
   if (cb > 4 * s->ctx->sm_count) cb = 4 * s->ctx->sm_count;
   screen_compact<<<cb, 256, 0, st>>>(s->keys, session->n_slots, s->ss, s->list);
   SCR_CUDA(cudaGetLastError(), "screen launches");
-  // exact rollout on the kept slots
+  // exact rollout on the kept slots (their number is known only on the device)
   TickArgs r = a;
   r.slot_list = s->list;
   r.n_list = &s->ss->n_list;
   r.result_flags = 1;
-  rc = launch_tick_args(session, r, false, st, k + k / 4 + 32);
+  rc = launch_tick_args(session, r, false, st, -1);
   if (rc != MPMI_OK) return rc;
   if (list_dev)
     SCR_CUDA(cudaMemcpyAsync(list_dev, s->list, sizeof(int) * session->n_slots,
@@ -1054,7 +1100,8 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
   if (n_list_dev)
     SCR_CUDA(cudaMemcpyAsync(n_list_dev, &s->ss->n_list, sizeof(int), cudaMemcpyDeviceToDevice,
                              st), "copy list size");
-  // full evaluation only when the kept slots hold no safe candidate
+  // full evaluation only when the kept slots hold no safe candidate and were not
+  // already every slot; its result counts the steps of both launches
   TickArgs f = a;
   f.skip_if_safe = result_dev;
   f.result_flags = 3;

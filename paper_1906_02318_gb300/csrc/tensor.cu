@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kTcM) tc_tick_kernel(const __grid_constant__ T
   __shared__ int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5;
-  if (a.skip_if_safe != nullptr && a.skip_if_safe->status == MPMI_SAFE) return;
+  if (fallback_not_needed(a)) return;
   const int n_eval = a.n_list ? *a.n_list : a.n_slots;
   const int H = a.horizon;
   const bool track_on = B::TRACK && a.safety.has_track;

@@ -169,6 +169,25 @@ struct HasSeq<P, decltype((void)sizeof(((P*)nullptr)->seq_out), void())> {
   static constexpr bool value = true;
 };
 
+// Parameter records that carry a screened tick's first result (TickArgs).
+template <class P, class = void>
+struct HasSkip {
+  static constexpr bool value = false;
+};
+template <class P>
+struct HasSkip<P, decltype((void)sizeof(((P*)nullptr)->skip_if_safe), void())> {
+  static constexpr bool value = true;
+};
+
+// A screened tick's fallback launch (skip_if_safe set) has nothing to do when the
+// kept slots held a safe candidate or were already every slot of the tick.
+template <class P>
+__device__ __forceinline__ bool fallback_not_needed(const P& a) {
+  if (a.skip_if_safe == nullptr) return false;
+  const mpmi_result* p = a.skip_if_safe;
+  return p->status == MPMI_SAFE || p->n_slots >= a.n_slots;
+}
+
 // The values that change from tick to tick: the Philox counter words of the
 // tick, the tick itself, u_h (float64, device) and the completion number of a
 // zero-copy host tick.  Normally the launch's parameters; a persistent kernel
@@ -369,6 +388,10 @@ __device__ __forceinline__ void write_result(const P& a, TickDyn d, unsigned lon
   r.cost = __uint_as_float((unsigned int)((k >> 23) & 0xFFFFFFFFull));
   r.n_slots = a.n_list ? *a.n_list : a.n_slots;
   r.executed_steps = cnt & ((1ull << 40) - 1);
+  if constexpr (HasSkip<P>::value) {
+    // a fallback launch reports the steps of the whole screened tick
+    if (a.skip_if_safe != nullptr) r.executed_steps += a.skip_if_safe->executed_steps;
+  }
   r.tick = d.tick;
   r.reserved = a.result_flags;
   *a.result = r;
@@ -688,7 +711,8 @@ template <int NU, class P>
 __device__ __forceinline__ void session_epilogue(const P& a, TickDyn d,
                                                  unsigned long long best, unsigned int n_safe,
                                                  unsigned int n_exec, const float* uh,
-                                                 bool failed = false) {
+                                                 bool failed = false,
+                                                 unsigned int n_blocks = 0) {
   __shared__ unsigned long long s_key[kMaxBlock / 32];
   __shared__ unsigned long long s_cnt[kMaxBlock / 32];
   __shared__ int s_last;
@@ -720,7 +744,7 @@ __device__ __forceinline__ void session_epilogue(const P& a, TickDyn d,
     // visible before the increment, and the last block sees every other block's
     unsigned int prev;
     asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&sc->done) : "memory");
-    s_last = (prev == gridDim.x - 1);
+    s_last = (prev == (n_blocks ? n_blocks : gridDim.x) - 1);
   }
   __syncthreads();
   if (s_last && tid == 0) {
@@ -742,8 +766,9 @@ __device__ __forceinline__ void session_epilogue(const P& a, TickDyn d,
 template <int NU, class P>
 __device__ __forceinline__ void session_epilogue(const P& a, unsigned long long best,
                                                  unsigned int n_safe, unsigned int n_exec,
-                                                 const float* uh, bool failed = false) {
-  session_epilogue<NU>(a, dyn_of(a), best, n_safe, n_exec, uh, failed);
+                                                 const float* uh, bool failed = false,
+                                                 unsigned int n_blocks = 0) {
+  session_epilogue<NU>(a, dyn_of(a), best, n_safe, n_exec, uh, failed, n_blocks);
 }
 
 // Template parameters of the tick kernel:
@@ -788,9 +813,21 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
     if (tid == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.scratch));
   }
   // a fallback launch has nothing to do when the screened result is already safe
-  if (a.skip_if_safe != nullptr && a.skip_if_safe->status == MPMI_SAFE) return;
+  if (fallback_not_needed(a)) return;
   // number of candidates this launch evaluates (all slots, or a device-side list)
   const int n_eval = a.n_list ? *a.n_list : a.n_slots;
+  // A launch over a device-side list is sized for the longest list; the blocks
+  // past the ones the list's warp-tiles need leave at once (no staging, no
+  // atomics) and the epilogue waits for the needed blocks only.  Launches over
+  // all slots are sized exactly, so there every block is needed.
+  unsigned int n_active = gridDim.x;
+  if constexpr (!PARTIALS) {
+    const int wpb0 = blockDim.x >> 5;
+    const long long tiles = ((long long)n_eval + GPW * C - 1) / (GPW * C);
+    const long long need = (tiles + wpb0 - 1) / wpb0;
+    n_active = (unsigned int)(need < 1 ? 1 : (need < (long long)gridDim.x ? need : gridDim.x));
+    if (blockIdx.x >= n_active) return;
+  }
 
   // stage K (KSMEM) and the track grid (race car) while the per-tick state is
   // prepared: bulk copies on an mbarrier (plain loads in the no-allocation
@@ -875,7 +912,7 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
                                       &s_x[L > 1 ? warp : 0][0][0][0], best, n_safe, n_exec);
 
   if constexpr (!PARTIALS) {
-    session_epilogue<NU>(a, best, n_safe, n_exec, uh, failed);
+    session_epilogue<NU>(a, best, n_safe, n_exec, uh, failed, n_active);
   } else {
     // warp -> block reduction, then per-block partials folded by the last block
 #pragma unroll

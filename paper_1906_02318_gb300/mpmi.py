@@ -128,7 +128,7 @@ _SIGNATURES = {
     "mpmi_screener_train_step": (c_i32, [c_vp, c_vp, c_vp, c_i32, ctypes.c_float, c_vp, c_vp]),
     "mpmi_screener_score": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
     "mpmi_evaluate_screened": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_i32, ctypes.c_float,
-                                       c_vp, c_vp, c_vp, c_vp]),
+                                       c_i32, c_vp, c_vp, c_vp, c_vp]),
     "mpmi_evaluate_candidates_noalloc": (c_i32, [ctypes.POINTER(BasisDesc), c_vp,
                                                  ctypes.POINTER(SafetySpecC),
                                                  ctypes.POINTER(SessionConfig), c_vp, c_vp,
@@ -663,11 +663,13 @@ class Screener:
 
 
 def evaluate_screened(s: Session, scr: Screener, x_t_dev, u_h_dev, result_dev, k: int = 4096,
-                      tau: float = 0.9, tick: int = 0, list_dev=None, n_list_dev=None,
-                      stream=None):
-    """mpmi_evaluate_screened: screened tick with on-device fallback."""
+                      tau: float = 0.9, m: int = 8, tick: int = 0, list_dev=None,
+                      n_list_dev=None, stream=None):
+    """mpmi_evaluate_screened: exact screened tick (a cost-order prefix of at least
+    k slots holding at least m predicted-safe ones when tau > 0) with on-device
+    fallback to the full evaluation."""
     _check(s.ctx.lib.mpmi_evaluate_screened(s.handle, scr.handle, _ptr(x_t_dev), _ptr(u_h_dev),
-                                            tick, k, tau, _ptr(result_dev), _ptr(list_dev),
+                                            tick, k, tau, m, _ptr(result_dev), _ptr(list_dev),
                                             _ptr(n_list_dev), _stream(stream)))
 
 

@@ -76,25 +76,26 @@ def train(screener, feats, targets, epochs=3, batch=8192, lr=2e-3, seed=0):
     return out
 
 
-def compare(session, screener, states, user_inputs, k=4096, tau=0.9, tick0=0):
+def compare(session, screener, states, user_inputs, k=4096, tau=0.9, m=8, tick0=0):
     """Screened vs exhaustive tick on each (state, user input): returns a dict with
     the agreement (same selected slot), the number of reported-safe picks that the
-    exhaustive evaluation finds unsafe (safety misses), and the fallback count."""
+    exhaustive evaluation finds unsafe (safety misses), the fallback count, the
+    mean number of kept slots and the mean rollout steps each form executed."""
     import torch
     dev = torch.device("cuda")
     n = session.n_slots
     r_plain = torch.zeros(lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
     r_scr = torch.zeros(lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
     ttv = torch.empty(n, dtype=torch.int32, device=dev)
+    nl = torch.zeros(1, dtype=torch.int32, device=dev)
     agree = misses = fallbacks = 0
-    kept = []
+    kept, steps, plain_steps = [], [], []
     for t, (x, u) in enumerate(zip(states, user_inputs)):
         xd = torch.tensor(x, dtype=torch.float64, device=dev)
         ud = torch.tensor(u, dtype=torch.float64, device=dev)
-        nl = torch.zeros(1, dtype=torch.int32, device=dev)
         lib.evaluate_candidates_device(session, xd, ud, r_plain, tick=tick0 + t, ttv_dev=ttv)
-        lib.evaluate_screened(session, screener, xd, ud, r_scr, k=k, tau=tau, tick=tick0 + t,
-                              n_list_dev=nl)
+        lib.evaluate_screened(session, screener, xd, ud, r_scr, k=k, tau=tau, m=m,
+                              tick=tick0 + t, n_list_dev=nl)
         a = lib.result_from_bytes(r_plain.cpu(), 2)
         b = lib.result_from_bytes(r_scr.cpu(), 2)
         full = ttv.cpu().numpy()
@@ -103,6 +104,25 @@ def compare(session, screener, states, user_inputs, k=4096, tau=0.9, tick0=0):
             misses += 1
         fallbacks += (b["flags"] & 2) != 0
         kept.append(int(nl.item()))
+        steps.append(b["executed_steps"])
+        plain_steps.append(a["executed_steps"])
     T = len(states)
     return dict(ticks=T, agreement=agree / T, safety_misses=misses, fallbacks=fallbacks,
-                mean_kept=float(np.mean(kept)))
+                mean_kept=float(np.mean(kept)), mean_executed_steps=float(np.mean(steps)),
+                plain_executed_steps=float(np.mean(plain_steps)))
+
+
+def calibrate(session, screener, states, user_inputs, taus=(0.5, 0.8, 0.9, 0.95),
+              ms=(1, 4, 16), k=1, tick0=0):
+    """Picks the screen's threshold tau and predicted-safe count m on held-out
+    calibration ticks: the pair with the fewest mean executed rollout steps (every
+    pair selects exactly, so only the work differs).  Returns the pair and the
+    table of means."""
+    table = {}
+    for tau in taus:
+        for m in ms:
+            r = compare(session, screener, states, user_inputs, k=k, tau=tau, m=m, tick0=tick0)
+            table[(tau, m)] = r["mean_executed_steps"]
+    tau, m = min(table, key=lambda key: (table[key], -key[0], key[1]))
+    return dict(tau=tau, m=m, k=k,
+                table={f"tau={a},m={b}": v for (a, b), v in table.items()})

@@ -100,8 +100,52 @@ def test_features_on_circle_chord_bisector():
     assert c.shape == (2, 12) and np.allclose(c[:, 10:], [[0.5, -0.5], [-1.0, 1.0]])
 
 
-def test_screen_orders_predicted_safe_by_cost():
-    scores = np.array([0.95, 0.2, 0.99, 0.91, 0.5, 0.97])
-    cost = np.array([0.3, 0.0, 0.5, 0.1, 0.05, 0.1])
-    assert sc.screen(scores, cost, 4, 0.9).tolist() == [3, 5, 0, 2]
-    assert sc.screen(scores, cost, 6, 0.9).tolist() == [3, 5, 0, 2, 1, 4]
+def test_cost_bins_follow_the_cost_order():
+    c = np.array([0.0, 1e-30, 0.125, 0.5, 0.51, 0.5625, 1.0, 4.64], dtype=np.float32)
+    b = sc.cost_bin(c)
+    assert np.all(np.diff(b) >= 0) and b[0] == 0
+    # 0.5 and 0.51 share the bin [0.5, 0.5625) (three mantissa bits); 0.5625 opens the next
+    assert b[3] == b[4] and b[5] == b[4] + 1
+    assert b.max() < 2048  # the device histograms have 2048 bins
+
+
+def test_screen_keeps_the_cost_prefix_the_scores_ask_for():
+    # costs in distinct bins; order by cost: 0, 5, 2, 1, 3, 4
+    cost = np.array([0.0, 0.5, 0.25, 1.0, 2.0, 0.125])
+    scores = np.array([0.1, 0.95, 0.2, 0.99, 0.97, 0.3])
+    assert sc.screen(scores, cost, 3, 0.0).tolist() == [0, 2, 5]
+    assert sc.screen(scores, cost, 1, 0.9, m=1).tolist() == [0, 1, 2, 5]
+    assert sc.screen(scores, cost, 1, 0.9, m=2).tolist() == [0, 1, 2, 3, 5]
+    assert sc.screen(scores, cost, 5, 0.9, m=1).tolist() == [0, 1, 2, 3, 5]
+    assert sc.screen(scores, cost, 1, 0.9, m=4).tolist() == [0, 1, 2, 3, 4, 5]  # only 3
+    assert sc.screen(scores, cost, 1, 0.05, m=1).tolist() == [0]
+    # a shared bin is kept whole
+    cost2 = np.array([0.0, 0.5, 0.51, 1.0])
+    assert sc.screen(np.zeros(4), cost2, 2, 0.0).tolist() == [0, 1, 2]
+
+
+def test_screened_selection_is_exhaustive_for_any_scores():
+    """Brute force over random ticks (random safety, random and adversarial
+    scores): the kept prefix either holds the least-cost safe slot or only unsafe
+    slots, so the screened selection equals the exhaustive one."""
+    rng = np.random.default_rng(11)
+    H = 7
+    for trial in range(3000):
+        n = int(rng.integers(1, 40))
+        cost = rng.choice([0.0, 0.01, 0.02, 0.1, 0.3, 0.31, 1.0, 2.5], n)
+        cost = (cost + rng.uniform(0, 0.05, n) * rng.integers(0, 2, n)).astype(np.float32)
+        ttv = np.where(rng.random(n) < rng.random(), H, rng.integers(0, H, n))
+        kind = trial % 3
+        scores = (rng.random(n) if kind == 0 else
+                  (ttv == H) * 1.0 if kind == 1 else (ttv != H) * 1.0)
+        k = int(rng.integers(1, n + 1))
+        tau = float(rng.choice([0.0, 0.5, 0.9]))
+        m = int(rng.integers(1, 6))
+        kept = sc.screen(scores, cost, k, tau, m)
+        got = sc.screened_selection(ttv, cost.astype(np.float64), kept, H)
+        # exhaustive by scalar loops: max ttv, then min cost, then min slot
+        best = 0
+        for i in range(1, n):
+            if (H - ttv[i], cost[i], i) < (H - ttv[best], cost[best], best):
+                best = i
+        assert got == best
