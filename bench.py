@@ -410,16 +410,28 @@ def run_gpu(args, rank, world):
                 gpu_name=props.name)
 
 
+SCREEN_FLOPS_PER_SLOT = 2 * 12 * 128 + 2 * 128 * 128  # the two tensor-core layers
+CAR_LIFTED_N = 32
+
+
 def run_learned(args):
     """Learned screener vs plain exhaustive evaluation on the race car (N = 16384 and
     65536, H = 60): a screener trained on ~2M labels from the plain path's own
-    closed-loop rollouts; agreement, safety misses and tick times on held-out
-    closed-loop states.  Also reports the exact cost-ordered search (tau = 0,
-    no network), the method without the learned part."""
+    closed-loop rollouts; its threshold tau and predicted-safe count m calibrated
+    on held-out ticks (fewest executed steps), then agreement, safety misses,
+    executed steps, tick times and per-kernel rooflines on other held-out ticks.
+    Also reports the exact cost-ordered search (tau = 0, fixed k = N / 16, no
+    network), the method without the learned part.  Every screened form selects
+    exactly what the exhaustive evaluation selects."""
     import torch
     from paper_1906_02318_gb300 import mpmi as lib
     from paper_1906_02318_gb300 import screener as drv
     dev = torch.device("cuda", torch.cuda.current_device())
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = props.multi_processor_count * SM_FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
     ctx = lib.Context(dev.index)
     x, u, xn = data.transitions("car", CAR_SEED, CAR_FIT_COUNT)
     model, _ = lib.fit_model(ctx, "car", x, u, xn)
@@ -439,20 +451,33 @@ def run_learned(args):
     train_s = time.perf_counter() - t0
     n_labels = int(feats.shape[0])
     del feats, targets
-    sess = lib.Session(ctx, model, 1023, 60, lo, hi, seed=6)
+
+    def held_out(seed, ticks, tick0):
+        s1 = lib.Session(ctx, model, 1023, 60, lo, hi, seed=6)
+        uu = data.ou_user_input(seed, ticks, plants.CAR_DT, lo, hi)
+        _, _, xx = drv.collect_labels(s1, scr, plants.bicycle_step, x0, uu, track,
+                                      data.CAR_TRACK_HALF_WIDTH, tick0=tick0)
+        s1.close()
+        return xx, uu
+
     ticks = args.learned_ticks
-    uev = data.ou_user_input(6, ticks, plants.CAR_DT, lo, hi)
-    _, _, xev = drv.collect_labels(sess, scr, plants.bicycle_step, x0, uev, track,
-                                   data.CAR_TRACK_HALF_WIDTH, tick0=10000)
-    sess.close()
+    xev, uev = held_out(6, ticks, 10000)
+    xcal, ucal = held_out(8, 100, 20000)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     res = torch.zeros(lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
     out = {"workload": "race car, H=60, held-out closed-loop states", "labels": n_labels,
            "train_epochs": len(losses), "train_loss": losses[-1], "train_s": train_s,
-           "ticks": ticks, "tau_learned": 0.05, "runs": []}
+           "ticks": ticks, "calibration_ticks": len(xcal), "runs": [],
+           "what": "every form selects exactly the exhaustive evaluation's slot; the learned "
+                   "form rolls out the cost-order prefix holding m predicted-safe slots",
+           "rates": "executed = rollout steps actually run / tick time; "
+                    "nominal_equivalent = (N + 1) * H / tick time, the rate of the exhaustive "
+                    "evaluation the tick replaces"}
     for N in (16384, 65536):
         sess = lib.Session(ctx, model, N, 60, lo, hi, seed=7)
         k = N // 16
+        cal = drv.calibrate(sess, scr, xcal, ucal, taus=(0.8, 0.9, 0.95, 0.98, 0.99),
+                            ms=(16, 64, 256, 1024), k=1, tick0=50000)
 
         def timed(fn):
             ts = []
@@ -468,21 +493,125 @@ def run_learned(args):
                 ts.append(e0.elapsed_time(e1) * 1e-3)
             return np.array(ts)
 
+        def phases(k_, tau_, m_):
+            """Per-launch CUDA-event durations of the screened ticks (a separate pass)."""
+            scr.set_timing(True)
+            acc = {"screen": [], "compact": [], "rollout": [], "fallback": []}
+            for t in range(ticks):
+                xd = torch.tensor(xev[t], dtype=torch.float64, device=dev)
+                ud = torch.tensor(uev[t], dtype=torch.float64, device=dev)
+                flush.zero_()
+                lib.evaluate_screened(sess, scr, xd, ud, res, k=k_, tau=tau_, m=m_,
+                                      tick=40000 + t)
+                for key, v in scr.phase_times().items():
+                    acc[key].append(v * 1e-3)
+            scr.set_timing(False)
+            return {key: float(np.mean(v)) for key, v in acc.items()}
+
         tp = timed(lambda xd, ud, t: lib.evaluate_candidates_device(sess, xd, ud, res, tick=t))
-        run = {"N": N, "k": k, "plain": {"mean_us": tp.mean() * 1e6,
-                                         "p99_us": np.percentile(tp, 99) * 1e6,
-                                         "steps_per_s": (N + 1) * 60 / tp.mean()}}
-        for name, tau in (("cost_ordered", 0.0), ("learned", 0.05)):
-            st = drv.compare(sess, scr, xev, uev, k=k, tau=tau, tick0=40000)
-            ts = timed(lambda xd, ud, t: lib.evaluate_screened(sess, scr, xd, ud, res, k=k,
-                                                               tau=tau, tick=t))
-            run[name] = dict(st, mean_us=ts.mean() * 1e6, p99_us=np.percentile(ts, 99) * 1e6,
-                             steps_per_s=(N + 1) * 60 / ts.mean())
+        st_plain = drv.compare(sess, scr, xev, uev, k=N + 1, tau=0.0, tick0=40000)
+        ex_plain = st_plain["plain_executed_steps"]
+        run = {"N": N, "k_cost_ordered": k, "calibration": cal,
+               "plain": {"mean_us": tp.mean() * 1e6, "p99_us": np.percentile(tp, 99) * 1e6,
+                         "executed_steps_per_tick": ex_plain,
+                         "executed_steps_per_s": ex_plain / tp.mean(),
+                         "nominal_equivalent_steps_per_s": (N + 1) * 60 / tp.mean(),
+                         "roofline": {"kernel": "tick_kernel (full rollout)", "bound": "alu",
+                                      "achieved": ex_plain * 2 * CAR_LIFTED_N ** 2
+                                      / tp.mean() / 1e12,
+                                      "peak": fp32_peak, "unit": "TFLOP/s"}}}
+        run["plain"]["roofline"]["frac"] = run["plain"]["roofline"]["achieved"] / fp32_peak
+        for name, kk, tau, m in (("cost_ordered", k, 0.0, 1),
+                                 ("learned", 1, cal["tau"], cal["m"])):
+            st = drv.compare(sess, scr, xev, uev, k=kk, tau=tau, m=m, tick0=40000)
+            ts = timed(lambda xd, ud, t: lib.evaluate_screened(sess, scr, xd, ud, res, k=kk,
+                                                               tau=tau, m=m, tick=t))
+            ph = phases(kk, tau, m)
+            ex = st["mean_executed_steps"]
+            roll = {"kernel": "tick_kernel over the kept slots (and the fallback launch)",
+                    "bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak,
+                    "achieved": ex * 2 * CAR_LIFTED_N ** 2
+                    / max(ph["rollout"] + ph["fallback"], 1e-9) / 1e12,
+                    "mean_us": (ph["rollout"] + ph["fallback"]) * 1e6}
+            roll["frac"] = roll["achieved"] / fp32_peak
+            forms = {"rollout": roll}
+            if tau > 0:
+                scr_tf = (N + 1) * SCREEN_FLOPS_PER_SLOT / ph["screen"] / 1e12
+                forms["screen_score"] = {"kernel": "screen_score (tcgen05, bf16 x bf16 -> f32)",
+                                         "bound": "tensor", "unit": "TFLOP/s",
+                                         "achieved": scr_tf, "peak": bf16_peak,
+                                         "frac": scr_tf / bf16_peak,
+                                         "mean_us": ph["screen"] * 1e6}
+            else:
+                forms["screen_cost"] = {"kernel": "screen_cost (costs and histogram)",
+                                        "mean_us": ph["screen"] * 1e6}
+            forms["compact_us"] = ph["compact"] * 1e6
+            run[name] = dict(st, tau=tau, m=m, k=kk, mean_us=ts.mean() * 1e6,
+                             p99_us=np.percentile(ts, 99) * 1e6,
+                             executed_steps_per_tick=ex,
+                             executed_steps_per_s=ex / ts.mean(),
+                             nominal_equivalent_steps_per_s=(N + 1) * 60 / ts.mean(),
+                             roofline=forms)
         out["runs"].append(run)
         sess.close()
     scr.free()
     model.free()
     return out
+
+
+INFLATION_GRID = (0.0, 0.1, 0.2, 0.3, 0.35, 0.4)
+INFLATION_SEEDS = (102, 103)  # held-out user-input seeds for choosing the radius
+
+
+def run_inflation(args):
+    """The paper's inflated barrier (Sec. V-C.1) in the balance-bot closed loop: the
+    radius is chosen on held-out user-input seeds (fewest trial failures, then the
+    smallest radius), then the benchmark's own closed loop (N = 16384, H = 50, 1000
+    ticks, seed 2) runs with and without it."""
+    import torch
+    from paper_1906_02318_gb300 import mpmi as lib
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = lib.Context(dev.index)
+    x, u, xn = data.transitions("bot", FIT_SEED, FIT_COUNT)
+
+    def loop(seed, iota):
+        model, _ = lib.fit_model(ctx, "bot", x, u, xn)
+        lib.set_safety_set(model, data.BOT_SAFE_LO, data.BOT_SAFE_HI, iota)
+        sess = lib.Session(ctx, model, N_SAMPLES, HORIZON, plants.BOT_INPUT_LO,
+                           plants.BOT_INPUT_HI, seed=seed)
+        uhs = data.ou_user_input(seed, TICKS, plants.BOT_DT, plants.BOT_INPUT_LO,
+                                 plants.BOT_INPUT_HI)
+        x_t, trials, recs = X0.copy(), 1, []
+        for t in range(TICKS):
+            lib.evaluate_candidates(sess, x_t, uhs[t], tick=t)
+            r = lib.select_input(sess)
+            x_t = plants.cartpole_step(x_t, r["u_r"])
+            inside = bool(np.all(np.isfinite(x_t)) and np.all(x_t > data.BOT_SAFE_LO)
+                          and np.all(x_t < data.BOT_SAFE_HI))
+            recs.append(metrics.tick_record(r, uhs[t], t, trials - 1, N_SAMPLES,
+                                            failed=not inside))
+            if not inside:
+                x_t, trials = X0.copy(), trials + 1
+        sess.close()
+        model.free()
+        pm = metrics.summarize(recs, plants.BOT_DT)
+        return {"trials": pm["trials"], "failures": trials - 1,
+                "fallback_ticks": pm["fallback_ticks"],
+                "safe_trial_fraction": pm["safe_trial_fraction"],
+                "mean_time_to_failure_s": pm["mean_time_to_failure_s"],
+                "avg_deviation": pm["avg_deviation"]}
+
+    sweep = {}
+    for iota in INFLATION_GRID:
+        sweep[iota] = sum(loop(seed, iota)["failures"] for seed in INFLATION_SEEDS)
+    best = min(INFLATION_GRID, key=lambda i: (sweep[i], i))
+    return {"workload": "balance-bot closed loop: N=16384 (+u_h), H=50, 100 Hz, 1000 ticks, "
+                        f"user-input seed {LOOP_SEED}",
+            "selection": {"seeds": list(INFLATION_SEEDS),
+                          "failures_by_radius": {str(k): v for k, v in sweep.items()},
+                          "rule": "fewest trial failures on the held-out seeds, then the "
+                                  "smallest radius"},
+            "radius": best, "without": loop(LOOP_SEED, 0.0), "with": loop(LOOP_SEED, best)}
 
 
 def run_serving(args, bot_states):
@@ -524,13 +653,43 @@ def run_serving(args, bot_states):
         tuned["bot" if m == 0 else "car"] = {k: r[k] for k in ("lanes", "cands", "block",
                                                                  "n_tried", "us", "default_us")}
     streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
-    stats = serve.run([bs, cs], sessions, duration=args.serve_seconds, streams=streams)
+
+    def serve_twice(servers, sess_list, seconds):
+        """The same sessions served with up to four batches per model on the GPU at
+        once, then with one batch at a time (ticks restart at 0 for the second run)."""
+        runs = {}
+        for name, overlap in (("overlap", 4), ("one_batch_at_a_time", 1)):
+            for ss in sess_list:
+                ss.next_tick, ss.outstanding, ss.latencies = 0, False, []
+            runs[name] = serve.run(servers, sess_list, duration=seconds, streams=streams,
+                                   overlap=overlap)
+        return runs
+
+    runs = serve_twice([bs, cs], sessions, args.serve_seconds)
+    stats = dict(runs["overlap"])
     stats.update(sessions=n_sess, mix="half balance bot (100 Hz), half race car (60 Hz)",
                  n_range="log-uniform 1024..65536", h_range="uniform 20..100",
-                 launch="one persistent graph-replayed launch per batch and model",
-                 autotuned=tuned)
+                 launch="one graph-replayed launch per batch; up to 4 batches per model in "
+                        "flight, each on the server's own stream",
+                 autotuned=tuned,
+                 one_batch_at_a_time={k: runs["one_batch_at_a_time"][k]
+                                      for k in ("ticks_per_s", "rollout_steps_per_s",
+                                                "batches", "mean_batch", "latency")})
     bs.free()
     cs.free()
+    # a heavier race-car-only mix (the GPU busy most of the time), with and without
+    # overlapping batches
+    n_heavy = 320
+    hs = lib.Server(ctx, cm, n_heavy)
+    heavy = serve.make_sessions([(hs, plants.CAR_INPUT_LO, plants.CAR_INPUT_HI, 1.0 / 60.0)],
+                                n_heavy, 5, [car_pool])
+    hruns = serve_twice([hs], heavy, min(args.serve_seconds, 3.0))
+    stats["car_heavy"] = {
+        "sessions": n_heavy, "mix": "race car only, 60 Hz, N log-uniform 1024..65536, "
+                                    "H uniform 20..100",
+        **{name: {k: r[k] for k in ("ticks_per_s", "rollout_steps_per_s", "batches",
+                                     "mean_batch", "latency")} for name, r in hruns.items()}}
+    hs.free()
     bm.free()
     cm.free()
     return stats
@@ -749,6 +908,8 @@ def main():
                     help="seconds of oracle work per host worker for cpu_baseline")
     ap.add_argument("--learned-ticks", type=int, default=300,
                     help="held-out ticks for the learned-vs-plain comparison (0 = skip)")
+    ap.add_argument("--inflation", type=int, default=1,
+                    help="run the inflated-barrier closed loops (0 = skip)")
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="wall time of the 256-session serving run (0 = skip)")
     ap.add_argument("--serve-sessions", type=int, default=256)
@@ -815,12 +976,13 @@ def main():
         "value": value, "unit": "rollout steps/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": t_max / K * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(cfg, lanes=out["lanes"], cands_per_thread=out["cands"], block=out["block"],
-                       autotuned={"n_tried": out["tuned"]["n_tried"],
-                                  "winner_us": out["tuned"]["us"],
-                                  "default_shape_us": out["tuned"]["default_us"],
-                                  "what": "warm device ticks, median of 30 per shape"},
-                       parallelism=f"replicas{world}" if world > 1 else "single"),
+        "config": dict(cfg, parallelism=f"replicas{world}" if world > 1 else "single"),
+        "launch": {"lanes": out["lanes"], "cands_per_thread": out["cands"],
+                   "block": out["block"],
+                   "autotuned": {"n_tried": out["tuned"]["n_tried"],
+                                 "winner_us": out["tuned"]["us"],
+                                 "default_shape_us": out["tuned"]["default_us"],
+                                 "what": "warm device ticks, median of 30 per shape"}},
         "executed_steps_per_s": world * float(out["executed"].sum()) / t_max,
         "latency_ms": {"p50": float(np.percentile(out["lat"], 50) * 1e3),
                        "p99": float(np.percentile(out["lat"], 99) * 1e3),
@@ -851,6 +1013,8 @@ def main():
     }
     if rank == 0 and args.learned_ticks > 0:
         line["learned"] = run_learned(args)
+    if rank == 0 and args.inflation:
+        line["closed_loop_inflated"] = run_inflation(args)
     if rank == 0 and args.serve_seconds > 0:
         line["serving"] = run_serving(args, out["states"])
     if rank == 0 and args.variant_ticks > 0:
@@ -894,7 +1058,9 @@ def run_reference(args, cfg):
             "value": value, "unit": "rollout steps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": cfg, "impl": "reference",
+            "data": "synthetic",
+            "config": dict(cfg, parallelism=f"replicas{args.gpus}" if args.gpus > 1 else "single"),
+            "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "rollout steps/s", "cores": workers,
                              "kind": "oracle",
                              "sample": f"{args.steps} full ticks over {workers} spawned "

@@ -418,37 +418,50 @@ int mpmi_debug_trajectories(mpmi_session* s, const double* x_t_dev,
 /* ---- continuous-batching server ------------------------------------------ */
 /* Serves many control sessions of one model together: each admitted session has
  * its own N, H, input box, sampler seed/stream and tick counter; the requests
- * staged for a batch run in one persistent launch (replayed from a CUDA graph)
- * whose warps stride over all requests' candidates, and every request's result is
+ * staged for a batch run in one launch (replayed from a CUDA graph) whose warps
+ * stride over all requests' candidates, and every request's result is
  * bit-identical to the same tick evaluated alone (same per-candidate arithmetic,
- * exact min-reduction).  Two batch buffers: requests for the next batch are staged
- * on the host while the current one runs.  The server snapshots the model's
- * operator and safety set when it is created.  Served sessions draw uniform
- * samples. */
+ * exact min-reduction).  Up to four batches of the server run at once, each on a
+ * stream of the server's own, while the requests of the next one are staged on
+ * the host; a launch's blocks beyond its batch's candidates leave at once, so
+ * batches in flight share the device.  A session has at most one request staged
+ * or on the GPU at a time.  The server snapshots the model's operator and safety
+ * set when it is created.  Served sessions draw uniform samples. */
 typedef struct mpmi_server mpmi_server;
-/* max_sessions session slots; their reduction records and two batch tables are
+/* max_sessions session slots; their reduction records and five batch tables are
  * allocated here (and counted against the context's memory budget). */
 int mpmi_server_create(mpmi_ctx* ctx, const mpmi_model* model, int32_t max_sessions,
                        mpmi_server** out);
-void mpmi_server_free(mpmi_server* s);
+void mpmi_server_free(mpmi_server* s); /* waits for the batches in flight */
 /* Admission: a free slot and room in the context's memory budget for the
  * session's share, else MPMI_E_OOM.  *slot_out identifies the session. */
 int mpmi_server_admit(mpmi_server* s, const mpmi_session_config* cfg, int32_t* slot_out);
 /* Frees a session slot (NOT_READY while it has a staged or running request). */
 int mpmi_server_release(mpmi_server* s, int32_t slot);
 /* Stages n requests for the next batch (host arrays): slots[n], x_t (n x nx),
- * u_h (n x nu), ticks[n].  A session may have one request per batch. */
+ * u_h (n x nu), ticks[n].  INVALID_ARG for a session that already has a request
+ * staged or on the GPU (a controller needs its last output before its next
+ * input). */
 int mpmi_server_submit(mpmi_server* s, int32_t n, const int32_t* slots, const double* x_t,
                        const double* u_h, const uint64_t* ticks);
 /* Requests staged so far for the next batch. */
 int mpmi_server_staged(const mpmi_server* s, int32_t* n_out);
-/* Launches the staged batch on `stream` (one graph launch) and returns; NOT_READY
- * while the previous batch has not been collected.  *n_launched may be 0. */
+/* Launches the staged batch (one graph launch) and returns.  The batch is ordered
+ * after the work queued so far on `stream` and runs on its buffer's own stream,
+ * so it overlaps the batches already in flight.  NOT_READY when max_in_flight
+ * batches are on the GPU.  *n_launched may be 0 (nothing staged). */
 int mpmi_server_launch(mpmi_server* s, void* stream, int32_t* n_launched);
-/* *done = 1 when the batch in flight has finished (0 if none is in flight). */
+/* How many batches may be on the GPU at once: 1..4 (default 4).  1 gives one batch
+ * at a time (a launch waits for the previous batch to be collected). */
+int mpmi_server_set_max_in_flight(mpmi_server* s, int32_t n);
+/* Batches on the GPU now (launched, not yet collected). */
+int mpmi_server_in_flight(const mpmi_server* s, int32_t* n_out);
+/* *done = 1 when a batch in flight has finished (0 if none has, or none flies). */
 int mpmi_server_poll(mpmi_server* s, int32_t* done);
-/* Waits for the batch in flight and copies its results (host, in submission
- * order) with the sessions they belong to; *n_out = number of results. */
+/* Collects one batch in flight: the earliest launched of those that have
+ * finished, else waits for the earliest launched.  Copies its results (host, in
+ * submission order) with the sessions they belong to; *n_out = number of
+ * results.  NOT_READY if no batch is in flight. */
 int mpmi_server_collect(mpmi_server* s, mpmi_result* out, int32_t* slots_out, int32_t* n_out);
 /* Autotunes the server's launch shape for a request mix: for every compiled
  * shape of the model's basis (lanes per candidate x candidates per thread) at 64,
@@ -530,6 +543,16 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
                            const double* u_h_dev, uint64_t tick, int32_t k, float tau,
                            int32_t m, mpmi_result* result_dev, int32_t* list_dev,
                            int32_t* n_list_dev, void* stream);
+
+/* Phase timing of screened ticks (a measurement aid, not part of the method):
+ * with on != 0 every later mpmi_evaluate_screened of this screener records CUDA
+ * events on its stream around its four launches; mpmi_screener_phase_times waits
+ * for the last tick's events and writes ms_out[4] (host): the screen (network or
+ * cost keys and histograms), the compaction, the exact rollout of the kept slots
+ * and the fallback launch (which returns at once when it is not needed).  The
+ * events are created on the first switch-on.  NOT_READY if timing was never on. */
+int mpmi_screener_set_timing(mpmi_screener* s, int32_t on);
+int mpmi_screener_phase_times(mpmi_screener* s, float* ms_out);
 
 /* ---- a tick that allocates nothing -------------------------------------- */
 /* The paper has no counterpart to this entry point; it serves callers that may

@@ -790,6 +790,10 @@ struct mpmi_screener {
   int* list = nullptr;
   mpmi::ScreenScratch* ss = nullptr;
   uint64_t bytes = 0;
+  // optional phase timing of screened ticks: events around the screen, the
+  // compaction, the kept rollout and the fallback launch
+  bool timing = false;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace mpmi {
@@ -965,8 +969,28 @@ void mpmi_screener_free(mpmi_screener* s) {
   cudaFree(s->keys);
   cudaFree(s->list);
   cudaFree(s->ss);
+  for (cudaEvent_t& e : s->ev)
+    if (e) cudaEventDestroy(e);
   if (s->ctx) s->ctx->used -= s->bytes;
   delete s;
+}
+
+int mpmi_screener_set_timing(mpmi_screener* s, int32_t on) {
+  if (!s) return fail(MPMI_E_INVALID_ARG, "screener_set_timing: NULL screener");
+  if (on && !s->ev[0])  // on the current device, like the screener's launches
+    for (cudaEvent_t& e : s->ev) SCR_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+  s->timing = on != 0;
+  return MPMI_OK;
+}
+
+int mpmi_screener_phase_times(mpmi_screener* s, float* ms_out) {
+  if (!s || !ms_out) return fail(MPMI_E_INVALID_ARG, "screener_phase_times: NULL argument");
+  if (!s->ev[0]) return fail(MPMI_E_NOT_READY, "screener_phase_times: timing is off");
+  for (int i = 0; i < 4; ++i) {
+    SCR_CUDA(cudaEventSynchronize(s->ev[i + 1]), "cudaEventSynchronize");
+    SCR_CUDA(cudaEventElapsedTime(&ms_out[i], s->ev[i], s->ev[i + 1]), "cudaEventElapsedTime");
+  }
+  return MPMI_OK;
 }
 
 int mpmi_screener_get_weights(const mpmi_screener* s, float* out) {
@@ -1070,6 +1094,7 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
   a.x_t = x_t_dev;
   a.u_h = u_h_dev;
   a.result = result_dev;
+  if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[0], st), "cudaEventRecord");
   // at most two blocks per SM: with the network each holds 128 TMEM columns and
   // the staged weights; more blocks would only repeat the per-tick features
   if (tau > 0.f) {
@@ -1083,10 +1108,12 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
     if (blocks > 2 * s->ctx->sm_count) blocks = 2 * s->ctx->sm_count;
     screen_cost<<<blocks, 128, 0, st>>>(a, k, s->keys, s->ss);
   }
+  if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[1], st), "cudaEventRecord");
   int cb = (session->n_slots + 255) / 256;
   if (cb > 4 * s->ctx->sm_count) cb = 4 * s->ctx->sm_count;
   screen_compact<<<cb, 256, 0, st>>>(s->keys, session->n_slots, s->ss, s->list);
   SCR_CUDA(cudaGetLastError(), "screen launches");
+  if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[2], st), "cudaEventRecord");
   // exact rollout on the kept slots (their number is known only on the device)
   TickArgs r = a;
   r.slot_list = s->list;
@@ -1094,6 +1121,7 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
   r.result_flags = 1;
   rc = launch_tick_args(session, r, false, st, -1);
   if (rc != MPMI_OK) return rc;
+  if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[3], st), "cudaEventRecord");
   if (list_dev)
     SCR_CUDA(cudaMemcpyAsync(list_dev, s->list, sizeof(int) * session->n_slots,
                              cudaMemcpyDeviceToDevice, st), "copy list");
@@ -1105,7 +1133,9 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
   TickArgs f = a;
   f.skip_if_safe = result_dev;
   f.result_flags = 3;
-  return launch_tick_args(session, f, false, st, 0);
+  rc = launch_tick_args(session, f, false, st, 0);
+  if (rc == MPMI_OK && s->timing) SCR_CUDA(cudaEventRecord(s->ev[4], st), "cudaEventRecord");
+  return rc;
 }
 
 }  // extern "C"

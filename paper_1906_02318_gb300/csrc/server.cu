@@ -10,9 +10,12 @@
 // is therefore bit-identical whether it is served alone or in a mix.
 //
 // Host side: admission (a free session slot and room in the context's memory
-// budget), two batch buffers (one in flight while requests for the next are
-// staged), and one captured graph per buffer (table upload, kernel, result
-// download) so a batch costs one graph launch.
+// budget), kBuffers batch buffers, each with one captured graph (table upload,
+// kernel, result download) and a stream of its own, so a batch costs one graph
+// launch and up to max_in_flight batches of the model run at once while the
+// requests for the next one are staged.  A session has at most one request
+// staged or on the GPU, so batches in flight touch disjoint reduction records;
+// batches are collected in the order they complete.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -74,6 +77,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) serve_kernel(const __grid_consta
   __shared__ __align__(16) float s_x[(L > 1) ? NW : 1][2][GPW][S];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int q = lane % L;
+  // the grid covers the largest batch; a block past the batch's warp-tiles leaves
+  // before staging anything, so that a small batch holds few SMs and batches in
+  // flight at the same time share the device
+  if ((long long)blockIdx.x * (blockDim.x >> 5) >= (long long)sa.table->total_tiles) return;
 
   if constexpr (KSMEM) stage_k<N>(sa.Ks, s_dyn, tid, blockDim.x);
   TrackView tv{nullptr, nullptr, nullptr, nullptr};
@@ -210,25 +217,35 @@ static ServeKernel pick_serve(int kind) {
 }  // namespace mpmi
 
 // ---------------------------------------------------------------- host side
+constexpr int kServeBuffers = 5;                      // batch buffers
+constexpr int kServeMaxInFlight = kServeBuffers - 1;  // one is always free for staging
+
 struct mpmi_server {
   mpmi_ctx* ctx = nullptr;
   const mpmi_model* model = nullptr;
   int max_sessions = 0;
   std::vector<mpmi_session_config> cfg;
   std::vector<char> used;
+  // per session slot: 0 idle, 1 staged in the stage buffer, 2 on the GPU
+  std::vector<char> state;
   mpmi::TickScratch* scratch = nullptr;  // one record per session slot
-  // double-buffered batch state
-  mpmi::ServeHeader* table_host[2] = {nullptr, nullptr};  // pinned
-  mpmi::ServeHeader* table_dev[2] = {nullptr, nullptr};
-  mpmi_result* res_dev[2] = {nullptr, nullptr};
-  mpmi_result* res_host[2] = {nullptr, nullptr};         // pinned
-  std::vector<int> slots[2];
-  std::vector<char> in_batch;                            // per slot, staged this batch
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  cudaEvent_t done[2] = {nullptr, nullptr};
+  // batch buffers
+  mpmi::ServeHeader* table_host[kServeBuffers] = {};  // pinned
+  mpmi::ServeHeader* table_dev[kServeBuffers] = {};
+  mpmi_result* res_dev[kServeBuffers] = {};
+  mpmi_result* res_host[kServeBuffers] = {};         // pinned
+  std::vector<int> slots[kServeBuffers];
+  cudaGraphExec_t graph[kServeBuffers] = {};
+  cudaStream_t bstream[kServeBuffers] = {};  // each buffer's batches run here
+  cudaEvent_t start[kServeBuffers] = {};     // before the graph (timing)
+  cudaEvent_t done[kServeBuffers] = {};      // after the graph
+  cudaEvent_t after[kServeBuffers] = {};     // the caller's stream at launch
+  bool flying[kServeBuffers] = {};
+  unsigned long long seq[kServeBuffers] = {};  // launch order
+  unsigned long long next_seq = 0;
   cudaStream_t capture = nullptr;
-  int stage = 0;       // buffer receiving requests
-  int in_flight = -1;  // buffer on the GPU, or -1
+  int stage = 0;  // buffer receiving requests (never in flight)
+  int max_in_flight = kServeMaxInFlight;
   size_t table_bytes = 0, smem = 0;
   int grid = 0, block = 128;
   mpmi::ServeKernel kern;
@@ -268,10 +285,18 @@ static int build_graph(mpmi_server* s, int b) {
   return MPMI_OK;
 }
 
+static int n_flying(const mpmi_server* s) {
+  int n = 0;
+  for (int b = 0; b < kServeBuffers; ++b) n += s->flying[b] ? 1 : 0;
+  return n;
+}
+
 static void server_release_device(mpmi_server* s) {
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < kServeBuffers; ++b) {
     if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
-    if (s->done[b]) cudaEventDestroy(s->done[b]);
+    for (cudaEvent_t e : {s->start[b], s->done[b], s->after[b]})
+      if (e) cudaEventDestroy(e);
+    if (s->bstream[b]) cudaStreamDestroy(s->bstream[b]);
     cudaFreeHost(s->table_host[b]);
     cudaFreeHost(s->res_host[b]);
     cudaFree(s->table_dev[b]);
@@ -303,24 +328,29 @@ int mpmi_server_create(mpmi_ctx* ctx, const mpmi_model* model, int32_t max_sessi
   s->kern = kern;
   s->cfg.resize(max_sessions);
   s->used.assign(max_sessions, 0);
-  s->in_batch.assign(max_sessions, 0);
+  s->state.assign(max_sessions, 0);
   s->table_bytes = sizeof(ServeHeader) + sizeof(SessionTick) * (size_t)max_sessions;
   s->smem = kern.k_smem + (model->dev_safety.has_track ? (size_t)model->dev_safety.track.blob_bytes : 0);
-  s->per_session_bytes = sizeof(TickScratch) + 2 * (sizeof(SessionTick) + sizeof(mpmi_result));
-  const uint64_t fixed = 2 * (s->table_bytes + sizeof(mpmi_result) * (size_t)max_sessions) +
-                         sizeof(TickScratch) * (size_t)max_sessions;
+  s->per_session_bytes =
+      sizeof(TickScratch) + kServeBuffers * (sizeof(SessionTick) + sizeof(mpmi_result));
+  const uint64_t fixed =
+      kServeBuffers * (s->table_bytes + sizeof(mpmi_result) * (size_t)max_sessions) +
+      sizeof(TickScratch) * (size_t)max_sessions;
   if (ctx->budget && ctx->used + fixed > ctx->budget) {
     delete s;
     return fail(MPMI_E_OOM, "server: tables exceed the memory budget");
   }
   bool ok = cudaMalloc(&s->scratch, sizeof(TickScratch) * max_sessions) == cudaSuccess &&
             cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking) == cudaSuccess;
-  for (int b = 0; b < 2 && ok; ++b)
+  for (int b = 0; b < kServeBuffers && ok; ++b)
     ok = cudaMallocHost(&s->table_host[b], s->table_bytes) == cudaSuccess &&
          cudaMalloc(&s->table_dev[b], s->table_bytes) == cudaSuccess &&
          cudaMalloc(&s->res_dev[b], sizeof(mpmi_result) * max_sessions) == cudaSuccess &&
          cudaMallocHost(&s->res_host[b], sizeof(mpmi_result) * max_sessions) == cudaSuccess &&
-         cudaEventCreateWithFlags(&s->done[b], cudaEventDisableTiming) == cudaSuccess;
+         cudaStreamCreateWithFlags(&s->bstream[b], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreate(&s->start[b]) == cudaSuccess &&
+         cudaEventCreate(&s->done[b]) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s->after[b], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     server_release_device(s);
     delete s;
@@ -332,7 +362,7 @@ int mpmi_server_create(mpmi_ctx* ctx, const mpmi_model* model, int32_t max_sessi
     r.key = ~0ull;
   }
   cudaMemcpy(s->scratch, init.data(), sizeof(TickScratch) * max_sessions, cudaMemcpyHostToDevice);
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < kServeBuffers; ++b) {
     memset(s->table_host[b], 0, s->table_bytes);
     cudaMemset(s->table_dev[b], 0, s->table_bytes);
   }
@@ -342,7 +372,7 @@ int mpmi_server_create(mpmi_ctx* ctx, const mpmi_model* model, int32_t max_sessi
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern.fn, s->block, s->smem);
   s->grid = (nb < 1 ? 1 : nb) * ctx->sm_count;
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < kServeBuffers; ++b) {
     int rc = build_graph(s, b);
     if (rc != MPMI_OK) {
       server_release_device(s);
@@ -358,7 +388,8 @@ int mpmi_server_create(mpmi_ctx* ctx, const mpmi_model* model, int32_t max_sessi
 
 void mpmi_server_free(mpmi_server* s) {
   if (!s) return;
-  if (s->in_flight >= 0) cudaEventSynchronize(s->done[s->in_flight]);
+  for (int b = 0; b < kServeBuffers; ++b)
+    if (s->flying[b]) cudaEventSynchronize(s->done[b]);
   server_release_device(s);
   for (int i = 0; i < s->max_sessions; ++i)
     if (s->used[i]) s->ctx->used -= s->per_session_bytes;
@@ -401,10 +432,9 @@ int mpmi_server_admit(mpmi_server* s, const mpmi_session_config* cfg, int32_t* s
 int mpmi_server_release(mpmi_server* s, int32_t slot) {
   if (!s || slot < 0 || slot >= s->max_sessions || !s->used[slot])
     return fail(MPMI_E_INVALID_ARG, "server_release: no such session");
-  if (s->in_batch[slot]) return fail(MPMI_E_NOT_READY, "server_release: session has a staged request");
-  if (s->in_flight >= 0)
-    for (int v : s->slots[s->in_flight])
-      if (v == slot) return fail(MPMI_E_NOT_READY, "server_release: session is on the GPU");
+  if (s->state[slot] == 1)
+    return fail(MPMI_E_NOT_READY, "server_release: session has a staged request");
+  if (s->state[slot] == 2) return fail(MPMI_E_NOT_READY, "server_release: session is on the GPU");
   s->used[slot] = 0;
   s->ctx->used -= s->per_session_bytes;
   return MPMI_OK;
@@ -422,7 +452,10 @@ int mpmi_server_submit(mpmi_server* s, int32_t n, const int32_t* slots, const do
     const int sl = slots[r];
     if (sl < 0 || sl >= s->max_sessions || !s->used[sl])
       return fail(MPMI_E_INVALID_ARG, "server_submit: no such session");
-    if (s->in_batch[sl]) return fail(MPMI_E_INVALID_ARG, "server_submit: session already staged");
+    if (s->state[sl] == 1) return fail(MPMI_E_INVALID_ARG, "server_submit: session already staged");
+    if (s->state[sl] == 2)
+      return fail(MPMI_E_INVALID_ARG,
+                  "server_submit: session's previous request is on the GPU (collect it first)");
     for (int j = 0; j < m->nx; ++j)
       if (!isfinite(x_t[(size_t)r * m->nx + j])) return fail(MPMI_E_NONFINITE, "server_submit: x_t");
     for (int j = 0; j < m->nu; ++j)
@@ -462,57 +495,110 @@ int mpmi_server_submit(mpmi_server* s, int32_t n, const int32_t* slots, const do
     hdr->n_requests += 1;
     hdr->total_tiles += e.n_tiles;
     s->slots[s->stage].push_back(sl);
-    s->in_batch[sl] = 1;
+    s->state[sl] = 1;
   }
   return MPMI_OK;
 }
 
 int mpmi_server_launch(mpmi_server* s, void* stream, int32_t* n_launched) {
   if (!s) return fail(MPMI_E_INVALID_ARG, "server_launch: NULL argument");
-  if (s->in_flight >= 0) return fail(MPMI_E_NOT_READY, "server_launch: a batch is in flight");
   const int b = s->stage;
   const int n = s->table_host[b]->n_requests;
-  if (n_launched) *n_launched = n;
+  if (n_launched) *n_launched = 0;
   if (n == 0) return MPMI_OK;
+  if (n_flying(s) >= s->max_in_flight)
+    return fail(MPMI_E_NOT_READY, "server_launch: the most batches allowed in flight are on the "
+                                  "GPU (collect one first)");
+  // the batch follows the work queued so far on the caller's stream, and runs
+  // on its buffer's own stream so that it overlaps the batches in flight
   cudaStream_t st = (cudaStream_t)stream;
-  SRV_CUDA(cudaGraphLaunch(s->graph[b], st), "server graph launch");
-  SRV_CUDA(cudaEventRecord(s->done[b], st), "server event");
-  s->in_flight = b;
-  s->stage = 1 - b;
-  for (int sl : s->slots[b]) s->in_batch[sl] = 0;
-  // the other buffer starts empty
-  s->table_host[s->stage]->n_requests = 0;
-  s->table_host[s->stage]->total_tiles = 0;
-  s->slots[s->stage].clear();
+  SRV_CUDA(cudaEventRecord(s->after[b], st), "server event");
+  SRV_CUDA(cudaStreamWaitEvent(s->bstream[b], s->after[b], 0), "server stream wait");
+  SRV_CUDA(cudaEventRecord(s->start[b], s->bstream[b]), "server event");
+  SRV_CUDA(cudaGraphLaunch(s->graph[b], s->bstream[b]), "server graph launch");
+  SRV_CUDA(cudaEventRecord(s->done[b], s->bstream[b]), "server event");
+  if (n_launched) *n_launched = n;
+  s->flying[b] = true;
+  s->seq[b] = s->next_seq++;
+  for (int sl : s->slots[b]) s->state[sl] = 2;
+  // the next buffer not in flight receives the requests (one always is: at most
+  // kServeBuffers - 1 batches fly)
+  int nb = b;
+  for (int i = 1; i < kServeBuffers; ++i) {
+    const int c = (b + i) % kServeBuffers;
+    if (!s->flying[c]) {
+      nb = c;
+      break;
+    }
+  }
+  s->stage = nb;
+  s->table_host[nb]->n_requests = 0;
+  s->table_host[nb]->total_tiles = 0;
+  s->slots[nb].clear();
   return MPMI_OK;
+}
+
+int mpmi_server_set_max_in_flight(mpmi_server* s, int32_t n) {
+  if (!s || n < 1 || n > kServeMaxInFlight)
+    return fail(MPMI_E_INVALID_ARG, "server_set_max_in_flight: n must be in 1.." +
+                                        std::to_string(kServeMaxInFlight));
+  s->max_in_flight = n;
+  return MPMI_OK;
+}
+
+int mpmi_server_in_flight(const mpmi_server* s, int32_t* n_out) {
+  if (!s || !n_out) return fail(MPMI_E_INVALID_ARG, "server_in_flight: NULL argument");
+  *n_out = n_flying(s);
+  return MPMI_OK;
+}
+
+// The in-flight batch to collect: the earliest launched among those finished,
+// else the earliest launched (-1 if none flies).  *finished tells which.
+static int next_batch(const mpmi_server* s, bool* finished, cudaError_t* err) {
+  int oldest = -1, first_done = -1;
+  *err = cudaSuccess;
+  for (int b = 0; b < kServeBuffers; ++b) {
+    if (!s->flying[b]) continue;
+    if (oldest < 0 || s->seq[b] < s->seq[oldest]) oldest = b;
+    const cudaError_t e = cudaEventQuery(s->done[b]);
+    if (e == cudaSuccess) {
+      if (first_done < 0 || s->seq[b] < s->seq[first_done]) first_done = b;
+    } else if (e != cudaErrorNotReady) {
+      *err = e;
+      return b;
+    }
+  }
+  *finished = first_done >= 0;
+  return first_done >= 0 ? first_done : oldest;
 }
 
 int mpmi_server_poll(mpmi_server* s, int32_t* done) {
   if (!s || !done) return fail(MPMI_E_INVALID_ARG, "server_poll: NULL argument");
-  if (s->in_flight < 0) {
-    *done = 0;
-    return MPMI_OK;
-  }
-  const cudaError_t e = cudaEventQuery(s->done[s->in_flight]);
-  if (e == cudaSuccess) *done = 1;
-  else if (e == cudaErrorNotReady) *done = 0;
-  else return sfail(e, "server_poll");
+  bool finished = false;
+  cudaError_t e;
+  const int b = next_batch(s, &finished, &e);
+  if (e != cudaSuccess) return sfail(e, "server_poll");
+  *done = (b >= 0 && finished) ? 1 : 0;
   return MPMI_OK;
 }
 
 int mpmi_server_collect(mpmi_server* s, mpmi_result* out, int32_t* slots_out, int32_t* n_out) {
   if (!s || !out || !n_out) return fail(MPMI_E_INVALID_ARG, "server_collect: NULL argument");
-  if (s->in_flight < 0) return fail(MPMI_E_NOT_READY, "server_collect: no batch in flight");
-  const int b = s->in_flight;
-  SRV_CUDA(cudaEventSynchronize(s->done[b]), "server_collect");
+  bool finished = false;
+  cudaError_t e;
+  const int b = next_batch(s, &finished, &e);
+  if (e != cudaSuccess) return sfail(e, "server_collect");
+  if (b < 0) return fail(MPMI_E_NOT_READY, "server_collect: no batch in flight");
+  if (!finished) SRV_CUDA(cudaEventSynchronize(s->done[b]), "server_collect");
   const int n = (int)s->slots[b].size();
   memcpy(out, s->res_host[b], sizeof(mpmi_result) * n);
   if (slots_out) memcpy(slots_out, s->slots[b].data(), sizeof(int32_t) * n);
   *n_out = n;
+  for (int sl : s->slots[b]) s->state[sl] = 0;
   s->slots[b].clear();
   s->table_host[b]->n_requests = 0;
   s->table_host[b]->total_tiles = 0;
-  s->in_flight = -1;
+  s->flying[b] = false;
   return MPMI_OK;
 }
 
@@ -541,7 +627,7 @@ static int server_set_shape(mpmi_server* s, const ServeKernel& k, int block) {
   s->block = block;
   s->smem = smem;
   s->grid = nb * s->ctx->sm_count;
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < kServeBuffers; ++b) {
     if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
     s->graph[b] = nullptr;
     const int rc = build_graph(s, b);
@@ -560,7 +646,7 @@ int mpmi_server_tune(mpmi_server* s, int32_t n, const mpmi_session_config* cfgs,
   if (!s || !cfgs || !x_t || !u_h || !out || n < 1)
     return fail(MPMI_E_INVALID_ARG, "server_tune: NULL argument or n < 1");
   if (reps < 1 || reps > 100) return fail(MPMI_E_INVALID_ARG, "server_tune: reps must be in 1..100");
-  if (s->in_flight >= 0 || s->table_host[s->stage]->n_requests > 0)
+  if (n_flying(s) > 0 || s->table_host[s->stage]->n_requests > 0)
     return fail(MPMI_E_NOT_READY, "server_tune: a batch is staged or in flight");
   std::vector<int32_t> slots;
   auto release_all = [&]() {
@@ -574,12 +660,6 @@ int mpmi_server_tune(mpmi_server* s, int32_t n, const mpmi_session_config* cfgs,
       return rc;
     }
     slots.push_back(sl);
-  }
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-    if (e0) cudaEventDestroy(e0);
-    release_all();
-    return fail(MPMI_E_CUDA, "server_tune: events");
   }
   std::vector<mpmi_result> res(n);
   std::vector<int32_t> got(n);
@@ -608,15 +688,13 @@ int mpmi_server_tune(mpmi_server* s, int32_t n, const mpmi_session_config* cfgs,
         rc = mpmi_server_submit(s, n, slots.data(), x_t, u_h, ticks.data());
         if (rc != MPMI_OK) break;
         int32_t launched = 0, n_out = 0;
-        cudaEventRecord(e0, 0);
+        const int b = s->stage;  // the buffer this batch launches from
         rc = mpmi_server_launch(s, nullptr, &launched);
-        cudaEventRecord(e1, 0);
         if (rc != MPMI_OK) break;
         rc = mpmi_server_collect(s, res.data(), got.data(), &n_out);
         if (rc != MPMI_OK) break;
         float ms = 0.f;
-        if (cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        if (cudaEventElapsedTime(&ms, s->start[b], s->done[b]) != cudaSuccess) {
           rc = fail(MPMI_E_CUDA, "server_tune: timing a batch");
           break;
         }
@@ -641,8 +719,6 @@ int mpmi_server_tune(mpmi_server* s, int32_t n, const mpmi_session_config* cfgs,
   // keep the winner (or go back to the initial shape after a failure)
   const int rc2 = rc == MPMI_OK ? server_set_shape(s, best_k, best_block)
                                 : server_set_shape(s, initial, initial_block);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   release_all();
   if (rc != MPMI_OK) return rc;
   if (rc2 != MPMI_OK) return rc2;

@@ -117,6 +117,8 @@ _SIGNATURES = {
     "mpmi_server_staged": (c_i32, [c_vp, ctypes.POINTER(c_i32)]),
     "mpmi_server_launch": (c_i32, [c_vp, c_vp, ctypes.POINTER(c_i32)]),
     "mpmi_server_poll": (c_i32, [c_vp, ctypes.POINTER(c_i32)]),
+    "mpmi_server_set_max_in_flight": (c_i32, [c_vp, c_i32]),
+    "mpmi_server_in_flight": (c_i32, [c_vp, ctypes.POINTER(c_i32)]),
     "mpmi_server_collect": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(c_i32)]),
     "mpmi_screener_create": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, ctypes.POINTER(c_vp)]),
     "mpmi_screener_free": (None, [c_vp]),
@@ -127,6 +129,8 @@ _SIGNATURES = {
     "mpmi_screener_gradients": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
     "mpmi_screener_train_step": (c_i32, [c_vp, c_vp, c_vp, c_i32, ctypes.c_float, c_vp, c_vp]),
     "mpmi_screener_score": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
+    "mpmi_screener_set_timing": (c_i32, [c_vp, c_i32]),
+    "mpmi_screener_phase_times": (c_i32, [c_vp, c_vp]),
     "mpmi_evaluate_screened": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_i32, ctypes.c_float,
                                        c_i32, c_vp, c_vp, c_vp, c_vp]),
     "mpmi_evaluate_candidates_noalloc": (c_i32, [ctypes.POINTER(BasisDesc), c_vp,
@@ -656,6 +660,16 @@ class Screener:
         _check(self.ctx.lib.mpmi_screener_score(self.handle, _ptr(feats_dev), feats_dev.shape[0],
                                                 _ptr(scores_dev), _stream(stream)))
 
+    def set_timing(self, on: bool):
+        """mpmi_screener_set_timing: record CUDA events around a screened tick's launches."""
+        _check(self.ctx.lib.mpmi_screener_set_timing(self.handle, int(on)))
+
+    def phase_times(self) -> dict:
+        """mpmi_screener_phase_times: the last screened tick's launch durations (ms)."""
+        out = (ctypes.c_float * 4)()
+        _check(self.ctx.lib.mpmi_screener_phase_times(self.handle, out))
+        return dict(screen=out[0], compact=out[1], rollout=out[2], fallback=out[3])
+
     def free(self):
         if self.handle:
             self.ctx.lib.mpmi_screener_free(self.handle)
@@ -724,12 +738,23 @@ class Server:
         return n.value
 
     def poll(self) -> bool:
+        """True when a batch in flight has finished."""
         d = c_i32()
         _check(self.ctx.lib.mpmi_server_poll(self.handle, ctypes.byref(d)))
         return bool(d.value)
 
+    def set_max_in_flight(self, n: int):
+        """mpmi_server_set_max_in_flight: batches allowed on the GPU at once (1..4)."""
+        _check(self.ctx.lib.mpmi_server_set_max_in_flight(self.handle, int(n)))
+
+    def in_flight(self) -> int:
+        n = c_i32()
+        _check(self.ctx.lib.mpmi_server_in_flight(self.handle, ctypes.byref(n)))
+        return n.value
+
     def collect(self):
-        """[(slot, result dict), ...] of the batch in flight (waits for it)."""
+        """[(slot, result dict), ...] of one batch in flight: the earliest launched
+        of the finished ones, else the earliest launched (waits for it)."""
         n = c_i32()
         _check(self.ctx.lib.mpmi_server_collect(self.handle, self._res, self._slots.ctypes.data,
                                                 ctypes.byref(n)))

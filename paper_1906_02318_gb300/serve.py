@@ -3,11 +3,13 @@
 Sessions tick at their own rate (100 Hz balance bot, 60 Hz race car) with a
 seeded +-2 ms jitter; a tick's request is staged as soon as it is due and the
 session's previous request has completed (a controller needs its last output
-before its next input).  Each server runs at most one batch; while it runs, the
-requests that arrive are staged for the next one, and the servers' batches run
-on separate streams so they overlap on the device.  Latency is measured from a
-request's scheduled arrival to the moment its batch has been collected.  All
-computation runs in libmpmi; this module keeps clocks and queues.
+before its next input).  A server launches its staged requests as soon as it
+has fewer than `overlap` batches on the GPU, so requests that arrive while a
+batch runs start in a batch of their own that overlaps it on the device (with
+overlap = 1 they wait for the running batch to be collected); finished batches
+are collected in completion order.  Latency is measured from a request's
+scheduled arrival to the moment its batch has been collected.  All computation
+runs in libmpmi; this module keeps clocks and queues.
 """
 from __future__ import annotations
 
@@ -35,11 +37,15 @@ class ServedSession:
     latencies: list = field(default_factory=list)
 
 
-def run(servers, sessions, duration: float, streams=None, record=None):
-    """Serve `sessions` for `duration` seconds of wall time.  Returns stats; if
-    `record` is a dict, every result is stored under (session index, tick)."""
+def run(servers, sessions, duration: float, streams=None, record=None, overlap: int = 4):
+    """Serve `sessions` for `duration` seconds of wall time with at most `overlap`
+    batches per server on the GPU.  Returns stats; if `record` is a dict, every
+    result is stored under (session index, tick)."""
     import torch
     streams = streams or [torch.cuda.Stream() for _ in servers]
+    for srv in servers:
+        srv.set_max_in_flight(overlap)
+        srv._n_flying = srv._n_staged = 0
     by_server = [[] for _ in servers]
     for i, s in enumerate(sessions):
         by_server[s.server].append(i)
@@ -54,8 +60,7 @@ def run(servers, sessions, duration: float, streams=None, record=None):
         if now >= duration:
             break
         for si, srv in enumerate(servers):
-            in_flight = getattr(srv, "_in_flight", False)
-            if in_flight and srv.poll():
+            while srv._n_flying and srv.poll():
                 t_done = time.perf_counter() - t0
                 for slot, r in srv.collect():
                     ss = sessions[slot_to_sess[si][slot]]
@@ -67,7 +72,7 @@ def run(servers, sessions, duration: float, streams=None, record=None):
                     done_ticks += 1
                     if record is not None:
                         record[(slot_to_sess[si][slot], k)] = r
-                srv._in_flight = False
+                srv._n_flying -= 1
             # stage every due request of this server's sessions
             due = []
             for i in by_server[si]:
@@ -83,15 +88,17 @@ def run(servers, sessions, duration: float, streams=None, record=None):
                 for i in due:
                     sessions[i].outstanding = True
                     sessions[i].next_tick += 1
-            if not getattr(srv, "_in_flight", False) and srv.staged() > 0:
+            srv._n_staged += len(due)
+            if srv._n_flying < overlap and srv._n_staged:
                 batch_sizes.append(srv.launch(streams[si]))
-                srv._in_flight = True
+                srv._n_flying += 1
+                srv._n_staged = 0
                 batches += 1
     # drain
     for srv in servers:
-        if getattr(srv, "_in_flight", False):
+        while srv._n_flying:
             srv.collect()
-            srv._in_flight = False
+            srv._n_flying -= 1
     wall = time.perf_counter() - t0
     lat = {}
     for kind in sorted({s.period for s in sessions}):

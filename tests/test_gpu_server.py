@@ -113,19 +113,70 @@ def test_protocol_errors(lib, ctx):
         srv.collect()                                   # nothing in flight
     srv.submit([a], [[0.1, 0, 0, 0]], [[0.2]], [0])
     with pytest.raises(lib.MpmiError):
-        srv.submit([a], [[0.1, 0, 0, 0]], [[0.2]], [1])  # one request per batch
+        srv.submit([a], [[0.1, 0, 0, 0]], [[0.2]], [1])  # one request per session
     with pytest.raises(lib.MpmiError):
         srv.release(a)                                  # staged
     with pytest.raises(lib.MpmiError) as e:
         srv.submit([b], [[np.nan, 0, 0, 0]], [[0.2]], [0])
     assert e.value.code == -3
-    assert srv.launch() == 1
+    assert srv.launch() == 1 and srv.in_flight() == 1
+    assert srv.launch() == 0                            # nothing staged
     with pytest.raises(lib.MpmiError):
-        srv.launch()                                    # previous batch not collected
-    srv.submit([a, b], [[0.1, 0, 0, 0], [0.0, 0.1, 0, 0]], [[0.2], [0.3]], [1, 0])
-    assert len(srv.collect()) == 1
-    assert srv.launch() == 2
-    assert {s for s, _ in srv.collect()} == {a, b}
+        srv.submit([a], [[0.1, 0, 0, 0]], [[0.2]], [1])  # its request is on the GPU
+    with pytest.raises(lib.MpmiError):
+        srv.release(a)                                  # on the GPU
+    # one batch at a time: the next launch waits for a collect
+    srv.set_max_in_flight(1)
+    srv.submit([b], [[0.0, 0.1, 0, 0]], [[0.3]], [0])
+    with pytest.raises(lib.MpmiError) as e:
+        srv.launch()
+    assert e.value.code == -5
+    assert [s for s, _ in srv.collect()] == [a]
+    srv.set_max_in_flight(4)
+    assert srv.launch() == 1
+    srv.submit([a], [[0.1, 0, 0, 0]], [[0.2]], [1])
+    assert srv.launch() == 1 and srv.in_flight() == 2   # two batches of one model
+    got = [srv.collect(), srv.collect()]
+    assert sorted(s for batch in got for s, _ in batch) == [a, b]
+    assert srv.in_flight() == 0
+    with pytest.raises(lib.MpmiError):
+        srv.set_max_in_flight(5)
+    srv.free()
+    model.free()
+
+
+@pytest.mark.parametrize("which", ["bot", "car"])
+def test_overlapping_batches_equal_alone(lib, ctx, which):
+    """Batches of one model launched while earlier ones are still on the GPU (up
+    to four at once) run concurrently; every result is bit-identical to the same
+    tick alone, whichever batch carried it and in whatever order they finish."""
+    env = bot_env() if which == "bot" else car_env()
+    model = gpu_model(lib, ctx, env)
+    srv = lib.Server(ctx, model, max_sessions=16)
+    rng = np.random.default_rng(5)
+    specs = [(65535, 60), (30000, 100), (1023, 20), (7, 5), (4096, 50), (20000, 33),
+             (0, 9), (12000, 80)]
+    slots = [srv.admit(n, H, env.lo, env.hi, seed=300 + i, stream_id=40 + i)
+             for i, (n, H) in enumerate(specs)]
+    xs = _states(env, which, len(specs), 21)
+    us = data.to_f32_exact(rng.uniform(env.lo, env.hi, (len(specs), len(env.lo))))
+    ticks = [500 + 3 * i for i in range(len(specs))]
+    groups = [[0, 1], [2, 3], [4, 5, 6], [7]]           # a big batch first, then smaller
+    for g in groups:
+        srv.submit([slots[i] for i in g], xs[g], us[g], [ticks[i] for i in g])
+        assert srv.launch() == len(g)
+    assert srv.in_flight() == len(groups)
+    got = {}
+    for _ in groups:
+        for sl, r in srv.collect():
+            got[sl] = r
+    assert srv.in_flight() == 0 and len(got) == len(specs)
+    for i, (n, H) in enumerate(specs):
+        a = _alone(lib, ctx, model, env, n, H, 300 + i, 40 + i, xs[i], us[i], ticks[i])
+        r = got[slots[i]]
+        for k in ("index", "status", "n_safe", "ttv", "executed_steps", "n_slots", "tick"):
+            assert r[k] == a[k], (i, k)
+        assert np.array_equal(r["u_r"], a["u_r"]) and r["cost"] == a["cost"]
     srv.free()
     model.free()
 
