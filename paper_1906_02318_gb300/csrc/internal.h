@@ -47,6 +47,7 @@ struct TickScratch {
 struct TickArgs {
   const float* K;      // n x n float32 row-major (device)
   const float* Ks;     // the same K with each row's columns in staging order
+  const float* Kp;     // the free rows of K in pairs (KPair layout; race car)
                        // (free columns, then held ones; shared-memory shapes)
   const double* x_t;   // device, nx
   const double* u_h;   // device, nu
@@ -129,7 +130,9 @@ struct mpmi_model {
   mpmi_ctx* ctx = nullptr;
   int basis = 0, kind = 0, n = 0, nx = 0, nu = 0, np = 0;
   std::vector<double> K64;
-  float* K32_dev = nullptr;  // n x n row-major, then the same rows in staging order
+  // n x n row-major, then the same rows in staging order, then (race car) the
+  // pair layout of the one-lane shared-memory shapes
+  float* K32_dev = nullptr;
   bool has_safety = false;
   mpmi_safety_spec spec{};
   std::vector<double> track_host;

@@ -112,6 +112,7 @@ TickArgs make_tick_args(const mpmi_session* s, uint64_t tick) {
   memset(&a, 0, sizeof(a));
   a.K = m->K32_dev;
   a.Ks = m->K32_dev + (size_t)m->n * m->n;
+  a.Kp = m->K32_dev + 2 * (size_t)m->n * m->n;
   a.safety = m->dev_safety;
   a.kind = m->kind;
   a.n_samples = s->cfg.n_samples;
@@ -341,17 +342,29 @@ static void free_model_device(mpmi_model* m) {
   m->track_dev = nullptr;
 }
 
-// K in float32 twice: row-major, then with each row's columns in staging order
-// (the layout the shared-memory shapes copy in one piece).
+// 16-byte words of the pair layout of K for a basis (0 where no shape uses it).
+static size_t kpair_words(int kind) {
+  return kind == kCar ? (size_t)KPair<kCar>::WORDS : 0;
+}
+
+// K in float32: row-major, then with each row's columns in staging order (the
+// layout the row-split shared-memory shapes copy in one piece), then the pair
+// layout of the one-lane shared-memory shapes (race car).
 static int model_upload(mpmi_ctx* ctx, mpmi_model* m) {
   const size_t nn = (size_t)m->n * m->n;
-  const size_t bytes = sizeof(float) * 2 * nn;
+  const size_t np = 4 * kpair_words(m->kind);
+  const size_t bytes = sizeof(float) * (2 * nn + np);
   if (!budget_ok(ctx, bytes)) return fail(MPMI_E_OOM, "model exceeds the memory budget");
-  std::vector<float> k32(2 * nn);
+  std::vector<float> k32(2 * nn + np);
   for (size_t i = 0; i < nn; ++i) k32[i] = (float)m->K64[i];
   for (int r = 0; r < m->n; ++r)
     for (int p = 0; p < m->n; ++p)
       k32[nn + (size_t)r * m->n + p] = (float)m->K64[(size_t)r * m->n + staged_col(m->kind, m->n, p)];
+  for (size_t i = 0; i < np; ++i) {
+    const int wpp = (int)(kpair_words(m->kind) / (size_t)KPair<kCar>::PAIRS);
+    const int e = (int)(i & 3), w = (int)(i / 4) % wpp, p = (int)(i / 4) / wpp;
+    k32[2 * nn + i] = kpair_value(m->kind, m->n, k32.data(), p, w, e);
+  }
   if (cudaMalloc(&m->K32_dev, bytes) != cudaSuccess)
     return fail(MPMI_E_OOM, "cudaMalloc of K failed");
   MPMI_CUDA(cudaMemcpy(m->K32_dev, k32.data(), bytes, cudaMemcpyHostToDevice), "upload K");

@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(kMaxBlock)
   constexpr int S = (N % 32 == 0) ? N + 4 : ((N % 4 == 0) ? N : N + (4 - N % 4));
   constexpr int NW = kMaxBlock / 32;
   constexpr int ANG = (KIND == kBot) ? 0 : ((KIND == kCar) ? 2 : -1);
-  constexpr int KWORDS = KSMEM ? KSmem<N>::WORDS : 0;
+  constexpr int KWORDS = ksmem_words<KIND, L, KSMEM, true>();
+  constexpr bool PK = pair_k<KIND, L, KSMEM, true>();
 
   extern __shared__ uint4 s_dyn[];
   __shared__ __align__(16) float s_x[(L > 1) ? NW : 1][2][GPW][S];
@@ -106,8 +107,9 @@ __global__ void __launch_bounds__(kMaxBlock)
     if (tid == 0) bar_init(&s_bar);
     __syncthreads();
     if (tid == 0)
-      stage_issue(&s_bar, s_dyn, a.Ks, KSMEM ? N : 0, N, KSmem<N>::S4, a.safety.track.blob,
-                  track_on ? a.safety.track.blob_bytes : 0, a.withhold_staging != 0);
+      stage_issue(&s_bar, s_dyn, a.Ks, (KSMEM && !PK) ? N : 0, N, KSmem<N>::S4,
+                  a.safety.track.blob, track_on ? a.safety.track.blob_bytes : 0,
+                  a.withhold_staging != 0, a.Kp, PK ? (int)KPair<KIND>::BYTES : 0);
   }
   TrackView tv{nullptr, nullptr, nullptr, nullptr};
   if constexpr (B::TRACK) {
@@ -216,7 +218,7 @@ template <int KIND, int L, int C, bool KSMEM>
 static PersistKernel make_persist() {
   PersistKernel k;
   k.fn = reinterpret_cast<const void*>(&tick_persistent<KIND, L, C, KSMEM>);
-  k.k_smem = KSMEM ? KSmem<BasisTraits<KIND>::N>::BYTES : 0;
+  k.k_smem = (size_t)ksmem_words<KIND, L, KSMEM, true>() * 16;
   return k;
 }
 

@@ -60,6 +60,7 @@ struct ServeHeader {
 struct ServeArgs {
   const float* K;
   const float* Ks;  // K with each row's columns in staging order
+  const float* Kp;  // the free rows of K in pairs (KPair layout; race car)
   DevSafety safety;
   const ServeHeader* table;  // header followed by SessionTick entries
 };
@@ -72,7 +73,8 @@ __global__ void __launch_bounds__(kMaxBlock, 1) serve_kernel(const __grid_consta
   constexpr int S = (N % 32 == 0) ? N + 4 : ((N % 4 == 0) ? N : N + (4 - N % 4));
   constexpr int NW = kMaxBlock / 32;
   constexpr int ANG = (KIND == kBot) ? 0 : ((KIND == kCar) ? 2 : -1);
-  constexpr int KWORDS = KSMEM ? KSmem<N>::WORDS : 0;
+  constexpr int KWORDS = ksmem_words<KIND, L, KSMEM, true>();
+  constexpr bool PK = pair_k<KIND, L, KSMEM, true>();
   extern __shared__ uint4 s_dyn[];
   __shared__ __align__(16) float s_x[(L > 1) ? NW : 1][2][GPW][S];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -82,7 +84,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) serve_kernel(const __grid_consta
   // flight at the same time share the device
   if ((long long)blockIdx.x * (blockDim.x >> 5) >= (long long)sa.table->total_tiles) return;
 
-  if constexpr (KSMEM) stage_k<N>(sa.Ks, s_dyn, tid, blockDim.x);
+  if constexpr (PK) {
+    const uint4* src = reinterpret_cast<const uint4*>(sa.Kp);
+    for (int i = tid; i < KWORDS; i += blockDim.x) s_dyn[i] = __ldg(&src[i]);
+  } else if constexpr (KSMEM) {
+    stage_k<N>(sa.Ks, s_dyn, tid, blockDim.x);
+  }
   TrackView tv{nullptr, nullptr, nullptr, nullptr};
   if constexpr (B::TRACK) {
     if (sa.safety.has_track) {
@@ -184,7 +191,7 @@ static ServeKernel make_serve() {
   ServeKernel k;
   k.fn = reinterpret_cast<const void*>(&serve_kernel<KIND, L, C, KSMEM>);
   k.launch = &launch_serve<KIND, L, C, KSMEM>;
-  k.k_smem = KSMEM ? KSmem<BasisTraits<KIND>::N>::BYTES : 0;
+  k.k_smem = (size_t)ksmem_words<KIND, L, KSMEM, true>() * 16;
   k.per_warp = 32 / L * C;
   k.lanes = L;
   k.cands = C;
@@ -268,6 +275,7 @@ static int build_graph(mpmi_server* s, int b) {
   memset(&a, 0, sizeof(a));
   a.K = s->model->K32_dev;
   a.Ks = s->model->K32_dev + (size_t)s->model->n * s->model->n;
+  a.Kp = s->model->K32_dev + 2 * (size_t)s->model->n * s->model->n;
   a.safety = s->model->dev_safety;
   a.table = s->table_dev[b];
   cudaGraph_t g = nullptr;

@@ -27,7 +27,7 @@ static TickKernel make_kernel() {
   TickKernel k;
   k.fn = reinterpret_cast<const void*>(&tick_kernel<KIND, L, C, KSMEM, TRAJ, false, NOISE>);
   k.launch = &launch_tick<KIND, L, C, KSMEM, TRAJ, NOISE>;
-  k.k_smem = KSMEM ? KSmem<BasisTraits<KIND>::N>::BYTES : 0;
+  k.k_smem = (size_t)ksmem_words<KIND, L, KSMEM, true>() * 16;
   return k;
 }
 

@@ -80,14 +80,17 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
 
 // Issues the copies of one staging (thread 0): K with padded rows (k_rows > 0,
 // row r of n floats to word r * s4) and then `blob_bytes` of blob.
+// With kp_bytes > 0 K is one contiguous blob (the pair layout) copied first instead.
 __device__ __forceinline__ void stage_issue(uint64_t* bar, uint4* dst, const float* K, int k_rows,
                                             int k_cols, int s4, const uint4* blob, int blob_bytes,
-                                            bool withhold) {
+                                            bool withhold, const float* Kp = nullptr,
+                                            int kp_bytes = 0) {
   const uint32_t row_bytes = (uint32_t)k_cols * 4u;
-  bar_expect(bar, (uint32_t)k_rows * row_bytes + (uint32_t)blob_bytes);
+  bar_expect(bar, (uint32_t)k_rows * row_bytes + (uint32_t)kp_bytes + (uint32_t)blob_bytes);
   if (withhold) return;
   for (int r = 0; r < k_rows; ++r) bulk_g2s(dst + r * s4, K + (size_t)r * k_cols, row_bytes, bar);
-  uint4* bd = dst + k_rows * s4;
+  if (kp_bytes > 0) bulk_g2s(dst, Kp, (uint32_t)kp_bytes, bar);
+  uint4* bd = dst + k_rows * s4 + kp_bytes / 16;
   for (int off = 0; off < blob_bytes; off += 32768) {
     const int b = blob_bytes - off < 32768 ? blob_bytes - off : 32768;
     bulk_g2s(reinterpret_cast<char*>(bd) + off, reinterpret_cast<const char*>(blob) + off,
@@ -139,6 +142,77 @@ static_assert(staged_order_ok(kBot, 12) && staged_order_ok(kCar, 32) &&
                   staged_order_ok(kLin41, 5),
               "staging order");
 
+// The i-th free (not held) feature of a basis, ascending, or the i-th held one,
+// in closed form so that unrolled loops index z with constants (checked against
+// held_feature below).  Bot: held 4, 11; race car: held 6, 7, 30, 31; linear
+// bases: the held inputs come last.
+MPMI_HD constexpr int nth_feature(int kind, int n, int i, bool held) {
+  return kind == kBot   ? (held ? (i == 0 ? 4 : 11) : (i < 4 ? i : i + 1))
+         : kind == kCar ? (held ? (i < 2 ? 6 + i : 28 + i) : (i < 6 ? i : i + 2))
+                        : (held ? free_cols(kind, n) + i : i);
+}
+
+constexpr bool nth_feature_ok(int kind, int n) {
+  const int nf = free_cols(kind, n);
+  for (int i = 0; i < n; ++i) {
+    const bool held = i >= nf;
+    const int k = nth_feature(kind, n, held ? i - nf : i, held);
+    if (k < 0 || k >= n || held_feature(kind, k) != held) return false;
+    if (i > 0 && i != nf && nth_feature(kind, n, held ? i - nf - 1 : i - 1, held) >= k)
+      return false;
+  }
+  return true;
+}
+static_assert(nth_feature_ok(kBot, 12) && nth_feature_ok(kCar, 32) && nth_feature_ok(kLin11, 2) &&
+                  nth_feature_ok(kLin22, 4) && nth_feature_ok(kLin41, 5),
+              "free and held feature order");
+
+// K for the one-lane shapes with K in shared memory, rows in pairs: the free rows
+// go two at a time (free features 2p and 2p + 1) through packed two-wide FMAs
+// (fma.rn.f32x2), each half of which is the same fused multiply-add of its own
+// row's chain.  Pair p holds WPP 16-byte words: word j < NF / 2 is {K[r0][c],
+// K[r1][c], K[r0][c'], K[r1][c']} for the free columns c = 2j-th and c' =
+// (2j + 1)-th, ascending; the last NH / 2 words hold the held columns the same
+// way.  One broadcast LDS.128 thus feeds two packed FMAs, and each packed FMA
+// advances two rows' chains at once (the rows' FMA chains, not the FMA pipe,
+// limit a step with one warp per sub-partition).  The model builds this copy on
+// the host (model_upload); the kernels stage it verbatim.
+template <int KIND>
+struct KPair {
+  static constexpr int N = BasisTraits<KIND>::N;
+  static constexpr int NF = free_cols(KIND, N);
+  static constexpr int NH = N - NF;
+  static constexpr bool OK = (NF % 4 == 0) && (NH % 2 == 0) && NF >= 2;
+  static constexpr int PAIRS = NF / 2;
+  static constexpr int WPP = NF / 2 + NH / 2;  // 16-byte words per pair of rows
+  static constexpr int WORDS = PAIRS * WPP;
+  static constexpr size_t BYTES = (size_t)WORDS * 16;
+};
+
+// Whether a shape stages K in the pair layout: one lane, K in shared memory, and
+// the held rows copied (HELD; the no-allocation variant computes every row from
+// the caller's K and keeps the row layout).
+template <int KIND, int L, bool KSMEM, bool HELD>
+MPMI_HD constexpr bool pair_k() {
+  return KSMEM && L == 1 && HELD && KPair<KIND>::OK;
+}
+
+// 16-byte words of K a shape stages in shared memory (the track grid follows).
+template <int KIND, int L, bool KSMEM, bool HELD>
+MPMI_HD constexpr int ksmem_words() {
+  return !KSMEM ? 0 : (pair_k<KIND, L, KSMEM, HELD>() ? KPair<KIND>::WORDS
+                                                       : KSmem<BasisTraits<KIND>::N>::WORDS);
+}
+
+// Float of the pair layout at (pair p, word w, element e) for a row-major K.
+MPMI_HD float kpair_value(int kind, int n, const float* K, int p, int w, int e) {
+  const int nf = free_cols(kind, n);
+  const int r = nth_feature(kind, n, 2 * p + (e & 1), false);
+  const int i = 2 * w + (e >> 1);
+  const int c = i < nf ? nth_feature(kind, n, i, false) : nth_feature(kind, n, i - nf, true);
+  return K[(size_t)r * n + c];
+}
+
 // K already in staging order (the model's staging copy) into padded rows.
 template <int N>
 __device__ __forceinline__ void stage_k(const float* Ks, uint4* dst, int tid, int nthreads) {
@@ -156,6 +230,23 @@ __device__ __forceinline__ void stage_k_gather(const float* K, uint4* dst, int t
   for (int i = tid; i < N * N; i += nthreads) {
     const int r = i / N, p = i % N;
     d[r * 4 * KSmem<N>::S4 + p] = __ldg(K + r * N + staged_col(KIND, N, p));
+  }
+}
+
+// K in row-major column order (a caller's buffer) into the pair layout, one
+// float at a time.
+template <int KIND>
+__device__ __forceinline__ void stage_kpair_gather(const float* K, uint4* dst, int tid,
+                                                   int nthreads) {
+  constexpr int N = BasisTraits<KIND>::N;
+  constexpr int WPP = KPair<KIND>::WPP;
+  float* d = reinterpret_cast<float*>(dst);
+  for (int i = tid; i < KPair<KIND>::WORDS * 4; i += nthreads) {
+    const int e = i & 3, w = (i >> 2) % WPP, p = (i >> 2) / WPP;
+    d[i] = __ldg(K + (size_t)nth_feature(KIND, N, 2 * p + (e & 1), false) * N +
+                 (2 * w + (e >> 1) < KPair<KIND>::NF
+                      ? nth_feature(KIND, N, 2 * w + (e >> 1), false)
+                      : nth_feature(KIND, N, 2 * w + (e >> 1) - KPair<KIND>::NF, true)));
   }
 }
 
@@ -505,8 +596,29 @@ __device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety&
 
   // the held columns' share of each row this lane computes (HELD only)
   constexpr int HR = (L == 1) ? N : R;  // rows per candidate held in hc
-  float hc[HELD ? C : 1][HELD ? HR : 1];
-  if constexpr (HELD) {
+  constexpr bool PK = pair_k<KIND, L, KSMEM, HELD>();
+  using KP = KPair<KIND>;
+  float hc[HELD && !PK ? C : 1][HELD && !PK ? HR : 1];
+  float2 hp[PK ? C : 1][PK ? KP::PAIRS : 1];  // the same, two rows per pair
+  if constexpr (PK) {
+    // held words of pair p: columns (held 2j, held 2j + 1) of both rows
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+#pragma unroll
+      for (int pp = 0; pp < KP::PAIRS; ++pp) {
+        float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < KP::NH / 2; ++j) {
+          const float4 w = sK4[pp * KP::WPP + KP::NF / 2 + j];
+          const float z0 = z[c][nth_feature(KIND, N, 2 * j, true)];
+          const float z1 = z[c][nth_feature(KIND, N, 2 * j + 1, true)];
+          v = __ffma2_rn(make_float2(w.x, w.y), make_float2(z0, z0), v);
+          v = __ffma2_rn(make_float2(w.z, w.w), make_float2(z1, z1), v);
+        }
+        hp[c][pp] = v;
+      }
+    }
+  } else if constexpr (HELD) {
 #pragma unroll
     for (int c = 0; c < C; ++c) {
 #pragma unroll
@@ -527,8 +639,56 @@ __device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety&
     }
   }
 
+  // the first PREG pairs' free words stay in registers for the whole horizon
+  // (fewer shared-memory wavefronts per step; the registers a single candidate
+  // per thread leaves free)
+  constexpr int PREG = (PK && C == 1) ? 2 : 0;
+  float4 kreg[PREG > 0 ? PREG : 1][PREG > 0 ? KP::NF / 2 : 1];
+  if constexpr (PREG > 0) {
+#pragma unroll
+    for (int pp = 0; pp < PREG; ++pp)
+#pragma unroll
+      for (int j = 0; j < KP::NF / 2; ++j) kreg[pp][j] = sK4[pp * KP::WPP + j];
+  }
   for (int t = 1; t <= H; ++t) {
-    if constexpr (KSMEM && L == 1) {
+    if constexpr (PK) {
+      // z <- K z with the free rows in pairs (see KPair): per pair one chain of
+      // packed FMAs, continuing from the held columns' share, over the free
+      // columns ascending; the held rows are copied.
+      asm volatile("" ::: "memory");
+      float acc[C][N];
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int r = 0; r < N; ++r)
+          if (held_feature(KIND, r)) acc[c][r] = z[c][r];
+#pragma unroll
+      for (int pp = 0; pp < KP::PAIRS; ++pp) {
+        float2 v[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) v[c] = hp[c][pp];
+#pragma unroll
+        for (int j = 0; j < KP::NF / 2; ++j) {
+          const float4 w = pp < PREG ? kreg[pp < PREG ? pp : 0][j] : sK4[pp * KP::WPP + j];
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            const float z0 = z[c][nth_feature(KIND, N, 2 * j, false)];
+            const float z1 = z[c][nth_feature(KIND, N, 2 * j + 1, false)];
+            v[c] = __ffma2_rn(make_float2(w.x, w.y), make_float2(z0, z0), v[c]);
+            v[c] = __ffma2_rn(make_float2(w.z, w.w), make_float2(z1, z1), v[c]);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          acc[c][nth_feature(KIND, N, 2 * pp, false)] = v[c].x;
+          acc[c][nth_feature(KIND, N, 2 * pp + 1, false)] = v[c].y;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int r = 0; r < N; ++r) z[c][r] = acc[c][r];
+    } else if constexpr (KSMEM && L == 1) {
       // z <- K z with K read from shared memory (one broadcast LDS.128 feeds 4 C
       // FMAs).  The empty asm keeps the compiler from hoisting the loop-invariant
       // K loads out of the step loop (1024 values would not fit in registers).
@@ -796,7 +956,8 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
   constexpr int S = (N % 32 == 0) ? N + 4 : ((N % 4 == 0) ? N : N + (4 - N % 4));
   constexpr int NW = kMaxBlock / 32;
   constexpr int ANG = (KIND == kBot) ? 0 : ((KIND == kCar) ? 2 : -1);
-  constexpr int KWORDS = KSMEM ? KSmem<N>::WORDS : 0;  // 16-byte words of K in shared memory
+  constexpr int KWORDS = ksmem_words<KIND, L, KSMEM, !PARTIALS>();  // 16-byte words of K
+  constexpr bool PK = pair_k<KIND, L, KSMEM, !PARTIALS>();
 
   extern __shared__ uint4 s_dyn[];  // [K in staging order (KSMEM)] [track blob (race car)]
   __shared__ __align__(16) float s_x[(L > 1) ? NW : 1][2][GPW][S];
@@ -841,8 +1002,9 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
       if (tid == 0) bar_init(&s_bar);
       __syncthreads();
       if (tid == 0)
-        stage_issue(&s_bar, s_dyn, a.Ks, KSMEM ? N : 0, N, KSmem<N>::S4, a.safety.track.blob,
-                    track_on ? a.safety.track.blob_bytes : 0, a.withhold_staging != 0);
+        stage_issue(&s_bar, s_dyn, a.Ks, (KSMEM && !PK) ? N : 0, N, KSmem<N>::S4,
+                    a.safety.track.blob, track_on ? a.safety.track.blob_bytes : 0,
+                    a.withhold_staging != 0, a.Kp, PK ? (int)KPair<KIND>::BYTES : 0);
     }
   } else {
     if constexpr (KSMEM) stage_k_gather<KIND>(a.K, s_dyn, tid, blockDim.x);
