@@ -86,6 +86,9 @@ struct TickArgs {
   int ro_idx[MPMI_MAX_NX];
   // test hook: stage nothing, so the bounded staging wait runs out
   int withhold_staging;
+  // launched as a programmatic dependent of the previous kernel on the stream
+  // (a screened tick's chain): wait for it before reading anything
+  int chained;
   // zero-copy host ticks: after the result, the decoding block stores seq here
   // (pinned host memory) behind a system-scope fence
   unsigned long long* seq_out;

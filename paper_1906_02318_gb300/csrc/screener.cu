@@ -673,6 +673,7 @@ __global__ void __launch_bounds__(kScoreThreads) screen_score(TickArgs a, Featur
   __shared__ float s_feat[12];
   __shared__ uint64_t s_bar;
   __shared__ uint32_t s_tmem;
+  grid_dep_release();  // the compaction may launch now; it waits for this kernel
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) {
     s_hist[i] = 0;
     s_hsafe[i] = 0;
@@ -731,6 +732,7 @@ __global__ void __launch_bounds__(kScoreThreads) screen_score(TickArgs a, Featur
 __global__ void __launch_bounds__(128) screen_cost(TickArgs a, int k, unsigned int* keys,
                                                   ScreenScratch* ss) {
   __shared__ unsigned int s_hist[kBins];
+  grid_dep_release();  // the compaction may launch now; it waits for this kernel
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) s_hist[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
@@ -757,6 +759,8 @@ __global__ void __launch_bounds__(128) screen_cost(TickArgs a, int k, unsigned i
 // Keeps the slots whose cost bin is at or below the threshold (warp-aggregated append).
 __global__ void screen_compact(const unsigned int* keys, int n_slots, ScreenScratch* ss,
                                int* list) {
+  grid_dep_wait();     // the screen's keys and threshold
+  grid_dep_release();  // the rollout of the kept slots may launch now
   const int bstar = ss->bstar;
   const int lane = threadIdx.x & 31;
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_slots;
@@ -1111,7 +1115,22 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
   if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[1], st), "cudaEventRecord");
   int cb = (session->n_slots + 255) / 256;
   if (cb > 4 * s->ctx->sm_count) cb = 4 * s->ctx->sm_count;
-  screen_compact<<<cb, 256, 0, st>>>(s->keys, session->n_slots, s->ss, s->list);
+  {
+    // the compaction, the rollout and the fallback run as programmatic
+    // dependents: each may launch while its predecessor runs and waits for it
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cb);
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SCR_CUDA(cudaLaunchKernelEx(&cfg, screen_compact, (const unsigned int*)s->keys,
+                                (int)session->n_slots, s->ss, s->list),
+             "screen_compact launch");
+  }
   SCR_CUDA(cudaGetLastError(), "screen launches");
   if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[2], st), "cudaEventRecord");
   // exact rollout on the kept slots (their number is known only on the device)
@@ -1119,6 +1138,7 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
   r.slot_list = s->list;
   r.n_list = &s->ss->n_list;
   r.result_flags = 1;
+  r.chained = 1;
   rc = launch_tick_args(session, r, false, st, -1);
   if (rc != MPMI_OK) return rc;
   if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[3], st), "cudaEventRecord");
@@ -1133,6 +1153,7 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
   TickArgs f = a;
   f.skip_if_safe = result_dev;
   f.result_flags = 3;
+  f.chained = 1;
   rc = launch_tick_args(session, f, false, st, 0);
   if (rc == MPMI_OK && s->timing) SCR_CUDA(cudaEventRecord(s->ev[4], st), "cudaEventRecord");
   return rc;

@@ -17,9 +17,26 @@ struct TickKernel {
   size_t k_smem = 0;  // bytes of K staged in shared memory
 };
 
+// A TickArgs with `chained` set is launched with programmatic stream
+// serialisation (it may start before the previous kernel on the stream ends and
+// waits for it in the kernel); any other launch is an ordinary one.
 template <int KIND, int L, int C, bool KSMEM, bool TRAJ, bool NOISE>
 static void launch_tick(const TickArgs& a, int grid, int block, size_t smem, cudaStream_t st) {
-  tick_kernel<KIND, L, C, KSMEM, TRAJ, false, NOISE><<<grid, block, smem, st>>>(a);
+  if (!a.chained) {
+    tick_kernel<KIND, L, C, KSMEM, TRAJ, false, NOISE><<<grid, block, smem, st>>>(a);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, tick_kernel<KIND, L, C, KSMEM, TRAJ, false, NOISE>, a);
 }
 
 template <int KIND, int L, int C, bool KSMEM, bool TRAJ, bool NOISE>

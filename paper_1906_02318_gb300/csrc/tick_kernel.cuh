@@ -78,6 +78,18 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the previous kernel on the stream still runs;
+// grid_dep_wait() returns once that kernel has completed and its memory is
+// visible (at once for a kernel launched without the attribute), and
+// grid_dep_release() lets the next such kernel start launching.
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Issues the copies of one staging (thread 0): K with padded rows (k_rows > 0,
 // row r of n floats to word r * s4) and then `blob_bytes` of blob.
 // With kp_bytes > 0 K is one contiguous blob (the pair layout) copied first instead.
@@ -967,6 +979,14 @@ __global__ void __launch_bounds__(kMaxBlock) tick_kernel(const __grid_constant__
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int q = lane % L;
+  // a screened tick's launches run as a chain of programmatic dependents: this
+  // one was allowed to launch early, so wait for the previous kernel's results
+  // (the kept-slot list, the first result, the reset reduction record), then let
+  // the next launch start
+  if (a.chained) {
+    grid_dep_wait();
+    grid_dep_release();
+  }
   // The session's reduction record is usually cold in L2 (other work ran since
   // the last tick): start fetching it now, so that the epilogue's atomics do
   // not wait for HBM on the tick's critical path.
