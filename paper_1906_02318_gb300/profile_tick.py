@@ -10,7 +10,8 @@ executed steps.
 exact rollout of the kept slots, fallback) with an untrained screener and the
 given --tau / --k.
 --mode serve: --ticks batches of --sessions requests (N log-uniform 1k..64k, H
-20..100) through one continuous-batching server of the chosen model.
+20..100) through one continuous-batching server of the chosen model, one batch
+at a time (host wall time from launch to collected result).
 --rollout factored: plain ticks in the factorised read-out form (one launch of
 the factorised kernel per tick after the one-off powers of K).
 --noise s1,s2,..: Alg. 2's per-step noise with these standard deviations on the
@@ -47,6 +48,7 @@ def main():
     ap.add_argument("--mode", choices=["plain", "screened", "serve"], default="plain")
     ap.add_argument("--k", type=int, default=4096)
     ap.add_argument("--tau", type=float, default=0.0)
+    ap.add_argument("--m", type=int, default=8, help="predicted-safe slots the prefix holds")
     ap.add_argument("--sessions", type=int, default=64)
     ap.add_argument("--rollout", choices=["full", "factored", "tensor"], default="full")
     ap.add_argument("--noise", default="", help="comma-separated sigma per state coordinate")
@@ -100,7 +102,7 @@ def main():
         e0[t].record(st)
         if args.mode == "screened":
             lib.evaluate_screened(sess, scr, xs[t], us[t], res[t], k=args.k, tau=args.tau,
-                                  tick=t, stream=st)
+                                  m=args.m, tick=t, stream=st)
         else:
             lib.evaluate_candidates_device(sess, xs[t], us[t], res[t], tick=t, stream=st)
         e1[t].record(st)
@@ -131,18 +133,19 @@ def serve_mode(args, ctx, model, lo, hi, states, uhs):
     hs = rng.integers(20, 101, args.sessions)
     slots = [srv.admit(int(n), int(h), lo, hi, seed=i, stream_id=i)
              for i, (n, h) in enumerate(zip(ns, hs))]
+    import time
     st = torch.cuda.current_stream()
     ms = []
     for t in range(args.ticks):
         idx = [i % len(states) for i in range(args.sessions)]
         srv.submit(slots, states[idx], np.repeat(uhs[t:t + 1], args.sessions, axis=0),
                    [t] * args.sessions)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
+        # the batch runs on the server's own stream: time launch to collected result
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         srv.launch(st)
-        e1.record(st)
         srv.collect()
-        ms.append(e0.elapsed_time(e1))
+        ms.append((time.perf_counter() - t0) * 1e3)
     steps = float(np.sum((ns + 1) * hs))
     t = np.mean(ms[1:]) * 1e-3 if len(ms) > 1 else ms[0] * 1e-3
     print(f"serve {args.basis} sessions={args.sessions} batches={args.ticks} "
