@@ -68,42 +68,35 @@ static TickKernel pick_tick(int kind, int lanes, int cands, bool traj, bool nois
 }
 
 // Default launch shape (lanes, candidates per thread, block).  A tick is one
-// warp's serial chain of H steps when the candidates fit the GPU several times
-// over, so few candidates take more lanes each (measured on GB300: race car
-// N = 1024..8192 with 8 lanes 31..70 us against 75 us with one; balance bot
-// N <= 4096 with 4 lanes 12.6 against 13.4..14.1 us).  Otherwise one lane per
-// candidate; the race car keeps K in shared memory and takes two candidates per
-// thread once there are enough candidates to fill the GPU.  Blocks of 128
-// threads (one warp per SM sub-partition per block) measured never slower than
-// 64 or 256 (bot N = 8192..65536, race car N = 16384..65536; 256 concentrates two
-// warps on a sub-partition while SMs stay idle at N = 16384: 17.0 / 137 us
-// against 13.6 / 82 us), and fewer blocks stage K and the track grid fewer times.
+// warp's serial chain of H steps until the candidates fill the GPU several times
+// over, so few candidates take more lanes each.  Measured on GB300 (race car,
+// H = 60, CUDA events, L2 flushed): N = 1024 16 lanes 28 us; N = 4096 8 lanes
+// 38 us against 47 (2 lanes) and 69 (1 lane); N = 8192 2 lanes 47 us against 62
+// (8 lanes) and 69; N = 16384 2 lanes 60 us against 69 (1 lane); N = 32768 1 lane
+// 103 us against 110 (2 lanes); from ~48k slots two candidates per thread.  The
+// two-lane shape keeps two warps per SM sub-partition while they fit one wave
+// (two 128-thread blocks per SM), hiding each other's latency.  Balance bot
+// N <= 4096 with 4 lanes 12.6 against 13.4..14.1 us, else one lane.  Blocks of
+// 128 threads (one warp per SM sub-partition per block) measured never slower
+// than 64 or 256 (bot N = 8192..65536, race car N = 16384..65536), and fewer
+// blocks stage K and the track grid fewer times.
 constexpr int kDefaultBlock = 128;
 
 static void default_shape(int kind, int n_slots, int sms, int* lanes, int* cands, int* block) {
-  if (kind == kCar && (long long)n_slots * 16 <= (long long)sms * 128) {
-    // at most one warp per SM sub-partition even with 16 lanes per candidate
-    // (N = 1024: 28.1 us against 31.0 us with 8 lanes)
-    *lanes = 16;
-    *cands = 1;
-    *block = 128;
-    return;
-  }
-  if (kind == kCar && (long long)n_slots * 8 <= (long long)sms * 512) {
-    *lanes = 8;
-    *cands = 1;
-    *block = 128;
-    return;
-  }
-  if (kind == kBot && (long long)n_slots * 4 <= (long long)sms * 128) {
-    *lanes = 4;
-    *cands = 1;
-    *block = 128;
-    return;
-  }
-  *lanes = 1;
-  *cands = (kind == kCar && n_slots > 48 * 1024) ? 2 : 1;
+  *cands = 1;
   *block = kDefaultBlock;
+  if (kind == kCar) {
+    const long long n = n_slots;
+    if (n * 16 <= (long long)sms * 128) *lanes = 16;      // at most one warp per sub-partition
+    else if (n * 8 <= (long long)sms * 256) *lanes = 8;   // up to ~2 warps per sub-partition
+    else if (n <= (long long)sms * 128) *lanes = 2;       // two-lane warps fit one wave
+    else {
+      *lanes = 1;
+      *cands = n > 48 * 1024 ? 2 : 1;
+    }
+    return;
+  }
+  *lanes = (kind == kBot && (long long)n_slots * 4 <= (long long)sms * 128) ? 4 : 1;
 }
 
 TickArgs make_tick_args(const mpmi_session* s, uint64_t tick) {
@@ -361,8 +354,8 @@ static int model_upload(mpmi_ctx* ctx, mpmi_model* m) {
     for (int p = 0; p < m->n; ++p)
       k32[nn + (size_t)r * m->n + p] = (float)m->K64[(size_t)r * m->n + staged_col(m->kind, m->n, p)];
   for (size_t i = 0; i < np; ++i) {
-    const int wpp = (int)(kpair_words(m->kind) / (size_t)KPair<kCar>::PAIRS);
-    const int e = (int)(i & 3), w = (int)(i / 4) % wpp, p = (int)(i / 4) / wpp;
+    const int stride = KPair<kCar>::STRIDE;
+    const int e = (int)(i & 3), w = (int)(i / 4) % stride, p = (int)(i / 4) / stride;
     k32[2 * nn + i] = kpair_value(m->kind, m->n, k32.data(), p, w, e);
   }
   if (cudaMalloc(&m->K32_dev, bytes) != cudaSuccess)

@@ -179,13 +179,15 @@ static_assert(nth_feature_ok(kBot, 12) && nth_feature_ok(kCar, 32) && nth_featur
                   nth_feature_ok(kLin22, 4) && nth_feature_ok(kLin41, 5),
               "free and held feature order");
 
-// K for the one-lane shapes with K in shared memory, rows in pairs: the free rows
-// go two at a time (free features 2p and 2p + 1) through packed two-wide FMAs
-// (fma.rn.f32x2), each half of which is the same fused multiply-add of its own
-// row's chain.  Pair p holds WPP 16-byte words: word j < NF / 2 is {K[r0][c],
-// K[r1][c], K[r0][c'], K[r1][c']} for the free columns c = 2j-th and c' =
-// (2j + 1)-th, ascending; the last NH / 2 words hold the held columns the same
-// way.  One broadcast LDS.128 thus feeds two packed FMAs, and each packed FMA
+// K for the one- and two-lane shapes with K in shared memory, rows in pairs: the
+// free rows go two at a time (free features 2p and 2p + 1) through packed
+// two-wide FMAs (fma.rn.f32x2), each half of which is the same fused multiply-add
+// of its own row's chain.  Pair p starts at 16-byte word p * STRIDE and holds WPP
+// words: word j < NF / 2 is {K[r0][c], K[r1][c], K[r0][c'], K[r1][c']} for the
+// free columns c = 2j-th and c' = (2j + 1)-th, ascending; the last NH / 2 words
+// hold the held columns the same way; one word of padding follows, so that the
+// two lanes of a two-lane group, which read pairs 2i and 2i + 1 at once, hit
+// different banks.  One LDS.128 thus feeds two packed FMAs, and each packed FMA
 // advances two rows' chains at once (the rows' FMA chains, not the FMA pipe,
 // limit a step with one warp per sub-partition).  The model builds this copy on
 // the host (model_upload); the kernels stage it verbatim.
@@ -194,19 +196,20 @@ struct KPair {
   static constexpr int N = BasisTraits<KIND>::N;
   static constexpr int NF = free_cols(KIND, N);
   static constexpr int NH = N - NF;
-  static constexpr bool OK = (NF % 4 == 0) && (NH % 2 == 0) && NF >= 2;
+  static constexpr bool OK = (NF % 4 == 0) && (NH % 2 == 0) && NF >= 2 && (NF / 2) % 2 == 0;
   static constexpr int PAIRS = NF / 2;
   static constexpr int WPP = NF / 2 + NH / 2;  // 16-byte words per pair of rows
-  static constexpr int WORDS = PAIRS * WPP;
+  static constexpr int STRIDE = WPP + 1;       // with the padding word
+  static constexpr int WORDS = PAIRS * STRIDE;
   static constexpr size_t BYTES = (size_t)WORDS * 16;
 };
 
-// Whether a shape stages K in the pair layout: one lane, K in shared memory, and
-// the held rows copied (HELD; the no-allocation variant computes every row from
-// the caller's K and keeps the row layout).
+// Whether a shape stages K in the pair layout: one or two lanes, K in shared
+// memory, and the held rows copied (HELD; the no-allocation variant computes
+// every row from the caller's K and keeps the row layout).
 template <int KIND, int L, bool KSMEM, bool HELD>
 MPMI_HD constexpr bool pair_k() {
-  return KSMEM && L == 1 && HELD && KPair<KIND>::OK;
+  return KSMEM && (L == 1 || L == 2) && HELD && KPair<KIND>::OK;
 }
 
 // 16-byte words of K a shape stages in shared memory (the track grid follows).
@@ -216,9 +219,11 @@ MPMI_HD constexpr int ksmem_words() {
                                                        : KSmem<BasisTraits<KIND>::N>::WORDS);
 }
 
-// Float of the pair layout at (pair p, word w, element e) for a row-major K.
+// Float of the pair layout at (pair p, word w < STRIDE, element e) for a
+// row-major K (0 in the padding word).
 MPMI_HD float kpair_value(int kind, int n, const float* K, int p, int w, int e) {
   const int nf = free_cols(kind, n);
+  if (2 * w >= n) return 0.f;
   const int r = nth_feature(kind, n, 2 * p + (e & 1), false);
   const int i = 2 * w + (e >> 1);
   const int c = i < nf ? nth_feature(kind, n, i, false) : nth_feature(kind, n, i - nf, true);
@@ -242,23 +247,6 @@ __device__ __forceinline__ void stage_k_gather(const float* K, uint4* dst, int t
   for (int i = tid; i < N * N; i += nthreads) {
     const int r = i / N, p = i % N;
     d[r * 4 * KSmem<N>::S4 + p] = __ldg(K + r * N + staged_col(KIND, N, p));
-  }
-}
-
-// K in row-major column order (a caller's buffer) into the pair layout, one
-// float at a time.
-template <int KIND>
-__device__ __forceinline__ void stage_kpair_gather(const float* K, uint4* dst, int tid,
-                                                   int nthreads) {
-  constexpr int N = BasisTraits<KIND>::N;
-  constexpr int WPP = KPair<KIND>::WPP;
-  float* d = reinterpret_cast<float*>(dst);
-  for (int i = tid; i < KPair<KIND>::WORDS * 4; i += nthreads) {
-    const int e = i & 3, w = (i >> 2) % WPP, p = (i >> 2) / WPP;
-    d[i] = __ldg(K + (size_t)nth_feature(KIND, N, 2 * p + (e & 1), false) * N +
-                 (2 * w + (e >> 1) < KPair<KIND>::NF
-                      ? nth_feature(KIND, N, 2 * w + (e >> 1), false)
-                      : nth_feature(KIND, N, 2 * w + (e >> 1) - KPair<KIND>::NF, true)));
   }
 }
 
@@ -611,17 +599,21 @@ __device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety&
   constexpr bool PK = pair_k<KIND, L, KSMEM, HELD>();
   using KP = KPair<KIND>;
   float hc[HELD && !PK ? C : 1][HELD && !PK ? HR : 1];
-  float2 hp[PK ? C : 1][PK ? KP::PAIRS : 1];  // the same, two rows per pair
+  // with two lanes, lane q takes the pairs q, q + 2, ...: MYP pairs; pair i of
+  // this lane is pair_of(i)
+  constexpr int MYP = PK ? KP::PAIRS / L : 1;
+  const auto pair_of = [q](int i) { return L == 1 ? i : q + L * i; };
+  float2 hp[PK ? C : 1][MYP];  // the held columns' share, two rows per pair
   if constexpr (PK) {
     // held words of pair p: columns (held 2j, held 2j + 1) of both rows
 #pragma unroll
     for (int c = 0; c < C; ++c) {
 #pragma unroll
-      for (int pp = 0; pp < KP::PAIRS; ++pp) {
+      for (int pp = 0; pp < MYP; ++pp) {
         float2 v = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < KP::NH / 2; ++j) {
-          const float4 w = sK4[pp * KP::WPP + KP::NF / 2 + j];
+          const float4 w = sK4[pair_of(pp) * KP::STRIDE + KP::NF / 2 + j];
           const float z0 = z[c][nth_feature(KIND, N, 2 * j, true)];
           const float z1 = z[c][nth_feature(KIND, N, 2 * j + 1, true)];
           v = __ffma2_rn(make_float2(w.x, w.y), make_float2(z0, z0), v);
@@ -651,37 +643,35 @@ __device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety&
     }
   }
 
-  // the first PREG pairs' free words stay in registers for the whole horizon
-  // (fewer shared-memory wavefronts per step; the registers a single candidate
-  // per thread leaves free)
+  // this lane's first PREG pairs' free words stay in registers for the whole
+  // horizon (fewer shared-memory wavefronts per step; the registers a single
+  // candidate per thread leaves free)
   constexpr int PREG = (PK && C == 1) ? 2 : 0;
   float4 kreg[PREG > 0 ? PREG : 1][PREG > 0 ? KP::NF / 2 : 1];
   if constexpr (PREG > 0) {
 #pragma unroll
     for (int pp = 0; pp < PREG; ++pp)
 #pragma unroll
-      for (int j = 0; j < KP::NF / 2; ++j) kreg[pp][j] = sK4[pp * KP::WPP + j];
+      for (int j = 0; j < KP::NF / 2; ++j) kreg[pp][j] = sK4[pair_of(pp) * KP::STRIDE + j];
   }
   for (int t = 1; t <= H; ++t) {
     if constexpr (PK) {
       // z <- K z with the free rows in pairs (see KPair): per pair one chain of
       // packed FMAs, continuing from the held columns' share, over the free
-      // columns ascending; the held rows are copied.
+      // columns ascending; the held rows are copied.  With two lanes each lane
+      // computes its pairs and the group exchanges the new free coordinates
+      // through the warp's buffer (double-buffered by step parity).
       asm volatile("" ::: "memory");
-      float acc[C][N];
+      float2 nv[C][MYP];
 #pragma unroll
-      for (int c = 0; c < C; ++c)
-#pragma unroll
-        for (int r = 0; r < N; ++r)
-          if (held_feature(KIND, r)) acc[c][r] = z[c][r];
-#pragma unroll
-      for (int pp = 0; pp < KP::PAIRS; ++pp) {
+      for (int pp = 0; pp < MYP; ++pp) {
         float2 v[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) v[c] = hp[c][pp];
 #pragma unroll
         for (int j = 0; j < KP::NF / 2; ++j) {
-          const float4 w = pp < PREG ? kreg[pp < PREG ? pp : 0][j] : sK4[pp * KP::WPP + j];
+          const float4 w = pp < PREG ? kreg[pp < PREG ? pp : 0][j]
+                                     : sK4[pair_of(pp) * KP::STRIDE + j];
 #pragma unroll
           for (int c = 0; c < C; ++c) {
             const float z0 = z[c][nth_feature(KIND, N, 2 * j, false)];
@@ -691,15 +681,32 @@ __device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety&
           }
         }
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          acc[c][nth_feature(KIND, N, 2 * pp, false)] = v[c].x;
-          acc[c][nth_feature(KIND, N, 2 * pp + 1, false)] = v[c].y;
+        for (int c = 0; c < C; ++c) nv[c][pp] = v[c];
+      }
+      if constexpr (L == 1) {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int pp = 0; pp < MYP; ++pp) {
+            z[c][nth_feature(KIND, N, 2 * pp, false)] = nv[c][pp].x;
+            z[c][nth_feature(KIND, N, 2 * pp + 1, false)] = nv[c][pp].y;
+          }
+      } else {
+        // the group's new free coordinates in free-feature order
+        float* buf = xbuf + ((t & 1) * GPW + g) * S;
+#pragma unroll
+        for (int pp = 0; pp < MYP; ++pp)
+          *reinterpret_cast<float2*>(buf + 2 * pair_of(pp)) = nv[0][pp];
+        __syncwarp();
+#pragma unroll
+        for (int w4 = 0; w4 < KP::NF / 4; ++w4) {
+          const float4 v = *reinterpret_cast<const float4*>(buf + 4 * w4);
+          z[0][nth_feature(KIND, N, 4 * w4, false)] = v.x;
+          z[0][nth_feature(KIND, N, 4 * w4 + 1, false)] = v.y;
+          z[0][nth_feature(KIND, N, 4 * w4 + 2, false)] = v.z;
+          z[0][nth_feature(KIND, N, 4 * w4 + 3, false)] = v.w;
         }
       }
-#pragma unroll
-      for (int c = 0; c < C; ++c)
-#pragma unroll
-        for (int r = 0; r < N; ++r) z[c][r] = acc[c][r];
     } else if constexpr (KSMEM && L == 1) {
       // z <- K z with K read from shared memory (one broadcast LDS.128 feeds 4 C
       // FMAs).  The empty asm keeps the compiler from hoisting the loop-invariant
