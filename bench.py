@@ -552,10 +552,61 @@ def run_learned(args):
                              executed_steps_per_s=ex / ts.mean(),
                              nominal_equivalent_steps_per_s=(N + 1) * 60 / ts.mean(),
                              roofline=forms)
+        run["concurrent"] = concurrent_screened(lib, ctx, model, scr, N, k, cal, xev, uev, lo,
+                                                hi)
         out["runs"].append(run)
         sess.close()
     scr.free()
     model.free()
+    return out
+
+
+def concurrent_screened(lib, ctx, model, scr, N, k, cal, xev, uev, lo, hi, S=8, ticks=60):
+    """Throughput when S sessions share the GPU: each with its own screener (same
+    trained weights) and stream, every session queues `ticks` ticks back to back;
+    ticks/s and executed rollout steps/s over the wall time, for the plain,
+    cost-ordered and learned forms.  A lone tick is a latency chain; here the
+    executed steps are what the GPU spends."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    weights = scr.get_weights()
+    sessions = [lib.Session(ctx, model, N, 60, lo, hi, seed=11 + i) for i in range(S)]
+    screeners = [lib.Screener(ctx, model, weights, max_batch=256, max_slots=N + 1)
+                 for _ in range(S)]
+    streams = [torch.cuda.Stream(dev) for _ in range(S)]
+    xs = torch.tensor(np.asarray(xev[:ticks]), dtype=torch.float64, device=dev)
+    us = torch.tensor(np.asarray(uev[:ticks]), dtype=torch.float64, device=dev)
+    res = torch.zeros((S, ticks, lib.RESULT_BYTES), dtype=torch.uint8, device=dev)
+    forms = {"plain": None, "cost_ordered": (k, 0.0, 1), "learned": (1, cal["tau"], cal["m"])}
+    out = {"sessions": S, "ticks_per_session": ticks,
+           "what": "S sessions on S streams queue their ticks back to back; wall time from the "
+                   "first launch to the last result"}
+    for name, form in forms.items():
+        def launch(t):
+            for i in range(S):
+                if form is None:
+                    lib.evaluate_candidates_device(sessions[i], xs[t], us[t], res[i, t],
+                                                   tick=70000 + t, stream=streams[i])
+                else:
+                    lib.evaluate_screened(sessions[i], screeners[i], xs[t], us[t], res[i, t],
+                                          k=form[0], tau=form[1], m=form[2], tick=70000 + t,
+                                          stream=streams[i])
+        launch(0)                       # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for t in range(ticks):
+            launch(t)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        r = res.cpu().numpy()
+        ex = sum(lib.result_from_bytes(r[i, t], 2)["executed_steps"]
+                 for i in range(S) for t in range(ticks))
+        out[name] = {"ticks_per_s": S * ticks / wall, "executed_steps_per_s": ex / wall,
+                     "nominal_equivalent_steps_per_s": S * ticks * (N + 1) * 60 / wall}
+    for s_ in sessions:
+        s_.close()
+    for sc in screeners:
+        sc.free()
     return out
 
 
