@@ -311,13 +311,16 @@ __device__ __forceinline__ bool mma_wait(uint64_t* bar, uint32_t phase) {
   return all;
 }
 
-// Per scoring block: TMEM for the accumulator and the mbarrier of the MMAs.
+// Per scoring block: TMEM for the accumulator, the mbarrier of the MMAs and the
+// mbarrier of the weights' bulk copy (waited for before the first MMA).
 struct ScoreCtx {
   unsigned char* smem;  // staged InferW | A1 | A2
   uint32_t tmem;
   uint64_t* bar;
+  uint64_t* wbar;
   uint32_t phase;
   bool ok;
+  bool staged;
 };
 
 // Row of the tile (TMEM lane) and half of the row's columns this thread takes.
@@ -326,13 +329,22 @@ __device__ __forceinline__ int score_row() {
 }
 __device__ __forceinline__ int score_half() { return (int)(threadIdx.x >> 7); }
 
-// Stages the weights and allocates the accumulator (all threads; ends synced).
-__device__ void score_begin(const InferW* w, unsigned char* smem, uint64_t* bar,
+// Starts the weights' bulk copy into shared memory (thread 0, on wbar; the first
+// score_tile waits for it, so the caller's work in between overlaps the copy)
+// and allocates the accumulator (all threads; ends synced).
+__device__ void score_begin(const InferW* w, unsigned char* smem, uint64_t* bar, uint64_t* wbar,
                             uint32_t* s_tmem, ScoreCtx* c) {
-  const uint4* src = reinterpret_cast<const uint4*>(w);
-  uint4* dst = reinterpret_cast<uint4*>(smem);
-  for (int i = threadIdx.x; i < (int)(sizeof(InferW) / 16); i += blockDim.x) dst[i] = __ldg(&src[i]);
-  if (threadIdx.x == 0) bar_init(bar);
+  if (threadIdx.x == 0) {
+    bar_init(bar);
+    bar_init(wbar);
+    constexpr uint32_t kBytes = (uint32_t)sizeof(InferW);
+    bar_expect(wbar, kBytes);
+    const char* src = reinterpret_cast<const char*>(w);
+    for (uint32_t off = 0; off < kBytes; off += 32768u) {
+      const uint32_t b = kBytes - off < 32768u ? kBytes - off : 32768u;
+      bulk_g2s(smem + off, src + off, b, wbar);
+    }
+  }
   if ((threadIdx.x >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(s_tmem)), "n"(kTmemCols)
@@ -345,8 +357,10 @@ __device__ void score_begin(const InferW* w, unsigned char* smem, uint64_t* bar,
   c->smem = smem;
   c->tmem = *s_tmem;
   c->bar = bar;
+  c->wbar = wbar;
   c->phase = 0;
   c->ok = true;
+  c->staged = false;
 }
 
 // Frees the accumulator (all threads, after the last tile).
@@ -375,6 +389,14 @@ __device__ float score_tile(ScoreCtx* c, const float* f8) {
   *reinterpret_cast<uint4*>(a1 + bf_off(row, 8 * h, kInP / 8)) =
       make_uint4(pack_bf16(f8[0], f8[1]), pack_bf16(f8[2], f8[3]), pack_bf16(f8[4], f8[5]),
                  pack_bf16(f8[6], f8[7]));
+  if (!c->staged) {
+    // the weights' bulk copy (bounded wait, retried once; the CTA agrees)
+    bool ok = bar_wait(c->wbar, 0);
+    if (!ok) ok = bar_wait(c->wbar, 0);
+    c->staged = true;
+    c->ok = __syncthreads_and(ok) != 0;
+    if (!c->ok) return 1.f;
+  }
   tc_handoff();
   const uint32_t sa1 = smem_u32(a1), sa2 = smem_u32(a2);
   const uint32_t sw1 = smem_u32(sw->W1), sw2 = smem_u32(sw->W2);
@@ -435,10 +457,10 @@ __device__ float score_tile(ScoreCtx* c, const float* f8) {
 __global__ void __launch_bounds__(kScoreThreads) score_rows(const InferW* w, const float* feats,
                                                             int B, float* out) {
   extern __shared__ __align__(1024) unsigned char s_score[];
-  __shared__ uint64_t s_bar;
+  __shared__ uint64_t s_bar, s_wbar;
   __shared__ uint32_t s_tmem;
   ScoreCtx c;
-  score_begin(w, s_score, &s_bar, &s_tmem, &c);
+  score_begin(w, s_score, &s_bar, &s_wbar, &s_tmem, &c);
   const int row = score_row(), h = score_half();
   const int tiles = (B + kTileRows - 1) / kTileRows;
   for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
@@ -467,64 +489,90 @@ struct FeatureSrc {
 __device__ void block_tick_features(const FeatureSrc& fs, const double* x_t, float* s_feat) {
   __shared__ float s_d[32];
   __shared__ int s_i[32];
+  __shared__ float4 s_win[2];  // the nearest segment and its look-ahead curvatures
+  __shared__ float s_winv;     // and its 1 / |d|^2
   const char* base = reinterpret_cast<const char*>(fs.track.blob);
   const float4* seg = reinterpret_cast<const float4*>(base + fs.track.off_seg);
   const float* inv = reinterpret_cast<const float*>(base + fs.track.off_inv);
+  const float4* look4 = reinterpret_cast<const float4*>(fs.look);
   const int S = (fs.track.off_inv - fs.track.off_seg) / 16;
-  const float px = (float)x_t[0], py = (float)x_t[1];
+  // every load the features need is issued before any of them is used: the
+  // state, and for each of this thread's segments its geometry and its row of
+  // the look-ahead table (the winner keeps them, so no load follows the search)
+  const double x0 = x_t[0], x1 = x_t[1], x2 = x_t[2], x3 = x_t[3], x4 = x_t[4], x5 = x_t[5];
+  const float px = (float)x0, py = (float)x1;
   float best = INFINITY;
   int bi = 0x7fffffff;
+  float4 bseg = make_float4(0.f, 0.f, 0.f, 0.f), blook = bseg;
+  float binv = 0.f;
   for (int i = threadIdx.x; i < S; i += blockDim.x) {
     const float4 sg = seg[i];
+    const float iv = inv[i];
+    const float4 lk = look4[i];
     const float rx = px - sg.x, ry = py - sg.y;
-    const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * inv[i], 0.f), 1.f);
+    const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * iv, 0.f), 1.f);
     const float ex = rx - t * sg.z, ey = ry - t * sg.w;
     const float d2 = ex * ex + ey * ey;
     if (d2 < best || (d2 == best && i < bi)) {
       best = d2;
       bi = i;
+      bseg = sg;
+      blook = lk;
+      binv = iv;
     }
   }
+  const int own = bi;  // this thread's candidate
+  float gbest = best;
+  int gbi = bi;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ob < best || (ob == best && oi < bi)) {
-      best = ob;
-      bi = oi;
+    const float ob = __shfl_xor_sync(0xffffffffu, gbest, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, gbi, o);
+    if (ob < gbest || (ob == gbest && oi < gbi)) {
+      gbest = ob;
+      gbi = oi;
     }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
-    s_d[warp] = best;
-    s_i[warp] = bi;
+    s_d[warp] = gbest;
+    s_i[warp] = gbi;
+  }
+  __syncthreads();
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+    if (s_d[w] < gbest || (s_d[w] == gbest && s_i[w] < gbi)) {
+      gbest = s_d[w];
+      gbi = s_i[w];
+    }
+  if (own == gbi) {  // exactly one thread holds the nearest segment
+    s_win[0] = bseg;
+    s_win[1] = blook;
+    s_winv = binv;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-      if (s_d[w] < best || (s_d[w] == best && s_i[w] < bi)) {
-        best = s_d[w];
-        bi = s_i[w];
-      }
-    const float4 sg = seg[bi];
+    const float4 sg = s_win[0];
+    const float4 lk = s_win[1];
     const float rx = px - sg.x, ry = py - sg.y;
-    const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * inv[bi], 0.f), 1.f);
+    const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * s_winv, 0.f), 1.f);
     const float len = sqrtf(sg.z * sg.z + sg.w * sg.w);
     const float tx = sg.z / len, ty = sg.w / len;
     const float ex = rx - t * sg.z, ey = ry - t * sg.w;
     const float e_y = (ex * (-ty) + ey * tx) / fs.half_width;
     float se, ce;
-    sincosf((float)x_t[2] - atan2f(ty, tx), &se, &ce);
+    sincosf((float)x2 - atan2f(ty, tx), &se, &ce);
     s_feat[0] = e_y;
     s_feat[1] = se;
     s_feat[2] = ce;
-    s_feat[3] = (float)x_t[3] / 25.f;
-    s_feat[4] = (float)x_t[4] / 5.f;
-    s_feat[5] = (float)x_t[5] / 2.f;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) s_feat[6 + m] = 10.f * fs.look[4 * bi + m];
-    s_feat[10] = (float)bi;
-    s_feat[11] = sqrtf(best);
+    s_feat[3] = (float)x3 / 25.f;
+    s_feat[4] = (float)x4 / 5.f;
+    s_feat[5] = (float)x5 / 2.f;
+    s_feat[6] = 10.f * lk.x;
+    s_feat[7] = 10.f * lk.y;
+    s_feat[8] = 10.f * lk.z;
+    s_feat[9] = 10.f * lk.w;
+    s_feat[10] = (float)gbi;
+    s_feat[11] = sqrtf(gbest);
   }
   __syncthreads();
 }
@@ -616,14 +664,16 @@ __device__ int first_bin_reaching(const unsigned int* s_hist, unsigned int targe
 // End of a scoring launch (every thread of the block): this block's histograms
 // into the tick's; the last block finds the threshold bin (the larger of the bin
 // reaching k slots and, with s_safe, the bin reaching m predicted-safe slots),
-// then clears the histograms and the list counter for the next tick.
+// then clears the histograms and the list counter for the next tick.  s_all may
+// be null when k <= m: a prefix holding m predicted-safe slots holds at least k
+// slots, so the predicted-safe bin alone is the threshold.
 __device__ void screen_finish(unsigned int* s_all, unsigned int* s_safe, int k, int m,
                               ScreenScratch* ss) {
   __shared__ int s_last, s_bin;
   __shared__ unsigned int s_run[128];
   __syncthreads();
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) {
-    if (s_all[i]) atomicAdd(&ss->hist[i], s_all[i]);
+    if (s_all && s_all[i]) atomicAdd(&ss->hist[i], s_all[i]);
     if (s_safe && s_safe[i]) atomicAdd(&ss->hist_safe[i], s_safe[i]);
   }
   __threadfence();
@@ -633,11 +683,12 @@ __device__ void screen_finish(unsigned int* s_all, unsigned int* s_safe, int k, 
   if (!s_last) return;
   __threadfence();
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) {
-    s_all[i] = *reinterpret_cast<volatile unsigned int*>(&ss->hist[i]);
+    if (s_all) s_all[i] = *reinterpret_cast<volatile unsigned int*>(&ss->hist[i]);
     if (s_safe) s_safe[i] = *reinterpret_cast<volatile unsigned int*>(&ss->hist_safe[i]);
   }
   __syncthreads();
-  int b = first_bin_reaching(s_all, (unsigned int)k, s_run, &s_bin);
+  int b = 0;
+  if (s_all) b = first_bin_reaching(s_all, (unsigned int)k, s_run, &s_bin);
   if (s_safe) {
     const int bs = first_bin_reaching(s_safe, (unsigned int)m, s_run, &s_bin);
     b = bs > b ? bs : b;
@@ -671,7 +722,7 @@ __global__ void __launch_bounds__(kScoreThreads) screen_score(TickArgs a, Featur
   __shared__ unsigned int s_hist[kBins];
   __shared__ unsigned int s_hsafe[kBins];
   __shared__ float s_feat[12];
-  __shared__ uint64_t s_bar;
+  __shared__ uint64_t s_bar, s_wbar;
   __shared__ uint32_t s_tmem;
   grid_dep_release();  // the compaction may launch now; it waits for this kernel
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) {
@@ -679,7 +730,7 @@ __global__ void __launch_bounds__(kScoreThreads) screen_score(TickArgs a, Featur
     s_hsafe[i] = 0;
   }
   ScoreCtx c;
-  score_begin(w, s_score, &s_bar, &s_tmem, &c);
+  score_begin(w, s_score, &s_bar, &s_wbar, &s_tmem, &c);  // weights' copy in flight
   block_tick_features(fs, a.x_t, s_feat);  // ends with __syncthreads
   float uh[2] = {__double2float_rn(a.u_h[0]), __double2float_rn(a.u_h[1])};
   // the first half of the block feeds the per-tick inputs 0..7; the second half
@@ -710,11 +761,14 @@ __global__ void __launch_bounds__(kScoreThreads) screen_score(TickArgs a, Featur
         keys[r] = key;
       }
       // one shared-memory atomic per distinct bin of the warp (neighbouring slots'
-      // costs share few bins), for all slots and for the predicted-safe ones
+      // costs share few bins), for all slots (only when k > m) and for the
+      // predicted-safe ones
       const unsigned int bin = live ? key >> kBinShift : 0xFFFFFFFFu;
-      const unsigned int same = __match_any_sync(kFull, bin);
-      if (live && (threadIdx.x & 31) == (unsigned int)(__ffs(same) - 1))
-        atomicAdd(&s_hist[bin], (unsigned int)__popc(same));
+      if (k > m) {
+        const unsigned int same = __match_any_sync(kFull, bin);
+        if (live && (threadIdx.x & 31) == (unsigned int)(__ffs(same) - 1))
+          atomicAdd(&s_hist[bin], (unsigned int)__popc(same));
+      }
       const bool safe = live && y >= tau;
       const unsigned int sbin = safe ? bin : 0xFFFFFFFFu;
       const unsigned int ssame = __match_any_sync(kFull, sbin);
@@ -723,7 +777,7 @@ __global__ void __launch_bounds__(kScoreThreads) screen_score(TickArgs a, Featur
     }
   }
   score_end(c);
-  screen_finish(s_hist, s_hsafe, k, m, ss);
+  screen_finish(k > m ? s_hist : nullptr, s_hsafe, k, m, ss);
 }
 
 // Cost order alone (tau <= 0; no network): warps take 16-slot tiles, lanes
