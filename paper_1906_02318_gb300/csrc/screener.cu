@@ -311,16 +311,13 @@ __device__ __forceinline__ bool mma_wait(uint64_t* bar, uint32_t phase) {
   return all;
 }
 
-// Per scoring block: TMEM for the accumulator, the mbarrier of the MMAs and the
-// mbarrier of the weights' bulk copy (waited for before the first MMA).
+// Per scoring block: TMEM for the accumulator and the mbarrier of the MMAs.
 struct ScoreCtx {
   unsigned char* smem;  // staged InferW | A1 | A2
   uint32_t tmem;
   uint64_t* bar;
-  uint64_t* wbar;
   uint32_t phase;
   bool ok;
-  bool staged;
 };
 
 // Row of the tile (TMEM lane) and half of the row's columns this thread takes.
@@ -329,22 +326,38 @@ __device__ __forceinline__ int score_row() {
 }
 __device__ __forceinline__ int score_half() { return (int)(threadIdx.x >> 7); }
 
-// Starts the weights' bulk copy into shared memory (thread 0, on wbar; the first
-// score_tile waits for it, so the caller's work in between overlaps the copy)
-// and allocates the accumulator (all threads; ends synced).
-__device__ void score_begin(const InferW* w, unsigned char* smem, uint64_t* bar, uint64_t* wbar,
-                            uint32_t* s_tmem, ScoreCtx* c) {
-  if (threadIdx.x == 0) {
-    bar_init(bar);
-    bar_init(wbar);
-    constexpr uint32_t kBytes = (uint32_t)sizeof(InferW);
-    bar_expect(wbar, kBytes);
-    const char* src = reinterpret_cast<const char*>(w);
-    for (uint32_t off = 0; off < kBytes; off += 32768u) {
-      const uint32_t b = kBytes - off < 32768u ? kBytes - off : 32768u;
-      bulk_g2s(smem + off, src + off, b, wbar);
-    }
+// The weights pass through registers on their way to shared memory: a thread
+// issues its loads (weights_load), the block does other work while they are in
+// flight, then stores them (weights_store; the first MMA hand-off makes them
+// visible).  Plain loads: every block reads the same 38 KB, which the L2 serves
+// to plain loads faster than to one bulk copy per block (measured: 1.3 TB/s
+// with 304 blocks copying at once).
+constexpr int kW16 = (int)(sizeof(InferW) / 16);
+constexpr int kWPerThread = (kW16 + kScoreThreads - 1) / kScoreThreads;
+struct WeightRegs {
+  uint4 v[kWPerThread];
+};
+__device__ __forceinline__ void weights_load(const InferW* w, WeightRegs& r) {
+  const uint4* src = reinterpret_cast<const uint4*>(w);
+#pragma unroll
+  for (int j = 0; j < kWPerThread; ++j) {
+    const int i = (int)threadIdx.x + j * kScoreThreads;
+    if (i < kW16) r.v[j] = __ldg(&src[i]);
   }
+}
+__device__ __forceinline__ void weights_store(const WeightRegs& r, unsigned char* smem) {
+  uint4* dst = reinterpret_cast<uint4*>(smem);
+#pragma unroll
+  for (int j = 0; j < kWPerThread; ++j) {
+    const int i = (int)threadIdx.x + j * kScoreThreads;
+    if (i < kW16) dst[i] = r.v[j];
+  }
+}
+
+// Allocates the accumulator and initialises the MMA barrier (all threads; ends
+// synced).  The weights go into shared memory separately (weights_load/store).
+__device__ void score_begin(unsigned char* smem, uint64_t* bar, uint32_t* s_tmem, ScoreCtx* c) {
+  if (threadIdx.x == 0) bar_init(bar);
   if ((threadIdx.x >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(s_tmem)), "n"(kTmemCols)
@@ -357,10 +370,8 @@ __device__ void score_begin(const InferW* w, unsigned char* smem, uint64_t* bar,
   c->smem = smem;
   c->tmem = *s_tmem;
   c->bar = bar;
-  c->wbar = wbar;
   c->phase = 0;
   c->ok = true;
-  c->staged = false;
 }
 
 // Frees the accumulator (all threads, after the last tile).
@@ -389,14 +400,6 @@ __device__ float score_tile(ScoreCtx* c, const float* f8) {
   *reinterpret_cast<uint4*>(a1 + bf_off(row, 8 * h, kInP / 8)) =
       make_uint4(pack_bf16(f8[0], f8[1]), pack_bf16(f8[2], f8[3]), pack_bf16(f8[4], f8[5]),
                  pack_bf16(f8[6], f8[7]));
-  if (!c->staged) {
-    // the weights' bulk copy (bounded wait, retried once; the CTA agrees)
-    bool ok = bar_wait(c->wbar, 0);
-    if (!ok) ok = bar_wait(c->wbar, 0);
-    c->staged = true;
-    c->ok = __syncthreads_and(ok) != 0;
-    if (!c->ok) return 1.f;
-  }
   tc_handoff();
   const uint32_t sa1 = smem_u32(a1), sa2 = smem_u32(a2);
   const uint32_t sw1 = smem_u32(sw->W1), sw2 = smem_u32(sw->W2);
@@ -457,10 +460,13 @@ __device__ float score_tile(ScoreCtx* c, const float* f8) {
 __global__ void __launch_bounds__(kScoreThreads) score_rows(const InferW* w, const float* feats,
                                                             int B, float* out) {
   extern __shared__ __align__(1024) unsigned char s_score[];
-  __shared__ uint64_t s_bar, s_wbar;
+  __shared__ uint64_t s_bar;
   __shared__ uint32_t s_tmem;
   ScoreCtx c;
-  score_begin(w, s_score, &s_bar, &s_wbar, &s_tmem, &c);
+  WeightRegs wr;
+  weights_load(w, wr);
+  score_begin(s_score, &s_bar, &s_tmem, &c);
+  weights_store(wr, s_score);
   const int row = score_row(), h = score_half();
   const int tiles = (B + kTileRows - 1) / kTileRows;
   for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
@@ -505,20 +511,33 @@ __device__ void block_tick_features(const FeatureSrc& fs, const double* x_t, flo
   int bi = 0x7fffffff;
   float4 bseg = make_float4(0.f, 0.f, 0.f, 0.f), blook = bseg;
   float binv = 0.f;
-  for (int i = threadIdx.x; i < S; i += blockDim.x) {
-    const float4 sg = seg[i];
-    const float iv = inv[i];
-    const float4 lk = look4[i];
-    const float rx = px - sg.x, ry = py - sg.y;
-    const float t = fminf(fmaxf((rx * sg.z + ry * sg.w) * iv, 0.f), 1.f);
-    const float ex = rx - t * sg.z, ey = ry - t * sg.w;
-    const float d2 = ex * ex + ey * ey;
-    if (d2 < best || (d2 == best && i < bi)) {
-      best = d2;
-      bi = i;
-      bseg = sg;
-      blook = lk;
-      binv = iv;
+  // two segments per round, both loaded before either is used
+  for (int i0 = threadIdx.x; i0 < S; i0 += 2 * blockDim.x) {
+    float4 sg[2], lk[2];
+    float iv[2];
+    int idx[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      idx[e] = i0 + e * (int)blockDim.x;
+      const int j = idx[e] < S ? idx[e] : i0;
+      sg[e] = seg[j];
+      iv[e] = inv[j];
+      lk[e] = look4[j];
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      if (idx[e] >= S) continue;
+      const float rx = px - sg[e].x, ry = py - sg[e].y;
+      const float t = fminf(fmaxf((rx * sg[e].z + ry * sg[e].w) * iv[e], 0.f), 1.f);
+      const float ex = rx - t * sg[e].z, ey = ry - t * sg[e].w;
+      const float d2 = ex * ex + ey * ey;
+      if (d2 < best || (d2 == best && idx[e] < bi)) {
+        best = d2;
+        bi = idx[e];
+        bseg = sg[e];
+        blook = lk[e];
+        binv = iv[e];
+      }
     }
   }
   const int own = bi;  // this thread's candidate
@@ -722,7 +741,7 @@ __global__ void __launch_bounds__(kScoreThreads) screen_score(TickArgs a, Featur
   __shared__ unsigned int s_hist[kBins];
   __shared__ unsigned int s_hsafe[kBins];
   __shared__ float s_feat[12];
-  __shared__ uint64_t s_bar, s_wbar;
+  __shared__ uint64_t s_bar;
   __shared__ uint32_t s_tmem;
   grid_dep_release();  // the compaction may launch now; it waits for this kernel
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) {
@@ -730,8 +749,11 @@ __global__ void __launch_bounds__(kScoreThreads) screen_score(TickArgs a, Featur
     s_hsafe[i] = 0;
   }
   ScoreCtx c;
-  score_begin(w, s_score, &s_bar, &s_wbar, &s_tmem, &c);  // weights' copy in flight
+  WeightRegs wr;
+  weights_load(w, wr);  // in flight while the accumulator and the features are prepared
+  score_begin(s_score, &s_bar, &s_tmem, &c);
   block_tick_features(fs, a.x_t, s_feat);  // ends with __syncthreads
+  weights_store(wr, s_score);
   float uh[2] = {__double2float_rn(a.u_h[0]), __double2float_rn(a.u_h[1])};
   // the first half of the block feeds the per-tick inputs 0..7; the second half
   // inputs 8..11 (two per-tick, the candidate's two) and writes the keys
