@@ -208,7 +208,7 @@ static std::vector<ServeKernel> serve_shapes(int kind) {
               make_serve<kBot, 2, 1, false>(), make_serve<kBot, 4, 1, false>()};
     case kCar:
       return {make_serve<kCar, 1, 1, true>(), make_serve<kCar, 1, 2, true>(),
-              make_serve<kCar, 8, 1, false>()};
+              make_serve<kCar, 2, 1, true>(), make_serve<kCar, 8, 1, false>()};
     case kLin11: return {make_serve<kLin11, 1, 1, false>()};
     case kLin22: return {make_serve<kLin22, 1, 1, false>()};
     case kLin41: return {make_serve<kLin41, 1, 1, false>()};

@@ -207,7 +207,7 @@ def test_short_serving_run(lib, ctx):
     cs.free()
 
 
-@pytest.mark.parametrize("which,n_shapes", [("bot", 4), ("car", 3)])
+@pytest.mark.parametrize("which,n_shapes", [("bot", 4), ("car", 4)])
 def test_tuned_server_results_equal_alone(lib, ctx, which, n_shapes):
     """The server's autotuner tries every compiled serve shape at three block
     sizes on a request mix, keeps the fastest, and served results stay
