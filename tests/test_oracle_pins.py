@@ -61,7 +61,7 @@ def test_philox_single_round_zero_counter_is_key_placement():
 def test_philox_second_round_uses_bumped_key():
     k0, k1 = 0x01020304, 0x05060708
     out = philox.philox4x32(0, 0, 0, 0, k0, k1, rounds=2)
-    # round 2 input is (k0, 0, k1, 0); key bumped by the Weyl constants
+    # the second round sees (k0, 0, k1, 0) with the key bumped by the Weyl constants
     p0, p1 = philox.M0 * k0, philox.M1 * k1
     kb0, kb1 = (k0 + philox.W0) & 0xFFFFFFFF, (k1 + philox.W1) & 0xFFFFFFFF
     want = [(p1 >> 32) ^ kb0, p1 & 0xFFFFFFFF, (p0 >> 32) ^ kb1, p0 & 0xFFFFFFFF]
