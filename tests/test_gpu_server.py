@@ -6,7 +6,10 @@ import pytest
 
 from workloads import data, plants
 
-from parity import bot_env, car_env, gpu_model, run_gpu
+from oracle import mpmi as omp
+from oracle import safety as osafe
+from parity import (BOUNDARY_TOL, TIE_RTOL, TRAJ_RTOL, bot_env, car_env, gpu_model,
+                    oracle_samples, run_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -64,6 +67,55 @@ def test_served_results_equal_alone(lib, ctx, which):
             for k in ("index", "status", "n_safe", "ttv", "executed_steps", "n_slots", "tick"):
                 assert r[k] == a[k], (batch, i, k)
             assert np.array_equal(r["u_r"], a["u_r"]) and r["cost"] == a["cost"]
+    srv.free()
+    model.free()
+
+
+@pytest.mark.parametrize("which", ["bot", "car"])
+def test_served_results_match_oracle(lib, ctx, which):
+    """A served batch against the float64 oracle directly (not only against the
+    same tick alone): the pick is the oracle's unless the two picks tie in cost or
+    one of them passes within the trajectory tolerance of a safety bound, the
+    status and the pick's cost agree, and the number of safe candidates differs
+    only by boundary cases (at most 0.2 % of the slots)."""
+    env = bot_env() if which == "bot" else car_env()
+    model = gpu_model(lib, ctx, env)
+    srv = lib.Server(ctx, model, max_sessions=8)
+    H = 30
+    # (N, stream); the race car's oracle tests every segment of the track per step
+    specs = [(500, 0), (2047, 1), (3000, 2)] if which == "bot" else [(300, 0), (1023, 1),
+                                                                      (1500, 2)]
+    slots = [srv.admit(n, H, env.lo, env.hi, seed=77, stream_id=sid) for n, sid in specs]
+    xs = _states(env, which, len(specs), 31)
+    us = data.to_f32_exact(np.random.default_rng(8).uniform(env.lo, env.hi,
+                                                          (len(specs), len(env.lo))))
+    ticks = [900 + i for i in range(len(specs))]
+    srv.submit(slots, xs, us, ticks)
+    assert srv.launch() == len(specs)
+    got = dict(srv.collect())
+    for i, (n, sid) in enumerate(specs):
+        r = got[slots[i]]
+        o = omp.tick(env.K32, env.basis, xs[i], us[i], oracle_samples(env, n, 77, sid, ticks[i]),
+                     H, env.spec, record=True)
+        gi, oi = r["index"], o.index
+        if gi != oi:
+            tie = o.ttv[gi] == o.ttv[oi] and abs(o.cost[gi] - o.cost[oi]) <= \
+                TIE_RTOL * max(o.cost[gi], o.cost[oi]) + 1e-12
+
+            def near_bound(slot):
+                steps = min(int(o.ttv[slot]) + 1, H)
+                zs = o.traj[slot, 1:steps + 1]
+                scale = np.maximum(np.abs(zs).max(axis=1), 1.0)
+                m = np.abs(osafe.margin(env.spec, zs))
+                return bool(np.any(m <= (TRAJ_RTOL + BOUNDARY_TOL) * scale))
+            assert tie or near_bound(gi) or near_bound(oi), (which, i, gi, oi)
+        else:
+            assert r["ttv"] == int(o.ttv[oi])
+            assert abs(r["cost"] - o.cost[oi]) <= 1e-6 * max(o.cost[oi], 1e-12) + 1e-12
+        assert r["status"] == (omp.SAFE if o.ttv[oi] == H else omp.FALLBACK) or gi != oi
+        n_safe_o = int(np.count_nonzero(o.ttv == H))
+        assert abs(r["n_safe"] - n_safe_o) <= max(1, 0.002 * (n + 1))
+        assert r["n_slots"] == n + 1 and r["tick"] == ticks[i]
     srv.free()
     model.free()
 
