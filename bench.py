@@ -24,6 +24,9 @@ test, cost, device-wide argmin and decode (every row of the hot path).
                against 152 SMs x 128 FP32 lanes x 2 flops x max SM clock.
   cpu_baseline the FP64 oracle on the host cores (spawned worker processes), on
                a bounded sample of the same ticks.
+  roofline_over_n  the same plain tick (bot H = 50, race car H = 60) at N = 16384
+               .. 1048576, one session each: the fraction of the FP32 peak as the
+               candidates fill the GPU.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -64,8 +67,8 @@ SM_FP32_LANES = 128
 # DRAM bytes per tick-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum); valid only for the kernel source and launch shape
 # (lanes, candidates per thread, block) it was taken on.
-TRAFFIC = {"tick_kernel_sha1": "fe3c6903ea6bdb59a2660255b8e77a06d98a0eeb",
-           "bytes_per_launch": {(1, 1, 128): 26112, (1, 1, 64): 25856}}
+TRAFFIC = {"tick_kernel_sha1": "b4e8942d8bde13dda59f917c5d64d1070d921782",
+           "bytes_per_launch": {(1, 1, 128): 26112, (1, 1, 64): 26112}}
 
 
 def kernel_sha1() -> str:
@@ -932,6 +935,77 @@ def run_variants(args, bot_states):
     return out
 
 
+OVER_N = (16384, 65536, 262144, 1048576)
+
+
+def run_over_n(args, bot_states):
+    """The plain tick's roofline fraction as N grows, one session, the library's
+    default launch shape, device-resident (L2 flushed before every tick): the
+    balance bot at H = 50 and the race car at H = 60.  At the benchmark's N the
+    candidates fill one warp per SM sub-partition and a tick is one warp's serial
+    chain plus fixed costs; with more candidates the same kernel approaches the
+    FP32 pipe.  Work counted: executed prediction steps x 2 n^2 flops."""
+    import torch
+    from paper_1906_02318_gb300 import mpmi as lib
+    dev = torch.device("cuda", torch.cuda.current_device())
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(measured_peaks().get("sm_max_mhz", 2070.0))
+    peak = props.multi_processor_count * SM_FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    ctx = lib.Context(dev.index)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ticks = min(args.over_n_ticks, len(bot_states))
+    x, u, xn = data.transitions("bot", FIT_SEED, FIT_COUNT)
+    bm, _ = lib.fit_model(ctx, "bot", x, u, xn)
+    lib.set_safety_set(bm, data.BOT_SAFE_LO, data.BOT_SAFE_HI)
+    x, u, xn = data.transitions("car", 3, 20000)
+    cm, _ = lib.fit_model(ctx, "car", x, u, xn)
+    track = data.track_polyline(3)
+    lib.set_safety_set(cm, data.CAR_SAFE_LO, data.CAR_SAFE_HI, 0.0, track,
+                       data.CAR_TRACK_HALF_WIDTH)
+    x0 = data.car_start_state(track, vx=12.0)
+    car_states = x0[None, :] + data.states_in_box(8, ticks, [-1.5, -1.5, -0.1, -3, -0.3, -0.2],
+                                                  [1.5, 1.5, 0.1, 3, 0.3, 0.2])
+    plans = {"bot": (bm, plants.BOT_INPUT_LO, plants.BOT_INPUT_HI, HORIZON, LIFTED_N,
+                     bot_states[:ticks]),
+             "car": (cm, plants.CAR_INPUT_LO, plants.CAR_INPUT_HI, 60, CAR_LIFTED_N, car_states)}
+    out = {"ticks": ticks, "l2": "flushed before every tick", "peak_tflops": peak,
+           "work": "executed prediction steps x 2 n^2 flops", "runs": {}}
+    res = torch.zeros((ticks, lib.RESULT_BYTES), dtype=torch.uint8, device=dev)
+    for name, (model, lo, hi, H, n, states) in plans.items():
+        uhs = data.ou_user_input(9, ticks, 0.01, lo, hi)
+        xs = torch.tensor(np.asarray(states), dtype=torch.float64, device=dev)
+        us = torch.tensor(uhs, dtype=torch.float64, device=dev)
+        rows = []
+        for N in OVER_N:
+            sess = lib.Session(ctx, model, N, H, lo, hi, seed=11)
+            for i in range(3):
+                lib.evaluate_candidates_device(sess, xs[i], us[i], res[i], tick=i)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(ticks)]
+            for i in range(ticks):
+                flush.zero_()
+                ev[i][0].record()
+                lib.evaluate_candidates_device(sess, xs[i], us[i], res[i], tick=100 + i)
+                ev[i][1].record()
+            torch.cuda.synchronize()
+            mean = float(np.mean([a.elapsed_time(b) for a, b in ev])) * 1e-3
+            rr = [lib.result_from_bytes(r, sess.nu) for r in res.cpu().numpy()]
+            executed = float(np.mean([r["executed_steps"] for r in rr]))
+            tflops = executed * 2 * n * n / mean / 1e12
+            lanes, cands, block = sess.launch_shape()
+            rows.append({"N": N, "H": H, "lanes": lanes, "cands_per_thread": cands,
+                         "block": block, "mean_us": mean * 1e6,
+                         "executed_steps_per_s": executed / mean,
+                         "nominal_steps_per_s": sess.n_slots * H / mean,
+                         "tflops": tflops, "frac": tflops / peak})
+            sess.close()
+        out["runs"][name] = rows
+    bm.free()
+    cm.free()
+    return out
+
+
 def max_over_ranks(values, world: int, device: str = "cpu"):
     """Element-wise maximum of per-rank timings (the slowest rank sets the job time)."""
     if world <= 1:
@@ -966,6 +1040,8 @@ def main():
     ap.add_argument("--serve-sessions", type=int, default=256)
     ap.add_argument("--variant-ticks", type=int, default=200,
                     help="ticks per paper variant / factorised ablation (0 = skip)")
+    ap.add_argument("--over-n-ticks", type=int, default=40,
+                    help="ticks per N of the plain tick's roofline over N (0 = skip)")
     ap.add_argument("--car-ticks", type=int, default=600,
                     help="race-car closed-loop ticks (0 = skip)")
     ap.add_argument("--launched-host-ticks", action="store_true",
@@ -1072,6 +1148,8 @@ def main():
         line["variants"] = run_variants(args, out["states"])
     if rank == 0 and args.car_ticks > 0:
         line["car_closed_loop"] = run_car_loop(args)
+    if rank == 0 and args.over_n_ticks > 0:
+        line["roofline_over_n"] = run_over_n(args, out["states"])
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)

@@ -664,24 +664,35 @@ __device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety&
       asm volatile("" ::: "memory");
       float2 nv[C][MYP];
 #pragma unroll
-      for (int pp = 0; pp < MYP; ++pp) {
-        float2 v[C];
+      for (int c = 0; c < C; ++c)
 #pragma unroll
-        for (int c = 0; c < C; ++c) v[c] = hp[c][pp];
+        for (int pp = 0; pp < MYP; ++pp) nv[c][pp] = hp[c][pp];
+      // one packed FMA of pair pp, candidate c, over free word j (two columns)
+      const auto pair_word = [&](int pp, int j) {
+        const float4 w = pp < PREG ? kreg[pp < PREG ? pp : 0][j]
+                                   : sK4[pair_of(pp) * KP::STRIDE + j];
 #pragma unroll
-        for (int j = 0; j < KP::NF / 2; ++j) {
-          const float4 w = pp < PREG ? kreg[pp < PREG ? pp : 0][j]
-                                     : sK4[pair_of(pp) * KP::STRIDE + j];
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            const float z0 = z[c][nth_feature(KIND, N, 2 * j, false)];
-            const float z1 = z[c][nth_feature(KIND, N, 2 * j + 1, false)];
-            v[c] = __ffma2_rn(make_float2(w.x, w.y), make_float2(z0, z0), v[c]);
-            v[c] = __ffma2_rn(make_float2(w.z, w.w), make_float2(z1, z1), v[c]);
-          }
+        for (int c = 0; c < C; ++c) {
+          const float z0 = z[c][nth_feature(KIND, N, 2 * j, false)];
+          const float z1 = z[c][nth_feature(KIND, N, 2 * j + 1, false)];
+          nv[c][pp] = __ffma2_rn(make_float2(w.x, w.y), make_float2(z0, z0), nv[c][pp]);
+          nv[c][pp] = __ffma2_rn(make_float2(w.z, w.w), make_float2(z1, z1), nv[c][pp]);
         }
+      };
+      // Each pair's chain runs over the free words in ascending order either way;
+      // only the interleaving of the chains differs.  One lane: word-major (all
+      // 14 chains advance together, hiding the packed FMA's latency); two lanes:
+      // pair-major (measured faster there, 60.0 against 61.0 us at N = 16384).
+      if constexpr (L == 1) {
 #pragma unroll
-        for (int c = 0; c < C; ++c) nv[c][pp] = v[c];
+        for (int j = 0; j < KP::NF / 2; ++j)
+#pragma unroll
+          for (int pp = 0; pp < MYP; ++pp) pair_word(pp, j);
+      } else {
+#pragma unroll
+        for (int pp = 0; pp < MYP; ++pp)
+#pragma unroll
+          for (int j = 0; j < KP::NF / 2; ++j) pair_word(pp, j);
       }
       if constexpr (L == 1) {
 #pragma unroll
