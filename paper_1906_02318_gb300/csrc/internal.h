@@ -181,7 +181,8 @@ struct mpmi_session {
   int fact_grid = 0;               // resident blocks of the factorised kernel
   size_t fact_smem = 0;
   int tc_grid[2] = {0, 0};         // resident CTAs of the tensor-core rollout (plain, traj)
-  size_t tc_smem[2] = {0, 0};
+  size_t tc_smem[2] = {0, 0};        // its shared memory need, and what a launch asks for
+  size_t tc_req[2] = {0, 0};
   int withhold_staging = 0;        // test hook (mpmi_debug_withhold_staging)
   // persistent host ticks (persistent.cu)
   bool persist = false;            // requested by mpmi_session_set_persistent

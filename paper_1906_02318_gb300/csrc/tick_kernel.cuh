@@ -897,14 +897,15 @@ __device__ __forceinline__ void run_tile(const P& a, TickDyn d, const DevSafety&
 // End of a tick launch: warp -> block -> grid reduction of the selection key
 // and the counts into the session's reduction record (one atomicMin/atomicAdd per
 // block); the block that finishes last decodes the result and resets the record.
-template <int NU, class P>
+// MAXW: the most warps a launch's blocks have.
+template <int NU, class P, int MAXW = kMaxBlock / 32>
 __device__ __forceinline__ void session_epilogue(const P& a, TickDyn d,
                                                  unsigned long long best, unsigned int n_safe,
                                                  unsigned int n_exec, const float* uh,
                                                  bool failed = false,
                                                  unsigned int n_blocks = 0) {
-  __shared__ unsigned long long s_key[kMaxBlock / 32];
-  __shared__ unsigned long long s_cnt[kMaxBlock / 32];
+  __shared__ unsigned long long s_key[MAXW];
+  __shared__ unsigned long long s_cnt[MAXW];
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wpb = blockDim.x >> 5;
@@ -953,12 +954,12 @@ __device__ __forceinline__ void session_epilogue(const P& a, TickDyn d,
   }
 }
 
-template <int NU, class P>
+template <int NU, class P, int MAXW = kMaxBlock / 32>
 __device__ __forceinline__ void session_epilogue(const P& a, unsigned long long best,
                                                  unsigned int n_safe, unsigned int n_exec,
                                                  const float* uh, bool failed = false,
                                                  unsigned int n_blocks = 0) {
-  session_epilogue<NU>(a, dyn_of(a), best, n_safe, n_exec, uh, failed, n_blocks);
+  session_epilogue<NU, P, MAXW>(a, dyn_of(a), best, n_safe, n_exec, uh, failed, n_blocks);
 }
 
 // Template parameters of the tick kernel:

@@ -157,3 +157,47 @@ def test_tensor_refusals_and_timeout(lib, ctx, car):
     again = run_gpu(lib, sess, x_t, u_h, tick=1)
     assert np.array_equal(again["ttv"], want["ttv"])
     sess.close()
+
+
+def test_tensor_nonfinite_state_is_unsafe(lib, ctx, car):
+    """A NaN state reaches the MMAs through the TF32 split as a NaN: every
+    candidate fails at step 1, as in the CUDA-core rollout."""
+    env, model = car
+    x_t = _states(env)[0].copy()
+    x_t[3] = np.nan
+    sess = lib.Session(ctx, model, 1000, 60, env.lo, env.hi, seed=2)
+    sess.set_rollout("tensor")
+    g = run_gpu(lib, sess, x_t, [0.1, 0.2])
+    sess.close()
+    assert np.all(g["ttv"] == 0) and g["result"]["status"] == lib.FALLBACK
+    assert g["result"]["index"] == 0 and g["result"]["n_safe"] == 0
+
+
+def test_tensor_two_tiles_per_cta_sampled_oracle(lib, ctx, car):
+    """80,001 slots: more tiles than resident CTAs, so both halves of every CTA
+    carry tiles and CTAs take several.  Per-candidate ttv and cost of 600 slots
+    spread over the range (every tile boundary region included) against the
+    float64 oracle run on those candidates alone, and the whole tick against the
+    CUDA-core rollout."""
+    env, model = car
+    N, H, seed = 80000, 60, 21
+    x_t = _states(env)[1]
+    u_h = data.to_f32_exact(data.user_input_once(31, env.lo, env.hi))
+    outs = {}
+    for mode in ("full", "tensor"):
+        sess = lib.Session(ctx, model, N, H, env.lo, env.hi, seed=seed, stream_id=2)
+        sess.set_rollout(mode)
+        outs[mode] = run_gpu(lib, sess, x_t, u_h, tick=4)
+        sess.close()
+    g, c = outs["tensor"], outs["full"]
+    assert np.array_equal(g["cost"], c["cost"])
+    assert np.count_nonzero(g["ttv"] != c["ttv"]) <= 0.004 * (N + 1)
+    assert g["result"]["index"] == c["result"]["index"]
+    samples = oracle_samples(env, N, seed, 2, 4)          # slots 1..N
+    rng = np.random.default_rng(5)
+    pick = np.unique(np.concatenate([rng.integers(1, N + 1, 560),
+                                     np.arange(1, 41), np.arange(N - 39, N + 1)]))
+    o = omp.tick(env.K32, env.basis, x_t, u_h, samples[pick - 1], H, env.spec,
+                 include_user=False)
+    assert np.allclose(g["cost"][pick], o.cost, rtol=1e-6, atol=0)
+    assert np.count_nonzero(g["ttv"][pick] != o.ttv) <= max(3, 0.01 * pick.size)
