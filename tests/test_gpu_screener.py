@@ -233,6 +233,27 @@ def test_screened_tick_invariants(lib, setup, k, tau, m):
             assert b["executed_steps"] == kept_steps and b["n_slots"] == len(lst)
 
 
+
+@pytest.mark.slow
+def test_screened_tick_full_size(lib, setup):
+    """N = 65536, the learned-screener configuration's size: the kept slots are the
+    oracle's rule on the device's own costs and scores, and the cost-ordered and
+    network-set screens select exactly what the exhaustive evaluation selects."""
+    ctx, env, model, _, w0 = setup
+    scr = lib.Screener(ctx, model, w0, max_batch=256, max_slots=65537)
+    try:
+        for i, x in enumerate(_states(env, 2, 21)):
+            u_h = data.to_f32_exact(data.user_input_once(80 + i, env.lo, env.hi))
+            for k, tau, m in ((4096, 0.0, 1), (1, 0.5, 16)):
+                a, b, ttv, cost, lst, y = _plain_and_screened(lib, ctx, env, model, scr, x, u_h,
+                                                              65536, k, tau, 500 + i, m=m)
+                assert lst.tolist() == osc.screen(y, cost, k, np.float32(tau), m).tolist()
+                for key in ("index", "status", "ttv"):
+                    assert a[key] == b[key], (i, k, key)
+                assert np.array_equal(a["u_r"], b["u_r"]) and a["cost"] == b["cost"]
+    finally:
+        scr.free()
+
 def test_screen_score_network_matches_reference(lib, setup):
     """The network inside the screened tick (tensor cores) against the float64
     network on the same slot inputs: with tau at the median reference score, the

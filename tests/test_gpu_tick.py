@@ -181,6 +181,40 @@ def test_car_full_size(lib, ctx, car):
     assert compare(g, o, env, 60) <= 0.002 * 16385
 
 
+
+@pytest.mark.slow
+def test_car_learned_config_full_size(lib, ctx, car):
+    """N = 65536, H = 60 in the default launch configuration at that size (the
+    learned-screener comparison's plain tick): the pick is the lexicographic
+    minimum of the GPU's own per-candidate outputs, and sampled slots (the user's,
+    the first and last 64 and 256 others) agree with the oracle except at a safety
+    boundary."""
+    env, model = car
+    N, H, seed, tick = 65536, 60, 3, 7
+    x_t = data.car_start_state(env.track, vx=12.0)
+    u_h = data.to_f32_exact(data.user_input_once(4, env.lo, env.hi))
+    sess = lib.Session(ctx, model, N, H, env.lo, env.hi, seed=seed)
+    g = run_gpu(lib, sess, x_t, u_h, tick=tick)
+    sess.close()
+    ttv, cost, r = g["ttv"], g["cost"], g["result"]
+    slots = np.arange(N + 1)
+    order = np.lexsort((slots, cost.astype(np.float64), H - ttv))
+    assert r["index"] == int(order[0]) and r["n_slots"] == N + 1
+    assert r["n_safe"] == int(np.count_nonzero(ttv == H))
+    assert r["executed_steps"] == int(np.minimum(ttv + 1, H).sum())
+    samples = oracle_samples(env, N, seed, 0, tick)
+    pick = np.unique(np.concatenate([np.arange(1, 65), np.arange(N - 63, N + 1),
+                                     np.random.default_rng(1).integers(1, N + 1, 256)]))
+    o = omp.tick(env.K32, env.basis, x_t, u_h, samples[pick - 1], H, env.spec, record=True)
+    got = np.concatenate([[0], pick])        # the oracle's slot 0 is the user's input
+    assert np.allclose(cost[got], o.cost, rtol=1e-6, atol=1e-12)
+    for i in np.nonzero(ttv[got] != o.ttv)[0]:  # only at a safety boundary
+        s_ = int(min(ttv[got[i]], o.ttv[i])) + 1
+        marg = float(osafe.margin(env.spec, o.traj[i, s_][None, :])[0])
+        assert abs(marg) < 1e-4 * max(1.0, float(np.abs(o.traj[i, s_]).max()))
+    assert np.count_nonzero(ttv[got] != o.ttv) <= 2
+
+
 # ------------------------------------------------------------ closed forms on GPU
 def test_drift_model_closed_form(lib, ctx):
     """x' = x + dt u (linear basis n = 2): ttv has a closed form per candidate."""
