@@ -555,12 +555,42 @@ def run_learned(args):
                              executed_steps_per_s=ex / ts.mean(),
                              nominal_equivalent_steps_per_s=(N + 1) * 60 / ts.mean(),
                              roofline=forms)
+        run["host_ticks"] = host_screened(lib, sess, scr, k, cal, xev, uev)
         run["concurrent"] = concurrent_screened(lib, ctx, model, scr, N, k, cal, xev, uev, lo,
                                                 hi)
         out["runs"].append(run)
         sess.close()
     scr.free()
     model.free()
+    return out
+
+
+def host_screened(lib, sess, scr, k, cal, xev, uev):
+    """Host-to-host control-tick latency through the host C ABI on the same
+    held-out states: the plain tick (mpmi_evaluate_candidates) and the two screened
+    forms (mpmi_evaluate_screened_host), each collected with mpmi_select_input;
+    wall clock around the two calls, one tick at a time, no cache flush; the same
+    ticks (states, user inputs, candidate draws) as the device-timed forms."""
+    import torch
+    forms = {"plain": None, "cost_ordered": (k, 0.0, 1), "learned": (1, cal["tau"], cal["m"])}
+    out = {"what": "host-to-host tick (evaluate + select_input), one launch chain per tick, "
+                   "p50/p99 over the held-out ticks, 16.7 ms deadline (60 Hz)"}
+    for name, form in forms.items():
+        lat = []
+        for t in range(len(xev)):
+            t0 = time.perf_counter()
+            if form is None:
+                lib.evaluate_candidates(sess, xev[t], uev[t], tick=40000 + t)
+            else:
+                lib.evaluate_screened_host(sess, scr, xev[t], uev[t], k=form[0], tau=form[1],
+                                           m=form[2], tick=40000 + t)
+            lib.select_input(sess)
+            lat.append(time.perf_counter() - t0)
+        lat = np.array(lat[3:])  # the first ticks warm the host path
+        out[name] = {"p50_ms": float(np.percentile(lat, 50) * 1e3),
+                     "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                     "misses": int(np.count_nonzero(lat > 1.0 / 60.0))}
+    torch.cuda.synchronize()
     return out
 
 

@@ -544,6 +544,20 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
                            int32_t m, mpmi_result* result_dev, int32_t* list_dev,
                            int32_t* n_list_dev, void* stream);
 
+/* The same screened tick from host buffers (x_t: nx doubles, u_h: nu doubles,
+ * both read before the call returns), for a closed loop on the host: queued on
+ * `stream` like mpmi_evaluate_candidates, and its result is collected with
+ * mpmi_select_input (flags and counts as above).  On devices that can map host
+ * memory the kernels read x_t and u_h from the session's pinned buffer and write
+ * the result into pinned memory, and the launch whose result is final stores
+ * the tick's number, which select_input polls; otherwise the inputs and the
+ * result are copied.  A tick still in flight on the session is waited for
+ * first.  Errors as mpmi_evaluate_screened, and NONFINITE for a NaN or
+ * infinite x_t or u_h. */
+int mpmi_evaluate_screened_host(mpmi_session* session, mpmi_screener* s, const double* x_t,
+                                const double* u_h, uint64_t tick, int32_t k, float tau,
+                                int32_t m, void* stream);
+
 /* Phase timing of screened ticks (a measurement aid, not part of the method):
  * with on != 0 every later mpmi_evaluate_screened of this screener records CUDA
  * events on its stream around its four launches; mpmi_screener_phase_times waits

@@ -93,6 +93,10 @@ struct TickArgs {
   // (pinned host memory) behind a system-scope fence
   unsigned long long* seq_out;
   unsigned long long seq;
+  // a screened host tick's kept-slot rollout: store seq only when its result is
+  // the tick's final one (a safe pick, or every slot kept); otherwise the
+  // fallback launch, which then runs the full evaluation, stores it
+  int seq_if_final;
 };
 
 // Persistent host ticks: the mailbox (pinned host memory) and its device copy
@@ -199,9 +203,29 @@ struct mpmi_session {
 };
 
 namespace mpmi {
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) {
+      err = cudaSetDevice(dev);
+      changed = err == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
 // tick launch helpers shared by the API and the screener (mpmi_api.cu)
 TickArgs make_tick_args(const mpmi_session* s, uint64_t tick);
 int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint);
+// host ticks: wait for the one in flight; record the completion event after the launches
+int host_tick_begin(mpmi_session* s);
+int host_tick_end(mpmi_session* s, cudaStream_t st);
 // factorised rollout (factored.cu)
 int compute_powers(int kind, const float* K, int H, float* out, cudaStream_t st);
 int launch_factored(mpmi_session* s, TickArgs& a, cudaStream_t st, int n_hint);

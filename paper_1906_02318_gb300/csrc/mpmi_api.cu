@@ -40,22 +40,6 @@ static int cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
-// Makes the context's device current for the duration of a call.
-struct DeviceGuard {
-  int prev = -1;
-  bool changed = false;
-  cudaError_t err = cudaSuccess;
-  explicit DeviceGuard(int dev) {
-    err = cudaGetDevice(&prev);
-    if (err == cudaSuccess && prev != dev) {
-      err = cudaSetDevice(dev);
-      changed = err == cudaSuccess;
-    }
-  }
-  ~DeviceGuard() {
-    if (changed) cudaSetDevice(prev);
-  }
-};
 
 static bool budget_ok(mpmi_ctx* ctx, uint64_t bytes) {
   return ctx->budget == 0 || ctx->used + bytes <= ctx->budget;
@@ -247,6 +231,28 @@ static int persist_wait(mpmi_session* s) {
   if (poll_published(s, std::chrono::nanoseconds(0))) return MPMI_OK;
   if (rc != MPMI_OK) return rc;
   return fail(MPMI_E_TIMEOUT, "persistent tick: no result within the idle limit plus a second");
+}
+
+// A host tick (results through select_input) may start once the previous one
+// has finished: wait for it if it is still in flight.
+int host_tick_begin(mpmi_session* s) {
+  if (!s->in_flight) return MPMI_OK;
+  if (s->persist_posted) {
+    const int rc = persist_wait(s);
+    if (rc != MPMI_OK) return rc;
+  } else {
+    MPMI_CUDA(cudaEventSynchronize(s->done), "waiting for the previous tick");
+  }
+  s->in_flight = false;
+  s->persist_posted = false;
+  return MPMI_OK;
+}
+
+// After a host tick's launches on st: the event select_input falls back to.
+int host_tick_end(mpmi_session* s, cudaStream_t st) {
+  MPMI_CUDA(cudaEventRecord(s->done, st), "cudaEventRecord");
+  s->in_flight = true;
+  return MPMI_OK;
 }
 
 int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint) {
@@ -953,15 +959,7 @@ int mpmi_evaluate_candidates(mpmi_session* s, const double* x_t, const double* u
   DeviceGuard guard(s->ctx->device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
-  if (s->in_flight) {
-    if (s->persist_posted) {
-      if ((rc = persist_wait(s)) != MPMI_OK) return rc;
-    } else {
-      MPMI_CUDA(cudaEventSynchronize(s->done), "waiting for the previous tick");
-    }
-    s->in_flight = false;
-    s->persist_posted = false;
-  }
+  if ((rc = host_tick_begin(s)) != MPMI_OK) return rc;
   if (s->persist && s->rollout == MPMI_ROLLOUT_FULL && s->n_noise == 0 &&
       s->cfg.sampler != MPMI_SAMPLER_EXTERNAL) {
     // hand the tick to the resident kernel: mailbox words, then the number
@@ -1000,9 +998,7 @@ int mpmi_evaluate_candidates(mpmi_session* s, const double* x_t, const double* u
     MPMI_CUDA(cudaMemcpyAsync(s->result_host, s->result_dev, sizeof(mpmi_result),
                               cudaMemcpyDeviceToHost, st), "copy the result to the host");
   }
-  MPMI_CUDA(cudaEventRecord(s->done, st), "cudaEventRecord");
-  s->in_flight = true;
-  return MPMI_OK;
+  return host_tick_end(s, st);
 }
 
 int mpmi_select_input(mpmi_session* s, mpmi_result* out) {

@@ -967,6 +967,95 @@ static int gradients(mpmi_screener* s, const float* feats, const float* target, 
 
 using namespace mpmi;
 
+namespace mpmi {
+
+static int screened_checks(const mpmi_session* session, const mpmi_screener* s, int32_t k,
+                           float tau, int32_t m) {
+  if (session->model != s->model) return fail(MPMI_E_INVALID_ARG, "screener: another model");
+  if (session->cfg.sampler == MPMI_SAMPLER_EXTERNAL)
+    return fail(MPMI_E_UNSUPPORTED, "evaluate_screened: sampled candidates only");
+  if (session->n_slots > s->max_slots)
+    return fail(MPMI_E_INVALID_ARG, "evaluate_screened: session has more slots than max_slots");
+  if (k < 1) return fail(MPMI_E_INVALID_ARG, "evaluate_screened: k must be >= 1");
+  if (tau > 0.f && m < 1)
+    return fail(MPMI_E_INVALID_ARG, "evaluate_screened: m must be >= 1 with the network");
+  return MPMI_OK;
+}
+
+// The screened tick's launches on stream st for the tick described by a (its
+// x_t, u_h and result pointers set; with a.seq_out the launch whose result is
+// final also stores a.seq there).
+static int screened_chain(mpmi_session* session, mpmi_screener* s, const TickArgs& a, int32_t k,
+                          float tau, int32_t m, int32_t* list_dev, int32_t* n_list_dev,
+                          cudaStream_t st) {
+  int rc = refresh_infer(s, st);
+  if (rc != MPMI_OK) return rc;
+  TickArgs sa = a;
+  sa.seq_out = nullptr;  // the screen writes no result
+  if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[0], st), "cudaEventRecord");
+  // at most two blocks per SM: with the network each holds 128 TMEM columns and
+  // the staged weights; more blocks would only repeat the per-tick features
+  if (tau > 0.f) {
+    const int tiles = (session->n_slots + kTileRows - 1) / kTileRows;
+    const int blocks = tiles < 2 * s->ctx->sm_count ? tiles : 2 * s->ctx->sm_count;
+    screen_score<<<blocks, kScoreThreads, kScoreSmem, st>>>(sa, feature_src(s), s->infer, tau,
+                                                            k, m, s->keys, s->ss);
+  } else {
+    const int tiles = (session->n_slots + 15) / 16;
+    int blocks = (tiles + 3) / 4;
+    if (blocks > 2 * s->ctx->sm_count) blocks = 2 * s->ctx->sm_count;
+    screen_cost<<<blocks, 128, 0, st>>>(sa, k, s->keys, s->ss);
+  }
+  if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[1], st), "cudaEventRecord");
+  int cb = (session->n_slots + 255) / 256;
+  if (cb > 4 * s->ctx->sm_count) cb = 4 * s->ctx->sm_count;
+  {
+    // the compaction, the rollout and the fallback run as programmatic
+    // dependents: each may launch while its predecessor runs and waits for it
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cb);
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SCR_CUDA(cudaLaunchKernelEx(&cfg, screen_compact, (const unsigned int*)s->keys,
+                                (int)session->n_slots, s->ss, s->list),
+             "screen_compact launch");
+  }
+  SCR_CUDA(cudaGetLastError(), "screen launches");
+  if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[2], st), "cudaEventRecord");
+  // exact rollout on the kept slots (their number is known only on the device)
+  TickArgs r = a;
+  r.slot_list = s->list;
+  r.n_list = &s->ss->n_list;
+  r.result_flags = 1;
+  r.chained = 1;
+  r.seq_if_final = 1;
+  rc = launch_tick_args(session, r, false, st, -1);
+  if (rc != MPMI_OK) return rc;
+  if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[3], st), "cudaEventRecord");
+  if (list_dev)
+    SCR_CUDA(cudaMemcpyAsync(list_dev, s->list, sizeof(int) * session->n_slots,
+                             cudaMemcpyDeviceToDevice, st), "copy list");
+  if (n_list_dev)
+    SCR_CUDA(cudaMemcpyAsync(n_list_dev, &s->ss->n_list, sizeof(int), cudaMemcpyDeviceToDevice,
+                             st), "copy list size");
+  // full evaluation only when the kept slots hold no safe candidate and were not
+  // already every slot; its result counts the steps of both launches
+  TickArgs f = a;
+  f.skip_if_safe = a.result;
+  f.result_flags = 3;
+  f.chained = 1;
+  rc = launch_tick_args(session, f, false, st, 0);
+  if (rc == MPMI_OK && s->timing) SCR_CUDA(cudaEventRecord(s->ev[4], st), "cudaEventRecord");
+  return rc;
+}
+
+}  // namespace mpmi
+
 extern "C" {
 
 int mpmi_screener_create(mpmi_ctx* ctx, const mpmi_model* model, const float* weights,
@@ -1159,80 +1248,57 @@ int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double
                            int32_t* n_list_dev, void* stream) {
   if (!session || !s || !x_t_dev || !u_h_dev || !result_dev)
     return fail(MPMI_E_INVALID_ARG, "evaluate_screened: NULL argument");
-  if (session->model != s->model) return fail(MPMI_E_INVALID_ARG, "screener: another model");
-  if (session->cfg.sampler == MPMI_SAMPLER_EXTERNAL)
-    return fail(MPMI_E_UNSUPPORTED, "evaluate_screened: sampled candidates only");
-  if (session->n_slots > s->max_slots)
-    return fail(MPMI_E_INVALID_ARG, "evaluate_screened: session has more slots than max_slots");
-  if (k < 1) return fail(MPMI_E_INVALID_ARG, "evaluate_screened: k must be >= 1");
-  if (tau > 0.f && m < 1)
-    return fail(MPMI_E_INVALID_ARG, "evaluate_screened: m must be >= 1 with the network");
-  cudaStream_t st = (cudaStream_t)stream;
-  int rc = refresh_infer(s, st);
+  int rc = screened_checks(session, s, k, tau, m);
   if (rc != MPMI_OK) return rc;
   TickArgs a = make_tick_args(session, tick);
   a.x_t = x_t_dev;
   a.u_h = u_h_dev;
   a.result = result_dev;
-  if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[0], st), "cudaEventRecord");
-  // at most two blocks per SM: with the network each holds 128 TMEM columns and
-  // the staged weights; more blocks would only repeat the per-tick features
-  if (tau > 0.f) {
-    const int tiles = (session->n_slots + kTileRows - 1) / kTileRows;
-    const int blocks = tiles < 2 * s->ctx->sm_count ? tiles : 2 * s->ctx->sm_count;
-    screen_score<<<blocks, kScoreThreads, kScoreSmem, st>>>(a, feature_src(s), s->infer, tau, k,
-                                                            m, s->keys, s->ss);
-  } else {
-    const int tiles = (session->n_slots + 15) / 16;
-    int blocks = (tiles + 3) / 4;
-    if (blocks > 2 * s->ctx->sm_count) blocks = 2 * s->ctx->sm_count;
-    screen_cost<<<blocks, 128, 0, st>>>(a, k, s->keys, s->ss);
-  }
-  if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[1], st), "cudaEventRecord");
-  int cb = (session->n_slots + 255) / 256;
-  if (cb > 4 * s->ctx->sm_count) cb = 4 * s->ctx->sm_count;
-  {
-    // the compaction, the rollout and the fallback run as programmatic
-    // dependents: each may launch while its predecessor runs and waits for it
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)cb);
-    cfg.blockDim = dim3(256);
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    SCR_CUDA(cudaLaunchKernelEx(&cfg, screen_compact, (const unsigned int*)s->keys,
-                                (int)session->n_slots, s->ss, s->list),
-             "screen_compact launch");
-  }
-  SCR_CUDA(cudaGetLastError(), "screen launches");
-  if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[2], st), "cudaEventRecord");
-  // exact rollout on the kept slots (their number is known only on the device)
-  TickArgs r = a;
-  r.slot_list = s->list;
-  r.n_list = &s->ss->n_list;
-  r.result_flags = 1;
-  r.chained = 1;
-  rc = launch_tick_args(session, r, false, st, -1);
+  return screened_chain(session, s, a, k, tau, m, list_dev, n_list_dev, (cudaStream_t)stream);
+}
+
+int mpmi_evaluate_screened_host(mpmi_session* session, mpmi_screener* s, const double* x_t,
+                                const double* u_h, uint64_t tick, int32_t k, float tau,
+                                int32_t m, void* stream) {
+  if (!session || !s || !x_t || !u_h)
+    return fail(MPMI_E_INVALID_ARG, "evaluate_screened_host: NULL argument");
+  int rc = screened_checks(session, s, k, tau, m);
   if (rc != MPMI_OK) return rc;
-  if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[3], st), "cudaEventRecord");
-  if (list_dev)
-    SCR_CUDA(cudaMemcpyAsync(list_dev, s->list, sizeof(int) * session->n_slots,
-                             cudaMemcpyDeviceToDevice, st), "copy list");
-  if (n_list_dev)
-    SCR_CUDA(cudaMemcpyAsync(n_list_dev, &s->ss->n_list, sizeof(int), cudaMemcpyDeviceToDevice,
-                             st), "copy list size");
-  // full evaluation only when the kept slots hold no safe candidate and were not
-  // already every slot; its result counts the steps of both launches
-  TickArgs f = a;
-  f.skip_if_safe = result_dev;
-  f.result_flags = 3;
-  f.chained = 1;
-  rc = launch_tick_args(session, f, false, st, 0);
-  if (rc == MPMI_OK && s->timing) SCR_CUDA(cudaEventRecord(s->ev[4], st), "cudaEventRecord");
-  return rc;
+  const mpmi_model* mdl = session->model;
+  for (int j = 0; j < mdl->nx; ++j)
+    if (!isfinite(x_t[j])) return fail(MPMI_E_NONFINITE, "x_t holds NaN/Inf");
+  for (int j = 0; j < mdl->nu; ++j)
+    if (!isfinite(u_h[j])) return fail(MPMI_E_NONFINITE, "u_h holds NaN/Inf");
+  DeviceGuard guard(session->ctx->device);
+  if (guard.err != cudaSuccess) return cfail(guard.err, "cudaSetDevice");
+  if ((rc = host_tick_begin(session)) != MPMI_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  memcpy(session->in_host, x_t, sizeof(double) * mdl->nx);
+  memcpy(session->in_host + 8, u_h, sizeof(double) * mdl->nu);
+  TickArgs a = make_tick_args(session, tick);
+  if (session->zero_copy) {
+    // the kernels read x_t and u_h from the pinned buffer and write the result
+    // into pinned memory; the launch whose result is final stores the number
+    a.x_t = session->in_map;
+    a.u_h = session->in_map + 8;
+    a.result = session->result_map;
+    a.seq_out = session->seq_map;
+    a.seq = session->seq + 1;
+  } else {
+    SCR_CUDA(cudaMemcpyAsync(session->in_dev, session->in_host, 12 * sizeof(double),
+                             cudaMemcpyHostToDevice, st), "copy x_t/u_h to the device");
+    a.x_t = session->in_dev;
+    a.u_h = session->in_dev + 8;
+    a.result = session->result_dev;
+  }
+  if ((rc = screened_chain(session, s, a, k, tau, m, nullptr, nullptr, st)) != MPMI_OK) return rc;
+  if (session->zero_copy) {
+    ++session->seq;
+  } else {
+    SCR_CUDA(cudaMemcpyAsync(session->result_host, session->result_dev, sizeof(mpmi_result),
+                             cudaMemcpyDeviceToHost, st), "copy the result to the host");
+  }
+  return host_tick_end(session, st);
 }
 
 }  // extern "C"

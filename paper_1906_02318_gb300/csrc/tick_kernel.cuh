@@ -493,7 +493,9 @@ __device__ __forceinline__ void write_result(const P& a, TickDyn d, unsigned lon
   r.reserved = a.result_flags;
   *a.result = r;
   if constexpr (HasSeq<P>::value) {
-    if (a.seq_out != nullptr) {  // the host polls this word instead of an event
+    const bool final_result =
+        !a.seq_if_final || r.status == MPMI_SAFE || r.n_slots >= a.n_slots;
+    if (a.seq_out != nullptr && final_result) {  // the host polls this word instead of an event
       __threadfence_system();
       *reinterpret_cast<volatile unsigned long long*>(a.seq_out) = d.seq;
     }

@@ -133,6 +133,8 @@ _SIGNATURES = {
     "mpmi_screener_phase_times": (c_i32, [c_vp, c_vp]),
     "mpmi_evaluate_screened": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_i32, ctypes.c_float,
                                        c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "mpmi_evaluate_screened_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_i32,
+                                            ctypes.c_float, c_i32, c_vp]),
     "mpmi_evaluate_candidates_noalloc": (c_i32, [ctypes.POINTER(BasisDesc), c_vp,
                                                  ctypes.POINTER(SafetySpecC),
                                                  ctypes.POINTER(SessionConfig), c_vp, c_vp,
@@ -685,6 +687,19 @@ def evaluate_screened(s: Session, scr: Screener, x_t_dev, u_h_dev, result_dev, k
     _check(s.ctx.lib.mpmi_evaluate_screened(s.handle, scr.handle, _ptr(x_t_dev), _ptr(u_h_dev),
                                             tick, k, tau, m, _ptr(result_dev), _ptr(list_dev),
                                             _ptr(n_list_dev), _stream(stream)))
+
+
+def evaluate_screened_host(s: Session, scr: Screener, x_t, u_h, k: int = 4096, tau: float = 0.9,
+                           m: int = 8, tick: int = 0, stream=None):
+    """mpmi_evaluate_screened_host: the screened tick from host x_t / u_h (float64),
+    queued; collect it with select_input."""
+    buf = s._in
+    buf[:s.nx] = _f64(x_t, s.nx)
+    buf[MAX_NX:MAX_NX + s.nu] = _f64(u_h, s.nu)
+    rc = s.ctx.lib.mpmi_evaluate_screened_host(s.handle, scr.handle, s._x_ptr, s._u_ptr, tick,
+                                               k, tau, m, _stream(stream))
+    if rc:
+        _check(rc)
 
 
 # ---------------------------------------------------------------- continuous-batching server

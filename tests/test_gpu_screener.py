@@ -254,6 +254,46 @@ def test_screened_tick_full_size(lib, setup):
     finally:
         scr.free()
 
+
+def test_host_screened_tick_equals_device(lib, setup):
+    """The screened tick from host buffers, collected with select_input, gives the
+    device-resident screened tick's result field for field, over consecutive ticks
+    of one session interleaved with plain host ticks; a state off the road (every
+    kept slot unsafe) takes the on-device fallback, whose launch then completes
+    the tick."""
+    import torch
+    ctx, env, model, scr, w0 = setup
+    scr.set_weights(w0)
+    sess = lib.Session(ctx, model, 6000, 60, env.lo, env.hi, seed=7)
+    res = torch.zeros(lib.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    states = _states(env, 3, 31)
+    off_road = states[1].copy()
+    off_road[:2] += 60.0                 # far outside the track band: nothing is safe
+    flags = []
+    try:
+        for i, x in enumerate(states + [off_road]):
+            u_h = data.to_f32_exact(data.user_input_once(90 + i, env.lo, env.hi))
+            for k, tau, m in ((256, 0.0, 1), (1, 0.0, 1), (1, 0.5, 8)):
+                tick = 600 + 10 * i + k
+                lib.evaluate_screened(sess, scr, torch.tensor(x, dtype=torch.float64,
+                                                              device="cuda"),
+                                      torch.tensor(u_h, dtype=torch.float64, device="cuda"),
+                                      res, k=k, tau=tau, m=m, tick=tick)
+                torch.cuda.synchronize()
+                want = lib.result_from_bytes(res.cpu(), 2)
+                lib.evaluate_screened_host(sess, scr, x, u_h, k=k, tau=tau, m=m, tick=tick)
+                got = lib.select_input(sess)
+                for key in ("index", "status", "n_safe", "ttv", "cost", "n_slots",
+                            "executed_steps", "tick", "flags"):
+                    assert got[key] == want[key], (i, k, key)
+                assert np.array_equal(got["u_r"], want["u_r"])
+                flags.append(got["flags"])
+            lib.evaluate_candidates(sess, x, u_h, tick=900 + i)   # a plain host tick between
+            assert lib.select_input(sess)["tick"] == 900 + i
+    finally:
+        sess.close()
+    assert any(f & 2 for f in flags) and any(not f & 2 for f in flags)
+
 def test_screen_score_network_matches_reference(lib, setup):
     """The network inside the screened tick (tensor cores) against the float64
     network on the same slot inputs: with tau at the median reference score, the
