@@ -530,18 +530,15 @@ int mpmi_screener_score(mpmi_screener* s, const float* features_dev, int32_t bat
  * and, with the network (tau > 0), at least m slots the network predicts safe
  * (score >= tau); tau <= 0 skips the network (the k cheapest slots, the exact
  * cost-ordered search).  The kept slots go through the exact rollout; if none of
- * them is safe and they are not every slot, then with the network the slots of a
- * second prefix chosen the same way with 8 k and 8 m (beyond the first) go
- * through it, and if none of those is safe either (or without the network at
- * once), the full evaluation runs -- all on the device, with no host round trip.  Each prefix either contains the least-cost safe candidate of
- * the whole tick or holds only unsafe slots, so the selection is always the
- * exhaustive one: the network decides only how far down the cost order the tick
- * goes.  result_dev's reserved word carries flags: bit 0 the screened set was
- * evaluated, bit 2 the second prefix decided, bit 1 the full evaluation ran;
- * executed_steps counts the steps of every launch that ran, n_slots the slots of
- * the last.  list_dev (optional, n_slots int32) receives the first prefix's slots
- * and n_list_dev (optional, one int32) their number.  INVALID_ARG for k < 1, or
- * m < 1 with tau > 0. */
+ * them is safe and they are not every slot, the full evaluation runs on the
+ * device with no host round trip.  Either the kept slots contain the least-cost
+ * safe candidate of the whole tick or they are all unsafe, so the selection is
+ * always the exhaustive one: the network decides only how far down the cost
+ * order the tick goes.  result_dev's reserved word carries flags: bit 0 the
+ * screened set was evaluated, bit 1 the full evaluation ran; executed_steps
+ * counts the steps of both launches, n_slots the slots of the last.  list_dev
+ * (optional, n_slots int32) receives the kept slots and n_list_dev (optional,
+ * one int32) their number.  INVALID_ARG for k < 1, or m < 1 with tau > 0. */
 int mpmi_evaluate_screened(mpmi_session* session, mpmi_screener* s, const double* x_t_dev,
                            const double* u_h_dev, uint64_t tick, int32_t k, float tau,
                            int32_t m, mpmi_result* result_dev, int32_t* list_dev,
@@ -566,8 +563,7 @@ int mpmi_evaluate_screened_host(mpmi_session* session, mpmi_screener* s, const d
  * events on its stream around its four launches; mpmi_screener_phase_times waits
  * for the last tick's events and writes ms_out[4] (host): the screen (network or
  * cost keys and histograms), the compaction, the exact rollout of the kept slots
- * and the last two launches together (the second prefix and the fallback, each
- * returning at once when it is not needed).  The
+ * and the fallback launch (which returns at once when it is not needed).  The
  * events are created on the first switch-on.  NOT_READY if timing was never on. */
 int mpmi_screener_set_timing(mpmi_screener* s, int32_t on);
 int mpmi_screener_phase_times(mpmi_screener* s, float* ms_out);

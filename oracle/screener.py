@@ -187,24 +187,13 @@ def screen(scores: np.ndarray, cost: np.ndarray, k: int, tau: float, m: int = 1)
     return np.arange(len(b))
 
 
-# A screened tick with the network (tau > 0) that finds no safe slot in its
-# prefix tries a second prefix, WIDEN times as deep (k and m both scaled), before
-# the full evaluation; the cost-ordered search (tau <= 0) falls back at once.
-WIDEN = 8
-
-
-def screened_selection(ttv: np.ndarray, cost: np.ndarray, kept: np.ndarray, H: int,
-                       wider: np.ndarray | None = None) -> int:
+def screened_selection(ttv: np.ndarray, cost: np.ndarray, kept: np.ndarray, H: int) -> int:
     """Slot a screened tick selects from the exact rollout of the kept slots: the
-    least (cost, slot) safe kept slot; when none is safe, the same over the wider
-    prefix `wider` (if given); when that holds none either, the full evaluation's
+    least (cost, slot) safe kept slot; when none is safe, the full evaluation's
     choice over all slots (least (H - ttv, cost, slot))."""
-    for prefix in (kept, wider):
-        if prefix is None:
-            continue
-        prefix = np.asarray(prefix)
-        safe = prefix[np.asarray(ttv)[prefix] == H]
-        if len(safe):
-            return int(safe[np.lexsort((safe, np.asarray(cost)[safe]))[0]])
+    kept = np.asarray(kept)
+    safe = kept[np.asarray(ttv)[kept] == H]
+    if len(safe):
+        return int(safe[np.lexsort((safe, np.asarray(cost)[safe]))[0]])
     slot = np.arange(len(ttv))
     return int(np.lexsort((slot, cost, H - np.asarray(ttv)))[0])

@@ -50,22 +50,13 @@ __host__ __device__ constexpr uint32_t bf_off(int row, int k, int kc) {
   return (uint32_t)((((row >> 3) * kc + (k >> 3)) * 128) + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// A screened tick with the network rolls out a first cost-order prefix and, when
-// none of its slots is safe, a second one kScreenWiden times as deep (k and m
-// both scaled) before it falls back to the full evaluation.  (Without the
-// network the second prefix would hold kScreenWiden k slots, close to the full
-// evaluation's cost, so the cost-ordered search falls back at once.)
-constexpr int kScreenWiden = 8;
-
 struct ScreenScratch {
   unsigned int hist[kBins];       // all slots per cost bin
   unsigned int hist_safe[kBins];  // predicted-safe slots per cost bin
   unsigned int done;  // score blocks finished
-  int bstar;          // threshold bin of the first prefix
-  int bstar2;         // threshold bin of the second prefix (>= bstar)
-  int n_list;         // slots of the first prefix
-  int n_list2;        // slots of the second prefix not in the first
-  int pad[3];
+  int bstar;          // threshold bin
+  int n_list;         // kept slots
+  int pad;
 };
 
 // ---------------------------------------------------------------- float32 training
@@ -635,16 +626,13 @@ __global__ void slot_features(TickArgs a, FeatureSrc fs, float* out) {
 // that holds at least k slots and -- with the network (tau > 0) -- at least m
 // slots the network predicts safe (score >= tau).  Whatever the scores, the kept
 // slots either contain the least-cost safe candidate of the whole tick or are all
-// unsafe (then, with the network, the wider second prefix is tried, and then the
-// full evaluation runs): the selection is always the exhaustive one.  The network
-// only decides how far down the cost order to go.
+// unsafe (then the full evaluation runs): the selection is always the exhaustive
+// one.  The network only decides how far down the cost order to go.
 
-// One histogram: the first bins at which the inclusive count reaches `t1` and
-// `t2` (kBins - 1 for a target never reached), from one prefix sum (whole block;
-// s_hist in shared memory).
-__device__ void first_bins_reaching(const unsigned int* s_hist, unsigned int t1,
-                                    unsigned int t2, unsigned int* s_run, int* s_bin, int* b1,
-                                    int* b2) {
+// One histogram: the first bin at which the inclusive count reaches `target`, or
+// kBins - 1 if it never does (whole block; s_hist in shared memory).
+__device__ int first_bin_reaching(const unsigned int* s_hist, unsigned int target,
+                                  unsigned int* s_run, int* s_bin) {
   constexpr int kRun = kBins / 128;
   unsigned int run = 0;
   if (threadIdx.x < 128)
@@ -672,43 +660,35 @@ __device__ void first_bins_reaching(const unsigned int* s_hist, unsigned int t1,
       before += v[j];
     }
   }
-  if (threadIdx.x == 0) s_bin[0] = s_bin[1] = kBins - 1;  // never reached: keep everything
+  if (threadIdx.x == 0) *s_bin = kBins - 1;  // never reached: keep everything
   __syncthreads();
   if (threadIdx.x < 128) {
-    // the only run that crosses a target holds its bin
-    const unsigned int start = s_run[threadIdx.x];
-    const unsigned int ts[2] = {t1, t2};
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      unsigned int cum = start;
-      if (cum < ts[e]) {
-        for (int i = 0; i < kRun; ++i) {
-          cum += s_hist[threadIdx.x * kRun + i];
-          if (cum >= ts[e]) {
-            s_bin[e] = threadIdx.x * kRun + i;
-            break;
-          }
+    unsigned int cum = s_run[threadIdx.x];
+    if (cum < target) {
+      for (int i = 0; i < kRun; ++i) {
+        cum += s_hist[threadIdx.x * kRun + i];
+        if (cum >= target) {
+          *s_bin = threadIdx.x * kRun + i;  // the only run that crosses the target
+          break;
         }
       }
     }
   }
   __syncthreads();
-  *b1 = s_bin[0];
-  *b2 = s_bin[1];
+  const int b = *s_bin;
   __syncthreads();
+  return b;
 }
 
 // End of a scoring launch (every thread of the block): this block's histograms
 // into the tick's; the last block finds the threshold bin (the larger of the bin
-// reaching k slots and, with s_safe, the bin reaching m predicted-safe slots) and
-// that of the second prefix (with the network, s_safe: the same with kScreenWiden
-// k and kScreenWiden m; without it the first prefix's), then clears the
-// histograms and the list counters for the next tick.  s_all may be null when
-// k <= m: a prefix holding m predicted-safe slots holds at least k slots, so the
-// predicted-safe bins alone are the thresholds.
+// reaching k slots and, with s_safe, the bin reaching m predicted-safe slots),
+// then clears the histograms and the list counter for the next tick.  s_all may
+// be null when k <= m: a prefix holding m predicted-safe slots holds at least k
+// slots, so the predicted-safe bin alone is the threshold.
 __device__ void screen_finish(unsigned int* s_all, unsigned int* s_safe, int k, int m,
                               ScreenScratch* ss) {
-  __shared__ int s_last, s_bin[2];
+  __shared__ int s_last, s_bin;
   __shared__ unsigned int s_run[128];
   __syncthreads();
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) {
@@ -726,24 +706,15 @@ __device__ void screen_finish(unsigned int* s_all, unsigned int* s_safe, int k, 
     if (s_safe) s_safe[i] = *reinterpret_cast<volatile unsigned int*>(&ss->hist_safe[i]);
   }
   __syncthreads();
-  const auto widen = [](int v) {
-    const unsigned long long w = (unsigned long long)(v > 0 ? v : 0) * kScreenWiden;
-    return w > 0xFFFFFFFFull ? 0xFFFFFFFFu : (unsigned int)w;
-  };
-  const unsigned int wk = s_safe ? widen(k) : (unsigned int)k, wm = widen(m);
-  int b = 0, b2 = 0;
-  if (s_all) first_bins_reaching(s_all, (unsigned int)k, wk, s_run, s_bin, &b, &b2);
+  int b = 0;
+  if (s_all) b = first_bin_reaching(s_all, (unsigned int)k, s_run, &s_bin);
   if (s_safe) {
-    int bs, bs2;
-    first_bins_reaching(s_safe, (unsigned int)m, wm, s_run, s_bin, &bs, &bs2);
+    const int bs = first_bin_reaching(s_safe, (unsigned int)m, s_run, &s_bin);
     b = bs > b ? bs : b;
-    b2 = bs2 > b2 ? bs2 : b2;
   }
   if (threadIdx.x == 0) {
     ss->bstar = b;
-    ss->bstar2 = b2;
     ss->n_list = 0;
-    ss->n_list2 = 0;
     ss->done = 0;
   }
   for (int i = threadIdx.x; i < kBins; i += blockDim.x) {
@@ -861,30 +832,22 @@ __global__ void __launch_bounds__(128) screen_cost(TickArgs a, int k, unsigned i
   screen_finish(s_hist, nullptr, k, 0, ss);
 }
 
-// The two prefixes' slot lists: cost bin at or below the first threshold into
-// `list`, above it and at or below the second into `list2` (warp-aggregated
-// appends).
+// Keeps the slots whose cost bin is at or below the threshold (warp-aggregated append).
 __global__ void screen_compact(const unsigned int* keys, int n_slots, ScreenScratch* ss,
-                               int* list, int* list2) {
-  grid_dep_wait();     // the screen's keys and thresholds
+                               int* list) {
+  grid_dep_wait();     // the screen's keys and threshold
   grid_dep_release();  // the rollout of the kept slots may launch now
-  const int bstar = ss->bstar, bstar2 = ss->bstar2;
+  const int bstar = ss->bstar;
   const int lane = threadIdx.x & 31;
-  const unsigned int below = (1u << lane) - 1;
   for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_slots;
        base += gridDim.x * blockDim.x) {
     const int slot = base + lane;
-    const int bin = slot < n_slots ? (int)(keys[slot] >> kBinShift) : kBins;
-    const bool keep = bin <= bstar, keep2 = !keep && bin <= bstar2;
+    const bool keep = slot < n_slots && (int)(keys[slot] >> kBinShift) <= bstar;
     const unsigned int m = __ballot_sync(0xffffffffu, keep);
-    const unsigned int m2 = __ballot_sync(0xffffffffu, keep2);
-    int at = 0, at2 = 0;
+    int at = 0;
     if (lane == 0 && m) at = atomicAdd(&ss->n_list, __popc(m));
-    if (lane == 0 && m2) at2 = atomicAdd(&ss->n_list2, __popc(m2));
     at = __shfl_sync(0xffffffffu, at, 0);
-    at2 = __shfl_sync(0xffffffffu, at2, 0);
-    if (keep) list[at + __popc(m & below)] = slot;
-    if (keep2) list2[at2 + __popc(m2 & below)] = slot;
+    if (keep) list[at + __popc(m & ((1u << lane) - 1))] = slot;
   }
 }
 
@@ -905,7 +868,6 @@ struct mpmi_screener {
   float* gemm_out = nullptr; // gradient GEMM outputs
   unsigned int* keys = nullptr;
   int* list = nullptr;
-  int* list2 = nullptr;      // the second prefix's slots
   mpmi::ScreenScratch* ss = nullptr;
   uint64_t bytes = 0;
   // optional phase timing of screened ticks: events around the screen, the
@@ -1060,7 +1022,7 @@ static int screened_chain(mpmi_session* session, mpmi_screener* s, const TickArg
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     SCR_CUDA(cudaLaunchKernelEx(&cfg, screen_compact, (const unsigned int*)s->keys,
-                                (int)session->n_slots, s->ss, s->list, s->list2),
+                                (int)session->n_slots, s->ss, s->list),
              "screen_compact launch");
   }
   SCR_CUDA(cudaGetLastError(), "screen launches");
@@ -1081,22 +1043,8 @@ static int screened_chain(mpmi_session* session, mpmi_screener* s, const TickArg
   if (n_list_dev)
     SCR_CUDA(cudaMemcpyAsync(n_list_dev, &s->ss->n_list, sizeof(int), cudaMemcpyDeviceToDevice,
                              st), "copy list size");
-  // with the network, the second prefix's slots beyond the first, only when the
-  // first holds no safe candidate and was not every slot: the least-cost safe
-  // candidate of the tick, if the wider prefix holds one, is then among them
-  if (tau > 0.f) {
-    TickArgs r2 = a;
-    r2.slot_list = s->list2;
-    r2.n_list = &s->ss->n_list2;
-    r2.skip_if_safe = a.result;
-    r2.result_flags = 5;
-    r2.chained = 1;
-    r2.seq_if_final = 1;
-    rc = launch_tick_args(session, r2, false, st, -1);
-    if (rc != MPMI_OK) return rc;
-  }
-  // full evaluation only when neither prefix holds a safe candidate and the first
-  // was not already every slot; its result counts the steps of every launch
+  // full evaluation only when the kept slots hold no safe candidate and were not
+  // already every slot; its result counts the steps of both launches
   TickArgs f = a;
   f.skip_if_safe = a.result;
   f.result_flags = 3;
@@ -1131,7 +1079,7 @@ int mpmi_screener_create(mpmi_ctx* ctx, const mpmi_model* model, const float* we
   const size_t gemm_floats = kH * (kH + 1) + kH * (kIn + 1) + (kH + 1);
   const uint64_t bytes = 4 * kP * sizeof(float) + sizeof(InferW) + look.size() * sizeof(float) +
                          act_floats * sizeof(float) + gemm_floats * sizeof(float) +
-                         (size_t)max_slots * (sizeof(unsigned int) + 2 * sizeof(int)) +
+                         (size_t)max_slots * (sizeof(unsigned int) + sizeof(int)) +
                          sizeof(ScreenScratch);
   if (ctx->budget && ctx->used + bytes > ctx->budget) {
     delete s;
@@ -1147,7 +1095,6 @@ int mpmi_screener_create(mpmi_ctx* ctx, const mpmi_model* model, const float* we
             cudaMalloc(&s->gemm_out, gemm_floats * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&s->keys, (size_t)max_slots * sizeof(unsigned int)) == cudaSuccess &&
             cudaMalloc(&s->list, (size_t)max_slots * sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&s->list2, (size_t)max_slots * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&s->ss, sizeof(ScreenScratch)) == cudaSuccess;
   if (ok)
     ok = cudaMemcpy(s->params, weights, kP * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -1190,7 +1137,6 @@ void mpmi_screener_free(mpmi_screener* s) {
   cudaFree(s->gemm_out);
   cudaFree(s->keys);
   cudaFree(s->list);
-  cudaFree(s->list2);
   cudaFree(s->ss);
   for (cudaEvent_t& e : s->ev)
     if (e) cudaEventDestroy(e);

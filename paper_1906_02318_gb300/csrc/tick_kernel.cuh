@@ -276,16 +276,13 @@ struct HasSkip<P, decltype((void)sizeof(((P*)nullptr)->skip_if_safe), void())> {
   static constexpr bool value = true;
 };
 
-// A screened tick's later launches (skip_if_safe set: the second prefix, the
-// fallback) have nothing to do when an earlier launch's slots held a safe
-// candidate or were already every slot of the tick, or when their own list is
-// empty (a second prefix that adds no slot).
+// A screened tick's fallback launch (skip_if_safe set) has nothing to do when the
+// kept slots held a safe candidate or were already every slot of the tick.
 template <class P>
 __device__ __forceinline__ bool fallback_not_needed(const P& a) {
   if (a.skip_if_safe == nullptr) return false;
   const mpmi_result* p = a.skip_if_safe;
-  if (p->status == MPMI_SAFE || p->n_slots >= a.n_slots) return true;
-  return a.n_list != nullptr && *a.n_list == 0;
+  return p->status == MPMI_SAFE || p->n_slots >= a.n_slots;
 }
 
 // The values that change from tick to tick: the Philox counter words of the

@@ -79,10 +79,8 @@ def train(screener, feats, targets, epochs=3, batch=8192, lr=2e-3, seed=0):
 def compare(session, screener, states, user_inputs, k=4096, tau=0.9, m=8, tick0=0):
     """Screened vs exhaustive tick on each (state, user input): returns a dict with
     the agreement (same selected slot), the number of reported-safe picks that the
-    exhaustive evaluation finds unsafe (safety misses), the number of ticks the
-    second, wider prefix decided and of those that fell back to the full
-    evaluation, the mean number of slots in the first prefix and the mean rollout
-    steps each form executed."""
+    exhaustive evaluation finds unsafe (safety misses), the fallback count, the
+    mean number of kept slots and the mean rollout steps each form executed."""
     import torch
     dev = torch.device("cuda")
     n = session.n_slots
@@ -90,7 +88,7 @@ def compare(session, screener, states, user_inputs, k=4096, tau=0.9, m=8, tick0=
     r_scr = torch.zeros(lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
     ttv = torch.empty(n, dtype=torch.int32, device=dev)
     nl = torch.zeros(1, dtype=torch.int32, device=dev)
-    agree = misses = fallbacks = second = 0
+    agree = misses = fallbacks = 0
     kept, steps, plain_steps = [], [], []
     for t, (x, u) in enumerate(zip(states, user_inputs)):
         xd = torch.tensor(x, dtype=torch.float64, device=dev)
@@ -105,13 +103,11 @@ def compare(session, screener, states, user_inputs, k=4096, tau=0.9, m=8, tick0=
         if b["status"] == lib.SAFE and full[b["index"]] != session.horizon:
             misses += 1
         fallbacks += (b["flags"] & 2) != 0
-        second += (b["flags"] & 4) != 0
         kept.append(int(nl.item()))
         steps.append(b["executed_steps"])
         plain_steps.append(a["executed_steps"])
     T = len(states)
     return dict(ticks=T, agreement=agree / T, safety_misses=misses, fallbacks=fallbacks,
-                second_prefix=second,
                 mean_kept=float(np.mean(kept)), mean_executed_steps=float(np.mean(steps)),
                 plain_executed_steps=float(np.mean(plain_steps)))
 
