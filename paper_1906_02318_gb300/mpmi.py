@@ -442,6 +442,9 @@ class Session:
         self._in = np.zeros(MAX_NX + MAX_NU)
         self._x_ptr = self._in.ctypes.data
         self._u_ptr = self._x_ptr + 8 * MAX_NX
+        self._in_x = self._in[:self.nx]
+        self._in_u = self._in[MAX_NX:MAX_NX + self.nu]
+        self._stream_key = self._stream_arg = None  # the last stream object and its handle
 
     def launch_shape(self):
         """(lanes per candidate, candidates per thread, threads per block)."""
@@ -497,26 +500,48 @@ def measure_fp32_peak(device: int = 0, seconds: float = 0.5) -> float:
     return out.value
 
 
+def _stage(dst, a, n):
+    """Copies a host input (x_t or u_h) into the session's staging view."""
+    if isinstance(a, np.ndarray) and a.dtype == np.float64 and a.size == n:
+        np.copyto(dst, a.reshape(n))
+    else:
+        dst[:] = _f64(a, n)
+
+
+def _session_stream(s: Session, stream):
+    """The stream handle for a host tick; the last stream object's handle is kept,
+    so a loop on one stream converts it once."""
+    if stream is not None and stream is s._stream_key:
+        return s._stream_arg
+    arg = _stream(stream)
+    if stream is not None:
+        s._stream_key, s._stream_arg = stream, arg
+    return arg
+
+
+def _outcome(s: Session) -> dict:
+    r = s._result
+    return dict(u_r=s._u_r[:s.nu].copy(), index=r.index, status=r.status, n_safe=r.n_safe,
+                ttv=r.ttv, cost=r.cost, n_slots=r.n_slots, executed_steps=r.executed_steps,
+                tick=r.tick, flags=r.reserved)
+
+
 def evaluate_candidates(s: Session, x_t, u_h, candidates=None, tick: int = 0, stream=None):
     """mpmi_evaluate_candidates: queue one tick from host x_t / u_h (float64)."""
-    buf = s._in
-    buf[:s.nx] = _f64(x_t, s.nx)
-    buf[MAX_NX:MAX_NX + s.nu] = _f64(u_h, s.nu)
+    _stage(s._in_x, x_t, s.nx)
+    _stage(s._in_u, u_h, s.nu)
     rc = s.ctx.lib.mpmi_evaluate_candidates(s.handle, s._x_ptr, s._u_ptr,
-                                            _ptr(candidates), tick, _stream(stream))
+                                            _ptr(candidates), tick, _session_stream(s, stream))
     if rc:
         _check(rc)
 
 
 def select_input(s: Session) -> dict:
     """mpmi_select_input: wait for the queued tick and return its outcome."""
-    r = s._result
     rc = s.ctx.lib.mpmi_select_input(s.handle, s._result_ptr)
     if rc:
         _check(rc)
-    return dict(u_r=s._u_r[:s.nu].copy(), index=r.index, status=r.status, n_safe=r.n_safe,
-                ttv=r.ttv, cost=r.cost, n_slots=r.n_slots, executed_steps=r.executed_steps,
-                tick=r.tick, flags=r.reserved)
+    return _outcome(s)
 
 
 def evaluate_candidates_device(s: Session, x_t_dev, u_h_dev, result_dev, candidates=None,
@@ -693,11 +718,10 @@ def evaluate_screened_host(s: Session, scr: Screener, x_t, u_h, k: int = 4096, t
                            m: int = 8, tick: int = 0, stream=None):
     """mpmi_evaluate_screened_host: the screened tick from host x_t / u_h (float64),
     queued; collect it with select_input."""
-    buf = s._in
-    buf[:s.nx] = _f64(x_t, s.nx)
-    buf[MAX_NX:MAX_NX + s.nu] = _f64(u_h, s.nu)
+    _stage(s._in_x, x_t, s.nx)
+    _stage(s._in_u, u_h, s.nu)
     rc = s.ctx.lib.mpmi_evaluate_screened_host(s.handle, scr.handle, s._x_ptr, s._u_ptr, tick,
-                                               k, tau, m, _stream(stream))
+                                               k, tau, m, _session_stream(s, stream))
     if rc:
         _check(rc)
 
