@@ -64,6 +64,20 @@ LIFTED_N = 12
 FLUSH_BYTES = 256 << 20
 SM_FP32_LANES = 128
 
+# The paper's own throughput figures (its System Performance subsection; its only
+# hardware is a GeForce 860M laptop GPU), quoted beside the measurements as context:
+# another machine and other workloads, not a target.  The rollout-step rates are
+# derived here from its loop rates, sample counts and horizons.
+PAPER_CONTEXT = {
+    "hardware": "GeForce 860M",
+    "trajectories_per_tick": ">10,000 (balance bot N = 10,000, T = 30; race car N = 10,120, "
+                             "T = 25)",
+    "control_rate_hz": {"balance_bot": 100, "race_car": 60},
+    "trajectories_per_s": "600,000-1,000,000 with the safety checks",
+    "derived_rollout_steps_per_s": {"balance_bot": 100 * 10000 * 30, "race_car": 60 * 10120 * 25},
+    "note": "context only, not comparable: other hardware and workloads",
+}
+
 # DRAM bytes per tick-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum); valid only for the kernel source and launch shape
 # (lanes, candidates per thread, block) it was taken on.
@@ -1167,6 +1181,7 @@ def main():
         "clocks": out["clocks"],
         "fallback_ticks": out["n_fallback"], "trials": out["trials"],
         "paper_metrics": out["paper_metrics"],
+        "paper_context": PAPER_CONTEXT,
     }
     if rank == 0 and args.learned_ticks > 0:
         line["learned"] = run_learned(args)
