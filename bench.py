@@ -787,6 +787,31 @@ def run_serving(args, bot_states):
                                     "H uniform 20..100",
         **{name: {k: r[k] for k in ("ticks_per_s", "rollout_steps_per_s", "batches",
                                      "mean_batch", "latency")} for name, r in hruns.items()}}
+    # capacity: the same sessions, each submitting its next tick as soon as its last
+    # result is back (no pacing): the ticks/s the server sustains for this mix and
+    # the FP32 work its batches run (executed prediction steps x 2 n^2)
+    for ss in heavy:
+        ss.next_tick, ss.outstanding, ss.latencies = 0, False, []
+        ss.period, ss.offset = 1e-9, 0.0
+        ss.jitter = np.zeros_like(ss.jitter)
+    rec = {}
+    sat = serve.run([hs], heavy, duration=min(args.serve_seconds, 3.0), streams=streams,
+                    record=rec, overlap=4, max_batch=n_heavy // 4)
+    executed = float(sum(int(r["executed_steps"]) for r in rec.values()))
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(measured_peaks().get("sm_max_mhz", 2070.0))
+    fp32_peak = props.multi_processor_count * SM_FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    tflops = executed * 2 * CAR_LIFTED_N ** 2 / sat["wall_s"] / 1e12
+    stats["car_saturated"] = {
+        "sessions": n_heavy, "what": "the car_heavy sessions without pacing: each submits its "
+                                     "next tick when its last result is back; at most a "
+                                     "quarter of them per batch, up to four batches in flight",
+        "seconds": sat["wall_s"], "ticks_per_s": sat["ticks_per_s"],
+        "rollout_steps_per_s": sat["rollout_steps_per_s"],
+        "executed_steps_per_s": executed / sat["wall_s"], "batches": sat["batches"],
+        "mean_batch": sat["mean_batch"],
+        "roofline": {"bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": tflops / fp32_peak}}
     hs.free()
     bm.free()
     cm.free()

@@ -37,10 +37,13 @@ class ServedSession:
     latencies: list = field(default_factory=list)
 
 
-def run(servers, sessions, duration: float, streams=None, record=None, overlap: int = 4):
+def run(servers, sessions, duration: float, streams=None, record=None, overlap: int = 4,
+        max_batch: int | None = None):
     """Serve `sessions` for `duration` seconds of wall time with at most `overlap`
-    batches per server on the GPU.  Returns stats; if `record` is a dict, every
-    result is stored under (session index, tick)."""
+    batches per server on the GPU and, with max_batch, at most that many requests
+    per batch (the rest stay due for the next one, so that sessions which all come
+    due at once still spread over overlapping batches).  Returns stats; if `record`
+    is a dict, every result is stored under (session index, tick)."""
     import torch
     streams = streams or [torch.cuda.Stream() for _ in servers]
     for srv in servers:
@@ -73,9 +76,13 @@ def run(servers, sessions, duration: float, streams=None, record=None, overlap: 
                     if record is not None:
                         record[(slot_to_sess[si][slot], k)] = r
                 srv._n_flying -= 1
-            # stage every due request of this server's sessions
+            # stage the due requests of this server's sessions (up to max_batch per
+            # batch)
+            room = None if max_batch is None else max_batch - srv._n_staged
             due = []
             for i in by_server[si]:
+                if room is not None and len(due) >= room:
+                    break
                 ss = sessions[i]
                 k = ss.next_tick
                 if not ss.outstanding and ss.offset + k * ss.period + ss.jitter[k % len(ss.jitter)] <= now:
@@ -94,11 +101,17 @@ def run(servers, sessions, duration: float, streams=None, record=None, overlap: 
                 srv._n_flying += 1
                 srv._n_staged = 0
                 batches += 1
-    # drain
-    for srv in servers:
+    # drain: every batch in flight, then whatever is still staged, so the servers
+    # end empty (a later run on them starts from no pending request)
+    for si, srv in enumerate(servers):
         while srv._n_flying:
             srv.collect()
             srv._n_flying -= 1
+        if srv._n_staged:
+            srv.launch(streams[si])
+            batches += 1
+            srv.collect()
+            srv._n_staged = 0
     wall = time.perf_counter() - t0
     lat = {}
     for kind in sorted({s.period for s in sessions}):

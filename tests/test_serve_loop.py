@@ -89,7 +89,7 @@ def test_overlap_bound_and_every_request_answered(overlap):
     assert srv.most_in_flight <= overlap
     if overlap > 1:
         assert srv.most_in_flight > 1          # batches did overlap
-    assert not srv.flying and not srv.busy     # drained
+    assert not srv.flying and not srv.busy and not srv.staged  # drained, nothing left staged
     # every launched request answered once, per session in tick order from 0
     assert stats["ticks"] == sum(len(s.latencies) for s in sess)
     for i, s in enumerate(sess):
@@ -107,3 +107,29 @@ def test_overlap_lowers_latency_under_load():
         lat[overlap] = stats["latency"]["200Hz"]["p50_ms"]
     # with one batch at a time a request waits for the running batch to finish
     assert lat[4] < lat[1]
+
+
+def test_max_batch_caps_each_launch():
+    """With max_batch, sessions that come due together spread over several batches
+    (each at most max_batch requests) instead of one, and every request is still
+    answered once and in tick order."""
+    srv = FakeServer(service_s=0.004)
+    sizes = []
+    launch = srv.launch
+
+    def counting_launch(stream=None):
+        n = len(srv.staged)
+        sizes.append(n)
+        return launch(stream)
+    srv.launch = counting_launch
+    sess = _sessions(40, 1e-9, seed=3)           # no pacing: always due
+    for s in sess:
+        s.offset, s.jitter = 0.0, np.zeros_like(s.jitter)
+    stats = serve.run([srv], sess, duration=0.2, streams=[None], overlap=4, max_batch=10)
+    assert sizes and max(sizes) <= 10
+    assert srv.most_in_flight > 1
+    assert not srv.flying and not srv.busy and not srv.staged
+    for i, s in enumerate(sess):
+        ticks = [t for sl, t in srv.answered if sl == i]
+        assert ticks == list(range(len(ticks))) and len(ticks) == s.next_tick
+    assert stats["batches"] == srv.launches
