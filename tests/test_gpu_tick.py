@@ -523,6 +523,38 @@ def test_maximum_slot_count(lib, ctx, bot):
     assert e.value.code == -1
 
 
+@pytest.mark.slow
+def test_car_maximum_slot_count(lib, ctx, car):
+    """The race car at 2^23 - 1 slots (the key's slot field full) in its default
+    launch shape: the pick is the lexicographic minimum of the GPU's own outputs and
+    sampled slots (the last ones included) agree with the oracle, track test and
+    all, except at a safety boundary."""
+    env, model = car
+    N, H = lib.MAX_SLOTS - 1, 8
+    x_t = data.car_start_state(env.track, vx=15.0)
+    u_h = data.to_f32_exact(data.user_input_once(14, env.lo, env.hi))
+    sess = lib.Session(ctx, model, N, H, env.lo, env.hi, seed=19, stream_id=2)
+    g = run_gpu(lib, sess, x_t, u_h, tick=5)
+    sess.close()
+    ttv, cost, r = g["ttv"], g["cost"], g["result"]
+    assert r["n_slots"] == lib.MAX_SLOTS and ttv.size == lib.MAX_SLOTS
+    slots = np.arange(ttv.size)
+    order = np.lexsort((slots, cost.astype(np.float64), H - ttv))
+    assert r["index"] == int(order[0])
+    assert r["n_safe"] == int(np.count_nonzero(ttv == H))
+    assert r["executed_steps"] == int(np.minimum(ttv + 1, H).sum())
+    samples = osamp.uniform_samples(19, 2, 5, N, env.lo, env.hi)
+    pick = np.unique(np.concatenate([np.arange(N - 31, N + 1), np.arange(1, 33),
+                                     np.random.default_rng(2).integers(1, N + 1, 128)]))
+    o = omp.tick(env.K32, env.basis, x_t, u_h, samples[pick - 1], H, env.spec,
+                 include_user=False, record=True)
+    assert np.allclose(cost[pick], o.cost, rtol=1e-6, atol=1e-12)
+    for i in np.nonzero(ttv[pick] != o.ttv)[0]:   # only at a safety boundary
+        s_ = int(min(ttv[pick[i]], o.ttv[i])) + 1
+        marg = float(osafe.margin(env.spec, o.traj[i, s_][None, :])[0])
+        assert abs(marg) < 1e-4 * max(1.0, float(np.abs(o.traj[i, s_]).max()))
+
+
 @pytest.mark.parametrize("inflation", [0.5, 1.5])
 @pytest.mark.parametrize("rollout", ["full", "tensor", "factored"])
 def test_car_inflated_barrier(lib, ctx, inflation, rollout):
