@@ -171,6 +171,23 @@ def test_car_ticks(lib, ctx, car, lanes, cands):
         assert compare(g, o, env, 60) <= 10
 
 
+@pytest.mark.parametrize("lanes,cands", [(1, 1), (1, 2), (2, 1), (4, 1), (8, 1), (16, 1)])
+@pytest.mark.parametrize("N", [0, 1, 33, 129])
+def test_car_ragged_sizes(lib, ctx, car, lanes, cands, N):
+    """Few and ragged slot counts (the user's slot alone, one sample, partial warp
+    tiles and pairs) in every race-car launch shape, trajectories and all."""
+    env, model = car
+    x0 = data.car_start_state(env.track, vx=13.0)
+    states = [x0, x0 + np.array([1.0, -1.5, 0.08, 3.0, 0.2, 0.1])]
+    excused = 0
+    for k, x_t in enumerate(states):
+        u_h = data.to_f32_exact(data.user_input_once(400 + k, env.lo, env.hi))
+        g, o = _tick(lib, ctx, env, model, x_t, u_h, N, 60, seed=4, tick=k, lanes=lanes,
+                     cands=cands)
+        assert g["result"]["n_slots"] == N + 1
+        excused += compare(g, o, env, 60)
+    assert excused <= 2
+
 @pytest.mark.slow
 def test_car_full_size(lib, ctx, car):
     """N = 16384, H = 60 in the default launch configuration."""
