@@ -55,7 +55,7 @@ def _factored(lib, ctx, env, model, x_t, u_h, N, H, seed, stream, tick, include_
     return g, o
 
 
-@pytest.mark.parametrize("N,H", [(1000, 50), (4097, 50), (31, 1), (2047, 200)])
+@pytest.mark.parametrize("N,H", [(1000, 50), (4097, 50), (31, 1), (2047, 200), (0, 50), (1, 50)])
 def test_factored_bot_matches_oracle(lib, ctx, bot, N, H):
     env, model = bot
     states = data.states_in_box(17, 3, [-0.25, -0.6, -0.6, -0.6], [0.25, 0.6, 0.6, 0.6])
@@ -63,6 +63,18 @@ def test_factored_bot_matches_oracle(lib, ctx, bot, N, H):
         u_h = data.to_f32_exact(data.user_input_once(40 + k, env.lo, env.hi))
         g, o = _factored(lib, ctx, env, model, x_t, u_h, N, H, 5, k, 100 + k)
         assert compare(g, o, env, H) <= max(4, 0.002 * (N + 1))
+
+
+@pytest.mark.parametrize("N", [0, 1, 33])
+def test_factored_car_ragged_sizes(lib, ctx, car, N):
+    """The user's slot alone, one sample and a partial warp tile."""
+    env, model = car
+    x0 = data.car_start_state(env.track, vx=13.0)
+    for k, x_t in enumerate([x0, x0 + np.array([1.0, -1.5, 0.08, 3.0, 0.2, 0.1])]):
+        u_h = data.to_f32_exact(data.user_input_once(420 + k, env.lo, env.hi))
+        g, o = _factored(lib, ctx, env, model, x_t, u_h, N, 60, 6, k, 40 + k)
+        assert g["result"]["n_slots"] == N + 1
+        assert compare(g, o, env, 60) <= 2
 
 
 @pytest.mark.parametrize("include_user", [True, False])

@@ -72,6 +72,18 @@ def test_tensor_rollout_matches_oracle(lib, ctx, car, N, H):
         assert compare(g, o, env, H) <= max(6, 0.002 * (N + 1))
 
 
+@pytest.mark.parametrize("N", [0, 1, 33])
+def test_tensor_rollout_ragged_sizes(lib, ctx, car, N):
+    """The user's slot alone, one sample and a partial tile: one tile of 128 rows
+    with nearly all of them padding, trajectories and all."""
+    env, model = car
+    for k, x_t in enumerate(_states(env)[:2]):
+        u_h = data.to_f32_exact(data.user_input_once(410 + k, env.lo, env.hi))
+        g, o = _tensor_tick(lib, ctx, env, model, x_t, u_h, N, 60, 6, k, 30 + k)
+        assert g["result"]["n_slots"] == N + 1
+        assert compare(g, o, env, 60) <= 2
+
+
 def test_tensor_rollout_without_user_slot_and_full_size(lib, ctx, car):
     env, model = car
     x_t = _states(env)[1]

@@ -188,6 +188,7 @@ def test_car_ragged_sizes(lib, ctx, car, lanes, cands, N):
         excused += compare(g, o, env, 60)
     assert excused <= 2
 
+
 @pytest.mark.slow
 def test_car_full_size(lib, ctx, car):
     """N = 16384, H = 60 in the default launch configuration."""
@@ -196,7 +197,6 @@ def test_car_full_size(lib, ctx, car):
     u_h = data.to_f32_exact(data.user_input_once(3, env.lo, env.hi))
     g, o = _tick(lib, ctx, env, model, x_t, u_h, 16384, 60, seed=3)
     assert compare(g, o, env, 60) <= 0.002 * 16385
-
 
 
 @pytest.mark.slow
