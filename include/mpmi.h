@@ -235,7 +235,8 @@ typedef struct {
 } mpmi_tune_result;
 
 /* Times every compiled launch shape (lanes per candidate x candidates per thread)
- * at 64, 128 and 256 threads per block for one tick configuration -- the model,
+ * at 64, 128, 160, 192, 224 and 256 threads per block (every size the built-in
+ * rule picks) for one tick configuration -- the model,
  * cfg's N, H, sampler and user slot (cfg's lanes, cands_per_thread and block are
  * ignored) -- from the host state x_t (nx doubles) and input u_h (nu doubles):
  * two warm-up ticks, then `reps` device-resident ticks (1..1000) each timed with

@@ -38,10 +38,10 @@ def test_tuned_shape_is_used_and_changes_nothing(lib, which, N, H, n_shapes):
     default.close()
 
     r = lib.tune_launch_shape(ctx, model, N, H, env.lo, env.hi, x_t, u_h, reps=10, seed=5)
-    assert 1 <= r["n_tried"] <= 3 * n_shapes
+    assert 1 <= r["n_tried"] <= 6 * n_shapes  # six block sizes per shape
     assert np.isfinite(r["us"]) and np.isfinite(r["default_us"])
     assert r["us"] <= r["default_us"]
-    assert r["block"] in (64, 128, 256)
+    assert r["block"] in (64, 128, 160, 192, 224, 256)
 
     tuned = lib.Session(ctx, model, N, H, env.lo, env.hi, seed=5)
     assert tuned.launch_shape() == (r["lanes"], r["cands"], r["block"])
@@ -88,4 +88,34 @@ def test_tuner_argument_checks(lib):
     with pytest.raises(lib.MpmiError) as e:
         lib.tune_launch_shape(ctx, model, 1000, 0, env.lo, env.hi, x_t, u_h)
     assert e.value.code == -1
+    model.free()
+
+
+@pytest.mark.parametrize("N,cands", [(24000, 1), (65536, 2)])
+def test_car_one_lane_default_block_follows_the_sm_count(lib, N, cands):
+    """The built-in rule gives the race car's one-lane shapes one block of
+    ceil(warp-tiles / SMs) warps per SM where that is at most eight warps; the
+    results equal those of 128-thread blocks bit for bit."""
+    import math
+    import torch
+    ctx = lib.Context(0)
+    env = car_env()
+    model = gpu_model(lib, ctx, env)
+    x_t = data.car_start_state(env.track, vx=12.0)
+    u_h = data.to_f32_exact(data.user_input_once(12, env.lo, env.hi))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    warps = math.ceil(math.ceil((N + 1) / (32 * cands)) / sms)
+    default = lib.Session(ctx, model, N, 60, env.lo, env.hi, seed=6)
+    shape = default.launch_shape()
+    got = run_gpu(lib, default, x_t, u_h, tick=2)
+    default.close()
+    assert shape == (1, cands, 32 * warps if 4 < warps <= 8 else 128)
+    plain = lib.Session(ctx, model, N, 60, env.lo, env.hi, seed=6, lanes=1, cands=cands, block=128)
+    want = run_gpu(lib, plain, x_t, u_h, tick=2)
+    plain.close()
+    assert np.array_equal(got["ttv"], want["ttv"])
+    assert np.array_equal(got["cost"], want["cost"])
+    for k in ("index", "status", "n_safe", "ttv", "cost", "executed_steps"):
+        assert got["result"][k] == want["result"][k]
+    assert np.array_equal(got["result"]["u_r"], want["result"]["u_r"])
     model.free()
