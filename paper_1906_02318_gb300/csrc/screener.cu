@@ -1283,7 +1283,7 @@ int mpmi_evaluate_screened_host(mpmi_session* session, mpmi_screener* s, const d
     a.u_h = session->in_map + 8;
     a.result = session->result_map;
     a.seq_out = session->seq_map;
-    a.seq = session->seq + 1;
+    a.seq = ++session->seq;  // taken even if a launch fails: a later tick never reuses it
   } else {
     SCR_CUDA(cudaMemcpyAsync(session->in_dev, session->in_host, 12 * sizeof(double),
                              cudaMemcpyHostToDevice, st), "copy x_t/u_h to the device");
@@ -1291,13 +1291,15 @@ int mpmi_evaluate_screened_host(mpmi_session* session, mpmi_screener* s, const d
     a.u_h = session->in_dev + 8;
     a.result = session->result_dev;
   }
-  if ((rc = screened_chain(session, s, a, k, tau, m, nullptr, nullptr, st)) != MPMI_OK) return rc;
-  if (session->zero_copy) {
-    ++session->seq;
-  } else {
+  if ((rc = screened_chain(session, s, a, k, tau, m, nullptr, nullptr, st)) != MPMI_OK) {
+    // launches queued before the failing one may still run: later launches and
+    // closing the session wait for them
+    if (cudaEventRecord(session->done, st) == cudaSuccess) session->tail_pending = true;
+    return rc;
+  }
+  if (!session->zero_copy)
     SCR_CUDA(cudaMemcpyAsync(session->result_host, session->result_dev, sizeof(mpmi_result),
                              cudaMemcpyDeviceToHost, st), "copy the result to the host");
-  }
   return host_tick_end(session, st);
 }
 

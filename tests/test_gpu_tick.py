@@ -112,6 +112,36 @@ def test_external_candidates_are_used(lib, ctx, bot):
     compare(g, o, env, 30)
 
 
+@pytest.mark.parametrize("include_user", [True, False])
+def test_exact_ties_pick_the_lowest_slot(lib, ctx, bot, include_user):
+    """Caller samples drawn from four values, so every cost is one of three exact
+    values and each is shared by hundreds of slots: the pick is the lowest slot
+    of the least-cost safe group, as in the oracle, and u_h itself (cost 0) wins
+    when it is a slot."""
+    import torch
+    env, model = bot
+    rng = np.random.default_rng(21)
+    cand = rng.choice(np.array([-0.5, -0.25, 0.25, 0.5]), size=(3001, 1))
+    dev = torch.tensor(cand, dtype=torch.float32, device="cuda")
+    sess = lib.Session(ctx, model, 3001, 30, env.lo, env.hi, sampler="external",
+                       include_user=include_user)
+    for k, x_t in enumerate([np.array([0.05, 0.0, 0.0, 0.0]), np.array([0.2, 0.4, 0.3, 0.1])]):
+        u_h = np.array([0.0]) if k == 0 else np.array([0.25])
+        g = run_gpu(lib, sess, x_t, u_h, traj=True, candidates=dev)
+        o = omp.tick(env.K32, "bot", x_t, u_h, cand, 30, env.spec, include_user=include_user,
+                     record=True)
+        compare(g, o, env, 30)
+        assert g["result"]["index"] == o.index
+        if include_user and o.ttv[0] == 30:
+            assert o.index == 0
+        else:
+            # the lowest slot among the safe candidates of least cost
+            safe = np.nonzero(o.ttv == 30)[0]
+            best = safe[o.cost[safe] == o.cost[safe].min()]
+            assert o.index == int(best.min()) and len(best) > 100
+    sess.close()
+
+
 # ------------------------------------------------------------------ balance bot
 @pytest.mark.parametrize("lanes", [1, 2, 4])
 def test_bot_single_tick_paper_scale(lib, ctx, bot, lanes):
