@@ -433,12 +433,14 @@ __device__ __forceinline__ bool track_ok(const DevTrack& tr, const TrackView& v,
         ok = true;
       } else if (cls == kCellBoundary) {
         const int off = (int)((c >> 2) & 0x3FFFFFu), cnt = (int)(c >> 24);
-        // four independent segment tests per round (entries past the list end
+        // J independent segment tests per lane and round, J L >= 16 entries per
+        // round for the group (lists hold ~7-15; entries past the list end
         // repeat its last entry); the OR over the list is unchanged
-        for (int i0 = q; i0 < cnt; i0 += 4 * L) {
+        constexpr int J = L >= 16 ? 1 : (L >= 8 ? 2 : 4);
+        for (int i0 = q; i0 < cnt; i0 += J * L) {
           bool hit = false;
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
+          for (int j = 0; j < J; ++j) {
             const int s = v.list[off + min(i0 + j * L, cnt - 1)];
             const float4 sg = v.seg[s];
             const float rx = px - sg.x, ry = py - sg.y;
