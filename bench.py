@@ -81,8 +81,8 @@ PAPER_CONTEXT = {
 # DRAM bytes per tick-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum); valid only for the kernel source and launch shape
 # (lanes, candidates per thread, block) it was taken on.
-TRAFFIC = {"tick_kernel_sha1": "ec4d066e0f1b649fadaa707fba50eb6b3bb9509c",
-           "bytes_per_launch": {(1, 1, 128): 26624, (1, 1, 64): 26624}}
+TRAFFIC = {"tick_kernel_sha1": "97d5b009fbabb862887c3ebbe6a7ebfe623f6776",
+           "bytes_per_launch": {(1, 1, 128): 26880, (1, 1, 64): 26624}}
 
 
 def kernel_sha1() -> str:
