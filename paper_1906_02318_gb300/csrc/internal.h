@@ -157,9 +157,10 @@ struct mpmi_session {
   // resident blocks on the device per launch kind (plain or trajectories, all
   // slots or the few-candidate shape, with or without noise) and the dynamic
   // shared memory they assume
-  // (index: trajectories + 2 few-candidate shape + 4 noise)
-  int max_grid[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  size_t grid_smem[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // (index: trajectories + 2 few-candidate shape + 4 noise + 8 sixteen lanes in
+  // the few-candidate shape)
+  int max_grid[16] = {};
+  size_t grid_smem[16] = {};
   mpmi::TickScratch* scratch_dev = nullptr;
   mpmi_result* result_dev = nullptr;
   double* in_dev = nullptr;        // x_t (8 doubles) then u_h (4 doubles)
@@ -222,7 +223,10 @@ struct DeviceGuard {
 
 // tick launch helpers shared by the API and the screener (mpmi_api.cu)
 TickArgs make_tick_args(const mpmi_session* s, uint64_t tick);
-int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint);
+// list_lanes: lanes per race-car candidate of a launch over a device-side list
+// (16, or 0 for the built-in 8)
+int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint,
+                     int list_lanes = 0);
 // host ticks: wait for the one in flight; record the completion event after the launches
 int host_tick_begin(mpmi_session* s);
 int host_tick_end(mpmi_session* s, cudaStream_t st);

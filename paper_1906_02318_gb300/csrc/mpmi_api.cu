@@ -141,10 +141,10 @@ TickArgs make_tick_args(const mpmi_session* s, uint64_t tick) {
 // the warp-tiles need.  Occupancy is cached per dynamic shared-memory size.
 // Launch shape for a launch that evaluates few candidates (a screened list): more
 // lanes per candidate shorten the serial H-step chain each candidate carries.
-static void small_shape(int kind, int* lanes, int* cands, int* block) {
+static void small_shape(int kind, int list_lanes, int* lanes, int* cands, int* block) {
   *cands = 1;
   *block = 128;
-  *lanes = kind == kCar ? 8 : (kind == kBot ? 4 : 1);
+  *lanes = kind == kCar ? (list_lanes == 16 ? 16 : 8) : (kind == kBot ? 4 : 1);
 }
 
 // ---- persistent host ticks ----------------------------------------------------
@@ -262,7 +262,8 @@ int host_tick_end(mpmi_session* s, cudaStream_t st) {
   return MPMI_OK;
 }
 
-int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint) {
+int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, int n_hint,
+                     int list_lanes) {
   // a launched tick shares the session's reduction record with the resident kernel
   if (s->persist_running) {
     const int rc = persist_stop(s);
@@ -290,14 +291,14 @@ int launch_tick_args(mpmi_session* s, TickArgs& a, bool traj, cudaStream_t st, i
     if (a.n_noise > 0) return fail(MPMI_E_UNSUPPORTED, "the factorised rollout has no noise");
     return launch_factored(s, a, st, n_hint);
   }
-  if (small) small_shape(s->model->kind, &lanes, &cands, &block);
+  if (small) small_shape(s->model->kind, list_lanes, &lanes, &cands, &block);
   const bool noise = a.n_noise > 0;
   if (noise && a.tick >= (1ull << 48))
     return fail(MPMI_E_INVALID_ARG, "ticks with noise must stay below 2^48");
   TickKernel k = pick_tick(s->model->kind, lanes, cands, traj, noise);
   if (!k.fn) return fail(MPMI_E_UNSUPPORTED, "tick kernel not compiled for this launch shape");
   const size_t smem = k.k_smem + (a.safety.has_track ? (size_t)a.safety.track.blob_bytes : 0);
-  const int t = (traj ? 1 : 0) + (small ? 2 : 0) + (noise ? 4 : 0);
+  const int t = (traj ? 1 : 0) + (small ? 2 : 0) + (noise ? 4 : 0) + (small && lanes == 16 ? 8 : 0);
   if (s->max_grid[t] == 0 || s->grid_smem[t] != smem) {
     // static (lane exchange) plus dynamic shared memory may pass the 48 KB default
     if (smem > 0) {

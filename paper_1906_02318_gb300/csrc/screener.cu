@@ -1034,7 +1034,10 @@ static int screened_chain(mpmi_session* session, mpmi_screener* s, const TickArg
   r.result_flags = 1;
   r.chained = 1;
   r.seq_if_final = 1;
-  rc = launch_tick_args(session, r, false, st, -1);
+  // with the network the kept slots are mostly predicted safe and run the whole
+  // horizon, so sixteen lanes per race-car candidate shorten the chain; in cost
+  // order most kept slots leave early and eight lanes keep fewer warps
+  rc = launch_tick_args(session, r, false, st, -1, tau > 0.f ? 16 : 0);
   if (rc != MPMI_OK) return rc;
   if (s->timing) SCR_CUDA(cudaEventRecord(s->ev[3], st), "cudaEventRecord");
   if (list_dev)
