@@ -324,6 +324,11 @@ def test_track_spec_unsafe_off_road_and_fast():
     z[:, 0] = [R + 3.9, R - 4.1, R, R]
     z[:, 3] = [10, 10, 24.9, 25.0]
     assert safety.is_safe(spec, z).tolist() == [True, False, True, False]
+    # the inflated barrier narrows the road to w - iota and the speed bound to 25 - iota
+    spec.inflation = 0.5
+    z[:, 0] = [R + 3.4, R + 3.7, R, R]
+    z[:, 3] = [10, 10, 24.4, 24.6]
+    assert safety.is_safe(spec, z).tolist() == [True, False, True, False]
 
 
 # --------------------------------------------------------------------------- Alg. 2
@@ -489,3 +494,28 @@ def test_brute_force_tiny(kind):
         assert r.ttv.tolist() == [row[3] for row in rows]
         assert np.allclose(r.cost, [row[1] for row in rows], rtol=1e-15, atol=0)
         assert r.index == best[2]
+
+
+def test_exact_ties_go_to_the_lowest_slot():
+    """Brute force on candidates drawn from four values: every cost is shared by
+    a dozen slots, and the pick is the lowest slot of the least-cost group that
+    survives longest (the lexicographic minimum of (H - ttv, cost, slot))."""
+    x, u, xn = data.transitions("bot", 1, 2000)
+    K = fit.round_to_f32(fit.fit_koopman("bot", x, u, xn)[0])
+    spec = safety.SafetySpec(lo=data.BOT_SAFE_LO, hi=data.BOT_SAFE_HI)
+    rng = np.random.default_rng(13)
+    s = rng.choice(np.array([-0.5, -0.25, 0.25, 0.5]), size=(47, 1))
+    for x_t, u_h in ((np.array([0.05, 0.0, 0.0, 0.0]), [-0.25]),
+                     (np.array([0.2, 0.4, 0.3, 0.1]), [0.25]),
+                     (np.array([0.45, 1.5, 1.8, 1.0]), [0.5])):
+        for include_user in (True, False):
+            r = mpmi.tick(K, "bot", x_t, u_h, s, 30, spec, include_user=include_user)
+            rows, best = _bf_tick("bot", K.tolist(), x_t.tolist(), list(u_h), s.tolist(), 30,
+                                  spec.lo.tolist(), spec.hi.tolist())
+            if not include_user:  # the brute force puts u_h in slot 0: drop it
+                rows = [(a, b, c - 1, d) for a, b, c, d in rows[1:]]
+                best = sorted(rows)[0]
+            group = [row[2] for row in rows if row[:2] == best[:2]]
+            assert len(group) > 1
+            assert r.index == best[2] == min(group)
+
