@@ -4,8 +4,9 @@ dropped feature, a transposed operand, an off-by-one count, a closed instead of
 an open bound, a missing clamp, the wrong tie or fallback order, another norm
 -- is written into a copy of the oracle package, and the pins (the tests of
 test_oracle_pins.py and test_oracle_noise.py, run against the copy) must fail
-on it.  So the pins, not the oracle's agreement with itself, stand behind the
-parity tests."""
+on it; the same for the learned screener's oracle against test_oracle_screener.py.
+So the pins, not the oracle's agreement with itself, stand behind the parity
+tests."""
 import importlib
 import os
 import shutil
@@ -15,6 +16,7 @@ import pytest
 
 import test_oracle_noise
 import test_oracle_pins
+import test_oracle_screener
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ORACLE = os.path.join(os.path.dirname(HERE), "oracle")
@@ -65,17 +67,44 @@ MUTANTS = [
      "t = (rx * dx + ry * dy) * inv"),
     ("road without the inflation", "safety.py",
      "ok &= d < (spec.half_width - spec.inflation)", "ok &= d < spec.half_width"),
+    # the learned screener's oracle (features, network, training, screening rule)
+    ("curvature sign", "screener.py", "cross = a[:, 0] * b[:, 1] - a[:, 1] * b[:, 0]",
+     "cross = a[:, 1] * b[:, 0] - a[:, 0] * b[:, 1]"),
+    ("look-ahead one vertex short", "screener.py", "out[i, m] = kappa[j % S]",
+     "out[i, m] = kappa[(j - 1) % S]"),
+    ("lateral offset sign", "screener.py", "nrm = np.array([-tau[1], tau[0]])",
+     "nrm = np.array([tau[1], -tau[0]])"),
+    ("heading error sign", "screener.py", "e_psi = x[2] - math.atan2(tau[1], tau[0])",
+     "e_psi = math.atan2(tau[1], tau[0]) - x[2]"),
+    ("GELU cubic coefficient", "screener.py", "GELU_A = 0.044715", "GELU_A = 0.04715"),
+    ("GELU derivative without the factor 3", "screener.py",
+     "(1.0 + 3.0 * GELU_A * z * z)", "(1.0 + GELU_A * z * z)"),
+    ("loss gradient sign", "screener.py", "d3 = (2.0 / B) * (y - target) * y * (1.0 - y)",
+     "d3 = (2.0 / B) * (target - y) * y * (1.0 - y)"),
+    ("transposed weight gradient", "screener.py", 'g["W2"] = d2.T @ cache["h1"]',
+     'g["W2"] = cache["h1"].T @ d2'),
+    ("Adam without bias correction", "screener.py", "mh = m / (1 - beta1 ** step)", "mh = m"),
+    ("Adam without the square root", "screener.py",
+     "params[k] - lr * mh / (np.sqrt(vh) + eps)", "params[k] - lr * mh / (vh + eps)"),
+    ("screen prefix one slot too long", "screener.py", "if inside.sum() >= k and",
+     "if inside.sum() > k and"),
+    ("predicted-safe count outside the prefix", "screener.py",
+     "np.count_nonzero(inside & safe) >= m", "np.count_nonzero(safe) >= m"),
+    ("screened fallback order", "screener.py",
+     "return int(np.lexsort((slot, cost, H - np.asarray(ttv)))[0])",
+     "return int(np.lexsort((slot, cost, np.asarray(ttv)))[0])"),
 ]
 
-PIN_MODULES = (test_oracle_pins, test_oracle_noise)
+PIN_MODULES = (test_oracle_pins, test_oracle_noise, test_oracle_screener)
 PARAMS = {"test_philox_avalanche": [("counter",), ("key",)],
           "test_fit_held_input_rows_are_unit_rows": [("bot", (4, 11)),
                                                      ("car", (6, 7, 30, 31))],
           "test_brute_force_tiny": [("bot",), ("car",)]}
 
 
-def _pins():
-    for mod in PIN_MODULES:
+def _pins(first=None):
+    """Every pin; those of module `first` (the one that tests the edited file) first."""
+    for mod in sorted(PIN_MODULES, key=lambda m: m is not first):
         for name, fn in list(vars(mod).items()):
             if name.startswith("test_") and callable(fn):
                 for args in PARAMS.get(name, [()]):
@@ -103,7 +132,7 @@ def _mutant_package(tmp_path, file, text, replacement):
     try:
         importlib.invalidate_caches()
         mods = {n: importlib.import_module(f"{pkg}.{n}")
-                for n in ("philox", "sampling", "basis", "fit", "safety", "mpmi")}
+                for n in ("philox", "sampling", "basis", "fit", "safety", "mpmi", "screener")}
     finally:
         sys.path.remove(str(tmp_path))
     return pkg, mods
@@ -119,7 +148,8 @@ def _failing_pins(tmp_path, monkeypatch, file, text, replacement, first_only):
                 if len(sub) == 2 and sub[0] == "oracle" and sub[1] in mods:
                     monkeypatch.setattr(mod, attr, mods[sub[1]])
         failed = []
-        for mod, pin, fn, args in _pins():
+        first = test_oracle_screener if file == "screener.py" else None
+        for mod, pin, fn, args in _pins(first):
             try:
                 fn(*args)
             except Exception as e:  # noqa: BLE001 -- any failure of a pin counts

@@ -98,6 +98,11 @@ def test_features_on_circle_chord_bisector():
     assert np.allclose(f[6:], 10.0 / R, rtol=1e-9)
     c = sc.candidate_features(f, np.array([[0.2, -0.5], [-0.4, 1.0]]))
     assert c.shape == (2, 12) and np.allclose(c[:, 10:], [[0.5, -0.5], [-1.0, 1.0]])
+    # heading 0.3 rad to the left of the chord's direction: heading error +0.3
+    x[2] += 0.3
+    f = sc.tick_features(tr, w, x)
+    assert f[1] == pytest.approx(math.sin(0.3), abs=1e-9)
+    assert f[2] == pytest.approx(math.cos(0.3), abs=1e-9)
 
 
 def test_cost_bins_follow_the_cost_order():
