@@ -4,7 +4,8 @@ dropped feature, a transposed operand, an off-by-one count, a closed instead of
 an open bound, a missing clamp, the wrong tie or fallback order, another norm
 -- is written into a copy of the oracle package, and the pins (the tests of
 test_oracle_pins.py and test_oracle_noise.py, run against the copy) must fail
-on it; the same for the learned screener's oracle against test_oracle_screener.py.
+on it; the same for the learned screener's oracle (test_oracle_screener.py) and the
+sparsity-promoting basis selection (test_oracle_sparse.py).
 So the pins, not the oracle's agreement with itself, stand behind the parity
 tests."""
 import importlib
@@ -17,6 +18,7 @@ import pytest
 import test_oracle_noise
 import test_oracle_pins
 import test_oracle_screener
+import test_oracle_sparse
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ORACLE = os.path.join(os.path.dirname(HERE), "oracle")
@@ -93,13 +95,23 @@ MUTANTS = [
     ("screened fallback order", "screener.py",
      "return int(np.lexsort((slot, cost, H - np.asarray(ttv)))[0])",
      "return int(np.lexsort((slot, cost, np.asarray(ttv)))[0])"),
+    # the sparsity-promoting basis selection (group lasso by ADMM, then polishing)
+    ("group threshold halved", "fit.py", "shrink = 1.0 - (gamma / rho) / norms[j]",
+     "shrink = 1.0 - (gamma / (2.0 * rho)) / norms[j]"),
+    ("ADMM dual update sign", "fit.py", "U = U + V - Z", "U = U - V + Z"),
+    ("data term without its factor 2", "fit.py",
+     "G = 2.0 / m * (A.T @ A) + rho * np.eye(n)", "G = 1.0 / m * (A.T @ A) + rho * np.eye(n)"),
+    ("no polishing refit", "fit.py", "Ws, *_ = np.linalg.lstsq(X[:, cols], Y, rcond=None)",
+     "Ws = Z[cols] * rms_scale(Y)[None, :] / rms_scale(X)[cols][:, None]"),
 ]
 
-PIN_MODULES = (test_oracle_pins, test_oracle_noise, test_oracle_screener)
+PIN_MODULES = (test_oracle_pins, test_oracle_noise, test_oracle_screener, test_oracle_sparse)
 PARAMS = {"test_philox_avalanche": [("counter",), ("key",)],
           "test_fit_held_input_rows_are_unit_rows": [("bot", (4, 11)),
                                                      ("car", (6, 7, 30, 31))],
-          "test_brute_force_tiny": [("bot",), ("car",)]}
+          "test_brute_force_tiny": [("bot",), ("car",)],
+          "test_planted_support_and_exact_polish": [(1e-3,), (1e-2,), (0.05,)],
+          "test_group_lasso_optimality_conditions": [(0.02,), (0.2,)]}
 
 
 def _pins(first=None):
@@ -148,7 +160,7 @@ def _failing_pins(tmp_path, monkeypatch, file, text, replacement, first_only):
                 if len(sub) == 2 and sub[0] == "oracle" and sub[1] in mods:
                     monkeypatch.setattr(mod, attr, mods[sub[1]])
         failed = []
-        first = test_oracle_screener if file == "screener.py" else None
+        first = {"screener.py": test_oracle_screener, "fit.py": test_oracle_sparse}.get(file)
         for mod, pin, fn, args in _pins(first):
             try:
                 fn(*args)
