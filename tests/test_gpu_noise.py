@@ -181,8 +181,9 @@ def test_set_noise_argument_checks(lib, ctx, bot):
 
 
 def test_screened_exact_search_with_noise(lib, ctx, car):
-    """The noise is a function of (seed, stream, tick, slot): the exact
-    cost-ordered screened search (tau = 0) still picks what the full noisy
+    """The noise is a function of (seed, stream, tick, slot): the exact screened
+    search, in cost order (tau = 0) and with the network (tau > 0, whose kept
+    rollout takes 16 lanes per candidate), still picks what the full noisy
     evaluation picks."""
     import torch
     env, model = car
@@ -198,12 +199,15 @@ def test_screened_exact_search_with_noise(lib, ctx, car):
             ud = torch.tensor(u_h, dtype=torch.float64, device="cuda")
             rp = torch.zeros(lib.RESULT_BYTES, dtype=torch.uint8, device="cuda")
             rs = torch.zeros(lib.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+            rn = torch.zeros(lib.RESULT_BYTES, dtype=torch.uint8, device="cuda")
             lib.evaluate_candidates_device(sess, xd, ud, rp, tick=i)
             lib.evaluate_screened(sess, scr, xd, ud, rs, k=128, tau=0.0, tick=i)
+            lib.evaluate_screened(sess, scr, xd, ud, rn, k=1, tau=0.05, m=4, tick=i)
             torch.cuda.synchronize()
             sess.close()
-            a, b = lib.result_from_bytes(rp.cpu(), 2), lib.result_from_bytes(rs.cpu(), 2)
-            for key in ("index", "status", "ttv"):
-                assert a[key] == b[key], key
-            assert np.array_equal(a["u_r"], b["u_r"])
+            a = lib.result_from_bytes(rp.cpu(), 2)
+            for b in (lib.result_from_bytes(rs.cpu(), 2), lib.result_from_bytes(rn.cpu(), 2)):
+                for key in ("index", "status", "ttv"):
+                    assert a[key] == b[key], key
+                assert np.array_equal(a["u_r"], b["u_r"])
     scr.free()

@@ -471,6 +471,33 @@ def test_bot_closed_loop_matches_oracle(lib, ctx, bot):
     assert agree >= ticks * 0.9, f"closed loops diverged at tick {agree}"
 
 
+def test_car_closed_loop_matches_oracle(lib, ctx, car):
+    """The race car's receding horizon (Sec. IV-C, V-B) for one second at 60 Hz:
+    each side drives its own bicycle copy around the track from the same start
+    with the same user input; the applied inputs agree tick by tick."""
+    env, model = car
+    ticks, N, H = 60, 511, 60
+    u_seq = data.to_f32_exact(data.ou_user_input(4, ticks, plants.CAR_DT, env.lo, env.hi))
+    x0 = data.car_start_state(env.track, vx=12.0)
+    sess = lib.Session(ctx, model, N, H, env.lo, env.hi, seed=4)
+    x = x0.copy()
+    gpu_u = []
+    for t in range(ticks):
+        lib.evaluate_candidates(sess, x, u_seq[t], tick=t)
+        r = lib.select_input(sess)
+        gpu_u.append(r["u_r"].copy())
+        x = plants.bicycle_step(x, r["u_r"])
+    sess.close()
+    recs = omp.closed_loop(env.K32, "car", env.spec, plants.bicycle_step, x0, u_seq,
+                           lambda t: osamp.uniform_samples(4, 0, t, N, env.lo, env.hi), H)
+    agree = 0
+    for t, (_, _, o) in enumerate(recs):
+        if not np.array_equal(gpu_u[t], o.u_r):
+            break
+        agree += 1
+    assert agree >= ticks * 0.9, f"closed loops diverged at tick {agree}"
+
+
 @pytest.mark.parametrize("which", ["bot", "car"])
 def test_all_launch_shapes_agree_bit_for_bit(lib, ctx, bot, car, which):
     """Every compiled launch shape sums each row of K z in the same order, so the
