@@ -66,9 +66,22 @@ static TickKernel pick_tick(int kind, int lanes, int cands, bool traj, bool nois
 // blocks stage K and the track grid fewer times.
 constexpr int kDefaultBlock = 128;
 
+// Threads per block the library picks for a shape.  The race car's one-lane
+// shapes: where the warp-tiles fit one block of at most eight warps per SM,
+// blocks of ceil(tiles / SMs) warps, one per SM, load the SMs more evenly than
+// two four-warp blocks on some SMs and one on the rest (measured 4-10 % faster
+// from 20k to 76k slots); everything else kDefaultBlock.
+static int default_block(int kind, int lanes, int cands, long long n_slots, int sms) {
+  if (kind == kCar && lanes == 1) {
+    const long long tiles = (n_slots + 32LL * cands - 1) / (32LL * cands);
+    const long long w = (tiles + sms - 1) / sms;
+    if (w > 4 && w <= kMaxBlock / 32) return (int)(32 * w);
+  }
+  return kDefaultBlock;
+}
+
 static void default_shape(int kind, int n_slots, int sms, int* lanes, int* cands, int* block) {
   *cands = 1;
-  *block = kDefaultBlock;
   if (kind == kCar) {
     const long long n = n_slots;
     if (n * 16 <= (long long)sms * 128) *lanes = 16;      // at most one warp per sub-partition
@@ -77,17 +90,11 @@ static void default_shape(int kind, int n_slots, int sms, int* lanes, int* cands
     else {
       *lanes = 1;
       *cands = n > 48 * 1024 ? 2 : 1;
-      // where the warp-tiles fit one block of at most eight warps per SM, blocks
-      // of ceil(tiles / SMs) warps, one per SM, load the SMs more evenly than
-      // two four-warp blocks on some SMs and one on the rest (measured 4-10 %
-      // faster from 20k to 76k slots)
-      const long long tiles = (n + 32LL * *cands - 1) / (32LL * *cands);
-      const long long w = (tiles + sms - 1) / sms;
-      if (w > 4 && w <= kMaxBlock / 32) *block = (int)(32 * w);
     }
-    return;
+  } else {
+    *lanes = (kind == kBot && (long long)n_slots * 4 <= (long long)sms * 128) ? 4 : 1;
   }
-  *lanes = (kind == kBot && (long long)n_slots * 4 <= (long long)sms * 128) ? 4 : 1;
+  *block = default_block(kind, *lanes, *cands, n_slots, sms);
 }
 
 TickArgs make_tick_args(const mpmi_session* s, uint64_t tick) {
@@ -715,11 +722,10 @@ int mpmi_session_open(mpmi_ctx* ctx, const mpmi_model* model, const mpmi_session
     default_shape(model->kind, (int)slots, ctx->sm_count, &dl, &dc, &db);
     lanes = dl;
     if (cands == 0) cands = dc;
-    if (block == 0) block = db;
   } else {
     if (cands == 0) cands = (lanes == 1 && model->kind == kCar && slots > 48 * 1024) ? 2 : 1;
-    if (block == 0) block = kDefaultBlock;
   }
+  if (block == 0) block = default_block(model->kind, lanes, cands, slots, ctx->sm_count);
   if (block % 32 != 0 || block < 32 || block > kMaxBlock)
     return fail(MPMI_E_INVALID_ARG, "session_open: block must be a multiple of 32 in 32..256");
   if (!pick_tick(model->kind, lanes, cands, false, false).fn)
